@@ -1,0 +1,352 @@
+"""Benchmark of the HCA-DBSCAN hot path on one GB300 (or N independent replicas).
+
+One step = one full clustering (every stage: origin shift, binning, sort, cells, pencil
+hash, core counts, representative points, merge, labels) of the 3-D mixed workload
+(n = 2,000,000 float32 points on the 2^-16 lattice, 40 Gaussian blobs + 8 noisy arcs + 5%
+uniform noise in [0,1000]^3, eps = 2, minPts = 10), with the points already resident in
+device memory.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload mixed3d|blobs2d] [--no-cpu-baseline]
+
+--impl reference times the CPU oracle (the plain C implementation the CUDA path is checked
+against) on the host cores, on a bounded sample of the same workload each step.
+
+With N > 1 (torchrun) every rank clusters its own copy of the workload drawn with its own
+seed: the method has no exchange step, so the ranks are independent replicas and `value`
+is the points of all ranks divided by the slowest rank's time ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "points clustered/sec at 1 GB300 (labels == oracle)"
+L2_FLUSH_BYTES = 256 << 20
+
+# Algorithmic bytes per stage, per point (n) and per cell (C) / pencil (P): the data each
+# stage must move at least once (reads + writes), with 4-byte keys for <= 32 key bits.
+#   bin:   read the point (4 d), write key + index (8)
+#   sort:  per 8-bit pass read and write key + value (16)
+#   cells: read index (4) + the point (4 d), write the padded point (16 for d = 3) + cell id (4);
+#          per cell write start (4) + key (8)
+def stage_bytes(stage, n, d, C, P, passes, key_bytes):
+    pt = 4 * d
+    pad = 16 if d == 3 else pt
+    if stage == "minmax":
+        return n * pt
+    if stage == "bin":
+        return n * (pt + key_bytes + 4)
+    if stage == "sort":
+        return passes * n * 2 * (key_bytes + 4)
+    if stage == "cells":
+        return n * (4 + pt + pad + 4) + C * 12
+    if stage == "hash":
+        return C * 8 + P * 16
+    if stage == "reps":
+        return n * (pad + 4 + 1) + C * 8 * (26 if d == 3 else 8)
+    return None
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mixed3d", choices=["mixed3d", "blobs2d"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name, rank):
+    from paper_1912_00323_gb300 import workloads
+    seed = workloads.SEED_BASE + (1 if name == "mixed3d" else 0) + 1000 * rank
+    X, eps, min_pts = workloads.WORKLOADS[name](seed=seed)
+    desc = {
+        "mixed3d": "d=3, n=2,000,000 float32 on the 2^-16 lattice: 40 Gaussian blobs (sigma 0.5-3) "
+                   "+ 8 noisy arcs/rings + 5% uniform noise in [0,1000]^3; eps=2.0, minPts=10",
+        "blobs2d": "d=2, n=10,000 float64 on the 2^-12 lattice: 5 Gaussian blobs (sigma 2) + 10% "
+                   "uniform noise in [0,100]^2; eps=1.5, minPts=5",
+    }[name]
+    return X, eps, min_pts, desc
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                    rows.append(f)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline_oracle(X, eps, min_pts, budget_s=20.0):
+    """Time the oracle (as it stands, one host thread) on a bounded sample of the workload."""
+    import oracle
+    oracle.build()
+    n = len(X)
+    # first estimate on 10% of the points, then size the sample to about budget_s seconds
+    m = max(1000, n // 10)
+    t0 = time.perf_counter()
+    oracle.grid(X[:m].astype(np.float64), eps, min_pts)
+    t1 = time.perf_counter() - t0
+    m2 = int(min(n, m * max(1.0, budget_s / max(t1, 1e-3)) * 0.8))
+    if m2 > m:
+        t0 = time.perf_counter()
+        oracle.grid(X[:m2].astype(np.float64), eps, min_pts)
+        t1 = time.perf_counter() - t0
+        m = m2
+    return {"value": m / t1, "unit": "points/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {m:,} of the {n:,} workload points (oracle hca_oracle_grid, 1 thread), "
+                      f"{t1:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    X, eps, min_pts, desc = workload(args.workload, 0)
+    import oracle
+    oracle.build()
+    n = len(X)
+    m = min(n, 200_000)
+    sample = X[:m].astype(np.float64)
+    for _ in range(args.warmup):
+        oracle.grid(sample[: min(m, 20_000)], eps, min_pts)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.grid(sample, eps, min_pts)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = m / (ms / 1e3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload + ": " + desc, "sample_points_per_step": m},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {m:,} of the {n:,} workload points per step"},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import paper_1912_00323_gb300 as pkg
+    from paper_1912_00323_gb300 import build as pkg_build
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0 or ws == 1:
+        pkg_build.build()
+    if dist:
+        dist.barrier()
+    pkg.load()
+
+    X, eps, min_pts, desc = workload(args.workload, rank)
+    n, d = X.shape
+    pts = torch.from_numpy(X).to(dev)
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(timing):
+        return pkg.hca_dbscan_device(pts, eps, min_pts, labels=labels, stream=stream, stats=True,
+                                     timing=timing)
+
+    for _ in range(max(args.warmup, 0)):
+        step(False)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, stage_ms, stats = [], {}, None
+    with ClockSampler(dev.index) as clocks:
+        wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()                     # evict the previous step's data from L2
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, stats = step(True)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            for k, v in stats["stage_ms"].items():
+                stage_ms.setdefault(k, []).append(v)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = sum(step_ms) / len(step_ms)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n * ws / (ms / 1e3)
+
+    # end to end through the host entry point: pinned host points in, host labels out
+    host_pts = torch.from_numpy(X).pin_memory()
+    host_lab = torch.empty(n, dtype=torch.int32).pin_memory()
+    pkg.hca_dbscan(host_pts, eps, min_pts, labels=host_lab)
+    e2e_t = []
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pkg.hca_dbscan(host_pts, eps, min_pts, labels=host_lab)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(e2e_t)
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    if not np.array_equal(host_lab.numpy(), labels.cpu().numpy()):
+        raise RuntimeError("host and device entry points disagree")
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant memory-bound stage (stage times are CUDA events on `stream`)
+    peak, peak_kind = measured_peaks()
+    C, P = stats["n_cells"], stats["n_pencils"]
+    key_bytes = 4 if stats["key_bits"] <= 32 else 8
+    med = {k: statistics.median(v) for k, v in stage_ms.items()}
+    dominant = max(med, key=med.get)
+    roof_rows = {}
+    for k, t in med.items():
+        b = stage_bytes(k, n, d, C, P, stats["sort_passes"], key_bytes)
+        if b is not None and t > 0:
+            roof_rows[k] = {"ms": t, "bytes": b, "gbs": b / (t / 1e3) / 1e9}
+    mem_stage = max(roof_rows, key=lambda k: roof_rows[k]["ms"]) if roof_rows else None
+    roofline = None
+    if mem_stage:
+        r = roof_rows[mem_stage]
+        roofline = {"bound": "hbm", "kernel": mem_stage, "achieved": r["gbs"], "peak": peak,
+                    "unit": "GB/s", "frac": r["gbs"] / peak, "traffic": None,
+                    "peak_source": peak_kind}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload + ": " + desc, "n": n, "d": d, "eps": eps,
+                   "min_pts": min_pts, "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "e2e": {"value": n * ws / e2e_s, "unit": "points/s", "h2d_bytes_per_step": int(X.nbytes),
+                "d2h_bytes_per_step": 4 * n},
+        "gpu_launches": int(stats["kernel_launches"]) * args.steps,
+        "roofline": roofline,
+        "stage_ms": med, "dominant_stage": dominant,
+        "stage_gbs": {k: round(v["gbs"], 1) for k, v in roof_rows.items()},
+        "clocks": clocks.summary(),
+        "result": {"cells": C, "pencils": P, "dense_cells": stats["n_dense_cells"],
+                   "core_points": stats["n_core_points"], "clusters": stats["n_clusters"],
+                   "noise": stats["n_noise"]},
+        "wall_s": wall,
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline_oracle(X, eps, min_pts)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

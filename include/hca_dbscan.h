@@ -1,0 +1,148 @@
+/*
+ * hca_dbscan.h -- C ABI of the GB300 (sm_103a) HCA-DBSCAN library.
+ *
+ * HCA-DBSCAN (Mathur, Mehta, Singh; arXiv 1912.00323) clusters points with DBSCAN's
+ * definitions (supplement, "The DBSCAN Algorithm", Definitions 1-5) by overlaying a grid of
+ * hypercubes whose space diagonal is eps (Sec. 2, Algorithm 1), treating a hypercube that
+ * holds at least MINPTS points as core as a whole, comparing representative points of
+ * neighbouring hypercubes (Sec. 2, Algorithm 2), and merging hypercubes into clusters
+ * (Algorithms 3-4).  Every step runs in this library's CUDA kernels.
+ *
+ * Result (identical for every entry point that computes labels):
+ *   core(p)   iff |{q : dist(p,q) <= eps}| >= min_pts, p itself included (Definitions 1-2);
+ *             dist(p,q) <= eps is decided as  fl64(sum_i (x_pi - x_qi)^2) <= fl64(eps*eps)
+ *             with the sum taken in double precision in dimension order, which is exact
+ *             for coordinates on a binary lattice.
+ *   label(p)  core p: the smallest input index of a core point of its cluster (clusters are
+ *             the connected components of core points, Definitions 3-5);
+ *             non-core p within eps of a core point: the smallest label among those core
+ *             points' clusters; otherwise -1 (noise).
+ *
+ * Conventions shared by all entry points:
+ *   - points are row-major n x d (point i occupies elements [i*d, (i+1)*d)), of type float
+ *     (HCA_F32) or double (HCA_F64), every coordinate finite;
+ *   - labels are int32 in input order; the caller owns every buffer it passes;
+ *   - the library owns only its workspace, taken from a library-private stream-ordered
+ *     pool of device memory and returned to that pool before each call returns;
+ *   - "device" entry points take device pointers and a CUDA stream passed as void*
+ *     (a cudaStream_t; NULL = legacy default stream); they return once the result is
+ *     complete on that stream;
+ *   - every entry point returns HCA_OK (0) or a negative HCA_E* code; on a negative code the
+ *     output buffers hold no result (they may have been partly written); n = 0 succeeds
+ *     without touching any buffer.
+ * Limits: 1 <= d <= 4, n < 2^31, 0 < eps finite, min_pts >= 1, and the grid of cells
+ * (extent / (eps / sqrt(d)) per dimension) must fit 64-bit cell keys (HCA_ERANGE otherwise).
+ */
+#ifndef HCA_DBSCAN_H
+#define HCA_DBSCAN_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HCA_API __attribute__((visibility("default")))
+#else
+#define HCA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* point coordinate types */
+#define HCA_F32 0
+#define HCA_F64 1
+
+/* return codes */
+#define HCA_OK 0
+#define HCA_EINVAL (-1)    /* bad argument: n, d, eps, min_pts, dtype, NULL or non-finite input */
+#define HCA_ENOMEM (-2)    /* device workspace could not be allocated */
+#define HCA_ECUDA (-3)     /* a CUDA runtime call failed */
+#define HCA_ERANGE (-4)    /* coordinate extent too large for the cell grid at this eps */
+#define HCA_ENOTIMPL (-5)  /* supported by the interface, not by this build (e.g. d > 4) */
+#define HCA_EDEVICE (-6)   /* a kernel's own consistency check tripped (bounded loop limit,
+                              full hash table); the outputs hold no result */
+
+/* flags for hca_dbscan_device_ex */
+#define HCA_FLAG_TIMING 1     /* record CUDA events around each stage into stats->stage_ms */
+#define HCA_FLAG_FP64_ONLY 2  /* decide every distance in FP64 (no FP32 filter); same result */
+
+/* stages timed with HCA_FLAG_TIMING (index into hca_stats.stage_ms) */
+#define HCA_STAGE_MINMAX 0    /* origin shift: per-dimension min / max (Sec. 2) */
+#define HCA_STAGE_BIN 1       /* hypercube coordinates and cell keys (Algorithm 1) */
+#define HCA_STAGE_SORT 2      /* radix sort of (key, index) (the pre-sort of Sec. 2) */
+#define HCA_STAGE_CELLS 3     /* gather into cell order, run-length cell offsets */
+#define HCA_STAGE_HASH 4      /* neighbour lookup table */
+#define HCA_STAGE_CORE 5      /* dense cells and exact counts (Definition 2) */
+#define HCA_STAGE_REPS 6      /* representative points (Algorithm 2) */
+#define HCA_STAGE_MERGE 7     /* merging neighbouring cells, union-find (Algorithm 3) */
+#define HCA_STAGE_LABELS 8    /* cluster ids, border and noise points (Algorithm 4) */
+#define HCA_NUM_STAGES 9
+
+typedef struct hca_stats {
+    int64_t n_points;
+    int64_t n_cells;          /* non-empty hypercubes */
+    int64_t n_pencils;        /* non-empty lines of cells along the last dimension */
+    int64_t n_dense_cells;    /* cells with >= min_pts points */
+    int64_t n_core_points;
+    int64_t n_clusters;
+    int64_t n_noise;
+    int32_t key_bits;         /* bits of the packed cell key */
+    int32_t sort_passes;      /* 8-bit radix passes */
+    int32_t kernel_launches;  /* kernels this call launched */
+    int32_t reserved;
+    float stage_ms[HCA_NUM_STAGES];
+} hca_stats;
+
+/*
+ * hca_dbscan -- cluster host-resident points; labels written to host memory.
+ *   points  host, n*d values of `dtype`; read only.
+ *   labels  host, n int32; written on success.
+ * Copies the points to the device, runs hca_dbscan_device on an internal stream and copies
+ * the labels back.  Synchronous.  (Algorithm 4, HYPERCUBE-BASED-ACCELERATED-DBSCAN.)
+ */
+HCA_API int hca_dbscan(const void *points, int32_t dtype, int64_t n, int32_t d, double eps,
+               int32_t min_pts, int32_t *labels);
+
+/*
+ * hca_dbscan_device -- cluster device-resident points.
+ *   d_points  device, n*d values of `dtype`, 4-byte (F32) or 8-byte (F64) aligned; read only.
+ *   d_labels  device, n int32; written on success.
+ *   stream    cudaStream_t as void*; all work is ordered on it.
+ * Same result as hca_dbscan.  Returns after the labels are complete on `stream`.
+ */
+HCA_API int hca_dbscan_device(const void *d_points, int32_t dtype, int64_t n, int32_t d, double eps,
+                      int32_t min_pts, int32_t *d_labels, void *stream);
+
+/*
+ * hca_dbscan_device_ex -- hca_dbscan_device with optional extra outputs.
+ *   d_core  device, n uint8 (nullable): 1 for core points, 0 otherwise, input order.
+ *   stats   host (nullable): counts of the run; stage times when flags has HCA_FLAG_TIMING.
+ *   flags   bitwise OR of HCA_FLAG_*.
+ */
+HCA_API int hca_dbscan_device_ex(const void *d_points, int32_t dtype, int64_t n, int32_t d, double eps,
+                         int32_t min_pts, int32_t *d_labels, uint8_t *d_core, void *stream,
+                         hca_stats *stats, int32_t flags);
+
+/*
+ * hca_radix_sort_pairs -- stable ascending sort of (key, value) pairs on the device, by key
+ * bits [begin_bit, end_bit) (the pre-sort of Sec. 2 is done with this sort on cell keys).
+ *   d_keys     device, n keys of key_bytes (4 or 8) bytes, 8-byte aligned; sorted in place.
+ *   d_vals     device, n uint32 values; permuted with their keys in place.
+ *   begin_bit, end_bit  0 <= begin_bit < end_bit <= 8*key_bytes.
+ * Keys whose bits outside the range differ still sort only by the range (stable).
+ * Returns after the sort is complete on `stream`.
+ */
+HCA_API int hca_radix_sort_pairs(void *d_keys, uint32_t *d_vals, int64_t n, int32_t key_bytes,
+                         int32_t begin_bit, int32_t end_bit, void *stream);
+
+/* Static description of a return code; never NULL. */
+HCA_API const char *hca_strerror(int code);
+
+/* Library version: major*10000 + minor*100 + patch. */
+HCA_API int32_t hca_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HCA_DBSCAN_H */

@@ -1,0 +1,170 @@
+"""GB300-native HCA-DBSCAN (arXiv 1912.00323): Python binding of the C ABI.
+
+This module only marshals arguments for the CUDA library ``libhca_dbscan.so`` (built from
+``csrc/`` by ``build.py``); every step of the clustering runs in its kernels.  There is no
+CPU fallback: if the library is missing or cannot be loaded, every call raises.
+
+Names follow include/hca_dbscan.h:
+  hca_dbscan(points, eps, min_pts)               host numpy array in, int32 labels out
+  hca_dbscan_device(points, eps, min_pts, ...)   CUDA torch tensor in, CUDA labels out
+  hca_radix_sort_pairs(keys, vals, begin, end)   in-place device sort (the Sec. 2 pre-sort)
+  hca_strerror(code), hca_version()
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhca_dbscan.so")
+
+HCA_F32, HCA_F64 = 0, 1
+HCA_OK, HCA_EINVAL, HCA_ENOMEM, HCA_ECUDA, HCA_ERANGE, HCA_ENOTIMPL, HCA_EDEVICE = 0, -1, -2, -3, -4, -5, -6
+HCA_FLAG_TIMING, HCA_FLAG_FP64_ONLY = 1, 2
+STAGES = ("minmax", "bin", "sort", "cells", "hash", "core", "reps", "merge", "labels")
+
+ABI_FUNCTIONS = ("hca_dbscan", "hca_dbscan_device", "hca_dbscan_device_ex", "hca_radix_sort_pairs",
+                 "hca_strerror", "hca_version")
+
+
+class HcaStats(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("n_cells", ctypes.c_int64),
+                ("n_pencils", ctypes.c_int64), ("n_dense_cells", ctypes.c_int64),
+                ("n_core_points", ctypes.c_int64), ("n_clusters", ctypes.c_int64),
+                ("n_noise", ctypes.c_int64), ("key_bits", ctypes.c_int32),
+                ("sort_passes", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("stage_ms", ctypes.c_float * len(STAGES))]
+
+    def as_dict(self):
+        d = {name: getattr(self, name) for name, _ in self._fields_ if name not in ("stage_ms", "reserved")}
+        d["stage_ms"] = {s: float(self.stage_ms[i]) for i, s in enumerate(STAGES)}
+        return d
+
+
+class HcaError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {hca_strerror(code)} (code {code})")
+
+
+_lib = None
+
+
+def load():
+    """Load libhca_dbscan.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_1912_00323_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    lib.hca_dbscan.argtypes = [vp, i32, i64, i32, dbl, i32, vp]
+    lib.hca_dbscan_device.argtypes = [vp, i32, i64, i32, dbl, i32, vp, vp]
+    lib.hca_dbscan_device_ex.argtypes = [vp, i32, i64, i32, dbl, i32, vp, vp, vp,
+                                         ctypes.POINTER(HcaStats), i32]
+    lib.hca_radix_sort_pairs.argtypes = [vp, vp, i64, i32, i32, i32, vp]
+    lib.hca_strerror.argtypes = [ctypes.c_int]
+    lib.hca_strerror.restype = ctypes.c_char_p
+    lib.hca_version.restype = i32
+    for f in ("hca_dbscan", "hca_dbscan_device", "hca_dbscan_device_ex", "hca_radix_sort_pairs"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def hca_strerror(code: int) -> str:
+    return load().hca_strerror(int(code)).decode()
+
+
+def hca_version() -> int:
+    return int(load().hca_version())
+
+
+def _dtype_code(dt):
+    name = str(dt)
+    if name.endswith("float32"):
+        return HCA_F32
+    if name.endswith("float64"):
+        return HCA_F64
+    raise TypeError(f"points must be float32 or float64, got {dt}")
+
+
+def hca_dbscan(points, eps: float, min_pts: int, labels=None):
+    """Cluster host points (numpy (n, d) float32/float64, or a CPU torch tensor, possibly
+    pinned).  Returns int32 labels of length n (a numpy array unless `labels` is given)."""
+    lib = load()
+    if hasattr(points, "data_ptr"):  # torch CPU tensor
+        if points.is_cuda:
+            raise ValueError("hca_dbscan takes host points; use hca_dbscan_device for CUDA tensors")
+        pts = points.contiguous()
+        n, d = (pts.shape[0], pts.shape[1]) if pts.dim() == 2 else (pts.shape[0], 1)
+        code = _dtype_code(pts.dtype)
+        ptr = pts.data_ptr()
+    else:
+        pts = np.ascontiguousarray(points)
+        if pts.ndim == 1:
+            pts = pts[:, None]
+        n, d = pts.shape
+        code = _dtype_code(pts.dtype)
+        ptr = pts.ctypes.data
+    if labels is None:
+        labels = np.empty(n, np.int32)
+        lptr = labels.ctypes.data
+    else:
+        lptr = labels.data_ptr() if hasattr(labels, "data_ptr") else labels.ctypes.data
+    rc = lib.hca_dbscan(ptr, code, n, d, float(eps), int(min_pts), lptr)
+    if rc != HCA_OK:
+        raise HcaError(rc, "hca_dbscan")
+    return labels
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def hca_dbscan_device(points, eps: float, min_pts: int, labels=None, core=None, stream=None,
+                      stats: bool = False, timing: bool = False, fp64_only: bool = False):
+    """Cluster a CUDA tensor of shape (n, d).  Returns the int32 label tensor, or
+    (labels, stats_dict) when stats or timing is requested.  `core`, if given, is a uint8
+    CUDA tensor of length n that receives the core flags."""
+    import torch
+    lib = load()
+    if not points.is_cuda:
+        raise ValueError("hca_dbscan_device takes a CUDA tensor")
+    pts = points.contiguous()
+    n = pts.shape[0]
+    d = pts.shape[1] if pts.dim() == 2 else 1
+    code = _dtype_code(pts.dtype)
+    if labels is None:
+        labels = torch.empty(n, dtype=torch.int32, device=pts.device)
+    flags = (HCA_FLAG_TIMING if timing else 0) | (HCA_FLAG_FP64_ONLY if fp64_only else 0)
+    st = HcaStats()
+    rc = lib.hca_dbscan_device_ex(pts.data_ptr(), code, n, d, float(eps), int(min_pts),
+                                  labels.data_ptr(), core.data_ptr() if core is not None else None,
+                                  _stream_ptr(stream), ctypes.byref(st), flags)
+    if rc != HCA_OK:
+        raise HcaError(rc, "hca_dbscan_device")
+    if stats or timing:
+        return labels, st.as_dict()
+    return labels
+
+
+def hca_radix_sort_pairs(keys, vals, begin_bit: int = 0, end_bit: int | None = None, stream=None):
+    """Stable in-place sort of CUDA tensors keys (int32/int64 viewed as unsigned) and vals
+    (int32 viewed as uint32) by key bits [begin_bit, end_bit)."""
+    lib = load()
+    kb = keys.element_size()
+    if end_bit is None:
+        end_bit = 8 * kb
+    rc = lib.hca_radix_sort_pairs(keys.data_ptr(), vals.data_ptr(), keys.numel(), kb,
+                                  int(begin_bit), int(end_bit), _stream_ptr(stream))
+    if rc != HCA_OK:
+        raise HcaError(rc, "hca_radix_sort_pairs")
+    return keys, vals

@@ -1,0 +1,212 @@
+// C ABI entry points (include/hca_dbscan.h): argument checks, the library's device memory
+// pool, and dispatch to the per-(type, dimension) pipelines.
+#include <math.h>
+#include <mutex>
+
+#include "hca_internal.cuh"
+
+namespace hca {
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+int g_sms[kMaxDevices] = {};
+
+cudaError_t get_pool(cudaMemPool_t *out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p;
+        e = cudaMemPoolCreate(&p, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = ~0ull;  // keep freed blocks for reuse by later calls
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pools[dev] = p;
+    }
+    *out = g_pools[dev];
+    return cudaSuccess;
+}
+
+bool finite_positive(double x) { return isfinite(x) && x > 0.0; }
+
+}  // namespace
+
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s) {
+    cudaMemPool_t pool;
+    cudaError_t e = get_pool(&pool);
+    if (e != cudaSuccess) return e;
+    if (bytes == 0) bytes = 256;
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+cudaError_t pool_free(void *p, cudaStream_t s) {
+    if (!p) return cudaSuccess;
+    return cudaFreeAsync(p, s);
+}
+
+int device_sm_count() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
+    if (g_sms[dev] <= 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+        g_sms[dev] = v;
+    }
+    return g_sms[dev];
+}
+
+static int check_common(const void *pts, int32_t dtype, int64_t n, int32_t d, double eps,
+                        int32_t min_pts, const void *labels) {
+    if (n < 0 || n >= ((int64_t)1 << 31)) return HCA_EINVAL;
+    if (d < 1 || d > 64) return HCA_EINVAL;
+    if (dtype != HCA_F32 && dtype != HCA_F64) return HCA_EINVAL;
+    if (!finite_positive(eps) || min_pts < 1) return HCA_EINVAL;
+    if (n > 0 && (!pts || !labels)) return HCA_EINVAL;
+    return HCA_OK;
+}
+
+static int dispatch(const RunArgs &a, int32_t dtype) {
+    if (dtype == HCA_F32) {
+        switch (a.d) {
+            case 1: return run_lowd<float, 1>(a);
+            case 2: return run_lowd<float, 2>(a);
+            case 3: return run_lowd<float, 3>(a);
+            case 4: return run_lowd<float, 4>(a);
+        }
+    } else {
+        switch (a.d) {
+            case 1: return run_lowd<double, 1>(a);
+            case 2: return run_lowd<double, 2>(a);
+            case 3: return run_lowd<double, 3>(a);
+            case 4: return run_lowd<double, 4>(a);
+        }
+    }
+    return HCA_ENOTIMPL;
+}
+
+}  // namespace hca
+
+using namespace hca;
+
+extern "C" int hca_dbscan_device_ex(const void *d_points, int32_t dtype, int64_t n, int32_t d,
+                                    double eps, int32_t min_pts, int32_t *d_labels, uint8_t *d_core,
+                                    void *stream, hca_stats *stats, int32_t flags) {
+    int rc = check_common(d_points, dtype, n, d, eps, min_pts, d_labels);
+    if (rc) return rc;
+    if (stats) {
+        hca_stats z = {};
+        *stats = z;
+    }
+    if (n == 0) return HCA_OK;
+    const size_t esz = dtype == HCA_F32 ? 4 : 8;
+    if (((uintptr_t)d_points) % esz || ((uintptr_t)d_labels) % 4) return HCA_EINVAL;
+    RunArgs a;
+    a.d_points = d_points;
+    a.n = n;
+    a.d = d;
+    a.eps = eps;
+    a.min_pts = min_pts;
+    a.d_labels = d_labels;
+    a.d_core = d_core;
+    a.stream = (cudaStream_t)stream;
+    a.stats = stats;
+    a.flags = flags;
+    return dispatch(a, dtype);
+}
+
+extern "C" int hca_dbscan_device(const void *d_points, int32_t dtype, int64_t n, int32_t d, double eps,
+                                 int32_t min_pts, int32_t *d_labels, void *stream) {
+    return hca_dbscan_device_ex(d_points, dtype, n, d, eps, min_pts, d_labels, nullptr, stream, nullptr, 0);
+}
+
+extern "C" int hca_dbscan(const void *points, int32_t dtype, int64_t n, int32_t d, double eps,
+                          int32_t min_pts, int32_t *labels) {
+    int rc = check_common(points, dtype, n, d, eps, min_pts, labels);
+    if (rc) return rc;
+    if (n == 0) return HCA_OK;
+    if (d > kMaxD) return HCA_ENOTIMPL;
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return HCA_ECUDA;
+    const size_t in_bytes = (size_t)n * d * (dtype == HCA_F32 ? 4 : 8);
+    void *dp = nullptr, *dl = nullptr;
+    if (pool_alloc(&dp, in_bytes, s) != cudaSuccess || pool_alloc(&dl, (size_t)n * 4, s) != cudaSuccess) {
+        pool_free(dp, s);
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+        return HCA_ENOMEM;
+    }
+    rc = HCA_OK;
+    if (cudaMemcpyAsync(dp, points, in_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) rc = HCA_ECUDA;
+    if (rc == HCA_OK) rc = hca_dbscan_device(dp, dtype, n, d, eps, min_pts, (int32_t *)dl, (void *)s);
+    if (rc == HCA_OK &&
+        (cudaMemcpyAsync(labels, dl, (size_t)n * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         cudaStreamSynchronize(s) != cudaSuccess))
+        rc = HCA_ECUDA;
+    pool_free(dp, s);
+    pool_free(dl, s);
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    return rc;
+}
+
+extern "C" int hca_radix_sort_pairs(void *d_keys, uint32_t *d_vals, int64_t n, int32_t key_bytes,
+                                    int32_t begin_bit, int32_t end_bit, void *stream) {
+    if (n < 0 || n >= ((int64_t)1 << 31)) return HCA_EINVAL;
+    if (key_bytes != 4 && key_bytes != 8) return HCA_EINVAL;
+    if (begin_bit < 0 || end_bit <= begin_bit || end_bit > 8 * key_bytes) return HCA_EINVAL;
+    if (n > 0 && (!d_keys || !d_vals)) return HCA_EINVAL;
+    if (((uintptr_t)d_keys) % key_bytes || ((uintptr_t)d_vals) % 4) return HCA_EINVAL;
+    if (n <= 1) return HCA_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t hist = sort_hist_size(n);
+    const int64_t scan_max = n > (int64_t)hist ? n : (int64_t)hist;
+    const size_t bytes = (size_t)n * key_bytes + (size_t)n * 4 + 4 * hist + 4 * scan_partials_size(scan_max) + 1024;
+    void *ws = nullptr;
+    if (pool_alloc(&ws, bytes, s) != cudaSuccess) return HCA_ENOMEM;
+    char *b = (char *)ws;
+    void *kalt = b;
+    uint32_t *valt = (uint32_t *)(b + (((size_t)n * key_bytes + 255) & ~(size_t)255));
+    uint32_t *h = (uint32_t *)((char *)valt + (((size_t)n * 4 + 255) & ~(size_t)255));
+    uint32_t *part = h + ((hist + 63) & ~(size_t)63);
+    bool flipped;
+    if (key_bytes == 4)
+        flipped = radix_sort_pairs<uint32_t>((uint32_t *)d_keys, d_vals, (uint32_t *)kalt, valt, n,
+                                             begin_bit, end_bit, h, part, s, nullptr);
+    else
+        flipped = radix_sort_pairs<uint64_t>((uint64_t *)d_keys, d_vals, (uint64_t *)kalt, valt, n,
+                                             begin_bit, end_bit, h, part, s, nullptr);
+    int rc = HCA_OK;
+    if (flipped) {
+        if (cudaMemcpyAsync(d_keys, kalt, (size_t)n * key_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(d_vals, valt, (size_t)n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            rc = HCA_ECUDA;
+    }
+    if (cudaGetLastError() != cudaSuccess) rc = HCA_ECUDA;
+    pool_free(ws, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) rc = HCA_ECUDA;
+    return rc;
+}
+
+extern "C" const char *hca_strerror(int code) {
+    switch (code) {
+        case HCA_OK: return "success";
+        case HCA_EINVAL: return "invalid argument";
+        case HCA_ENOMEM: return "device workspace allocation failed";
+        case HCA_ECUDA: return "CUDA runtime error";
+        case HCA_ERANGE: return "coordinate extent too large for the cell grid at this eps";
+        case HCA_ENOTIMPL: return "not implemented in this build";
+        case HCA_EDEVICE: return "device-side consistency check failed";
+    }
+    return "unknown error";
+}
+
+extern "C" int32_t hca_version(void) { return 100; }

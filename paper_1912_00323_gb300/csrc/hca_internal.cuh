@@ -1,0 +1,131 @@
+// Internal declarations shared by the CUDA translation units of the HCA-DBSCAN library.
+// Nothing here is part of the public ABI (include/hca_dbscan.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hca_dbscan.h"
+
+namespace hca {
+
+constexpr int kMaxD = 4;            // dimensions handled by the hypercube-stencil path
+constexpr int kMaxPencils = 512;    // neighbour pencil offsets per cell (d = 4 needs 179)
+constexpr int kWarp = 32;
+constexpr uint64_t kEmptyKey = ~0ull;
+constexpr uint32_t kNoLabel = 0x7fffffffu;
+constexpr uint32_t kLoopLimit = 1u << 22;  // cap of every loop that reads concurrently written data
+
+// device-side status word bits (HCA_EDEVICE when non-zero)
+constexpr uint32_t kErrHashFull = 1u;
+constexpr uint32_t kErrLoop = 2u;
+
+// Device counters and status, one struct per call in the workspace.
+struct DevCounters {
+    uint32_t n_cells;      // C: non-empty cells
+    uint32_t n_pencils;    // P: non-empty pencils (cells sharing all but the last coordinate)
+    uint32_t hash_mask;    // capacity - 1 of the pencil hash table
+    uint32_t status;       // kErr* bits
+    uint32_t n_dense;
+    uint32_t n_core;
+    uint32_t n_clusters;
+    uint32_t n_noise;
+    uint32_t minmax_enc[2 * kMaxD * 2];  // order-preserving encodings of min / max per dim
+    uint32_t nan_seen;
+    uint32_t pad[3];
+};
+
+// Grid of hypercubes (Algorithm 1) and everything a kernel needs to bin, pack and compare.
+struct GridParams {
+    int d;
+    int64_t n;
+    double origin[kMaxD];        // per-dimension minimum (origin shift, Sec. 2)
+    float origin_f[kMaxD];
+    double inv_side;             // 1 / cell side (cells per unit length)
+    float inv_side_f;
+    uint32_t ncell[kMaxD];       // cells per dimension
+    uint32_t shift[kMaxD];       // bit offset of each coordinate in the packed key
+    uint32_t bits[kMaxD];
+    int key_bits;
+    int prefix_shift;            // key >> prefix_shift = pencil key (all but the last coordinate)
+    uint32_t min_pts;
+    double eps2;                 // fl64(eps * eps): the exact predicate's threshold
+    float lo32, hi32;            // FP32 filter: s < lo32 => within, s > hi32 => outside
+    int bin_fp64;                // bin FP32 input in double precision
+};
+
+// Neighbour pencils: offsets of the first d-1 coordinates and the reach along the last one.
+// Full list (every neighbour) and the upper half (pairs counted once) share the table:
+// entries [0, n_half) are the offsets that are lexicographically >= 0.
+struct Stencil {
+    int n_all;
+    int n_half;
+    int8_t off[kMaxPencils][kMaxD - 1 > 0 ? kMaxD - 1 : 1];
+    int8_t reach[kMaxPencils];   // max |delta_last| that can hold a point within eps
+};
+
+template <typename T, int D>
+struct PadDim {
+    static constexpr int value = (D == 3) ? 4 : D;
+};
+
+template <typename T, int D>
+struct alignas(sizeof(T) * PadDim<T, D>::value) Pt {
+    T x[PadDim<T, D>::value];
+};
+
+// Workspace carved out of one pool allocation per call.
+struct Workspace {
+    void *base;
+    size_t bytes;
+};
+
+// ---------------------------------------------------------------------------------------
+// Primitives implemented in sort.cu / scan.cu
+// ---------------------------------------------------------------------------------------
+
+// Exclusive scan of uint32 in[0, m) into out[0, m); total into *total (device, may be null).
+// If m_dev is non-null the length is min(*m_dev, m_max); elements past it are left untouched.
+// partials: device scratch of scan_partials_size(m_max) uint32.
+size_t scan_partials_size(int64_t m_max);
+void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t m_max, const uint32_t *m_dev,
+                        uint32_t *total, uint32_t *partials, cudaStream_t s, int *launches);
+
+// LSD radix sort of (key, value) pairs by bits [begin_bit, end_bit), 8 bits per pass.
+// Ping-pongs between (keys, vals) and (keys_alt, vals_alt); returns true when the sorted
+// result ends up in the alternate buffers.  hist: sort_hist_size(n) uint32 of scratch.
+size_t sort_hist_size(int64_t n);
+template <typename K>
+bool radix_sort_pairs(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt, int64_t n,
+                      int begin_bit, int end_bit, uint32_t *hist, uint32_t *partials,
+                      cudaStream_t s, int *launches);
+
+// Pool allocation (stream ordered) used by api.cu and the pipelines.
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s);
+cudaError_t pool_free(void *p, cudaStream_t s);
+
+int device_sm_count();
+
+// Host orchestration of one clustering call, instantiated per (T, D) in lowd_*.cu.
+struct RunArgs {
+    const void *d_points;
+    int64_t n;
+    int d;
+    double eps;
+    int min_pts;
+    int32_t *d_labels;
+    uint8_t *d_core;
+    cudaStream_t stream;
+    hca_stats *stats;
+    int flags;
+};
+template <typename T, int D>
+int run_lowd(const RunArgs &a);
+
+}  // namespace hca
+
+#define HCA_CUDA_TRY(expr)                                    \
+    do {                                                      \
+        cudaError_t _e = (expr);                              \
+        if (_e != cudaSuccess) return HCA_ECUDA;              \
+    } while (0)

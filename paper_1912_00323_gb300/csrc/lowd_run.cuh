@@ -1,0 +1,402 @@
+// Host orchestration of the hypercube-stencil path for one call: workspace layout, grid
+// parameters, neighbour stencil and the launch sequence of the stage kernels.
+#pragma once
+
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "lowd_kernels.cuh"
+
+namespace hca {
+
+namespace detail {
+
+inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+inline double dec_double(uint64_t e) {
+    uint64_t b = (e >> 63) ? (e & 0x7fffffffffffffffull) : ~e;
+    double f;
+    memcpy(&f, &b, 8);
+    return f;
+}
+
+// Grid of hypercubes (Algorithm 1).  The side is eps/sqrt(d) (space diagonal eps, Sec. 2)
+// shrunk so that a cell stays within eps even after the rounding of the band computation:
+// with tau the bound on |computed - exact| of (x - o)/side in cell units, every point of
+// cell c has an exact band coordinate in [c - tau, c + 1 + tau), and
+//     d * ((1 + 2 tau) side)^2 <= (eps (1 - 2^-20))^2
+// keeps the FP64 predicate of every pair in one cell at or below eps^2.
+inline int make_grid(int D, bool input_f32, double eps, int min_pts, int64_t n,
+                     const double *mn, const double *mx, int flags, GridParams &g, double &tau) {
+    memset(&g, 0, sizeof(g));
+    g.d = D;
+    g.n = n;
+    g.min_pts = (uint32_t)min_pts;
+    g.eps2 = eps * eps;
+    double range_max = 0.0;
+    for (int i = 0; i < D; ++i) range_max = fmax(range_max, mx[i] - mn[i]);
+    if (!isfinite(range_max)) return HCA_ERANGE;
+    const double shrink = 1.0 - ldexp(1.0, -20);
+    bool bin32 = input_f32;
+    double inv = 0.0;
+    for (int attempt = 0; attempt < 64; ++attempt) {
+        const double u = bin32 ? ldexp(1.0, -22) : ldexp(1.0, -51);
+        inv = sqrt((double)D) / (eps * shrink);
+        tau = 0.0;
+        for (int it = 0; it < 4; ++it) {
+            tau = (range_max * inv + 1.0) * u;
+            inv = sqrt((double)D) * (1.0 + 2.0 * tau) / (eps * shrink) * (1.0 + ldexp(1.0, -40));
+        }
+        if (!isfinite(inv) || inv <= 0.0) return HCA_ERANGE;
+        bool ok = false;
+        for (int bump = 0; bump < 64 && !ok; ++bump) {
+            double inv_used = inv;
+            if (bin32) {
+                float f = (float)inv;
+                if ((double)f < inv) f = nextafterf(f, INFINITY);
+                inv_used = (double)f;
+                g.inv_side_f = f;
+            }
+            tau = (range_max * inv_used + 1.0) * u;
+            const double side = 1.0 / inv_used;
+            const double w = side * (1.0 + 2.0 * tau);
+            if ((double)D * w * w <= (eps * shrink) * (eps * shrink)) {
+                ok = true;
+                inv = inv_used;
+            } else {
+                inv *= 1.0 + ldexp(1.0, -20);
+            }
+        }
+        if (!ok) return HCA_ERANGE;
+        if (bin32 && tau > ldexp(1.0, -8)) {  // too coarse a bound: bin in FP64 instead
+            bin32 = false;
+            continue;
+        }
+        break;
+    }
+    g.inv_side = inv;
+    if (!bin32) g.inv_side_f = (float)inv;
+    g.bin_fp64 = bin32 ? 0 : 1;
+    int total = 0;
+    for (int i = 0; i < D; ++i) {
+        g.origin[i] = mn[i];
+        g.origin_f[i] = (float)mn[i];
+        const double cells = floor((mx[i] - mn[i]) * inv * (1.0 + 1e-6)) + 2.0;
+        if (!(cells < 2147483648.0)) return HCA_ERANGE;
+        g.ncell[i] = (uint32_t)cells;
+        uint32_t b = 1;
+        while ((1ull << b) < (uint64_t)g.ncell[i]) ++b;
+        g.bits[i] = b;
+        total += (int)b;
+    }
+    if (total > 63) return HCA_ERANGE;
+    g.key_bits = total;
+    int sh = 0;
+    for (int i = D - 1; i >= 0; --i) {
+        g.shift[i] = (uint32_t)sh;
+        sh += (int)g.bits[i];
+    }
+    g.prefix_shift = (int)g.bits[D - 1];
+    // FP32 filter thresholds (guard band 2^-16 relative; valid for eps^2 in [2^-100, 2^100])
+    const bool filter = input_f32 && !(flags & HCA_FLAG_FP64_ONLY) && g.eps2 >= ldexp(1.0, -100) &&
+                        g.eps2 <= ldexp(1.0, 100);
+    if (filter) {
+        float lo = (float)(g.eps2 * (1.0 - ldexp(1.0, -16)));
+        if ((double)lo > g.eps2 * (1.0 - ldexp(1.0, -16))) lo = nextafterf(lo, 0.f);
+        float hi = (float)(g.eps2 * (1.0 + ldexp(1.0, -16)));
+        if ((double)hi < g.eps2 * (1.0 + ldexp(1.0, -16))) hi = nextafterf(hi, INFINITY);
+        g.lo32 = lo;
+        g.hi32 = hi;
+    } else {
+        g.lo32 = -1.0f;
+        g.hi32 = INFINITY;
+    }
+    return HCA_OK;
+}
+
+// Neighbour pencils (the stencil of Sec. 2, "Depth First Search" and "Layering", reached
+// exactly): a cell at offset delta can hold a point within eps of a point of the current
+// cell only if sum_i gap(|delta_i|)^2 <= eps^2, gap(k) = max(k - 1 - 2 tau, 0) * side.  The
+// first d-1 offsets form the pencil offset; along the last coordinate the reach is the
+// largest k that still passes.  Entry 0 is the zero pencil offset, then the offsets that are
+// lexicographically positive (the upper half, used to visit each pair of cells once), then
+// the negative ones.
+inline int make_stencil(int D, double eps, double side, double tau, Stencil &st) {
+    memset(&st, 0, sizeof(st));
+    const double bound = eps * eps * (1.0 + ldexp(1.0, -20));
+    auto gap2 = [&](int k) {
+        double gg = (double)k - 1.0 - 2.0 * tau;
+        if (gg < 0.0) gg = 0.0;
+        gg *= side;
+        return gg * gg;
+    };
+    int R = 1;
+    while (gap2(R + 1) <= bound) ++R;
+    struct Entry { int off[kMaxD]; int reach; int cls; };
+    std::vector<Entry> all;
+    const int P = D - 1;
+    std::vector<int> delta(P > 0 ? P : 1, -R);
+    for (;;) {
+        double gp = 0.0;
+        bool zero = true;
+        int first = 0;
+        for (int i = 0; i < P; ++i) {
+            int a = delta[i] < 0 ? -delta[i] : delta[i];
+            gp += gap2(a);
+            if (delta[i] != 0 && zero) { zero = false; first = delta[i]; }
+        }
+        if (gp <= bound) {
+            Entry e;
+            memset(&e, 0, sizeof(e));
+            for (int i = 0; i < P; ++i) e.off[i] = delta[i];
+            int r = 1;
+            while (r < R && gp + gap2(r + 1) <= bound) ++r;
+            e.reach = r;
+            e.cls = zero ? 0 : (first > 0 ? 1 : 2);
+            all.push_back(e);
+        }
+        int i = 0;
+        while (i < P && delta[i] == R) delta[i++] = -R;
+        if (i >= P) break;
+        ++delta[i];
+    }
+    if ((int)all.size() > kMaxPencils) return HCA_ENOTIMPL;
+    int k = 0;
+    for (int cls = 0; cls < 3; ++cls) {
+        for (const Entry &e : all) {
+            if (e.cls != cls) continue;
+            for (int i = 0; i < P; ++i) st.off[k][i] = (int8_t)e.off[i];
+            st.reach[k] = (int8_t)e.reach;
+            ++k;
+        }
+        if (cls == 1) st.n_half = k;
+    }
+    st.n_all = k;
+    return HCA_OK;
+}
+
+struct HostCounters {
+    DevCounters *p = nullptr;
+    HostCounters() {
+        if (cudaMallocHost((void **)&p, sizeof(DevCounters)) != cudaSuccess) p = nullptr;
+    }
+    ~HostCounters() {
+        if (p) cudaFreeHost(p);
+    }
+};
+
+inline DevCounters *host_counters() {
+    thread_local HostCounters hc;
+    return hc.p;
+}
+
+inline int grid_for(int64_t work, int per_block, int sms, int max_per_sm) {
+    int64_t b = (work + per_block - 1) / per_block;
+    const int64_t cap = (int64_t)sms * max_per_sm;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace detail
+
+template <typename T, int D>
+int run_lowd(const RunArgs &a) {
+    using namespace detail;
+    cudaStream_t s = a.stream;
+    const int64_t n = a.n;
+    constexpr int ndir = RepDirs<D>::value;
+    int launches = 0;
+    const int sms = device_sm_count();
+    if (sms <= 0) return HCA_ECUDA;
+
+    // ---- workspace layout (one pool allocation) ----
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+    int64_t cap_max = 64;
+    while (cap_max < 2 * n) cap_max <<= 1;
+    const size_t hist_elems = sort_hist_size(n);
+    const int64_t scan_max = n > (int64_t)hist_elems ? n : (int64_t)hist_elems;
+    const size_t o_ctr = take(sizeof(DevCounters));
+    const size_t o_ka = take(8 * n), o_kb = take(8 * n), o_ia = take(4 * n), o_ib = take(4 * n);
+    const size_t o_hist = take(4 * hist_elems);
+    const size_t o_part = take(4 * scan_partials_size(scan_max));
+    const size_t o_pts = take(sizeof(Pt<T, D>) * n);
+    const size_t o_flags = take(4 * n), o_excl = take(4 * n);
+    const size_t o_cstart = take(4 * (n + 1)), o_ckey = take(8 * n);
+    const size_t o_pflags = take(4 * n), o_pexcl = take(4 * n), o_pstart = take(4 * (n + 1));
+    const size_t o_hk = take(8 * cap_max), o_hv = take(4 * cap_max);
+    const size_t o_core = take(n), o_ccore = take(n);
+    const size_t o_parent = take(4 * n), o_cmin = take(4 * n);
+    const size_t o_reps = take(8 * (size_t)n * ndir);
+    void *ws = nullptr;
+    if (pool_alloc(&ws, off, s) != cudaSuccess || !ws) return HCA_ENOMEM;
+    char *b = (char *)ws;
+    DevCounters *ctr = (DevCounters *)(b + o_ctr);
+    DevCounters *h = host_counters();
+    int rc = HCA_OK;
+
+    cudaEvent_t ev[HCA_NUM_STAGES + 1] = {};
+    const bool timing = (a.flags & HCA_FLAG_TIMING) && a.stats;
+    if (timing)
+        for (int i = 0; i <= HCA_NUM_STAGES; ++i) cudaEventCreate(&ev[i]);
+    auto mark = [&](int i) { if (timing) cudaEventRecord(ev[i], s); };
+
+    GridParams g;
+    Stencil st;
+    double tau = 0.0;
+    const int gpts = grid_for(n, 256, sms, 8);
+    const int gwarp = grid_for(n, 8, sms, 16);
+    LowdView<T, D> v;
+    memset(&v, 0, sizeof(v));
+    bool flipped = false;
+
+    if (!h) { rc = HCA_ECUDA; goto out; }
+    mark(0);
+    cudaMemsetAsync(ctr, 0, sizeof(DevCounters), s);
+    cudaMemsetAsync(ctr->minmax_enc, 0xff, sizeof(uint64_t) * kMaxD, s);
+    k_minmax<T, D><<<gpts, 256, 0, s>>>((const T *)a.d_points, n, ctr);
+    ++launches;
+    if (cudaMemcpyAsync(h, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) { rc = HCA_ECUDA; goto out; }
+    {
+        if (h->nan_seen) { rc = HCA_EINVAL; goto out; }
+        const uint64_t *mm = reinterpret_cast<const uint64_t *>(h->minmax_enc);
+        double mn[kMaxD], mx[kMaxD];
+        for (int i = 0; i < D; ++i) {
+            mn[i] = dec_double(mm[i]);
+            mx[i] = dec_double(mm[kMaxD + i]);
+            if (!isfinite(mn[i]) || !isfinite(mx[i])) { rc = HCA_EINVAL; goto out; }
+        }
+        rc = make_grid(D, sizeof(T) == 4, a.eps, a.min_pts, n, mn, mx, a.flags, g, tau);
+        if (rc) goto out;
+        rc = make_stencil(D, a.eps, 1.0 / g.inv_side, tau, st);
+        if (rc) goto out;
+    }
+    mark(1);
+    // ---- Algorithm 1: cell keys; pre-sort (Sec. 2) by a radix sort of (key, index) ----
+    {
+        uint32_t *ia = (uint32_t *)(b + o_ia), *ib = (uint32_t *)(b + o_ib);
+        uint32_t *hist = (uint32_t *)(b + o_hist), *part = (uint32_t *)(b + o_part);
+        const bool use32 = g.key_bits <= 32;
+        if (use32) {
+            uint32_t *ka = (uint32_t *)(b + o_ka), *kb = (uint32_t *)(b + o_kb);
+            k_bin<T, D, uint32_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, g, ka, ia);
+            ++launches;
+            mark(2);
+            flipped = radix_sort_pairs<uint32_t>(ka, ia, kb, ib, n, 0, g.key_bits, hist, part, s, &launches);
+            mark(3);
+            k_gather<T, D, uint32_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, flipped ? kb : ka,
+                                                          flipped ? ib : ia, n, (Pt<T, D> *)(b + o_pts),
+                                                          (uint32_t *)(b + o_flags));
+        } else {
+            uint64_t *ka = (uint64_t *)(b + o_ka), *kb = (uint64_t *)(b + o_kb);
+            k_bin<T, D, uint64_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, g, ka, ia);
+            ++launches;
+            mark(2);
+            flipped = radix_sort_pairs<uint64_t>(ka, ia, kb, ib, n, 0, g.key_bits, hist, part, s, &launches);
+            mark(3);
+            k_gather<T, D, uint64_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, flipped ? kb : ka,
+                                                          flipped ? ib : ia, n, (Pt<T, D> *)(b + o_pts),
+                                                          (uint32_t *)(b + o_flags));
+        }
+        ++launches;
+        exclusive_scan_u32((uint32_t *)(b + o_flags), (uint32_t *)(b + o_excl), n, nullptr,
+                           &ctr->n_cells, part, s, &launches);
+        if (use32) {
+            k_cells<uint32_t><<<gpts, 256, 0, s>>>((const uint32_t *)(b + (flipped ? o_kb : o_ka)),
+                                                   (uint32_t *)(b + o_flags), (const uint32_t *)(b + o_excl),
+                                                   n, (uint32_t *)(b + o_cstart), (uint64_t *)(b + o_ckey));
+        } else {
+            k_cells<uint64_t><<<gpts, 256, 0, s>>>((const uint64_t *)(b + (flipped ? o_kb : o_ka)),
+                                                   (uint32_t *)(b + o_flags), (const uint32_t *)(b + o_excl),
+                                                   n, (uint32_t *)(b + o_cstart), (uint64_t *)(b + o_ckey));
+        }
+        ++launches;
+        v.perm = flipped ? ib : ia;
+    }
+    mark(4);
+    // ---- pencils and their hash table ----
+    {
+        uint32_t *part = (uint32_t *)(b + o_part);
+        k_pencil_flags<<<gpts, 256, 0, s>>>((const uint64_t *)(b + o_ckey), g.prefix_shift, ctr,
+                                            (uint32_t *)(b + o_pflags));
+        exclusive_scan_u32((uint32_t *)(b + o_pflags), (uint32_t *)(b + o_pexcl), n, &ctr->n_cells,
+                           &ctr->n_pencils, part, s, &launches);
+        k_hash_init<<<grid_for(cap_max, 256, sms, 8), 256, 0, s>>>((uint64_t *)(b + o_hk), ctr);
+        k_pencils<<<gpts, 256, 0, s>>>((const uint64_t *)(b + o_ckey), g.prefix_shift,
+                                       (const uint32_t *)(b + o_pflags), (const uint32_t *)(b + o_pexcl),
+                                       (uint32_t *)(b + o_pstart), (uint64_t *)(b + o_hk),
+                                       (uint32_t *)(b + o_hv), ctr);
+        launches += 3;
+    }
+    mark(5);
+    v.g = g;
+    v.in = (const T *)a.d_points;
+    v.pts = (const Pt<T, D> *)(b + o_pts);
+    v.cell_of = (const uint32_t *)(b + o_flags);
+    v.cell_start = (const uint32_t *)(b + o_cstart);
+    v.cell_key = (const uint64_t *)(b + o_ckey);
+    v.pencil_start = (const uint32_t *)(b + o_pstart);
+    v.hkeys = (uint64_t *)(b + o_hk);
+    v.hvals = (uint32_t *)(b + o_hv);
+    v.core = (uint8_t *)(b + o_core);
+    v.cell_core = (uint8_t *)(b + o_ccore);
+    v.parent = (uint32_t *)(b + o_parent);
+    v.reps = (uint64_t *)(b + o_reps);
+    v.comp_min = (uint32_t *)(b + o_cmin);
+    v.labels = a.d_labels;
+    v.core_out = a.d_core;
+    v.ctr = ctr;
+    // ---- Definition 2: dense cells and exact counts ----
+    k_core<T, D><<<gwarp, 256, 0, s>>>(v, st);
+    ++launches;
+    mark(6);
+    // ---- Algorithm 2: representative points ----
+    k_reps<T, D><<<gpts, 256, 0, s>>>(v);
+    ++launches;
+    mark(7);
+    // ---- Algorithm 3: merge neighbouring cells ----
+    k_merge<T, D><<<gwarp, 256, 0, s>>>(v, st);
+    k_compress<T, D><<<gpts, 256, 0, s>>>(v);
+    launches += 2;
+    mark(8);
+    // ---- Algorithm 4: cluster ids, border and noise ----
+    k_comp_min<T, D><<<gpts, 256, 0, s>>>(v);
+    k_labels<T, D><<<gwarp, 256, 0, s>>>(v, st);
+    launches += 2;
+    mark(9);
+    if (cudaGetLastError() != cudaSuccess) { rc = HCA_ECUDA; goto out; }
+    if (cudaMemcpyAsync(h, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) { rc = HCA_ECUDA; goto out; }
+    if (h->status) { rc = HCA_EDEVICE; goto out; }
+    if (a.stats) {
+        hca_stats *st_out = a.stats;
+        st_out->n_points = n;
+        st_out->n_cells = h->n_cells;
+        st_out->n_pencils = h->n_pencils;
+        st_out->n_dense_cells = h->n_dense;
+        st_out->n_core_points = h->n_core;
+        st_out->n_clusters = h->n_clusters;
+        st_out->n_noise = h->n_noise;
+        st_out->key_bits = g.key_bits;
+        st_out->sort_passes = (g.key_bits + 7) / 8;
+        st_out->kernel_launches = launches;
+        for (int i = 0; i < HCA_NUM_STAGES; ++i) {
+            float ms = 0.f;
+            if (timing) cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+            st_out->stage_ms[i] = ms;
+        }
+    }
+out:
+    if (timing)
+        for (int i = 0; i <= HCA_NUM_STAGES; ++i)
+            if (ev[i]) cudaEventDestroy(ev[i]);
+    pool_free(ws, s);
+    if (rc != HCA_OK) cudaStreamSynchronize(s);
+    return rc;
+}
+
+}  // namespace hca

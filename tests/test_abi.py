@@ -1,0 +1,84 @@
+"""The C-ABI library builds, loads and exports every function include/*.h declares; argument
+checks answer without touching a GPU."""
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        names += re.findall(r"^HCA_API\s+[\w\s\*]+?\b(\w+)\s*\(", open(h).read(), re.M)
+    return names
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_1912_00323_gb300 import build
+    build.build()
+    import paper_1912_00323_gb300 as p
+    p.load()
+    return p
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for f in ("hca_dbscan", "hca_dbscan_device", "hca_dbscan_device_ex", "hca_radix_sort_pairs",
+              "hca_strerror", "hca_version"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(pkg):
+    lib = pkg.load()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert set(pkg.ABI_FUNCTIONS) <= set(declared_functions())
+
+
+def test_strerror_and_version(pkg):
+    assert pkg.hca_version() >= 100
+    for code in (0, -1, -2, -3, -4, -5, -6):
+        assert pkg.hca_strerror(code)
+    assert pkg.hca_strerror(-999) == "unknown error"
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(eps=0.0), -1), (dict(eps=float("nan")), -1), (dict(eps=float("inf")), -1),
+    (dict(min_pts=0), -1), (dict(d=0), -1), (dict(dtype=7), -1), (dict(n=-1), -1),
+])
+def test_invalid_arguments_rejected_on_the_host(pkg, kw, code):
+    lib = pkg.load()
+    X = np.zeros((4, 2))
+    labels = np.zeros(4, np.int32)
+    a = dict(n=4, d=2, eps=1.0, min_pts=2, dtype=pkg.HCA_F64)
+    a.update(kw)
+    rc = lib.hca_dbscan(X.ctypes.data, a["dtype"], a["n"], a["d"], a["eps"], a["min_pts"], labels.ctypes.data)
+    assert rc == code
+
+
+def test_empty_input_is_ok_without_device(pkg):
+    lib = pkg.load()
+    assert lib.hca_dbscan(None, pkg.HCA_F32, 0, 3, 1.0, 2, None) == 0
+
+
+def test_sort_argument_checks(pkg):
+    lib = pkg.load()
+    assert lib.hca_radix_sort_pairs(None, None, 10, 3, 0, 8, None) == -1
+    assert lib.hca_radix_sort_pairs(None, None, 10, 4, 0, 40, None) == -1
+    assert lib.hca_radix_sort_pairs(None, None, 0, 8, 0, 64, None) == 0
+
+
+def test_oracle_and_library_share_no_code():
+    """The oracle and the CUDA path are independent: neither includes or imports the other."""
+    csrc = os.path.join(ROOT, "paper_1912_00323_gb300")
+    for path in glob.glob(os.path.join(csrc, "**", "*"), recursive=True):
+        if os.path.isfile(path) and path.endswith((".py", ".cu", ".cuh", ".h", ".c")):
+            assert "oracle" not in re.sub(r"#.*|//.*", "", open(path).read()).lower() or \
+                path.endswith("workloads.py"), path
+    src = open(os.path.join(ROOT, "oracle", "hca_oracle.c")).read()
+    assert "hca_dbscan.h" not in src and "csrc" not in src

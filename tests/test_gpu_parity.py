@@ -1,0 +1,217 @@
+"""Parity of the CUDA path with the CPU oracle, element by element, through the C ABI.
+
+Labels and core flags are integers and must be bit-identical.  Inputs are seeded synthetic
+point sets: hand-derived fixtures, lattice sets with many pairs at exactly eps, small and
+full-size copies of the workload recipes, and edge cases."""
+import os
+
+import numpy as np
+import pytest
+
+from golden_io import all_cases, load
+from paper_1912_00323_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1912_00323_gb300 import build
+    build.build()
+    import oracle
+    oracle.build()
+    import paper_1912_00323_gb300 as pkg
+    pkg.load()
+    return torch, pkg, oracle
+
+
+def run_device(env, X, eps, min_pts, **kw):
+    torch, pkg, _ = env
+    t = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    core = torch.empty(len(X), dtype=torch.uint8, device="cuda")
+    out = pkg.hca_dbscan_device(t, eps, min_pts, core=core, **kw)
+    torch.cuda.synchronize()
+    if isinstance(out, tuple):
+        return out[0].cpu().numpy(), core.cpu().numpy(), out[1]
+    return out.cpu().numpy(), core.cpu().numpy(), None
+
+
+def assert_parity(got, want):
+    lab, core = got[0], got[1]
+    bad = np.flatnonzero(lab != want[0])
+    assert len(bad) == 0, f"{len(bad)} labels differ, first at {bad[:5]}: got {lab[bad[:5]]} want {want[0][bad[:5]]}"
+    np.testing.assert_array_equal(core, want[1])
+
+
+@pytest.mark.parametrize("path", all_cases(), ids=lambda p: os.path.basename(p)[:-4])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_golden_fixtures(env, path, dtype):
+    X, eps, min_pts, exp = load(path)
+    if dtype == np.float32 and not np.array_equal(X.astype(np.float32).astype(np.float64), X):
+        pytest.skip("coordinates not exact in float32")
+    got = run_device(env, X.astype(dtype), eps, min_pts)
+    np.testing.assert_array_equal(got[0], exp["labels"])
+    np.testing.assert_array_equal(got[1], exp["core"])
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("min_pts", [1, 4, 9])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_lattice_ties(env, d, seed, min_pts, dtype):
+    """Points on a 0.25 lattice, eps = 1: many pairs sit at exactly eps (Definition 1, <=)."""
+    _, _, oracle = env
+    X, eps, _ = workloads.lattice(3000, d, seed=1000 * d + seed, spread=3.0 + d, box=10.0 + 5 * d)
+    want = oracle.grid(X, eps, min_pts)
+    assert_parity(run_device(env, X.astype(dtype), eps, min_pts), want)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 32, 33, 1000, 4097, 70001])
+def test_sizes_and_ragged_tails(env, n):
+    _, _, oracle = env
+    X, eps, min_pts = workloads.blobs2d(n=n, seed=77 + n)
+    want = oracle.grid(X, eps, min_pts)
+    assert_parity(run_device(env, X, eps, min_pts), want)
+
+
+def test_blobs2d_full_float64(env):
+    """The 2-D workload at its full size (n = 10,000, float64, eps 1.5, minPts 5)."""
+    _, _, oracle = env
+    X, eps, min_pts = workloads.blobs2d()
+    want = oracle.bruteforce(X, eps, min_pts)
+    assert_parity(run_device(env, X, eps, min_pts), want)
+
+
+@pytest.mark.parametrize("n", [20_000, 200_000])
+def test_mixed3d_small(env, n):
+    _, _, oracle = env
+    X, eps, min_pts = workloads.mixed3d(n=n)
+    want = oracle.grid(X.astype(np.float64), eps, min_pts)
+    assert_parity(run_device(env, X, eps, min_pts), want)
+
+
+def test_mixed3d_full(env):
+    """The 3-D workload at full size (n = 2,000,000 float32 on the 2^-16 lattice, eps 2,
+    minPts 10), in the configuration the benchmark times."""
+    _, _, oracle = env
+    X, eps, min_pts = workloads.mixed3d()
+    want = oracle.grid(X.astype(np.float64), eps, min_pts)
+    got = run_device(env, X, eps, min_pts, stats=True)
+    assert_parity(got, want)
+    st = got[2]
+    assert st["n_core_points"] == int(want[1].sum())
+    assert st["n_noise"] == int((want[0] < 0).sum())
+    assert st["n_clusters"] == len(np.unique(want[0][want[1] == 1]))
+
+
+def test_fp64_only_matches_filtered(env):
+    X, eps, min_pts = workloads.mixed3d(n=100_000)
+    a = run_device(env, X, eps, min_pts)
+    b = run_device(env, X, eps, min_pts, fp64_only=True)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+
+
+def test_deterministic_across_runs(env):
+    X, eps, min_pts = workloads.mixed3d(n=300_000)
+    a = run_device(env, X, eps, min_pts)
+    for _ in range(3):
+        b = run_device(env, X, eps, min_pts)
+        np.testing.assert_array_equal(a[0], b[0])
+
+
+def test_host_entry_point_matches_device(env):
+    torch, pkg, oracle = env
+    X, eps, min_pts = workloads.mixed3d(n=50_000)
+    want = oracle.grid(X.astype(np.float64), eps, min_pts)
+    got = pkg.hca_dbscan(X, eps, min_pts)
+    np.testing.assert_array_equal(got, want[0])
+    pinned = torch.from_numpy(X).pin_memory()
+    out = torch.empty(len(X), dtype=torch.int32).pin_memory()
+    pkg.hca_dbscan(pinned, eps, min_pts, labels=out)
+    np.testing.assert_array_equal(out.numpy(), want[0])
+
+
+def test_runs_on_a_side_stream(env):
+    torch, pkg, oracle = env
+    X, eps, min_pts = workloads.mixed3d(n=40_000)
+    want = oracle.grid(X.astype(np.float64), eps, min_pts)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        t = torch.from_numpy(X).cuda()
+        lab = pkg.hca_dbscan_device(t, eps, min_pts, stream=s)
+    s.synchronize()
+    np.testing.assert_array_equal(lab.cpu().numpy(), want[0])
+
+
+@pytest.mark.parametrize("case", ["identical", "negative_offset", "wide_range", "all_noise",
+                                  "one_cluster", "minpts_one", "minpts_huge"])
+def test_edge_cases(env, case):
+    _, _, oracle = env
+    r = np.random.Generator(np.random.PCG64(5))
+    eps, min_pts = 1.0, 4
+    if case == "identical":
+        X = np.full((5000, 3), 7.25)
+    elif case == "negative_offset":
+        X, eps, min_pts = workloads.lattice(4000, 3, seed=3)
+        X = X - 5000.0
+    elif case == "wide_range":   # 2^20+ cells per dimension: 64-bit cell keys
+        X = np.round(r.uniform(-3e5, 3e5, size=(20000, 3)) * 4) / 4
+        X[:5000] = np.round(r.normal(0, 2, size=(5000, 3)) * 4) / 4
+        eps = 1.0
+    elif case == "all_noise":
+        X = np.arange(3000, dtype=np.float64)[:, None] * np.array([[10.0, 0.0]])
+    elif case == "one_cluster":
+        X = np.round(r.normal(0, 0.5, size=(20000, 2)) * 64) / 64
+    elif case == "minpts_one":
+        X, eps, _ = workloads.lattice(4000, 2, seed=11)
+        min_pts = 1
+    elif case == "minpts_huge":
+        X, eps, _ = workloads.lattice(4000, 2, seed=12)
+        min_pts = 100000
+    want = oracle.grid(X, eps, min_pts)
+    assert_parity(run_device(env, X, eps, min_pts), want)
+
+
+def test_error_codes(env):
+    torch, pkg, _ = env
+    X = torch.zeros((10, 5), device="cuda")
+    with pytest.raises(pkg.HcaError) as e:
+        pkg.hca_dbscan_device(X, 1.0, 2)
+    assert e.value.code == pkg.HCA_ENOTIMPL
+    Y = torch.zeros((10, 2), device="cuda")
+    Y[3, 1] = float("nan")
+    with pytest.raises(pkg.HcaError) as e:
+        pkg.hca_dbscan_device(Y, 1.0, 2)
+    assert e.value.code == pkg.HCA_EINVAL
+    Y[3, 1] = float("inf")
+    with pytest.raises(pkg.HcaError) as e:
+        pkg.hca_dbscan_device(Y, 1.0, 2)
+    assert e.value.code == pkg.HCA_EINVAL
+    Z = torch.zeros((10, 4), dtype=torch.float64, device="cuda")
+    Z[0] = 1e300
+    with pytest.raises(pkg.HcaError) as e:
+        pkg.hca_dbscan_device(Z, 1e-3, 2)
+    assert e.value.code == pkg.HCA_ERANGE
+
+
+@pytest.mark.parametrize("n", [2, 100, 4096, 4097, 1_000_003])
+@pytest.mark.parametrize("kbytes,bits", [(4, (0, 32)), (4, (0, 13)), (8, (0, 64)), (8, (5, 41))])
+def test_radix_sort_matches_stable_argsort(env, n, kbytes, bits):
+    torch, pkg, _ = env
+    r = np.random.Generator(np.random.PCG64(n + bits[1]))
+    dt = np.uint32 if kbytes == 4 else np.uint64
+    keys = r.integers(0, np.iinfo(dt).max, size=n, dtype=dt, endpoint=True)
+    keys[: n // 3] = keys[n // 2]   # many equal keys: stability matters
+    vals = np.arange(n, dtype=np.uint32)
+    lo, hi = bits
+    field = (keys >> dt(lo)) & dt((1 << (hi - lo)) - 1) if hi - lo < 64 else keys
+    order = np.argsort(field, kind="stable")
+    tk = torch.from_numpy(keys.view(np.int32 if kbytes == 4 else np.int64)).cuda()
+    tv = torch.from_numpy(vals.view(np.int32)).cuda()
+    pkg.hca_radix_sort_pairs(tk, tv, lo, hi)
+    np.testing.assert_array_equal(tv.cpu().numpy().view(np.uint32), order.astype(np.uint32))
+    np.testing.assert_array_equal(tk.cpu().numpy().view(dt), keys[order])
