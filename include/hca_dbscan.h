@@ -61,6 +61,10 @@ extern "C" {
 #define HCA_ENOTIMPL (-5)  /* supported by the interface, not by this build (e.g. d > 4) */
 #define HCA_EDEVICE (-6)   /* a kernel's own consistency check tripped (bounded loop limit,
                               full hash table); the outputs hold no result */
+#define HCA_ETOOLARGE (-7) /* n above the fixed scratch of hca_radix_sort_pairs_noalloc */
+
+/* largest n accepted by hca_radix_sort_pairs_noalloc */
+#define HCA_SORT_NOALLOC_MAX_PAIRS (1 << 18)
 
 /* flags for hca_dbscan_device_ex */
 #define HCA_FLAG_TIMING 1     /* record CUDA events around each stage into stats->stage_ms */
@@ -134,6 +138,25 @@ HCA_API int hca_dbscan_device_ex(const void *d_points, int32_t dtype, int64_t n,
  */
 HCA_API int hca_radix_sort_pairs(void *d_keys, uint32_t *d_vals, int64_t n, int32_t key_bytes,
                          int32_t begin_bit, int32_t end_bit, void *stream);
+
+/*
+ * hca_radix_sort_pairs_noalloc -- hca_radix_sort_pairs without allocating device memory.
+ * The paper has no counterpart: this entry point serves callers that cannot allocate device
+ * memory while they run (a fixed memory budget set at start-up, a framework whose allocator
+ * owns all device memory, code that must not risk the synchronisation cudaMalloc / cudaFree
+ * can cause).  Same arguments, result and stream semantics as hca_radix_sort_pairs.
+ *   n  at most HCA_SORT_NOALLOC_MAX_PAIRS (2^18); larger n returns HCA_ETOOLARGE.
+ * Scratch: a fixed array of about 3.1 MiB inside the library (a __device__ variable), held on
+ * every GPU that loads the library until the process exits.  The first call on a device looks
+ * up that array's device address (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture.  Calls no cudaMalloc, cudaFree or other allocating routine.
+ * Every call uses the same array: calls whose work overlaps on the GPU (other streams, other
+ * threads, without ordering between them) race and give wrong results; order them.  A call
+ * leaves its scratch contents behind; none of them is read by the next call.
+ */
+HCA_API int hca_radix_sort_pairs_noalloc(void *d_keys, uint32_t *d_vals, int64_t n,
+                                         int32_t key_bytes, int32_t begin_bit, int32_t end_bit,
+                                         void *stream);
 
 /* Static description of a return code; never NULL. */
 HCA_API const char *hca_strerror(int code);

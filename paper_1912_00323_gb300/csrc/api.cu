@@ -205,6 +205,7 @@ extern "C" const char *hca_strerror(int code) {
         case HCA_ERANGE: return "coordinate extent too large for the cell grid at this eps";
         case HCA_ENOTIMPL: return "not implemented in this build";
         case HCA_EDEVICE: return "device-side consistency check failed";
+        case HCA_ETOOLARGE: return "input larger than the fixed scratch of the no-allocation entry point";
     }
     return "unknown error";
 }
