@@ -62,7 +62,7 @@ def stage_bytes(stage, n, d, C, P, passes, key_bytes):
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mixed3d", choices=["mixed3d", "blobs2d"])
@@ -91,7 +91,7 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms during the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -108,7 +108,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -331,6 +331,8 @@ def run_ours(args):
         "result": {"cells": C, "pencils": P, "dense_cells": stats["n_dense_cells"],
                    "core_points": stats["n_core_points"], "clusters": stats["n_clusters"],
                    "noise": stats["n_noise"]},
+        "work": {k: stats[k] for k in ("n_count_chunks", "n_rep_tests", "n_rep_hits",
+                                       "n_exhaustive_pairs", "n_exhaustive_chunks", "n_border_chunks")},
         "wall_s": wall,
     }
     if not args.no_cpu_baseline and ws == 1:

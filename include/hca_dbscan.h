@@ -95,6 +95,15 @@ typedef struct hca_stats {
     int32_t kernel_launches;  /* kernels this call launched */
     int32_t reserved;
     float stage_ms[HCA_NUM_STAGES];
+    /* work counters: 32-point chunks compared while counting neighbours (Definition 2),
+       representative-point tests and hits (Algorithm 3), cell pairs that needed the
+       exhaustive core x core test and its 32-point chunks, chunks compared for border points */
+    int64_t n_count_chunks;
+    int64_t n_rep_tests;
+    int64_t n_rep_hits;
+    int64_t n_exhaustive_pairs;
+    int64_t n_exhaustive_chunks;
+    int64_t n_border_chunks;
 } hca_stats;
 
 /*

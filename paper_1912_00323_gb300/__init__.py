@@ -35,7 +35,10 @@ class HcaStats(ctypes.Structure):
                 ("n_core_points", ctypes.c_int64), ("n_clusters", ctypes.c_int64),
                 ("n_noise", ctypes.c_int64), ("key_bits", ctypes.c_int32),
                 ("sort_passes", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("stage_ms", ctypes.c_float * len(STAGES))]
+                ("reserved", ctypes.c_int32), ("stage_ms", ctypes.c_float * len(STAGES)),
+                ("n_count_chunks", ctypes.c_int64), ("n_rep_tests", ctypes.c_int64),
+                ("n_rep_hits", ctypes.c_int64), ("n_exhaustive_pairs", ctypes.c_int64),
+                ("n_exhaustive_chunks", ctypes.c_int64), ("n_border_chunks", ctypes.c_int64)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_ if name not in ("stage_ms", "reserved")}

@@ -33,6 +33,7 @@ struct DevCounters {
     uint32_t minmax_enc[2 * kMaxD * 2];  // order-preserving encodings of min / max per dim
     uint32_t nan_seen;
     uint32_t pad[3];
+    unsigned long long work[8];  // work counters (see hca_stats)
 };
 
 // Grid of hypercubes (Algorithm 1) and everything a kernel needs to bin, pack and compare.
@@ -52,6 +53,9 @@ struct GridParams {
     double eps2;                 // fl64(eps * eps): the exact predicate's threshold
     float lo32, hi32;            // FP32 filter: s < lo32 => within, s > hi32 => outside
     int bin_fp64;                // bin FP32 input in double precision
+    int box_ok;                  // band coordinates exact enough in FP32 for cell-box tests
+    float tau_box;               // widening of a cell box, band units
+    float box_full, box_none;    // eps^2 in band units^2 times (1 -/+ 2^-12)
 };
 
 // Neighbour pencils: offsets of the first d-1 coordinates and the reach along the last one.

@@ -10,6 +10,7 @@
 //   pencil_start[p] first cell of pencil p; a pencil is a maximal run of cells that share
 //                   every coordinate but the last, so its cells are consecutive in key order
 //   hash            pencil key -> pencil id (open addressing, linear probing)
+//   ranges[c * n_all + k]  cells [lo, hi) of stencil pencil k around cell c
 //   core[j], cell_core[c], parent[c] (union-find), reps[c * ndir + r], comp_min[c]
 #pragma once
 
@@ -36,6 +37,7 @@ struct LowdView {
     uint32_t *parent;
     uint64_t *reps;
     uint32_t *comp_min;
+    uint2 *ranges;                // [cell * n_all + k]: neighbour cells [lo, hi) in pencil k
     int32_t *labels;              // output, input order
     uint8_t *core_out;            // optional output, input order
     DevCounters *ctr;
@@ -249,6 +251,19 @@ __device__ __forceinline__ uint32_t uf_find(uint32_t *parent, uint32_t x, DevCou
     return x;
 }
 
+// Root of x without writing: used once merging is over, where a path-halving write could
+// overwrite another thread's flattened parent[c] = root with an intermediate ancestor.
+__device__ __forceinline__ uint32_t uf_root_readonly(const uint32_t *parent, uint32_t x, DevCounters *ctr) {
+    uint32_t it = 0;
+    uint32_t p = __ldcg(parent + x);
+    while (p != x) {
+        x = p;
+        p = __ldcg(parent + x);
+        if (++it > kLoopLimit) { set_error(ctr, kErrLoop); break; }
+    }
+    return x;
+}
+
 __device__ __forceinline__ void uf_union(uint32_t *parent, uint32_t a, uint32_t b, DevCounters *ctr) {
     for (uint32_t it = 0; it < kLoopLimit; ++it) {
         a = uf_find(parent, a, ctr);
@@ -262,31 +277,122 @@ __device__ __forceinline__ void uf_union(uint32_t *parent, uint32_t a, uint32_t 
 }
 
 // ------------------------------------------------------------------------------------------
+// Cell boxes and flattened neighbour lists
+// ------------------------------------------------------------------------------------------
+
+// Band coordinates of a point, t_i = (x_i - o_i) / side, in the arithmetic of the binning.
+template <typename T, int D>
+__device__ __forceinline__ void band_coords(const Pt<T, D> &p, const GridParams &g, float *t) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        if (sizeof(T) == 4 && !g.bin_fp64)
+            t[i] = __fmul_rn(__fsub_rn((float)p.x[i], g.origin_f[i]), g.inv_side_f);
+        else
+            t[i] = (float)__dmul_rn(__dsub_rn((double)p.x[i], g.origin[i]), g.inv_side);
+    }
+}
+
+// Where can the points of cell cb lie relative to eps of a point with band coordinates t?
+// 0: every point of the cell is farther than eps; 2: every point is within eps; 1: unknown.
+// The cell is widened by tau_box band units, which bounds the binning error of both the
+// point and the cell's points plus the FP32 error of this test; the thresholds carry a
+// relative margin of 2^-12, far above the FP32 error of the sums, so the answer agrees with
+// the exact predicate whenever it is 0 or 2.
+template <int D>
+__device__ __forceinline__ int box_class(const float *t, const int *cb, const GridParams &g) {
+    if (!g.box_ok) return 1;
+    float mn = 0.f, mx = 0.f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        const float lo = (float)cb[i] - g.tau_box, hi = (float)cb[i] + 1.0f + g.tau_box;
+        const float gap = fmaxf(fmaxf(lo - t[i], t[i] - hi), 0.f);
+        const float far = fmaxf(fabsf(t[i] - lo), fabsf(t[i] - hi));
+        mn = fmaf(gap, gap, mn);
+        mx = fmaf(far, far, mx);
+    }
+    if (mn > g.box_none) return 0;
+    if (mx < g.box_full) return 2;
+    return 1;
+}
+
+// Per lane a cell range [lo, lo + len); inclusive prefix sums of the lengths across the warp
+// let the warp walk all cells of up to 32 ranges, 32 at a time.
+struct LaneRanges {
+    uint32_t lo, len, incl, total;
+};
+
+__device__ __forceinline__ LaneRanges lane_ranges(uint32_t lo, uint32_t hi) {
+    LaneRanges r;
+    r.lo = lo;
+    r.len = hi > lo ? hi - lo : 0u;
+    uint32_t v = r.len;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    r.incl = v;
+    r.total = __shfl_sync(0xffffffffu, v, 31);
+    return r;
+}
+
+// Cell at flattened position f (< total).  Every lane of the warp must call it.
+__device__ __forceinline__ uint32_t flat_cell(const LaneRanges &r, uint32_t f) {
+    int k = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+        const uint32_t v = __shfl_sync(0xffffffffu, r.incl, k + step - 1);
+        if (v <= f) k += step;
+    }
+    const uint32_t excl = __shfl_sync(0xffffffffu, r.incl - r.len, k);
+    const uint32_t lo = __shfl_sync(0xffffffffu, r.lo, k);
+    return lo + (f - excl);
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void load_stencil(Stencil &st, const Stencil &st_in) {
+    for (int i = threadIdx.x; i < (int)(sizeof(Stencil) / 4); i += blockDim.x)
+        reinterpret_cast<uint32_t *>(&st)[i] = reinterpret_cast<const uint32_t *>(&st_in)[i];
+    __syncthreads();
+}
+
+__device__ __forceinline__ void add_counter(unsigned long long *ctr, uint32_t v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(ctr, (unsigned long long)v);
+}
+
+// ------------------------------------------------------------------------------------------
 // Stage kernels
 // ------------------------------------------------------------------------------------------
 
-// Origin shift (Sec. 2): per-dimension min and max, plus a NaN check.
+// Origin shift (Sec. 2): per-dimension min and max in the input's own precision, plus a NaN
+// check.
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_minmax(const T *__restrict__ in, int64_t n, DevCounters *ctr) {
-    double mn[D], mx[D];
+    T mn[D], mx[D];
 #pragma unroll
-    for (int i = 0; i < D; ++i) { mn[i] = DBL_MAX; mx[i] = -DBL_MAX; }
+    for (int i = 0; i < D; ++i) {
+        mn[i] = sizeof(T) == 4 ? (T)FLT_MAX : (T)DBL_MAX;
+        mx[i] = -mn[i];
+    }
     bool nan = false;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            double x = (double)in[j * D + i];
+            const T x = in[j * D + i];
             nan |= (x != x);
-            mn[i] = fmin(mn[i], x);
-            mx[i] = fmax(mx[i], x);
+            mn[i] = x < mn[i] ? x : mn[i];
+            mx[i] = x > mx[i] ? x : mx[i];
         }
     }
 #pragma unroll
     for (int i = 0; i < D; ++i) {
         for (int o = 16; o; o >>= 1) {
-            mn[i] = fmin(mn[i], __shfl_xor_sync(0xffffffffu, mn[i], o));
-            mx[i] = fmax(mx[i], __shfl_xor_sync(0xffffffffu, mx[i], o));
+            const T a = __shfl_xor_sync(0xffffffffu, mn[i], o), b = __shfl_xor_sync(0xffffffffu, mx[i], o);
+            mn[i] = a < mn[i] ? a : mn[i];
+            mx[i] = b > mx[i] ? b : mx[i];
         }
     }
     nan = __any_sync(0xffffffffu, nan);
@@ -294,8 +400,8 @@ __global__ void __launch_bounds__(256) k_minmax(const T *__restrict__ in, int64_
         uint64_t *mm = reinterpret_cast<uint64_t *>(ctr->minmax_enc);
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            atomicMin((unsigned long long *)&mm[i], (unsigned long long)enc_double(mn[i]));
-            atomicMax((unsigned long long *)&mm[kMaxD + i], (unsigned long long)enc_double(mx[i]));
+            atomicMin((unsigned long long *)&mm[i], (unsigned long long)enc_double((double)mn[i]));
+            atomicMax((unsigned long long *)&mm[kMaxD + i], (unsigned long long)enc_double((double)mx[i]));
         }
         if (nan) atomicOr(&ctr->nan_seen, 1u);
     }
@@ -365,8 +471,8 @@ __global__ void __launch_bounds__(256) k_cells(const K *__restrict__ keys, uint3
 
 // First cell of every pencil (cells sharing all coordinates but the last).
 static __global__ void __launch_bounds__(256) k_pencil_flags(const uint64_t *__restrict__ cell_key,
-                                                     int prefix_shift, const DevCounters *ctr,
-                                                     uint32_t *__restrict__ pflags) {
+                                                            int prefix_shift, const DevCounters *ctr,
+                                                            uint32_t *__restrict__ pflags) {
     const uint32_t C = ctr->n_cells;
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x)
         pflags[c] = (c == 0 || (cell_key[c] >> prefix_shift) != (cell_key[c - 1] >> prefix_shift)) ? 1u : 0u;
@@ -383,10 +489,10 @@ static __global__ void __launch_bounds__(256) k_hash_init(uint64_t *__restrict__
 }
 
 static __global__ void __launch_bounds__(256) k_pencils(const uint64_t *__restrict__ cell_key,
-                                                int prefix_shift, const uint32_t *__restrict__ pflags,
-                                                const uint32_t *__restrict__ pexcl,
-                                                uint32_t *__restrict__ pencil_start,
-                                                uint64_t *hkeys, uint32_t *hvals, DevCounters *ctr) {
+                                                       int prefix_shift, const uint32_t *__restrict__ pflags,
+                                                       const uint32_t *__restrict__ pexcl,
+                                                       uint32_t *__restrict__ pencil_start,
+                                                       uint64_t *hkeys, uint32_t *hvals, DevCounters *ctr) {
     const uint32_t C = ctr->n_cells;
     const uint32_t mask = ctr->hash_mask;
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
@@ -411,22 +517,41 @@ static __global__ void __launch_bounds__(256) k_pencils(const uint64_t *__restri
     }
 }
 
+// Neighbour cells of every cell, once: for cell c and stencil pencil k the range of cells
+// [lo, hi) of that pencil within reach (hash lookup of the pencil, then two binary searches
+// along its last coordinate).  One thread per (cell, pencil).
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_ranges(LowdView<T, D> v, Stencil st_in) {
+    __shared__ Stencil st;
+    load_stencil<T, D>(st, st_in);
+    const uint32_t C = v.ctr->n_cells;
+    const int na = st.n_all;
+    const uint64_t total = (uint64_t)C * na;
+    for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = (uint32_t)(idx / na);
+        const int k = (int)(idx - (uint64_t)c * na);
+        int ac[D];
+        unpack_key<D>(v.cell_key[c], v.g, ac);
+        uint32_t lo = 0, hi = 0;
+        if (!pencil_range<T, D>(v, st, k, ac, false, lo, hi)) lo = hi = 0;
+        v.ranges[idx] = make_uint2(lo, hi);
+    }
+}
+
 // Definition 2 with the hypercube shortcut: a cell holding >= MINPTS points is core as a
 // whole (its diagonal is at most eps); every point of another cell is counted exactly over
-// its own cell and the neighbour cells, stopping once it reaches MINPTS.  One warp per cell;
-// candidate points are held one per lane and every point of the cell is compared against
-// them with a warp ballot.  Also initialises the per-cell union-find, reps and labels.
+// its own cell and the neighbour cells, stopping once it reaches MINPTS.  One warp per cell:
+// the lanes hold the cell's points; the neighbour cells are walked 32 at a time; a neighbour
+// cell whose box lies wholly within eps of a point adds its size without tests, one wholly
+// beyond eps is skipped, and the rest are compared point by point with a warp ballot.  Also
+// initialises the per-cell union-find and cluster-id slots.
 template <typename T, int D>
-__global__ void __launch_bounds__(256) k_core(LowdView<T, D> v, Stencil st_in) {
-    __shared__ Stencil st;
-    for (int i = threadIdx.x; i < (int)(sizeof(Stencil) / 4); i += blockDim.x)
-        reinterpret_cast<uint32_t *>(&st)[i] = reinterpret_cast<const uint32_t *>(&st_in)[i];
-    __syncthreads();
-    constexpr int ndir = RepDirs<D>::value;
+__global__ void __launch_bounds__(256) k_core(LowdView<T, D> v, int n_all) {
     const uint32_t C = v.ctr->n_cells;
     const uint32_t min_pts = v.g.min_pts;
     const int lane = lane_id();
-    uint32_t dense_cells = 0;
+    uint32_t dense_cells = 0, chunks = 0;
     for (uint32_t A = global_warp(); A < C; A += total_warps()) {
         const uint32_t s = v.cell_start[A], e = v.cell_start[A + 1], m = e - s;
         if (lane == 0) {
@@ -435,48 +560,59 @@ __global__ void __launch_bounds__(256) k_core(LowdView<T, D> v, Stencil st_in) {
         }
         if (m >= min_pts) {
             for (uint32_t i = s + lane; i < e; i += 32) v.core[i] = 1;
-            for (int r = lane; r < ndir; r += 32) v.reps[(int64_t)A * ndir + r] = ~0ull;
+            for (int r = lane; r < RepDirs<D>::value; r += 32) v.reps[(uint64_t)A * RepDirs<D>::value + r] = ~0ull;
             if (lane == 0) v.cell_core[A] = 1;
             ++dense_cells;
             continue;
         }
-        int ac[D];
-        unpack_key<D>(v.cell_key[A], v.g, ac);
         bool any_core = false;
         for (uint32_t base = s; base < e; base += 32) {
             const uint32_t i = base + lane;
             const bool have = i < e;
             const Pt<T, D> pa = have ? v.pts[i] : zero_pt<T, D>();
-            const int nA = (int)min(32u, e - base);
-            uint32_t cnt = m;
+            float ta[D];
+            band_coords<T, D>(pa, v.g, ta);
+            uint32_t cnt = m;  // the own cell: every point within eps
             bool all_done = false;
-            for (int k0 = 0; k0 < st.n_all && !all_done; k0 += 32) {
-                const int k = k0 + lane;
-                uint32_t lo = 0, hi = 0;
-                const bool ok = k < st.n_all && pencil_range<T, D>(v, st, k, ac, false, lo, hi);
-                const uint32_t qlo = ok ? v.cell_start[lo] : 0u, qhi = ok ? v.cell_start[hi] : 0u;
-                unsigned rm = __ballot_sync(0xffffffffu, ok);
-                while (rm && !all_done) {
-                    const int L = __ffs(rm) - 1;
-                    rm &= rm - 1;
-                    const uint32_t q0 = __shfl_sync(0xffffffffu, qlo, L);
-                    const uint32_t q1 = __shfl_sync(0xffffffffu, qhi, L);
-                    // the zero offset's range contains this cell: skip its points
-                    for (int part = 0; part < 2 && !all_done; ++part) {
-                        const uint32_t a0 = part == 0 ? q0 : max(q0, e);
-                        const uint32_t a1 = part == 0 ? min(q1, s) : q1;
-                        for (uint32_t qb = a0; qb < a1 && !all_done; qb += 32) {
-                            const uint32_t q = qb + lane;
-                            const bool vq = q < a1;
-                            const Pt<T, D> pq = vq ? v.pts[q] : zero_pt<T, D>();
-                            for (int jj = 0; jj < nA; ++jj) {
-                                const Pt<T, D> aj = shfl_pt<T, D>(pa, jj);
-                                const bool hit = vq && within_eps<D>(aj, pq, v.g);
-                                const unsigned b = __ballot_sync(0xffffffffu, hit);
-                                if (lane == jj) cnt += __popc(b);
+            for (int g0 = 0; g0 < n_all && !all_done; g0 += 32) {
+                const int k = g0 + lane;
+                const uint2 rg = k < n_all ? v.ranges[(uint64_t)A * n_all + k] : make_uint2(0u, 0u);
+                const LaneRanges lr = lane_ranges(rg.x, rg.y);
+                for (uint32_t f0 = 0; f0 < lr.total && !all_done; f0 += 32) {
+                    const uint32_t f = f0 + lane;
+                    const uint32_t B = flat_cell(lr, f < lr.total ? f : 0u);
+                    const bool okb = f < lr.total && B != A;
+                    const uint32_t bs = okb ? v.cell_start[B] : 0u;
+                    const uint32_t be = okb ? v.cell_start[B + 1] : 0u;
+                    const uint64_t bkey = okb ? v.cell_key[B] : 0ull;
+                    const int nb = (int)min(32u, lr.total - f0);
+                    for (int jb = 0; jb < nb && !all_done; ++jb) {
+                        const uint32_t B_s = __shfl_sync(0xffffffffu, bs, jb);
+                        const uint32_t B_e = __shfl_sync(0xffffffffu, be, jb);
+                        if (B_s == B_e) continue;
+                        int cb[D];
+                        unpack_key<D>(__shfl_sync(0xffffffffu, bkey, jb), v.g, cb);
+                        const bool open = have && cnt < min_pts;
+                        const int cls = open ? box_class<D>(ta, cb, v.g) : 0;
+                        if (cls == 2) cnt += B_e - B_s;
+                        const unsigned partial = __ballot_sync(0xffffffffu, cls == 1);
+                        if (partial) {
+                            for (uint32_t qb = B_s; qb < B_e; qb += 32) {
+                                const uint32_t q = qb + lane;
+                                const bool vq = q < B_e;
+                                const Pt<T, D> pq = vq ? v.pts[q] : zero_pt<T, D>();
+                                ++chunks;
+                                unsigned rem = partial;
+                                while (rem) {
+                                    const int jj = __ffs(rem) - 1;
+                                    rem &= rem - 1;
+                                    const Pt<T, D> aj = shfl_pt<T, D>(pa, jj);
+                                    const unsigned hits = __ballot_sync(0xffffffffu, vq && within_eps<D>(aj, pq, v.g));
+                                    if (lane == jj) cnt += __popc(hits);
+                                }
                             }
-                            all_done = __all_sync(0xffffffffu, !have || cnt >= min_pts);
                         }
+                        all_done = __all_sync(0xffffffffu, !have || cnt >= min_pts);
                     }
                 }
             }
@@ -485,102 +621,173 @@ __global__ void __launch_bounds__(256) k_core(LowdView<T, D> v, Stencil st_in) {
             any_core |= __any_sync(0xffffffffu, is_core);
         }
         if (any_core)
-            for (int r = lane; r < ndir; r += 32) v.reps[(int64_t)A * ndir + r] = ~0ull;
+            for (int r = lane; r < RepDirs<D>::value; r += 32) v.reps[(uint64_t)A * RepDirs<D>::value + r] = ~0ull;
         if (lane == 0) v.cell_core[A] = any_core ? 1 : 0;
     }
     if (lane == 0 && dense_cells) atomicAdd(&v.ctr->n_dense, dense_cells);
+    add_counter(&v.ctr->work[0], lane == 0 ? chunks : 0u);
+}
+
+// Squared distance, in band units, from a point at cell-local position u (u_i in [0, 1)) to
+// the ideal position of direction r (the face / edge / corner of the cube in that direction,
+// Sec. 2): the sum over the dimensions the direction constrains of (1 - u_i)^2 or u_i^2.
+template <int D>
+__device__ __forceinline__ float rep_dist(int r, const float *lo2, const float *hi2) {
+    constexpr int ndir = RepDirs<D>::value;
+    float dist = 0.f;
+    if (D <= 3) {
+        int code = r < (ndir / 2) ? r : r + 1;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const int sgn = code % 3 - 1;
+            code /= 3;
+            dist += sgn > 0 ? hi2[k] : (sgn < 0 ? lo2[k] : 0.f);
+        }
+    } else {
+        const int ax = r >> 1;
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+            if (k == ax) dist = (r & 1) ? hi2[k] : lo2[k];
+    }
+    return dist;
 }
 
 // Algorithm 2: for every cell with core points and every direction delta, the core point
-// nearest to the ideal position (the face / edge / corner of the cube in direction delta),
-// measured in cell units.  Ties go to the smaller sorted index.  Point-parallel; a warp
-// whose points share one cell reduces before its atomic.
+// nearest to the ideal position of delta; ties go to the smaller sorted index.  The points
+// are taken in windows of 256 consecutive sorted points, one warp per window, so the work is
+// even however large a cell is.  A window inside one cell keeps per-lane minima over its
+// points and reduces once; a window spanning several cells reduces each 32-point group
+// within runs of equal cell id.  Results meet in the cell's slots by 64-bit atomicMin of
+// (distance bits, index): non-negative float bits order like the floats.
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_reps(LowdView<T, D> v) {
     constexpr int ndir = RepDirs<D>::value;
+    constexpr int kWin = 256;
     const int64_t n = v.g.n;
     const int lane = lane_id();
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
-        const int64_t j = base + lane;
-        const bool valid = j < n && v.core[j];
-        const uint32_t c = valid ? v.cell_of[j] : 0xffffffffu;
-        float u[D];
-        if (valid) {
-            const Pt<T, D> p = v.pts[j];
-            int cc[D];
-            unpack_key<D>(v.cell_key[c], v.g, cc);
+    const int64_t nwin = (n + kWin - 1) / kWin;
+    for (int64_t w = global_warp(); w < nwin; w += total_warps()) {
+        const int64_t j0 = w * kWin;
+        const int64_t j1 = min(j0 + kWin, n);
+        const uint32_t cfirst = v.cell_of[j0], clast = v.cell_of[j1 - 1];
+        if (cfirst == clast) {
+            if (!v.cell_core[cfirst]) continue;
+            int ac[D];
+            unpack_key<D>(v.cell_key[cfirst], v.g, ac);
+            float best[ndir];
+            uint32_t bidx[ndir];
 #pragma unroll
-            for (int i = 0; i < D; ++i) {
-                if (sizeof(T) == 4) {
-                    float t = ((float)p.x[i] - v.g.origin_f[i]) * v.g.inv_side_f;
-                    u[i] = t - (float)cc[i];
-                } else {
-                    double t = ((double)p.x[i] - v.g.origin[i]) * v.g.inv_side;
-                    u[i] = (float)(t - (double)cc[i]);
+            for (int r = 0; r < ndir; ++r) { best[r] = FLT_MAX; bidx[r] = 0xffffffffu; }
+            for (int64_t j = j0 + lane; j < j1; j += 32) {
+                if (!v.core[j]) continue;
+                float u[D], lo2[D], hi2[D];
+                band_coords<T, D>(v.pts[j], v.g, u);
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const float x = u[k] - (float)ac[k];
+                    lo2[k] = x * x;
+                    hi2[k] = (1.f - x) * (1.f - x);
+                }
+#pragma unroll
+                for (int r = 0; r < ndir; ++r) {
+                    const float dd = rep_dist<D>(r, lo2, hi2);
+                    if (dd < best[r]) { best[r] = dd; bidx[r] = (uint32_t)j; }
                 }
             }
-        } else {
 #pragma unroll
-            for (int i = 0; i < D; ++i) u[i] = 0.f;
-        }
-        const unsigned vm = __ballot_sync(0xffffffffu, valid);
-        if (!vm) continue;
-        const uint32_t c0 = __shfl_sync(0xffffffffu, c, __ffs(vm) - 1);
-        const bool uniform = __all_sync(0xffffffffu, !valid || c == c0);
-#pragma unroll 1
-        for (int r = 0; r < ndir; ++r) {
-            float dist = 0.f;
-            if (D <= 3) {
-                int code = r < (ndir / 2) ? r : r + 1;
-#pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    int s = code % 3 - 1;
-                    code /= 3;
-                    float w = s > 0 ? 1.f - u[i] : (s < 0 ? u[i] : 0.f);
-                    dist = fmaf(w, w, dist);
-                }
-            } else {
-                const int i = r >> 1;
-                float ui = 0.f;
-#pragma unroll
-                for (int t = 0; t < D; ++t) if (t == i) ui = u[t];
-                float w = (r & 1) ? 1.f - ui : ui;
-                dist = w * w;
-            }
-            uint64_t val = valid ? (((uint64_t)__float_as_uint(dist) << 32) | (uint64_t)(uint32_t)j) : ~0ull;
-            if (uniform) {
+            for (int r = 0; r < ndir; ++r) {
+                uint64_t val = ((uint64_t)__float_as_uint(best[r]) << 32) | bidx[r];
 #pragma unroll
                 for (int o = 16; o; o >>= 1) {
-                    uint64_t other = __shfl_xor_sync(0xffffffffu, val, o);
+                    const uint64_t other = __shfl_xor_sync(0xffffffffu, val, o);
                     val = other < val ? other : val;
                 }
-                if (lane == 0) atomicMin((unsigned long long *)&v.reps[(int64_t)c0 * ndir + r], (unsigned long long)val);
-            } else if (valid) {
-                atomicMin((unsigned long long *)&v.reps[(int64_t)c * ndir + r], (unsigned long long)val);
+                if (lane == 0 && val != ~0ull)
+                    atomicMin((unsigned long long *)&v.reps[(uint64_t)cfirst * ndir + r], (unsigned long long)val);
+            }
+        } else {
+            for (int64_t g0 = j0; g0 < j1; g0 += 32) {
+                const int64_t j = g0 + lane;
+                const bool inr = j < j1;
+                const uint32_t c = inr ? v.cell_of[j] : 0xffffffffu;
+                const bool valid = inr && v.core[j];
+                if (!__any_sync(0xffffffffu, valid)) continue;
+                float lo2[D], hi2[D];
+                if (valid) {
+                    int ac[D];
+                    unpack_key<D>(v.cell_key[c], v.g, ac);
+                    float u[D];
+                    band_coords<T, D>(v.pts[j], v.g, u);
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        const float x = u[k] - (float)ac[k];
+                        lo2[k] = x * x;
+                        hi2[k] = (1.f - x) * (1.f - x);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < D; ++k) lo2[k] = hi2[k] = 0.f;
+                }
+                // runs of equal cell id: lane L combines with L + o when both lie in one run
+                bool same[5];
+#pragma unroll
+                for (int t = 0; t < 5; ++t) {
+                    const uint32_t oc = __shfl_down_sync(0xffffffffu, c, 1 << t);
+                    same[t] = (lane + (1 << t) < 32) && oc == c;
+                }
+                const uint32_t prevc = __shfl_up_sync(0xffffffffu, c, 1);
+                const bool head = inr && (lane == 0 || prevc != c);
+#pragma unroll
+                for (int r = 0; r < ndir; ++r) {
+                    uint64_t val = valid ? (((uint64_t)__float_as_uint(rep_dist<D>(r, lo2, hi2)) << 32) | (uint32_t)j)
+                                         : ~0ull;
+#pragma unroll
+                    for (int t = 0; t < 5; ++t) {
+                        const uint64_t other = __shfl_down_sync(0xffffffffu, val, 1 << t);
+                        if (same[t] && other < val) val = other;
+                    }
+                    if (head && val != ~0ull)
+                        atomicMin((unsigned long long *)&v.reps[(uint64_t)c * ndir + r], (unsigned long long)val);
+                }
             }
         }
     }
 }
 
-// Does some core point of cell A lie within eps of some core point of cell B?  Warp-wide,
-// early exit on the first pair.
+// Does some core point of cell A lie within eps of some core point of cell B?  Warp-wide
+// with early exit.  Only points that can reach the other cell's box take part; a core point
+// whose distance to the whole other box is below eps settles it at once (B holds core points).
 template <typename T, int D>
-__device__ bool warp_core_pair(const LowdView<T, D> &v, uint32_t A, uint32_t B) {
+__device__ bool warp_core_pair(const LowdView<T, D> &v, uint32_t A, uint32_t B, const int *ac,
+                               const int *bc, uint32_t &chunks) {
     const int lane = lane_id();
     const uint32_t sa = v.cell_start[A], ea = v.cell_start[A + 1];
     const uint32_t sb = v.cell_start[B], eb = v.cell_start[B + 1];
     for (uint32_t ia = sa; ia < ea; ia += 32) {
         const uint32_t i = ia + lane;
-        const bool va = i < ea && v.core[i];
-        if (!__any_sync(0xffffffffu, va)) continue;
+        bool va = i < ea && v.core[i];
         const Pt<T, D> pa = va ? v.pts[i] : zero_pt<T, D>();
+        int cls = 0;
+        if (va) {
+            float t[D];
+            band_coords<T, D>(pa, v.g, t);
+            cls = box_class<D>(t, bc, v.g);
+        }
+        if (__any_sync(0xffffffffu, cls == 2)) return true;
+        va = cls != 0;
+        if (!__any_sync(0xffffffffu, va)) continue;
         for (uint32_t jb = sb; jb < eb; jb += 32) {
             const uint32_t j = jb + lane;
-            const bool vb = j < eb && v.core[j];
+            bool vb = j < eb && v.core[j];
+            const Pt<T, D> pb = vb ? v.pts[j] : zero_pt<T, D>();
+            if (vb) {
+                float t[D];
+                band_coords<T, D>(pb, v.g, t);
+                vb = box_class<D>(t, ac, v.g) != 0;
+            }
             const unsigned bm = __ballot_sync(0xffffffffu, vb);
             if (!bm) continue;
-            const Pt<T, D> pb = vb ? v.pts[j] : zero_pt<T, D>();
+            ++chunks;
             unsigned rem = bm;
             while (rem) {
                 const int t = __ffs(rem) - 1;
@@ -594,75 +801,88 @@ __device__ bool warp_core_pair(const LowdView<T, D> &v, uint32_t A, uint32_t B) 
 }
 
 // Algorithm 3: merge every pair of neighbouring cells that hold core points and have a core
-// pair within eps.  Each unordered pair is visited once (upper half of the stencil).  The
-// complementary representative points are tested first; a hit settles the pair, a miss falls
-// back to the exhaustive core x core test.  Pairs already in one set are skipped.
+// pair within eps.  Each unordered pair is visited once (upper half of the stencil).  Pass 0
+// takes the cells at Chebyshev offset 1, pass 1 the rest, so that most far pairs are already
+// joined through near ones when they are reached and are skipped.  The complementary
+// representative points are tested first (Algorithm 3); a miss falls back to the exhaustive
+// core x core test.  Lanes walk the flattened list of candidate cells of one cell.
 template <typename T, int D>
-__global__ void __launch_bounds__(256) k_merge(LowdView<T, D> v, Stencil st_in) {
-    __shared__ Stencil st;
-    for (int i = threadIdx.x; i < (int)(sizeof(Stencil) / 4); i += blockDim.x)
-        reinterpret_cast<uint32_t *>(&st)[i] = reinterpret_cast<const uint32_t *>(&st_in)[i];
-    __syncthreads();
+__global__ void __launch_bounds__(256) k_merge(LowdView<T, D> v, int n_all, int n_half, int pass) {
     constexpr int ndir = RepDirs<D>::value;
     const uint32_t C = v.ctr->n_cells;
     const int lane = lane_id();
+    uint32_t rep_tests = 0, rep_hits = 0, exhaustive = 0, chunks = 0;
     for (uint32_t A = global_warp(); A < C; A += total_warps()) {
         if (!v.cell_core[A]) continue;
         int ac[D];
         unpack_key<D>(v.cell_key[A], v.g, ac);
-        for (int k0 = 0; k0 < st.n_half; k0 += 32) {
-            const int k = k0 + lane;
-            uint32_t lo = 0, hi = 0;
-            const bool ok = k < st.n_half && pencil_range<T, D>(v, st, k, ac, true, lo, hi);
-            unsigned rm = __ballot_sync(0xffffffffu, ok);
-            while (rm) {
-                const int L = __ffs(rm) - 1;
-                rm &= rm - 1;
-                const uint32_t c0 = __shfl_sync(0xffffffffu, lo, L);
-                const uint32_t c1 = __shfl_sync(0xffffffffu, hi, L);
-                for (uint32_t cb = c0; cb < c1; cb += 32) {
-                    const uint32_t B = cb + lane;
-                    bool pending = B < c1 && v.cell_core[B];
-                    if (pending && uf_find(v.parent, A, v.ctr) == uf_find(v.parent, B, v.ctr)) pending = false;
-                    if (pending) {
-                        int bc[D], delta[D];
-                        unpack_key<D>(v.cell_key[B], v.g, bc);
+        for (int g0 = 0; g0 < n_half; g0 += 32) {
+            const int k = g0 + lane;
+            uint2 rg = k < n_half ? v.ranges[(uint64_t)A * n_all + k] : make_uint2(0u, 0u);
+            if (k == 0 && rg.x < A + 1) rg.x = min(A + 1, rg.y);  // own pencil: cells after A
+            const LaneRanges lr = lane_ranges(rg.x, rg.y);
+            for (uint32_t f0 = 0; f0 < lr.total; f0 += 32) {
+                const uint32_t f = f0 + lane;
+                const uint32_t B = flat_cell(lr, f < lr.total ? f : 0u);
+                bool pending = f < lr.total && v.cell_core[B];
+                int bc[D], delta[D];
+                if (pending) {
+                    unpack_key<D>(v.cell_key[B], v.g, bc);
+                    int cheb = 0;
 #pragma unroll
-                        for (int i = 0; i < D; ++i) delta[i] = bc[i] - ac[i];
-                        const int ra = rep_dir_of<D>(delta);
-                        const int rb = rep_dir_complement<D>(ra);
-                        const uint32_t pa = (uint32_t)v.reps[(int64_t)A * ndir + ra];
-                        const uint32_t pb = (uint32_t)v.reps[(int64_t)B * ndir + rb];
-                        if (within_eps<D>(v.pts[pa], v.pts[pb], v.g)) {
-                            uf_union(v.parent, A, B, v.ctr);
-                            pending = false;
-                        }
+                    for (int i = 0; i < D; ++i) {
+                        delta[i] = bc[i] - ac[i];
+                        cheb = max(cheb, abs(delta[i]));
                     }
-                    unsigned need = __ballot_sync(0xffffffffu, pending);
-                    while (need) {
-                        const int t = __ffs(need) - 1;
-                        need &= need - 1;
-                        const uint32_t B2 = __shfl_sync(0xffffffffu, B, t);
-                        bool same = false;
-                        if (lane == 0) same = uf_find(v.parent, A, v.ctr) == uf_find(v.parent, B2, v.ctr);
-                        same = __shfl_sync(0xffffffffu, same, 0);
-                        if (same) continue;
-                        if (warp_core_pair<T, D>(v, A, B2) && lane == 0) uf_union(v.parent, A, B2, v.ctr);
+                    pending = (pass == 0) == (cheb <= 1);
+                }
+                if (pending && uf_find(v.parent, A, v.ctr) == uf_find(v.parent, B, v.ctr)) pending = false;
+                if (pending) {
+                    const int ra = rep_dir_of<D>(delta);
+                    const int rb = rep_dir_complement<D>(ra);
+                    const uint32_t pa = (uint32_t)v.reps[(uint64_t)A * ndir + ra];
+                    const uint32_t pb = (uint32_t)v.reps[(uint64_t)B * ndir + rb];
+                    ++rep_tests;
+                    if (within_eps<D>(v.pts[pa], v.pts[pb], v.g)) {
+                        uf_union(v.parent, A, B, v.ctr);
+                        pending = false;
+                        ++rep_hits;
                     }
+                }
+                unsigned need = __ballot_sync(0xffffffffu, pending);
+                while (need) {
+                    const int t = __ffs(need) - 1;
+                    need &= need - 1;
+                    const uint32_t B2 = __shfl_sync(0xffffffffu, B, t);
+                    int bc2[D];
+#pragma unroll
+                    for (int i = 0; i < D; ++i) bc2[i] = __shfl_sync(0xffffffffu, bc[i], t);
+                    bool same = false;
+                    if (lane == 0) same = uf_find(v.parent, A, v.ctr) == uf_find(v.parent, B2, v.ctr);
+                    same = __shfl_sync(0xffffffffu, same, 0);
+                    if (same) continue;
+                    ++exhaustive;
+                    if (warp_core_pair<T, D>(v, A, B2, ac, bc2, chunks) && lane == 0)
+                        uf_union(v.parent, A, B2, v.ctr);
                 }
             }
         }
     }
+    add_counter(&v.ctr->work[1], rep_tests);
+    add_counter(&v.ctr->work[2], rep_hits);
+    add_counter(&v.ctr->work[3], lane == 0 ? exhaustive : 0u);
+    add_counter(&v.ctr->work[4], lane == 0 ? chunks : 0u);
 }
 
 // Flatten the union-find: parent[c] = root for every cell with core points; count roots.
+// The only writes are parent[c] = root, so every pointer ends at its root.
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_compress(LowdView<T, D> v) {
     const uint32_t C = v.ctr->n_cells;
     uint32_t roots = 0;
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
         if (!v.cell_core[c]) continue;
-        const uint32_t r = uf_find(v.parent, c, v.ctr);
+        const uint32_t r = uf_root_readonly(v.parent, c, v.ctr);
         v.parent[c] = r;
         roots += (r == c);
     }
@@ -700,71 +920,72 @@ __global__ void __launch_bounds__(256) k_comp_min(LowdView<T, D> v) {
 // Algorithm 4 and Definition 5 with the canonical rule: core points take their cluster id;
 // a non-core point takes the smallest id among the clusters of the core points within eps
 // (the core points of its own cell qualify without a test, the cell's diagonal being at most
-// eps), else -1.  One warp per cell; writes labels in input order.
+// eps), else -1.  One warp per cell; neighbour cells are walked 32 at a time and a cell whose
+// box lies wholly within eps settles a point without per-point tests.  Writes labels in
+// input order.
 template <typename T, int D>
-__global__ void __launch_bounds__(256) k_labels(LowdView<T, D> v, Stencil st_in) {
-    __shared__ Stencil st;
-    for (int i = threadIdx.x; i < (int)(sizeof(Stencil) / 4); i += blockDim.x)
-        reinterpret_cast<uint32_t *>(&st)[i] = reinterpret_cast<const uint32_t *>(&st_in)[i];
-    __syncthreads();
+__global__ void __launch_bounds__(256) k_labels(LowdView<T, D> v, int n_all) {
     const uint32_t C = v.ctr->n_cells;
     const int lane = lane_id();
-    uint32_t noise = 0;
+    uint32_t noise = 0, chunks = 0;
     for (uint32_t A = global_warp(); A < C; A += total_warps()) {
         const uint32_t s = v.cell_start[A], e = v.cell_start[A + 1];
         const bool hasc = v.cell_core[A];
         const uint32_t clA = hasc ? v.comp_min[v.parent[A]] : kNoLabel;
-        int ac[D];
-        unpack_key<D>(v.cell_key[A], v.g, ac);
         for (uint32_t base = s; base < e; base += 32) {
             const uint32_t i = base + lane;
             const bool have = i < e;
             const bool isc = have && v.core[i];
             uint32_t best = clA;
-            bool search = have && !isc;
-            const int nA = (int)min(32u, e - base);
+            const bool search = have && !isc;
             if (__any_sync(0xffffffffu, search)) {
                 const Pt<T, D> pa = have ? v.pts[i] : zero_pt<T, D>();
-                for (int k0 = 0; k0 < st.n_all; k0 += 32) {
-                    const int k = k0 + lane;
-                    uint32_t lo = 0, hi = 0;
-                    const bool ok = k < st.n_all && pencil_range<T, D>(v, st, k, ac, false, lo, hi);
-                    unsigned rm = __ballot_sync(0xffffffffu, ok);
-                    while (rm) {
-                        const int L = __ffs(rm) - 1;
-                        rm &= rm - 1;
-                        const uint32_t c0 = __shfl_sync(0xffffffffu, lo, L);
-                        const uint32_t c1 = __shfl_sync(0xffffffffu, hi, L);
-                        for (uint32_t cb = c0; cb < c1; cb += 32) {
-                            // current worst best among searching lanes
-                            uint32_t worst = search ? best : 0u;
-                            for (int o = 16; o; o >>= 1) worst = max(worst, __shfl_xor_sync(0xffffffffu, worst, o));
-                            const uint32_t B = cb + lane;
-                            const bool vb = B < c1 && B != A && v.cell_core[B];
-                            const uint32_t clB = vb ? v.comp_min[v.parent[B]] : kNoLabel;
-                            unsigned cm = __ballot_sync(0xffffffffu, vb && clB < worst);
-                            while (cm) {
-                                const int t = __ffs(cm) - 1;
-                                cm &= cm - 1;
-                                const uint32_t B2 = __shfl_sync(0xffffffffu, B, t);
-                                const uint32_t cl2 = __shfl_sync(0xffffffffu, clB, t);
-                                bool want = search && best > cl2;
-                                if (!__any_sync(0xffffffffu, want)) continue;
-                                const uint32_t sb = v.cell_start[B2], eb = v.cell_start[B2 + 1];
-                                for (uint32_t qb = sb; qb < eb; qb += 32) {
-                                    const uint32_t q = qb + lane;
-                                    const bool vq = q < eb && v.core[q];
-                                    const Pt<T, D> pq = vq ? v.pts[q] : zero_pt<T, D>();
-                                    for (int jj = 0; jj < nA; ++jj) {
-                                        if (!__shfl_sync(0xffffffffu, want, jj)) continue;
-                                        const Pt<T, D> aj = shfl_pt<T, D>(pa, jj);
-                                        const bool hit = vq && within_eps<D>(aj, pq, v.g);
-                                        if (__any_sync(0xffffffffu, hit) && lane == jj) {
-                                            best = cl2;
-                                            want = false;
-                                        }
+                float ta[D];
+                band_coords<T, D>(pa, v.g, ta);
+                for (int g0 = 0; g0 < n_all; g0 += 32) {
+                    const int k = g0 + lane;
+                    const uint2 rg = k < n_all ? v.ranges[(uint64_t)A * n_all + k] : make_uint2(0u, 0u);
+                    const LaneRanges lr = lane_ranges(rg.x, rg.y);
+                    for (uint32_t f0 = 0; f0 < lr.total; f0 += 32) {
+                        uint32_t worst = search ? best : 0u;
+                        for (int o = 16; o; o >>= 1) worst = max(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+                        const uint32_t f = f0 + lane;
+                        const uint32_t B = flat_cell(lr, f < lr.total ? f : 0u);
+                        const bool vb = f < lr.total && B != A && v.cell_core[B];
+                        const uint32_t clB = vb ? v.comp_min[v.parent[B]] : kNoLabel;
+                        unsigned cm = __ballot_sync(0xffffffffu, vb && clB < worst);
+                        const uint64_t bkey = cm ? v.cell_key[B] : 0ull;
+                        while (cm) {
+                            const int t = __ffs(cm) - 1;
+                            cm &= cm - 1;
+                            const uint32_t B2 = __shfl_sync(0xffffffffu, B, t);
+                            const uint32_t cl2 = __shfl_sync(0xffffffffu, clB, t);
+                            int cb[D];
+                            unpack_key<D>(__shfl_sync(0xffffffffu, bkey, t), v.g, cb);
+                            bool want = search && best > cl2;
+                            if (want) {
+                                const int cls = box_class<D>(ta, cb, v.g);
+                                if (cls == 2) best = cl2;
+                                want = cls == 1;
+                            }
+                            const unsigned wm = __ballot_sync(0xffffffffu, want);
+                            if (!wm) continue;
+                            const uint32_t sb = v.cell_start[B2], eb = v.cell_start[B2 + 1];
+                            unsigned open = wm;
+                            for (uint32_t qb = sb; qb < eb && open; qb += 32) {
+                                const uint32_t q = qb + lane;
+                                const bool vq = q < eb && v.core[q];
+                                const Pt<T, D> pq = vq ? v.pts[q] : zero_pt<T, D>();
+                                ++chunks;
+                                unsigned rem = open;
+                                while (rem) {
+                                    const int jj = __ffs(rem) - 1;
+                                    rem &= rem - 1;
+                                    const Pt<T, D> aj = shfl_pt<T, D>(pa, jj);
+                                    if (__any_sync(0xffffffffu, vq && within_eps<D>(aj, pq, v.g))) {
+                                        if (lane == jj) best = cl2;
+                                        open &= ~(1u << jj);
                                     }
-                                    if (!__any_sync(0xffffffffu, want)) break;
                                 }
                             }
                         }
@@ -782,6 +1003,7 @@ __global__ void __launch_bounds__(256) k_labels(LowdView<T, D> v, Stencil st_in)
     }
     for (int o = 16; o; o >>= 1) noise += __shfl_xor_sync(0xffffffffu, noise, o);
     if (lane == 0 && noise) atomicAdd(&v.ctr->n_noise, noise);
+    add_counter(&v.ctr->work[5], lane == 0 ? chunks : 0u);
 }
 
 }  // namespace hca

@@ -79,6 +79,13 @@ inline int make_grid(int D, bool input_f32, double eps, int min_pts, int64_t n,
     g.inv_side = inv;
     if (!bin32) g.inv_side_f = (float)inv;
     g.bin_fp64 = bin32 ? 0 : 1;
+    // cell-box tests in FP32 band units (see box_class)
+    const double tmax = range_max * inv + 2.0;
+    g.box_ok = tmax < ldexp(1.0, 22) ? 1 : 0;
+    g.tau_box = (float)(2.0 * tau + tmax * ldexp(1.0, -22));
+    const double eps2_band = eps * eps * inv * inv;
+    g.box_full = (float)(eps2_band * (1.0 - ldexp(1.0, -12)));
+    g.box_none = (float)(eps2_band * (1.0 + ldexp(1.0, -12)));
     int total = 0;
     for (int i = 0; i < D; ++i) {
         g.origin[i] = mn[i];
@@ -231,7 +238,7 @@ int run_lowd(const RunArgs &a) {
     const size_t o_core = take(n), o_ccore = take(n);
     const size_t o_parent = take(4 * n), o_cmin = take(4 * n);
     const size_t o_reps = take(8 * (size_t)n * ndir);
-    void *ws = nullptr;
+    void *ws = nullptr, *ws_ranges = nullptr;
     if (pool_alloc(&ws, off, s) != cudaSuccess || !ws) return HCA_ENOMEM;
     char *b = (char *)ws;
     DevCounters *ctr = (DevCounters *)(b + o_ctr);
@@ -274,6 +281,11 @@ int run_lowd(const RunArgs &a) {
         if (rc) goto out;
         rc = make_stencil(D, a.eps, 1.0 / g.inv_side, tau, st);
         if (rc) goto out;
+        // neighbour ranges: one (lo, hi) pair per cell and stencil pencil
+        if (pool_alloc(&ws_ranges, sizeof(uint2) * (size_t)n * st.n_all, s) != cudaSuccess || !ws_ranges) {
+            rc = HCA_ENOMEM;
+            goto out;
+        }
     }
     mark(1);
     // ---- Algorithm 1: cell keys; pre-sort (Sec. 2) by a radix sort of (key, index) ----
@@ -332,7 +344,6 @@ int run_lowd(const RunArgs &a) {
                                        (uint32_t *)(b + o_hv), ctr);
         launches += 3;
     }
-    mark(5);
     v.g = g;
     v.in = (const T *)a.d_points;
     v.pts = (const Pt<T, D> *)(b + o_pts);
@@ -347,25 +358,31 @@ int run_lowd(const RunArgs &a) {
     v.parent = (uint32_t *)(b + o_parent);
     v.reps = (uint64_t *)(b + o_reps);
     v.comp_min = (uint32_t *)(b + o_cmin);
+    v.ranges = (uint2 *)ws_ranges;
     v.labels = a.d_labels;
     v.core_out = a.d_core;
     v.ctr = ctr;
+    // ---- neighbour cells of every cell (stencil pencils -> cell ranges) ----
+    k_ranges<T, D><<<grid_for(n * (int64_t)st.n_all, 256, sms, 16), 256, 0, s>>>(v, st);
+    ++launches;
+    mark(5);
     // ---- Definition 2: dense cells and exact counts ----
-    k_core<T, D><<<gwarp, 256, 0, s>>>(v, st);
+    k_core<T, D><<<gwarp, 256, 0, s>>>(v, st.n_all);
     ++launches;
     mark(6);
     // ---- Algorithm 2: representative points ----
-    k_reps<T, D><<<gpts, 256, 0, s>>>(v);
+    k_reps<T, D><<<grid_for((n + 255) / 256, 8, sms, 16), 256, 0, s>>>(v);
     ++launches;
     mark(7);
-    // ---- Algorithm 3: merge neighbouring cells ----
-    k_merge<T, D><<<gwarp, 256, 0, s>>>(v, st);
+    // ---- Algorithm 3: merge neighbouring cells (near offsets, then far ones) ----
+    k_merge<T, D><<<gwarp, 256, 0, s>>>(v, st.n_all, st.n_half, 0);
+    k_merge<T, D><<<gwarp, 256, 0, s>>>(v, st.n_all, st.n_half, 1);
     k_compress<T, D><<<gpts, 256, 0, s>>>(v);
-    launches += 2;
+    launches += 3;
     mark(8);
     // ---- Algorithm 4: cluster ids, border and noise ----
     k_comp_min<T, D><<<gpts, 256, 0, s>>>(v);
-    k_labels<T, D><<<gwarp, 256, 0, s>>>(v, st);
+    k_labels<T, D><<<gwarp, 256, 0, s>>>(v, st.n_all);
     launches += 2;
     mark(9);
     if (cudaGetLastError() != cudaSuccess) { rc = HCA_ECUDA; goto out; }
@@ -384,6 +401,12 @@ int run_lowd(const RunArgs &a) {
         st_out->key_bits = g.key_bits;
         st_out->sort_passes = (g.key_bits + 7) / 8;
         st_out->kernel_launches = launches;
+        st_out->n_count_chunks = (int64_t)h->work[0];
+        st_out->n_rep_tests = (int64_t)h->work[1];
+        st_out->n_rep_hits = (int64_t)h->work[2];
+        st_out->n_exhaustive_pairs = (int64_t)h->work[3];
+        st_out->n_exhaustive_chunks = (int64_t)h->work[4];
+        st_out->n_border_chunks = (int64_t)h->work[5];
         for (int i = 0; i < HCA_NUM_STAGES; ++i) {
             float ms = 0.f;
             if (timing) cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
@@ -394,6 +417,7 @@ out:
     if (timing)
         for (int i = 0; i <= HCA_NUM_STAGES; ++i)
             if (ev[i]) cudaEventDestroy(ev[i]);
+    pool_free(ws_ranges, s);
     pool_free(ws, s);
     if (rc != HCA_OK) cudaStreamSynchronize(s);
     return rc;

@@ -30,13 +30,12 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const K *__restrict_
     const int64_t base = (int64_t)blockIdx.x * kSortTile;
 #pragma unroll 4
     for (int k = 0; k < kSortItems; ++k) {
-        int64_t i = base + (int64_t)k * kSortThreads + threadIdx.x;
-        if (i < n) {
-            uint32_t dg = (uint32_t)(keys[i] >> shift) & mask;
-            // aggregate equal digits of the warp into one shared-memory atomic
-            unsigned peers = __match_any_sync(__activemask(), dg);
-            if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[dg], __popc(peers));
-        }
+        const int64_t i = base + (int64_t)k * kSortThreads + threadIdx.x;
+        const bool valid = i < n;
+        const uint32_t dg = valid ? ((uint32_t)(keys[i] >> shift) & mask) : (uint32_t)kRadix;
+        // aggregate equal digits of the warp into one shared-memory atomic
+        const unsigned peers = __match_any_sync(0xffffffffu, dg);
+        if (valid && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[dg], __popc(peers));
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kRadix; i += kSortThreads) hist[(int64_t)i * nb + blockIdx.x] = h[i];

@@ -107,6 +107,22 @@ def test_mixed3d_full(env):
     assert st["n_clusters"] == len(np.unique(want[0][want[1] == 1]))
 
 
+def test_mixed3d_full_repeated(env):
+    """Twenty full-size runs in a row, each compared with the oracle: the union-find and the
+    atomics race differently on every run, the labels must not."""
+    torch, pkg, oracle = env
+    X, eps, min_pts = workloads.mixed3d()
+    want, want_core = oracle.grid(X.astype(np.float64), eps, min_pts)
+    t = torch.from_numpy(X).cuda()
+    lab = torch.empty(len(X), dtype=torch.int32, device="cuda")
+    core = torch.empty(len(X), dtype=torch.uint8, device="cuda")
+    for run in range(20):
+        pkg.hca_dbscan_device(t, eps, min_pts, labels=lab, core=core)
+        got = lab.cpu().numpy()
+        assert np.array_equal(got, want), f"run {run}: {int((got != want).sum())} labels differ"
+        assert np.array_equal(core.cpu().numpy(), want_core), f"run {run}: core flags differ"
+
+
 def test_fp64_only_matches_filtered(env):
     X, eps, min_pts = workloads.mixed3d(n=100_000)
     a = run_device(env, X, eps, min_pts)
