@@ -65,20 +65,22 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mixed3d", choices=["mixed3d", "blobs2d"])
+    ap.add_argument("--workload", default="mixed3d", choices=["mixed3d", "blobs2d", "aniso16d"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
 
 def workload(name, rank):
     from paper_1912_00323_gb300 import workloads
-    seed = workloads.SEED_BASE + (1 if name == "mixed3d" else 0) + 1000 * rank
+    seed = workloads.SEED_BASE + {"blobs2d": 0, "mixed3d": 1, "aniso16d": 2}[name] + 1000 * rank
     X, eps, min_pts = workloads.WORKLOADS[name](seed=seed)
     desc = {
         "mixed3d": "d=3, n=2,000,000 float32 on the 2^-16 lattice: 40 Gaussian blobs (sigma 0.5-3) "
                    "+ 8 noisy arcs/rings + 5% uniform noise in [0,1000]^3; eps=2.0, minPts=10",
         "blobs2d": "d=2, n=10,000 float64 on the 2^-12 lattice: 5 Gaussian blobs (sigma 2) + 10% "
                    "uniform noise in [0,100]^2; eps=1.5, minPts=5",
+        "aniso16d": "d=16, n=1,000,000 float32 on the 2^-12 lattice: 100 anisotropic Gaussian clusters "
+                    "in [0,100]^16 + 10% uniform noise; eps=4.0, minPts=20",
     }[name]
     return X, eps, min_pts, desc
 

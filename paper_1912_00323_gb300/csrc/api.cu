@@ -82,6 +82,10 @@ static int dispatch(const RunArgs &a, int32_t dtype) {
             case 3: return run_lowd<float, 3>(a);
             case 4: return run_lowd<float, 4>(a);
         }
+        if (a.d <= 8) return run_hd<float, 8>(a);
+        if (a.d <= 16) return run_hd<float, 16>(a);
+        if (a.d <= 32) return run_hd<float, 32>(a);
+        if (a.d <= 64) return run_hd<float, 64>(a);
     } else {
         switch (a.d) {
             case 1: return run_lowd<double, 1>(a);
@@ -89,8 +93,12 @@ static int dispatch(const RunArgs &a, int32_t dtype) {
             case 3: return run_lowd<double, 3>(a);
             case 4: return run_lowd<double, 4>(a);
         }
+        if (a.d <= 8) return run_hd<double, 8>(a);
+        if (a.d <= 16) return run_hd<double, 16>(a);
+        if (a.d <= 32) return run_hd<double, 32>(a);
+        if (a.d <= 64) return run_hd<double, 64>(a);
     }
-    return HCA_ENOTIMPL;
+    return HCA_EINVAL;
 }
 
 }  // namespace hca
@@ -133,7 +141,6 @@ extern "C" int hca_dbscan(const void *points, int32_t dtype, int64_t n, int32_t 
     int rc = check_common(points, dtype, n, d, eps, min_pts, labels);
     if (rc) return rc;
     if (n == 0) return HCA_OK;
-    if (d > kMaxD) return HCA_ENOTIMPL;
     cudaStream_t s;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return HCA_ECUDA;
     const size_t in_bytes = (size_t)n * d * (dtype == HCA_F32 ? 4 : 8);

@@ -32,7 +32,8 @@ struct DevCounters {
     uint32_t n_noise;
     uint32_t minmax_enc[2 * kMaxD * 2];  // order-preserving encodings of min / max per dim
     uint32_t nan_seen;
-    uint32_t pad[3];
+    uint32_t n_chunks;     // 32-point chunks of the coarse cells (high-dimensional path)
+    uint32_t pad[2];
     unsigned long long work[8];  // work counters (see hca_stats)
 };
 
@@ -125,6 +126,8 @@ struct RunArgs {
 };
 template <typename T, int D>
 int run_lowd(const RunArgs &a);
+template <typename T, int DP>
+int run_hd(const RunArgs &a);
 
 }  // namespace hca
 

@@ -1,0 +1,494 @@
+// Kernels of the high-dimensional path (5 <= d <= 64), templated on the coordinate type T and
+// the padded row width DP (8, 16, 32 or 64 >= d; the padding coordinates are zero and add
+// exact zeros to every distance).
+//
+// In d dimensions the hypercubes of side eps/sqrt(d) (Sec. 2, Algorithm 1) hold about one point
+// each on spread data and their neighbour block (2 ceil(sqrt d) + 1)^d (Sec. 2, "Depth First
+// Search") is astronomically large, so the neighbour search uses a coarse grid instead: cells
+// of side >= eps over the three dimensions of largest extent.  Two points within eps differ by
+// at most eps in every coordinate, so they lie in the same or adjacent coarse cells (the 3x3x3
+// block).  The coarse cells are binned, sorted, run-length encoded, hashed and given neighbour
+// ranges by the same kernels as the hypercube path (D = 3 on the projected coordinates).  The
+// clustering itself then works on points: exact counts with early exit at MINPTS
+// (Definition 2), union-find over core points (Definitions 3-5) and the canonical labels.
+//
+// Layout: pts[j * DP + i] (cell order, zero padded), perm[j], cell_start/cell_key/ranges of
+// the coarse cells, core[j], parent[j] and comp_min[j] over points.
+#pragma once
+
+#include "lowd_kernels.cuh"
+
+namespace hca {
+
+template <typename T, int DP>
+struct HdView {
+    GridParams g;                 // coarse grid on the projected dimensions; eps2, lo32, hi32, min_pts, n
+    int d;
+    const T *pts;                 // sorted, n x DP
+    const uint32_t *perm;
+    const uint32_t *cell_start;
+    const uint32_t *chunk_off;    // first 32-point chunk of each coarse cell
+    const uint64_t *cell_key;
+    const uint2 *ranges;
+    uint8_t *core;
+    uint8_t *cell_core;
+    uint32_t *parent;
+    uint32_t *comp_min;
+    int32_t *labels;
+    uint8_t *core_out;
+    DevCounters *ctr;
+    int n_all, n_half;
+};
+
+constexpr int kHdWarps = 4;   // warps per block in the point kernels of this path
+
+// dist(a, q) <= eps with a in shared memory and q in registers (same exact predicate and FP32
+// guard band as the hypercube path; summation in dimension order).
+template <int DP>
+__device__ __forceinline__ bool hd_within(const float *a, const float (&q)[DP], const GridParams &g) {
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < DP; i += 4) {
+        const float4 av = *reinterpret_cast<const float4 *>(a + i);
+        float t = __fsub_rn(av.x, q[i]);     s = __fmaf_rn(t, t, s);
+        t = __fsub_rn(av.y, q[i + 1]);       s = __fmaf_rn(t, t, s);
+        t = __fsub_rn(av.z, q[i + 2]);       s = __fmaf_rn(t, t, s);
+        t = __fsub_rn(av.w, q[i + 3]);       s = __fmaf_rn(t, t, s);
+    }
+    if (s < g.lo32) return true;
+    if (s > g.hi32) return false;
+    double e = 0.0;
+#pragma unroll
+    for (int i = 0; i < DP; ++i) {
+        const double t = __dsub_rn((double)a[i], (double)q[i]);
+        e = __dadd_rn(e, __dmul_rn(t, t));
+    }
+    return e <= g.eps2;
+}
+template <int DP>
+__device__ __forceinline__ bool hd_within(const double *a, const double (&q)[DP], const GridParams &g) {
+    double e = 0.0;
+#pragma unroll
+    for (int i = 0; i < DP; ++i) {
+        const double t = __dsub_rn(a[i], q[i]);
+        e = __dadd_rn(e, __dmul_rn(t, t));
+    }
+    return e <= g.eps2;
+}
+
+template <typename T, int DP>
+__device__ __forceinline__ void hd_load(const T *pts, uint32_t j, bool valid, T (&q)[DP]) {
+    if (sizeof(T) == 4) {
+        const float4 *src = reinterpret_cast<const float4 *>(pts + (uint64_t)j * DP);
+#pragma unroll
+        for (int i = 0; i < DP / 4; ++i) {
+            const float4 v4 = valid ? src[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            q[4 * i] = v4.x; q[4 * i + 1] = v4.y; q[4 * i + 2] = v4.z; q[4 * i + 3] = v4.w;
+        }
+    } else {
+        const double2 *src = reinterpret_cast<const double2 *>(pts + (uint64_t)j * DP);
+#pragma unroll
+        for (int i = 0; i < DP / 2; ++i) {
+            const double2 v2 = valid ? src[i] : make_double2(0.0, 0.0);
+            q[2 * i] = v2.x; q[2 * i + 1] = v2.y;
+        }
+    }
+}
+
+// Per-dimension min / max of row-major n x d input (origin shift, Sec. 2).  Each thread keeps
+// one dimension (the stride is a multiple of d).
+template <typename T>
+__global__ void __launch_bounds__(256) k_minmax_rt(const T *__restrict__ in, int64_t n, int d, DevCounters *ctr,
+                                                  unsigned long long *mm /* [2 * 64] */) {
+    const int64_t total = n * d;
+    const int64_t threads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t stride = (threads / d) * d;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (tid >= stride) return;
+    T mn = sizeof(T) == 4 ? (T)FLT_MAX : (T)DBL_MAX, mx = -mn;
+    bool nan = false;
+    for (int64_t e = tid; e < total; e += stride) {
+        const T x = in[e];
+        nan |= (x != x);
+        mn = x < mn ? x : mn;
+        mx = x > mx ? x : mx;
+    }
+    const int dim = (int)(tid % d);
+    atomicMin(&mm[dim], (unsigned long long)enc_double((double)mn));
+    atomicMax(&mm[64 + dim], (unsigned long long)enc_double((double)mx));
+    if (nan) atomicOr(&ctr->nan_seen, 1u);
+}
+
+// Coarse cell keys from the three projected dimensions (Algorithm 1 on a grid of side >= eps).
+template <typename T, typename K>
+__global__ void __launch_bounds__(256) k_bin_proj(const T *__restrict__ in, int d, int3 sel, GridParams g,
+                                                 K *__restrict__ keys, uint32_t *__restrict__ idx) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < g.n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int dims[3] = {sel.x, sel.y, sel.z};
+        uint64_t key = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const double t = __dmul_rn(__dsub_rn((double)in[j * d + dims[i]], g.origin[i]), g.inv_side);
+            uint32_t c = (uint32_t)floor(t);
+            if (c > g.ncell[i] - 1) c = g.ncell[i] - 1;
+            key |= (uint64_t)c << g.shift[i];
+        }
+        keys[j] = (K)key;
+        idx[j] = (uint32_t)j;
+    }
+}
+
+// Gather full rows into cell order (zero padded to DP) and flag the first point of each cell.
+template <typename T, int DP, typename K>
+__global__ void __launch_bounds__(256) k_gather_hd(const T *__restrict__ in, int d, const K *__restrict__ keys,
+                                                  const uint32_t *__restrict__ idx, int64_t n,
+                                                  T *__restrict__ pts, uint32_t *__restrict__ flags) {
+    // one warp per point row: lanes copy coordinates
+    const int lane = threadIdx.x & 31;
+    for (int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; j < n;
+         j += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const uint32_t o = idx[j];
+        for (int i = lane; i < DP; i += 32) pts[j * DP + i] = i < d ? in[(int64_t)o * d + i] : T(0);
+        if (lane == 0) flags[j] = (j == 0 || keys[j] != keys[j - 1]) ? 1u : 0u;
+    }
+}
+
+template <typename T, int DP>
+__device__ __forceinline__ void stage_rows(T *rows, const T *pts, uint32_t base, uint32_t e) {
+    // rows: 32 x DP for this warp; lane L copies row L
+    const int lane = threadIdx.x & 31;
+    const uint32_t i = base + lane;
+    T q[DP];
+    hd_load<T, DP>(pts, i, i < e, q);
+    if (sizeof(T) == 4) {
+        float4 *dst = reinterpret_cast<float4 *>(rows + lane * DP);
+#pragma unroll
+        for (int k = 0; k < DP / 4; ++k)
+            dst[k] = make_float4((float)q[4 * k], (float)q[4 * k + 1], (float)q[4 * k + 2], (float)q[4 * k + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < DP; ++k) rows[lane * DP + k] = q[k];
+    }
+    __syncwarp();
+}
+
+// Work is scheduled in chunks of 32 consecutive points of one coarse cell (a coarse cell can
+// hold a whole cluster, so one warp per cell would leave the largest cell to a single warp).
+// chunk_off[c] = first chunk of cell c (exclusive scan of ceil(size / 32)).
+static __global__ void __launch_bounds__(256) k_chunk_counts(const uint32_t *__restrict__ cell_start,
+                                                     const DevCounters *ctr, uint32_t *__restrict__ nch) {
+    const uint32_t C = ctr->n_cells;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x)
+        nch[c] = (cell_start[c + 1] - cell_start[c] + 31u) / 32u;
+}
+
+// Cell of chunk t (upper bound in chunk_off, minus one).  Warp-uniform.
+__device__ __forceinline__ uint32_t chunk_cell(const uint32_t *chunk_off, uint32_t C, uint32_t t) {
+    uint32_t lo = 0, hi = C;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(chunk_off + mid) <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+#define HD_FOR_EACH_CHUNK(v, A, base, e)                                                     \
+    const uint32_t C_ = (v).ctr->n_cells, NC_ = (v).ctr->n_chunks;                           \
+    for (uint32_t t_ = global_warp(); t_ < NC_; t_ += total_warps())                         \
+        for (uint32_t A = chunk_cell((v).chunk_off, C_, t_), once_ = 1; once_; once_ = 0)    \
+            for (uint32_t e = (v).cell_start[A + 1],                                         \
+                          base = (v).cell_start[A] + 32u * (t_ - (v).chunk_off[A]), o2_ = 1; \
+                 o2_; o2_ = 0)
+
+// Definition 2: |N_eps(p)| >= MINPTS, counted over the 27 neighbouring coarse cells (the own
+// point included), stopping once every point of the chunk has reached MINPTS.  The chunk's
+// points are staged in shared memory, candidates stream through the lanes, and each open
+// point is compared with a warp ballot.
+template <typename T, int DP>
+__global__ void __launch_bounds__(32 * kHdWarps) k_count_hd(HdView<T, DP> v) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *rows = reinterpret_cast<T *>(smem_raw) + (threadIdx.x >> 5) * 32 * DP;
+    const uint32_t min_pts = v.g.min_pts;
+    const int lane = lane_id();
+    uint32_t chunks = 0;
+    HD_FOR_EACH_CHUNK(v, A, base, e) {
+        stage_rows<T, DP>(rows, v.pts, base, e);
+        const bool have = base + lane < e;
+        uint32_t cnt = 0;
+        unsigned open = __ballot_sync(0xffffffffu, have);
+        for (int g0 = 0; g0 < v.n_all && open; g0 += 32) {
+            const int k = g0 + lane;
+            const uint2 rg = k < v.n_all ? v.ranges[(uint64_t)A * v.n_all + k] : make_uint2(0u, 0u);
+            // the cells of one pencil range are consecutive, so their points are one span
+            for (int kk = 0; kk < 32 && open; ++kk) {
+                const uint32_t lo = __shfl_sync(0xffffffffu, rg.x, kk);
+                const uint32_t hi = __shfl_sync(0xffffffffu, rg.y, kk);
+                if (lo >= hi) continue;
+                const uint32_t q0 = v.cell_start[lo], q1 = v.cell_start[hi];
+                for (uint32_t qb = q0; qb < q1 && open; qb += 32) {
+                    const uint32_t q = qb + lane;
+                    T qv[DP];
+                    hd_load<T, DP>(v.pts, q, q < q1, qv);
+                    ++chunks;
+                    unsigned rem = open;
+                    while (rem) {
+                        const int jj = __ffs(rem) - 1;
+                        rem &= rem - 1;
+                        const unsigned hits = __ballot_sync(0xffffffffu, q < q1 && hd_within<DP>(rows + jj * DP, qv, v.g));
+                        if (lane == jj) cnt += __popc(hits);
+                    }
+                    open &= __ballot_sync(0xffffffffu, have && cnt < min_pts);
+                }
+            }
+        }
+        const bool is_core = have && cnt >= min_pts;
+        if (have) v.core[base + lane] = is_core ? 1 : 0;
+        if (__any_sync(0xffffffffu, is_core) && lane == 0) v.cell_core[A] = 1;
+        __syncwarp();
+    }
+    add_counter(&v.ctr->work[0], lane == 0 ? chunks : 0u);
+}
+
+// Union-find over points: parent[j] = j for every point.
+template <typename T, int DP>
+__global__ void __launch_bounds__(256) k_uf_init_hd(HdView<T, DP> v) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < v.g.n; j += (int64_t)gridDim.x * blockDim.x) {
+        v.parent[j] = (uint32_t)j;
+        v.comp_min[j] = kNoLabel;
+    }
+}
+
+// First links of the core graph (Definitions 3-5): every core point p hooks to the first core
+// point q < p within eps that the scan meets (p keeps itself when there is none).  Each link
+// is an edge of the graph and points to a smaller index, so the links form a forest whose
+// trees lie inside clusters; the union pass that follows joins the trees.
+template <typename T, int DP>
+__global__ void __launch_bounds__(32 * kHdWarps) k_hook_hd(HdView<T, DP> v) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *rows = reinterpret_cast<T *>(smem_raw) + (threadIdx.x >> 5) * 32 * DP;
+    const int lane = lane_id();
+    uint32_t chunks = 0;
+    HD_FOR_EACH_CHUNK(v, A, base, e) {
+        const uint32_t p = base + lane;
+        unsigned open = __ballot_sync(0xffffffffu, p < e && v.core[p]);
+        if (!open) continue;
+        stage_rows<T, DP>(rows, v.pts, base, e);
+        for (int g0 = 0; g0 < v.n_all && open; g0 += 32) {
+            const int k = g0 + lane;
+            const uint2 rg = k < v.n_all ? v.ranges[(uint64_t)A * v.n_all + k] : make_uint2(0u, 0u);
+            for (int kk = 0; kk < 32 && open; ++kk) {
+                const uint32_t lo = __shfl_sync(0xffffffffu, rg.x, kk);
+                const uint32_t hi = __shfl_sync(0xffffffffu, rg.y, kk);
+                if (lo >= hi) continue;
+                const uint32_t q0 = v.cell_start[lo];
+                const uint32_t q1 = min(v.cell_start[hi], base + 31u);  // only q < p can link
+                for (uint32_t qb = q0; qb < q1 && open; qb += 32) {
+                    const uint32_t q = qb + lane;
+                    const bool qc = q < q1 && v.core[q];
+                    if (!__any_sync(0xffffffffu, qc)) continue;
+                    T qv[DP];
+                    hd_load<T, DP>(v.pts, q, qc, qv);
+                    ++chunks;
+                    unsigned rem = open;
+                    while (rem) {
+                        const int jj = __ffs(rem) - 1;
+                        rem &= rem - 1;
+                        const bool hit = qc && q < base + jj && hd_within<DP>(rows + jj * DP, qv, v.g);
+                        const unsigned hm = __ballot_sync(0xffffffffu, hit);
+                        if (hm) {
+                            if (lane == jj) v.parent[base + jj] = qb + (uint32_t)(__ffs(hm) - 1);
+                            open &= ~(1u << jj);
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+    add_counter(&v.ctr->work[1], lane == 0 ? chunks : 0u);
+}
+
+// One round of pointer jumping over core points: parent[p] = parent[parent[p]].
+template <typename T, int DP>
+__global__ void __launch_bounds__(256) k_jump_hd(HdView<T, DP> v) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < v.g.n; j += (int64_t)gridDim.x * blockDim.x) {
+        if (!v.core[j]) continue;
+        const uint32_t p = __ldcg(v.parent + j);
+        const uint32_t gp = __ldcg(v.parent + p);
+        if (gp != p) v.parent[j] = gp;
+    }
+}
+
+// Definitions 3-5, remaining edges: every pair of core points within eps of the upper half of
+// the neighbourhood (the own pencil from this chunk on) whose trees differ is joined
+// (lock-free union-find, root = smallest index).  A 32 x 32 tile whose core points all share
+// one root is skipped without loading coordinates.
+template <typename T, int DP>
+__global__ void __launch_bounds__(32 * kHdWarps) k_merge_hd(HdView<T, DP> v) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *rows = reinterpret_cast<T *>(smem_raw) + (threadIdx.x >> 5) * 32 * DP;
+    const int lane = lane_id();
+    uint32_t chunks = 0, tests = 0, skipped = 0;
+    HD_FOR_EACH_CHUNK(v, A, base, e) {
+        if (!v.cell_core[A]) continue;
+        const uint32_t p = base + lane;
+        const bool pc = p < e && v.core[p];
+        const unsigned amask = __ballot_sync(0xffffffffu, pc);
+        if (!amask) continue;
+        stage_rows<T, DP>(rows, v.pts, base, e);
+        uint32_t rp = pc ? uf_find(v.parent, p, v.ctr) : 0xffffffffu;
+        for (int g0 = 0; g0 < v.n_half; g0 += 32) {
+            const int k = g0 + lane;
+            uint2 rg = k < v.n_half ? v.ranges[(uint64_t)A * v.n_all + k] : make_uint2(0u, 0u);
+            if (k == 0) rg.x = A;  // own pencil: this cell and the ones after it
+            for (int kk = 0; kk < 32; ++kk) {
+                const uint32_t lo = __shfl_sync(0xffffffffu, rg.x, kk);
+                const uint32_t hi = __shfl_sync(0xffffffffu, rg.y, kk);
+                if (lo >= hi) continue;
+                // own pencil: start at this chunk (earlier points pair with it from their side)
+                const uint32_t q0 = (g0 + kk == 0) ? max(v.cell_start[lo], base) : v.cell_start[lo];
+                const uint32_t q1 = v.cell_start[hi];
+                for (uint32_t qb = q0; qb < q1; qb += 32) {
+                    const uint32_t q = qb + lane;
+                    const bool qc = q < q1 && v.core[q];
+                    if (!__any_sync(0xffffffffu, qc)) continue;
+                    uint32_t rq = qc ? uf_find(v.parent, q, v.ctr) : 0xfffffffeu;
+                    const uint32_t r0 = __shfl_sync(0xffffffffu, rp, __ffs(amask) - 1);
+                    if (__all_sync(0xffffffffu, (!pc || rp == r0) && (!qc || rq == r0))) {
+                        ++skipped;
+                        continue;
+                    }
+                    T qv[DP];
+                    hd_load<T, DP>(v.pts, q, qc, qv);
+                    ++chunks;
+                    unsigned rem = amask;
+                    while (rem) {
+                        const int jj = __ffs(rem) - 1;
+                        rem &= rem - 1;
+                        const uint32_t pj = base + jj;
+                        const uint32_t rj = __shfl_sync(0xffffffffu, rp, jj);
+                        const bool need = qc && q > pj && rq != rj;
+                        if (!__any_sync(0xffffffffu, need)) continue;
+                        ++tests;
+                        const bool hit = need && hd_within<DP>(rows + jj * DP, qv, v.g);
+                        if (hit) uf_union(v.parent, pj, q, v.ctr);
+                        if (__any_sync(0xffffffffu, hit)) {
+                            // roots moved: refresh every lane so later pairs of the tile skip
+                            rq = qc ? uf_find(v.parent, q, v.ctr) : 0xfffffffeu;
+                            rp = pc ? uf_find(v.parent, p, v.ctr) : 0xffffffffu;
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+    add_counter(&v.ctr->work[4], lane == 0 ? chunks : 0u);
+    add_counter(&v.ctr->work[3], lane == 0 ? tests : 0u);
+    add_counter(&v.ctr->work[2], lane == 0 ? skipped : 0u);
+}
+
+// Flatten the point union-find (read-only finds), count roots, canonical ids.
+template <typename T, int DP>
+__global__ void __launch_bounds__(256) k_compress_hd(HdView<T, DP> v) {
+    uint32_t roots = 0;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < v.g.n; j += (int64_t)gridDim.x * blockDim.x) {
+        if (!v.core[j]) continue;
+        const uint32_t r = uf_root_readonly(v.parent, (uint32_t)j, v.ctr);
+        v.parent[j] = r;
+        roots += (r == (uint32_t)j);
+    }
+    for (int o = 16; o; o >>= 1) roots += __shfl_xor_sync(0xffffffffu, roots, o);
+    if (lane_id() == 0 && roots) atomicAdd(&v.ctr->n_clusters, roots);
+}
+
+template <typename T, int DP>
+__global__ void __launch_bounds__(256) k_comp_min_hd(HdView<T, DP> v) {
+    const int64_t n = v.g.n;
+    const int lane = lane_id();
+    uint32_t ncore = 0;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = base + lane;
+        const bool valid = j < n && v.core[j];
+        const uint32_t r = valid ? v.parent[j] : 0xffffffffu;
+        uint32_t val = valid ? v.perm[j] : kNoLabel;
+        const unsigned vm = __ballot_sync(0xffffffffu, valid);
+        if (!vm) continue;
+        ncore += (lane == 0) ? __popc(vm) : 0u;
+        const uint32_t r0 = __shfl_sync(0xffffffffu, r, __ffs(vm) - 1);
+        if (__all_sync(0xffffffffu, !valid || r == r0)) {
+            for (int o = 16; o; o >>= 1) val = min(val, __shfl_xor_sync(0xffffffffu, val, o));
+            if (lane == 0) atomicMin(&v.comp_min[r0], val);
+        } else if (valid) {
+            atomicMin(&v.comp_min[r], val);
+        }
+    }
+    if (lane == 0 && ncore) atomicAdd(&v.ctr->n_core, ncore);
+}
+
+// Algorithm 4 / Definition 5 with the canonical rule, over points: core points take their
+// cluster id, a non-core point the smallest id among its core neighbours, else -1.
+template <typename T, int DP>
+__global__ void __launch_bounds__(32 * kHdWarps) k_labels_hd(HdView<T, DP> v) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *rows = reinterpret_cast<T *>(smem_raw) + (threadIdx.x >> 5) * 32 * DP;
+    const int lane = lane_id();
+    uint32_t noise = 0, chunks = 0;
+    HD_FOR_EACH_CHUNK(v, A, base, e) {
+        {
+            const uint32_t p = base + lane;
+            const bool have = p < e;
+            const bool isc = have && v.core[p];
+            uint32_t best = isc ? v.comp_min[v.parent[p]] : kNoLabel;
+            const unsigned smask = __ballot_sync(0xffffffffu, have && !isc);
+            if (smask) {
+                stage_rows<T, DP>(rows, v.pts, base, e);
+                for (int g0 = 0; g0 < v.n_all; g0 += 32) {
+                    const int k = g0 + lane;
+                    const uint2 rg = k < v.n_all ? v.ranges[(uint64_t)A * v.n_all + k] : make_uint2(0u, 0u);
+                    for (int kk = 0; kk < 32; ++kk) {
+                        const uint32_t lo = __shfl_sync(0xffffffffu, rg.x, kk);
+                        const uint32_t hi = __shfl_sync(0xffffffffu, rg.y, kk);
+                        if (lo >= hi) continue;
+                        const uint32_t q0 = v.cell_start[lo], q1 = v.cell_start[hi];
+                        for (uint32_t qb = q0; qb < q1; qb += 32) {
+                            const uint32_t q = qb + lane;
+                            const bool qc = q < q1 && v.core[q];
+                            if (!__any_sync(0xffffffffu, qc)) continue;
+                            const uint32_t lq = qc ? v.comp_min[v.parent[q]] : kNoLabel;
+                            T qv[DP];
+                            hd_load<T, DP>(v.pts, q, qc, qv);
+                            ++chunks;
+                            unsigned rem = smask;
+                            while (rem) {
+                                const int jj = __ffs(rem) - 1;
+                                rem &= rem - 1;
+                                const uint32_t bj = __shfl_sync(0xffffffffu, best, jj);
+                                const bool need = qc && lq < bj;
+                                if (!__any_sync(0xffffffffu, need)) continue;
+                                uint32_t cand = (need && hd_within<DP>(rows + jj * DP, qv, v.g)) ? lq : kNoLabel;
+                                for (int o = 16; o; o >>= 1) cand = min(cand, __shfl_xor_sync(0xffffffffu, cand, o));
+                                if (lane == jj && cand < best) best = cand;
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            if (have) {
+                const int32_t lab = best == kNoLabel ? -1 : (int32_t)best;
+                const uint32_t o = v.perm[p];
+                v.labels[o] = lab;
+                if (v.core_out) v.core_out[o] = isc ? 1 : 0;
+                noise += lab < 0;
+            }
+        }
+    }
+    for (int o = 16; o; o >>= 1) noise += __shfl_xor_sync(0xffffffffu, noise, o);
+    if (lane == 0 && noise) atomicAdd(&v.ctr->n_noise, noise);
+    add_counter(&v.ctr->work[5], lane == 0 ? chunks : 0u);
+}
+
+}  // namespace hca

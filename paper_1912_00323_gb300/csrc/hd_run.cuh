@@ -1,0 +1,310 @@
+// Host orchestration of the high-dimensional path (5 <= d <= 64) for one call.
+#pragma once
+
+#include "hd_kernels.cuh"
+#include "lowd_run.cuh"
+
+namespace hca {
+
+namespace detail {
+
+// Coarse grid over three projected dimensions with side eps (1 + 2^-10): two points within eps
+// differ by at most eps (1 + 2^-50) in every coordinate, and with band coordinates computed in
+// FP64 (error tau in band units, tau << 2^-12) they fall in the same or adjacent coarse cells.
+inline int make_coarse_grid(bool input_f32, double eps, int min_pts, int64_t n, const double *mn,
+                            const double *mx, int flags, GridParams &g, double &tau) {
+    memset(&g, 0, sizeof(g));
+    g.d = 3;
+    g.n = n;
+    g.min_pts = (uint32_t)min_pts;
+    g.eps2 = eps * eps;
+    const double side = eps * (1.0 + ldexp(1.0, -10));
+    const double inv = 1.0 / side;
+    double range_max = 0.0;
+    for (int i = 0; i < 3; ++i) range_max = fmax(range_max, mx[i] - mn[i]);
+    if (!isfinite(range_max) || !isfinite(inv)) return HCA_ERANGE;
+    tau = (range_max * inv + 1.0) * ldexp(1.0, -51);
+    if (tau > ldexp(1.0, -14)) return HCA_ERANGE;
+    g.inv_side = inv;
+    g.inv_side_f = (float)inv;
+    g.bin_fp64 = 1;
+    int total = 0;
+    for (int i = 0; i < 3; ++i) {
+        g.origin[i] = mn[i];
+        g.origin_f[i] = (float)mn[i];
+        const double cells = floor((mx[i] - mn[i]) * inv * (1.0 + 1e-6)) + 2.0;
+        if (!(cells < 2147483648.0)) return HCA_ERANGE;
+        g.ncell[i] = (uint32_t)cells;
+        uint32_t b = 1;
+        while ((1ull << b) < (uint64_t)g.ncell[i]) ++b;
+        g.bits[i] = b;
+        total += (int)b;
+    }
+    if (total > 63) return HCA_ERANGE;
+    g.key_bits = total;
+    int sh = 0;
+    for (int i = 2; i >= 0; --i) {
+        g.shift[i] = (uint32_t)sh;
+        sh += (int)g.bits[i];
+    }
+    g.prefix_shift = (int)g.bits[2];
+    const bool filter = input_f32 && !(flags & HCA_FLAG_FP64_ONLY) && g.eps2 >= ldexp(1.0, -100) &&
+                        g.eps2 <= ldexp(1.0, 100);
+    if (filter) {
+        float lo = (float)(g.eps2 * (1.0 - ldexp(1.0, -16)));
+        if ((double)lo > g.eps2 * (1.0 - ldexp(1.0, -16))) lo = nextafterf(lo, 0.f);
+        float hi = (float)(g.eps2 * (1.0 + ldexp(1.0, -16)));
+        if ((double)hi < g.eps2 * (1.0 + ldexp(1.0, -16))) hi = nextafterf(hi, INFINITY);
+        g.lo32 = lo;
+        g.hi32 = hi;
+    } else {
+        g.lo32 = -1.0f;
+        g.hi32 = INFINITY;
+    }
+    g.box_ok = 0;
+    return HCA_OK;
+}
+
+template <typename Kern>
+inline void allow_smem(Kern k, size_t bytes) {
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace detail
+
+template <typename T, int DP>
+int run_hd(const RunArgs &a) {
+    using namespace detail;
+    cudaStream_t s = a.stream;
+    const int64_t n = a.n;
+    const int d = a.d;
+    int launches = 0;
+    const int sms = device_sm_count();
+    if (sms <= 0) return HCA_ECUDA;
+
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+    int64_t cap_max = 64;
+    while (cap_max < 2 * n) cap_max <<= 1;
+    const size_t hist_elems = sort_hist_size(n);
+    const int64_t scan_max = n > (int64_t)hist_elems ? n : (int64_t)hist_elems;
+    const size_t o_ctr = take(sizeof(DevCounters));
+    const size_t o_mm = take(sizeof(unsigned long long) * 128);
+    const size_t o_ka = take(8 * n), o_kb = take(8 * n), o_ia = take(4 * n), o_ib = take(4 * n);
+    const size_t o_hist = take(4 * hist_elems);
+    const size_t o_part = take(4 * scan_partials_size(scan_max));
+    const size_t o_pts = take(sizeof(T) * DP * (size_t)n);
+    const size_t o_flags = take(4 * n), o_excl = take(4 * n);
+    const size_t o_cstart = take(4 * (n + 1)), o_ckey = take(8 * n);
+    const size_t o_pflags = take(4 * n), o_pexcl = take(4 * n), o_pstart = take(4 * (n + 1));
+    const size_t o_hk = take(8 * cap_max), o_hv = take(4 * cap_max);
+    const size_t o_core = take(n), o_ccore = take(n);
+    const size_t o_parent = take(4 * n), o_cmin = take(4 * n);
+    const size_t o_ranges = take(sizeof(uint2) * 9 * (size_t)n);
+    const size_t o_nch = take(4 * n), o_choff = take(4 * n);
+    void *ws = nullptr;
+    if (pool_alloc(&ws, off, s) != cudaSuccess || !ws) return HCA_ENOMEM;
+    char *b = (char *)ws;
+    DevCounters *ctr = (DevCounters *)(b + o_ctr);
+    unsigned long long *mm = (unsigned long long *)(b + o_mm);
+    DevCounters *h = host_counters();
+    int rc = HCA_OK;
+
+    cudaEvent_t ev[HCA_NUM_STAGES + 1] = {};
+    const bool timing = (a.flags & HCA_FLAG_TIMING) && a.stats;
+    if (timing)
+        for (int i = 0; i <= HCA_NUM_STAGES; ++i) cudaEventCreate(&ev[i]);
+    auto mark = [&](int i) { if (timing) cudaEventRecord(ev[i], s); };
+
+    GridParams g;
+    Stencil st;
+    double tau = 0.0;
+    int3 sel = make_int3(0, 1, 2);
+    const int gpts = grid_for(n, 256, sms, 8);
+    const int gcell = grid_for((n + 31) / 32 + 1, kHdWarps, sms, 16);
+    const size_t smem = (size_t)kHdWarps * 32 * DP * sizeof(T);
+    bool flipped = false;
+    std::vector<unsigned long long> hmm(128);
+    HdView<T, DP> hv;
+    LowdView<float, 3> lv;
+    memset(&hv, 0, sizeof(hv));
+    memset(&lv, 0, sizeof(lv));
+
+    if (!h) { rc = HCA_ECUDA; goto out; }
+    mark(0);
+    cudaMemsetAsync(ctr, 0, sizeof(DevCounters), s);
+    cudaMemsetAsync(mm, 0xff, sizeof(unsigned long long) * 64, s);
+    cudaMemsetAsync(mm + 64, 0, sizeof(unsigned long long) * 64, s);
+    k_minmax_rt<T><<<grid_for(n * d, 256, sms, 8), 256, 0, s>>>((const T *)a.d_points, n, d, ctr, mm);
+    ++launches;
+    if (cudaMemcpyAsync(h, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(hmm.data(), mm, sizeof(unsigned long long) * 128, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) { rc = HCA_ECUDA; goto out; }
+    {
+        if (h->nan_seen) { rc = HCA_EINVAL; goto out; }
+        double mn_all[64], mx_all[64];
+        for (int i = 0; i < d; ++i) {
+            mn_all[i] = dec_double(hmm[i]);
+            mx_all[i] = dec_double(hmm[64 + i]);
+            if (!isfinite(mn_all[i]) || !isfinite(mx_all[i])) { rc = HCA_EINVAL; goto out; }
+        }
+        // the three dimensions of largest extent (ties: lower index)
+        int pick[3] = {-1, -1, -1};
+        for (int k = 0; k < 3; ++k) {
+            double best = -1.0;
+            for (int i = 0; i < d; ++i) {
+                if (i == pick[0] || i == pick[1]) continue;
+                const double ext = mx_all[i] - mn_all[i];
+                if (ext > best) { best = ext; pick[k] = i; }
+            }
+        }
+        sel = make_int3(pick[0], pick[1], pick[2]);
+        const double mn3[3] = {mn_all[pick[0]], mn_all[pick[1]], mn_all[pick[2]]};
+        const double mx3[3] = {mx_all[pick[0]], mx_all[pick[1]], mx_all[pick[2]]};
+        rc = make_coarse_grid(sizeof(T) == 4, a.eps, a.min_pts, n, mn3, mx3, a.flags, g, tau);
+        if (rc) goto out;
+        rc = make_stencil(3, a.eps, 1.0 / g.inv_side, tau, st);
+        if (rc) goto out;
+    }
+    mark(1);
+    {
+        uint32_t *ia = (uint32_t *)(b + o_ia), *ib = (uint32_t *)(b + o_ib);
+        uint32_t *hist = (uint32_t *)(b + o_hist), *part = (uint32_t *)(b + o_part);
+        const bool use32 = g.key_bits <= 32;
+        if (use32) {
+            uint32_t *ka = (uint32_t *)(b + o_ka), *kb = (uint32_t *)(b + o_kb);
+            k_bin_proj<T, uint32_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, d, sel, g, ka, ia);
+            mark(2);
+            flipped = radix_sort_pairs<uint32_t>(ka, ia, kb, ib, n, 0, g.key_bits, hist, part, s, &launches);
+            mark(3);
+            k_gather_hd<T, DP, uint32_t><<<grid_for(n, 8, sms, 16), 256, 0, s>>>(
+                (const T *)a.d_points, d, flipped ? kb : ka, flipped ? ib : ia, n, (T *)(b + o_pts),
+                (uint32_t *)(b + o_flags));
+        } else {
+            uint64_t *ka = (uint64_t *)(b + o_ka), *kb = (uint64_t *)(b + o_kb);
+            k_bin_proj<T, uint64_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, d, sel, g, ka, ia);
+            mark(2);
+            flipped = radix_sort_pairs<uint64_t>(ka, ia, kb, ib, n, 0, g.key_bits, hist, part, s, &launches);
+            mark(3);
+            k_gather_hd<T, DP, uint64_t><<<grid_for(n, 8, sms, 16), 256, 0, s>>>(
+                (const T *)a.d_points, d, flipped ? kb : ka, flipped ? ib : ia, n, (T *)(b + o_pts),
+                (uint32_t *)(b + o_flags));
+        }
+        launches += 2;
+        exclusive_scan_u32((uint32_t *)(b + o_flags), (uint32_t *)(b + o_excl), n, nullptr,
+                           &ctr->n_cells, part, s, &launches);
+        if (use32)
+            k_cells<uint32_t><<<gpts, 256, 0, s>>>((const uint32_t *)(b + (flipped ? o_kb : o_ka)),
+                                                   (uint32_t *)(b + o_flags), (const uint32_t *)(b + o_excl),
+                                                   n, (uint32_t *)(b + o_cstart), (uint64_t *)(b + o_ckey));
+        else
+            k_cells<uint64_t><<<gpts, 256, 0, s>>>((const uint64_t *)(b + (flipped ? o_kb : o_ka)),
+                                                   (uint32_t *)(b + o_flags), (const uint32_t *)(b + o_excl),
+                                                   n, (uint32_t *)(b + o_cstart), (uint64_t *)(b + o_ckey));
+        ++launches;
+        hv.perm = flipped ? ib : ia;
+    }
+    mark(4);
+    {
+        uint32_t *part = (uint32_t *)(b + o_part);
+        k_pencil_flags<<<gpts, 256, 0, s>>>((const uint64_t *)(b + o_ckey), g.prefix_shift, ctr,
+                                            (uint32_t *)(b + o_pflags));
+        exclusive_scan_u32((uint32_t *)(b + o_pflags), (uint32_t *)(b + o_pexcl), n, &ctr->n_cells,
+                           &ctr->n_pencils, part, s, &launches);
+        k_hash_init<<<grid_for(cap_max, 256, sms, 8), 256, 0, s>>>((uint64_t *)(b + o_hk), ctr);
+        k_pencils<<<gpts, 256, 0, s>>>((const uint64_t *)(b + o_ckey), g.prefix_shift,
+                                       (const uint32_t *)(b + o_pflags), (const uint32_t *)(b + o_pexcl),
+                                       (uint32_t *)(b + o_pstart), (uint64_t *)(b + o_hk),
+                                       (uint32_t *)(b + o_hv), ctr);
+        lv.g = g;
+        lv.cell_key = (const uint64_t *)(b + o_ckey);
+        lv.pencil_start = (const uint32_t *)(b + o_pstart);
+        lv.hkeys = (uint64_t *)(b + o_hk);
+        lv.hvals = (uint32_t *)(b + o_hv);
+        lv.ranges = (uint2 *)(b + o_ranges);
+        lv.ctr = ctr;
+        k_ranges<float, 3><<<grid_for(n * (int64_t)st.n_all, 256, sms, 16), 256, 0, s>>>(lv, st);
+        k_chunk_counts<<<gpts, 256, 0, s>>>((const uint32_t *)(b + o_cstart), ctr, (uint32_t *)(b + o_nch));
+        exclusive_scan_u32((uint32_t *)(b + o_nch), (uint32_t *)(b + o_choff), n, &ctr->n_cells,
+                           &ctr->n_chunks, part, s, &launches);
+        launches += 5;
+    }
+    mark(5);
+    hv.g = g;
+    hv.d = d;
+    hv.pts = (const T *)(b + o_pts);
+    hv.cell_start = (const uint32_t *)(b + o_cstart);
+    hv.cell_key = (const uint64_t *)(b + o_ckey);
+    hv.chunk_off = (const uint32_t *)(b + o_choff);
+    hv.ranges = (const uint2 *)(b + o_ranges);
+    hv.core = (uint8_t *)(b + o_core);
+    hv.cell_core = (uint8_t *)(b + o_ccore);
+    hv.parent = (uint32_t *)(b + o_parent);
+    hv.comp_min = (uint32_t *)(b + o_cmin);
+    hv.labels = a.d_labels;
+    hv.core_out = a.d_core;
+    hv.ctr = ctr;
+    hv.n_all = st.n_all;
+    hv.n_half = st.n_half;
+    allow_smem(k_count_hd<T, DP>, smem);
+    allow_smem(k_hook_hd<T, DP>, smem);
+    allow_smem(k_merge_hd<T, DP>, smem);
+    allow_smem(k_labels_hd<T, DP>, smem);
+    // ---- Definition 2: exact counts over the neighbouring coarse cells ----
+    cudaMemsetAsync(hv.cell_core, 0, (size_t)n, s);
+    k_count_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
+    ++launches;
+    mark(6);
+    // (no representative points in this path: every pair of core points is a candidate)
+    mark(7);
+    // ---- Definitions 3-5: first links, pointer jumping, then the remaining unions ----
+    k_uf_init_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
+    k_hook_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
+    for (int r = 0; r < 6; ++r) k_jump_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
+    k_merge_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
+    k_compress_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
+    launches += 10;
+    mark(8);
+    // ---- Algorithm 4: canonical ids, border and noise points ----
+    k_comp_min_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
+    k_labels_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
+    launches += 2;
+    mark(9);
+    if (cudaGetLastError() != cudaSuccess) { rc = HCA_ECUDA; goto out; }
+    if (cudaMemcpyAsync(h, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) { rc = HCA_ECUDA; goto out; }
+    if (h->status) { rc = HCA_EDEVICE; goto out; }
+    if (a.stats) {
+        hca_stats *so = a.stats;
+        so->n_points = n;
+        so->n_cells = h->n_cells;
+        so->n_pencils = h->n_pencils;
+        so->n_dense_cells = 0;
+        so->n_core_points = h->n_core;
+        so->n_clusters = h->n_clusters;
+        so->n_noise = h->n_noise;
+        so->key_bits = g.key_bits;
+        so->sort_passes = (g.key_bits + 7) / 8;
+        so->kernel_launches = launches;
+        so->n_count_chunks = (int64_t)h->work[0];
+        so->n_rep_tests = (int64_t)h->work[1];   // hook-pass chunks in this path
+        so->n_rep_hits = (int64_t)h->work[2];    // tiles skipped because every root agreed
+        so->n_exhaustive_pairs = (int64_t)h->work[3];
+        so->n_exhaustive_chunks = (int64_t)h->work[4];
+        so->n_border_chunks = (int64_t)h->work[5];
+        for (int i = 0; i < HCA_NUM_STAGES; ++i) {
+            float ms = 0.f;
+            if (timing) cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+            so->stage_ms[i] = ms;
+        }
+    }
+out:
+    if (timing)
+        for (int i = 0; i <= HCA_NUM_STAGES; ++i)
+            if (ev[i]) cudaEventDestroy(ev[i]);
+    pool_free(ws, s);
+    if (rc != HCA_OK) cudaStreamSynchronize(s);
+    return rc;
+}
+
+}  // namespace hca

@@ -36,6 +36,9 @@ struct LowdView {
     uint8_t *cell_core;
     uint32_t *parent;
     uint64_t *reps;
+    Pt<T, D> *rep_pts;            // coordinates of reps[c * ndir + r]
+    const uint32_t *chunk_off;    // first 256-point chunk of each cell (representative pass)
+    uint32_t *chunk_cell;         // cell of each chunk
     uint32_t *comp_min;
     uint2 *ranges;                // [cell * n_all + k]: neighbour cells [lo, hi) in pencil k
     int32_t *labels;              // output, input order
@@ -396,15 +399,30 @@ __global__ void __launch_bounds__(256) k_minmax(const T *__restrict__ in, int64_
         }
     }
     nan = __any_sync(0xffffffffu, nan);
+    // one atomic per block and dimension (per-warp atomics on the same few words serialise)
+    __shared__ T smn[8][D], smx[8][D];
+    __shared__ int snan;
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) snan = 0;
+    __syncthreads();
     if (lane_id() == 0) {
-        uint64_t *mm = reinterpret_cast<uint64_t *>(ctr->minmax_enc);
 #pragma unroll
-        for (int i = 0; i < D; ++i) {
-            atomicMin((unsigned long long *)&mm[i], (unsigned long long)enc_double((double)mn[i]));
-            atomicMax((unsigned long long *)&mm[kMaxD + i], (unsigned long long)enc_double((double)mx[i]));
-        }
-        if (nan) atomicOr(&ctr->nan_seen, 1u);
+        for (int i = 0; i < D; ++i) { smn[warp][i] = mn[i]; smx[warp][i] = mx[i]; }
+        if (nan) snan = 1;
     }
+    __syncthreads();
+    if (threadIdx.x < D) {
+        const int i = threadIdx.x;
+        T a = smn[0][i], b = smx[0][i];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            a = smn[w][i] < a ? smn[w][i] : a;
+            b = smx[w][i] > b ? smx[w][i] : b;
+        }
+        uint64_t *mm = reinterpret_cast<uint64_t *>(ctr->minmax_enc);
+        atomicMin((unsigned long long *)&mm[i], (unsigned long long)enc_double((double)a));
+        atomicMax((unsigned long long *)&mm[kMaxD + i], (unsigned long long)enc_double((double)b));
+    }
+    if (threadIdx.x == 0 && snan) atomicOr(&ctr->nan_seen, 1u);
 }
 
 // Algorithm 1: band index of every coordinate, c_i = floor((x_i - o_i) / side), packed into a
@@ -540,12 +558,13 @@ __global__ void __launch_bounds__(256) k_ranges(LowdView<T, D> v, Stencil st_in)
 }
 
 // Definition 2 with the hypercube shortcut: a cell holding >= MINPTS points is core as a
-// whole (its diagonal is at most eps); every point of another cell is counted exactly over
-// its own cell and the neighbour cells, stopping once it reaches MINPTS.  One warp per cell:
-// the lanes hold the cell's points; the neighbour cells are walked 32 at a time; a neighbour
-// cell whose box lies wholly within eps of a point adds its size without tests, one wholly
-// beyond eps is skipped, and the rest are compared point by point with a warp ballot.  Also
-// initialises the per-cell union-find and cluster-id slots.
+// whole (its diagonal is at most eps); every point of another cell (fewer than MINPTS points)
+// is counted exactly over its own cell and the neighbour cells, stopping once it reaches
+// MINPTS.  One warp per cell.  The neighbour cells are walked 32 at a time, one per lane; for
+// each open point of the cell every lane classifies its cell's box against the point: a box
+// wholly within eps adds the cell's size (warp sum), one wholly beyond eps is dropped, and the
+// remaining cells are compared point by point with a warp ballot.  Also initialises the
+// per-cell union-find, representative and cluster-id slots.
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_core(LowdView<T, D> v, int n_all) {
     const uint32_t C = v.ctr->n_cells;
@@ -573,46 +592,59 @@ __global__ void __launch_bounds__(256) k_core(LowdView<T, D> v, int n_all) {
             float ta[D];
             band_coords<T, D>(pa, v.g, ta);
             uint32_t cnt = m;  // the own cell: every point within eps
-            bool all_done = false;
-            for (int g0 = 0; g0 < n_all && !all_done; g0 += 32) {
+            unsigned open = __ballot_sync(0xffffffffu, have && cnt < min_pts);
+            for (int g0 = 0; g0 < n_all && open; g0 += 32) {
                 const int k = g0 + lane;
                 const uint2 rg = k < n_all ? v.ranges[(uint64_t)A * n_all + k] : make_uint2(0u, 0u);
                 const LaneRanges lr = lane_ranges(rg.x, rg.y);
-                for (uint32_t f0 = 0; f0 < lr.total && !all_done; f0 += 32) {
+                for (uint32_t f0 = 0; f0 < lr.total && open; f0 += 32) {
                     const uint32_t f = f0 + lane;
                     const uint32_t B = flat_cell(lr, f < lr.total ? f : 0u);
                     const bool okb = f < lr.total && B != A;
                     const uint32_t bs = okb ? v.cell_start[B] : 0u;
                     const uint32_t be = okb ? v.cell_start[B + 1] : 0u;
-                    const uint64_t bkey = okb ? v.cell_key[B] : 0ull;
-                    const int nb = (int)min(32u, lr.total - f0);
-                    for (int jb = 0; jb < nb && !all_done; ++jb) {
-                        const uint32_t B_s = __shfl_sync(0xffffffffu, bs, jb);
-                        const uint32_t B_e = __shfl_sync(0xffffffffu, be, jb);
-                        if (B_s == B_e) continue;
-                        int cb[D];
-                        unpack_key<D>(__shfl_sync(0xffffffffu, bkey, jb), v.g, cb);
-                        const bool open = have && cnt < min_pts;
-                        const int cls = open ? box_class<D>(ta, cb, v.g) : 0;
-                        if (cls == 2) cnt += B_e - B_s;
-                        const unsigned partial = __ballot_sync(0xffffffffu, cls == 1);
-                        if (partial) {
-                            for (uint32_t qb = B_s; qb < B_e; qb += 32) {
-                                const uint32_t q = qb + lane;
-                                const bool vq = q < B_e;
-                                const Pt<T, D> pq = vq ? v.pts[q] : zero_pt<T, D>();
-                                ++chunks;
-                                unsigned rem = partial;
-                                while (rem) {
-                                    const int jj = __ffs(rem) - 1;
-                                    rem &= rem - 1;
-                                    const Pt<T, D> aj = shfl_pt<T, D>(pa, jj);
-                                    const unsigned hits = __ballot_sync(0xffffffffu, vq && within_eps<D>(aj, pq, v.g));
-                                    if (lane == jj) cnt += __popc(hits);
+                    int cb[D];
+                    unpack_key<D>(okb ? v.cell_key[B] : 0ull, v.g, cb);
+                    unsigned rem = open;
+                    while (rem) {
+                        const int jj = __ffs(rem) - 1;
+                        rem &= rem - 1;
+                        float tj[D];
+#pragma unroll
+                        for (int k2 = 0; k2 < D; ++k2) tj[k2] = __shfl_sync(0xffffffffu, ta[k2], jj);
+                        const int cls = okb ? box_class<D>(tj, cb, v.g) : 0;
+                        uint32_t full = cls == 2 ? be - bs : 0u;
+#pragma unroll
+                        for (int o = 16; o; o >>= 1) full += __shfl_xor_sync(0xffffffffu, full, o);
+                        uint32_t cj = __shfl_sync(0xffffffffu, cnt, jj) + full;
+                        unsigned partial = __ballot_sync(0xffffffffu, cls == 1);
+                        if (partial && cj < min_pts) {
+                            const Pt<T, D> aj = shfl_pt<T, D>(pa, jj);
+                            while (partial && cj < min_pts) {
+                                const int t = __ffs(partial) - 1;
+                                partial &= partial - 1;
+                                const uint32_t ps = __shfl_sync(0xffffffffu, bs, t);
+                                const uint32_t pe = __shfl_sync(0xffffffffu, be, t);
+                                for (uint32_t qb = ps; qb < pe && cj < min_pts; qb += 128) {
+                                    // four chunks of candidates in flight
+                                    Pt<T, D> q4[4];
+#pragma unroll
+                                    for (int u = 0; u < 4; ++u) {
+                                        const uint32_t q = qb + 32 * u + lane;
+                                        q4[u] = q < pe ? v.pts[q] : zero_pt<T, D>();
+                                    }
+#pragma unroll
+                                    for (int u = 0; u < 4; ++u) {
+                                        const uint32_t q = qb + 32 * u + lane;
+                                        const bool hit = q < pe && within_eps<D>(aj, q4[u], v.g);
+                                        cj += __popc(__ballot_sync(0xffffffffu, hit));
+                                    }
+                                    ++chunks;
                                 }
                             }
                         }
-                        all_done = __all_sync(0xffffffffu, !have || cnt >= min_pts);
+                        if (lane == jj) cnt = cj;
+                        if (cj >= min_pts) open &= ~(1u << jj);
                     }
                 }
             }
@@ -653,104 +685,93 @@ __device__ __forceinline__ float rep_dist(int r, const float *lo2, const float *
 }
 
 // Algorithm 2: for every cell with core points and every direction delta, the core point
-// nearest to the ideal position of delta; ties go to the smaller sorted index.  The points
-// are taken in windows of 256 consecutive sorted points, one warp per window, so the work is
-// even however large a cell is.  A window inside one cell keeps per-lane minima over its
-// points and reduces once; a window spanning several cells reduces each 32-point group
-// within runs of equal cell id.  Results meet in the cell's slots by 64-bit atomicMin of
-// (distance bits, index): non-negative float bits order like the floats.
+// nearest to the ideal position of delta; ties go to the smaller sorted index.  The work is
+// split into chunks of at most 256 points of one cell (chunk_off[c] = first chunk of cell c),
+// one warp per chunk, so a cell of any size is shared out evenly.  Each lane keeps its own
+// minima over its points of the chunk, the warp reduces once per direction, and a cell of
+// several chunks combines them by 64-bit atomicMin of (distance bits, index) (non-negative
+// float bits order like the floats).  Among equal distances any holder may be kept: the
+// representative only decides which pair is tested first, never a label.
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_reps(LowdView<T, D> v) {
     constexpr int ndir = RepDirs<D>::value;
-    constexpr int kWin = 256;
-    const int64_t n = v.g.n;
+    constexpr uint32_t kChunk = 256;
+    const uint32_t C = v.ctr->n_cells, NC = v.ctr->n_chunks;
     const int lane = lane_id();
-    const int64_t nwin = (n + kWin - 1) / kWin;
-    for (int64_t w = global_warp(); w < nwin; w += total_warps()) {
-        const int64_t j0 = w * kWin;
-        const int64_t j1 = min(j0 + kWin, n);
-        const uint32_t cfirst = v.cell_of[j0], clast = v.cell_of[j1 - 1];
-        if (cfirst == clast) {
-            if (!v.cell_core[cfirst]) continue;
-            int ac[D];
-            unpack_key<D>(v.cell_key[cfirst], v.g, ac);
-            float best[ndir];
-            uint32_t bidx[ndir];
+    (void)C;
+    for (uint32_t t = global_warp(); t < NC; t += total_warps()) {
+        const uint32_t A = v.chunk_cell[t];
+        const uint32_t s = v.cell_start[A], e = v.cell_start[A + 1];
+        const uint32_t j0 = s + kChunk * (t - v.chunk_off[A]);
+        const uint32_t j1 = min(j0 + kChunk, e);
+        int ac[D];
+        unpack_key<D>(v.cell_key[A], v.g, ac);
+        float best[ndir];
+        uint32_t bidx[ndir];
 #pragma unroll
-            for (int r = 0; r < ndir; ++r) { best[r] = FLT_MAX; bidx[r] = 0xffffffffu; }
-            for (int64_t j = j0 + lane; j < j1; j += 32) {
-                if (!v.core[j]) continue;
-                float u[D], lo2[D], hi2[D];
-                band_coords<T, D>(v.pts[j], v.g, u);
+        for (int r = 0; r < ndir; ++r) { best[r] = FLT_MAX; bidx[r] = 0xffffffffu; }
+        for (uint32_t j = j0 + lane; j < j1; j += 32) {
+            if (!v.core[j]) continue;
+            float u[D], lo2[D], hi2[D];
+            band_coords<T, D>(v.pts[j], v.g, u);
 #pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    const float x = u[k] - (float)ac[k];
-                    lo2[k] = x * x;
-                    hi2[k] = (1.f - x) * (1.f - x);
-                }
-#pragma unroll
-                for (int r = 0; r < ndir; ++r) {
-                    const float dd = rep_dist<D>(r, lo2, hi2);
-                    if (dd < best[r]) { best[r] = dd; bidx[r] = (uint32_t)j; }
-                }
+            for (int k = 0; k < D; ++k) {
+                const float x = u[k] - (float)ac[k];
+                lo2[k] = x * x;
+                hi2[k] = (1.f - x) * (1.f - x);
             }
 #pragma unroll
             for (int r = 0; r < ndir; ++r) {
-                uint64_t val = ((uint64_t)__float_as_uint(best[r]) << 32) | bidx[r];
-#pragma unroll
-                for (int o = 16; o; o >>= 1) {
-                    const uint64_t other = __shfl_xor_sync(0xffffffffu, val, o);
-                    val = other < val ? other : val;
-                }
-                if (lane == 0 && val != ~0ull)
-                    atomicMin((unsigned long long *)&v.reps[(uint64_t)cfirst * ndir + r], (unsigned long long)val);
-            }
-        } else {
-            for (int64_t g0 = j0; g0 < j1; g0 += 32) {
-                const int64_t j = g0 + lane;
-                const bool inr = j < j1;
-                const uint32_t c = inr ? v.cell_of[j] : 0xffffffffu;
-                const bool valid = inr && v.core[j];
-                if (!__any_sync(0xffffffffu, valid)) continue;
-                float lo2[D], hi2[D];
-                if (valid) {
-                    int ac[D];
-                    unpack_key<D>(v.cell_key[c], v.g, ac);
-                    float u[D];
-                    band_coords<T, D>(v.pts[j], v.g, u);
-#pragma unroll
-                    for (int k = 0; k < D; ++k) {
-                        const float x = u[k] - (float)ac[k];
-                        lo2[k] = x * x;
-                        hi2[k] = (1.f - x) * (1.f - x);
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < D; ++k) lo2[k] = hi2[k] = 0.f;
-                }
-                // runs of equal cell id: lane L combines with L + o when both lie in one run
-                bool same[5];
-#pragma unroll
-                for (int t = 0; t < 5; ++t) {
-                    const uint32_t oc = __shfl_down_sync(0xffffffffu, c, 1 << t);
-                    same[t] = (lane + (1 << t) < 32) && oc == c;
-                }
-                const uint32_t prevc = __shfl_up_sync(0xffffffffu, c, 1);
-                const bool head = inr && (lane == 0 || prevc != c);
-#pragma unroll
-                for (int r = 0; r < ndir; ++r) {
-                    uint64_t val = valid ? (((uint64_t)__float_as_uint(rep_dist<D>(r, lo2, hi2)) << 32) | (uint32_t)j)
-                                         : ~0ull;
-#pragma unroll
-                    for (int t = 0; t < 5; ++t) {
-                        const uint64_t other = __shfl_down_sync(0xffffffffu, val, 1 << t);
-                        if (same[t] && other < val) val = other;
-                    }
-                    if (head && val != ~0ull)
-                        atomicMin((unsigned long long *)&v.reps[(uint64_t)c * ndir + r], (unsigned long long)val);
-                }
+                const float dd = rep_dist<D>(r, lo2, hi2);
+                if (dd < best[r]) { best[r] = dd; bidx[r] = j; }
             }
         }
+        const bool single = e - s <= kChunk;
+#pragma unroll
+        for (int r = 0; r < ndir; ++r) {
+            // warp minimum of the distance, then the lowest lane holding it supplies the index
+            float m = best[r];
+#pragma unroll
+            for (int o = 16; o; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            const unsigned holders = __ballot_sync(0xffffffffu, best[r] == m && bidx[r] != 0xffffffffu);
+            if (!holders) continue;
+            const uint32_t idx = __shfl_sync(0xffffffffu, bidx[r], __ffs(holders) - 1);
+            if (lane == 0) {
+                const uint64_t val = ((uint64_t)__float_as_uint(m) << 32) | idx;
+                if (single) v.reps[(uint64_t)A * ndir + r] = val;
+                else atomicMin((unsigned long long *)&v.reps[(uint64_t)A * ndir + r], (unsigned long long)val);
+            }
+        }
+    }
+}
+
+// Chunks of the representative-point pass: ceil(size / 256) for cells with core points.
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_rep_chunks(LowdView<T, D> v, uint32_t *__restrict__ nch) {
+    const uint32_t C = v.ctr->n_cells;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x)
+        nch[c] = v.cell_core[c] ? (v.cell_start[c + 1] - v.cell_start[c] + 255u) / 256u : 0u;
+}
+
+// chunk_cell[t] = the cell of chunk t (every cell writes its id into its chunk slots).
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_chunk_cells(LowdView<T, D> v, const uint32_t *__restrict__ nch,
+                                                    uint32_t *__restrict__ chunk_cell) {
+    const uint32_t C = v.ctr->n_cells;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x)
+        for (uint32_t i = 0; i < nch[c]; ++i) chunk_cell[v.chunk_off[c] + i] = c;
+}
+
+// Coordinates of every representative point, so that a merge test reads them directly.
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_rep_pts(LowdView<T, D> v) {
+    constexpr int ndir = RepDirs<D>::value;
+    const uint64_t total = (uint64_t)v.ctr->n_cells * ndir;
+    for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = (uint32_t)(idx / ndir);
+        if (!v.cell_core[c]) continue;
+        v.rep_pts[idx] = v.pts[(uint32_t)v.reps[idx]];
     }
 }
 
@@ -800,10 +821,67 @@ __device__ bool warp_core_pair(const LowdView<T, D> &v, uint32_t A, uint32_t B, 
     return false;
 }
 
+// First links between cells (Algorithm 3's merging condition, tested on the complementary
+// representative points): every cell with core points links to the first neighbour cell of
+// lower index whose representative pair is within eps.  One plain store per cell and every
+// link points to a lower index, so the links form a forest whose trees lie inside clusters;
+// pointer jumping flattens it and the merge passes then join the trees.
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_hook(LowdView<T, D> v, int n_all, int n_half) {
+    constexpr int ndir = RepDirs<D>::value;
+    const uint32_t C = v.ctr->n_cells;
+    const int lane = lane_id();
+    for (uint32_t A = global_warp(); A < C; A += total_warps()) {
+        if (!v.cell_core[A]) continue;
+        int ac[D];
+        unpack_key<D>(v.cell_key[A], v.g, ac);
+        bool linked = false;
+        for (int g0 = 0; g0 < n_all && !linked; g0 += 32) {
+            const int k = g0 + lane;
+            uint2 rg = k < n_all ? v.ranges[(uint64_t)A * n_all + k] : make_uint2(0u, 0u);
+            if (k == 0) rg.y = min(rg.y, A);          // own pencil: cells before A
+            else if (k < n_half) rg.y = rg.x;         // upper-half pencils hold only cells after A
+            const LaneRanges lr = lane_ranges(rg.x, rg.y);
+            for (uint32_t f0 = 0; f0 < lr.total && !linked; f0 += 32) {
+                const uint32_t f = f0 + lane;
+                const uint32_t B = flat_cell(lr, f < lr.total ? f : 0u);
+                bool hit = f < lr.total && v.cell_core[B];
+                if (hit) {
+                    int bc[D], delta[D];
+                    unpack_key<D>(v.cell_key[B], v.g, bc);
+#pragma unroll
+                    for (int i = 0; i < D; ++i) delta[i] = bc[i] - ac[i];
+                    const int ra = rep_dir_of<D>(delta);
+                    const int rb = rep_dir_complement<D>(ra);
+                    hit = within_eps<D>(v.rep_pts[(uint64_t)A * ndir + ra], v.rep_pts[(uint64_t)B * ndir + rb], v.g);
+                }
+                const unsigned hm = __ballot_sync(0xffffffffu, hit);
+                if (hm) {
+                    const uint32_t target = __shfl_sync(0xffffffffu, B, __ffs(hm) - 1);
+                    if (lane == 0) v.parent[A] = target;
+                    linked = true;
+                }
+            }
+        }
+    }
+}
+
+// One round of pointer jumping over cells with core points: parent[c] = parent[parent[c]].
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_jump(LowdView<T, D> v) {
+    const uint32_t C = v.ctr->n_cells;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+        if (!v.cell_core[c]) continue;
+        const uint32_t p = __ldcg(v.parent + c);
+        const uint32_t gp = __ldcg(v.parent + p);
+        if (gp != p) v.parent[c] = gp;
+    }
+}
+
 // Algorithm 3: merge every pair of neighbouring cells that hold core points and have a core
 // pair within eps.  Each unordered pair is visited once (upper half of the stencil).  Pass 0
-// takes the cells at Chebyshev offset 1, pass 1 the rest, so that most far pairs are already
-// joined through near ones when they are reached and are skipped.  The complementary
+// takes the cells at Chebyshev offset 1, pass 1 the rest, pass 2 all of them; a pair already in
+// one set (after the first links and pointer jumping, most pairs of a cluster) is skipped.  The complementary
 // representative points are tested first (Algorithm 3); a miss falls back to the exhaustive
 // core x core test.  Lanes walk the flattened list of candidate cells of one cell.
 template <typename T, int D>
@@ -834,16 +912,14 @@ __global__ void __launch_bounds__(256) k_merge(LowdView<T, D> v, int n_all, int 
                         delta[i] = bc[i] - ac[i];
                         cheb = max(cheb, abs(delta[i]));
                     }
-                    pending = (pass == 0) == (cheb <= 1);
+                    pending = pass == 2 || (pass == 0) == (cheb <= 1);
                 }
                 if (pending && uf_find(v.parent, A, v.ctr) == uf_find(v.parent, B, v.ctr)) pending = false;
                 if (pending) {
                     const int ra = rep_dir_of<D>(delta);
                     const int rb = rep_dir_complement<D>(ra);
-                    const uint32_t pa = (uint32_t)v.reps[(uint64_t)A * ndir + ra];
-                    const uint32_t pb = (uint32_t)v.reps[(uint64_t)B * ndir + rb];
                     ++rep_tests;
-                    if (within_eps<D>(v.pts[pa], v.pts[pb], v.g)) {
+                    if (within_eps<D>(v.rep_pts[(uint64_t)A * ndir + ra], v.rep_pts[(uint64_t)B * ndir + rb], v.g)) {
                         uf_union(v.parent, A, B, v.ctr);
                         pending = false;
                         ++rep_hits;
@@ -877,7 +953,7 @@ __global__ void __launch_bounds__(256) k_merge(LowdView<T, D> v, int n_all, int 
 // Flatten the union-find: parent[c] = root for every cell with core points; count roots.
 // The only writes are parent[c] = root, so every pointer ends at its root.
 template <typename T, int D>
-__global__ void __launch_bounds__(256) k_compress(LowdView<T, D> v) {
+__global__ void __launch_bounds__(256) k_compress(LowdView<T, D> v, int count_roots) {
     const uint32_t C = v.ctr->n_cells;
     uint32_t roots = 0;
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
@@ -887,7 +963,7 @@ __global__ void __launch_bounds__(256) k_compress(LowdView<T, D> v) {
         roots += (r == c);
     }
     for (int o = 16; o; o >>= 1) roots += __shfl_xor_sync(0xffffffffu, roots, o);
-    if (lane_id() == 0 && roots) atomicAdd(&v.ctr->n_clusters, roots);
+    if (count_roots && lane_id() == 0 && roots) atomicAdd(&v.ctr->n_clusters, roots);
 }
 
 // Canonical cluster id (Algorithm 4 numbers clusters in traversal order; the fixed rule
@@ -917,12 +993,25 @@ __global__ void __launch_bounds__(256) k_comp_min(LowdView<T, D> v) {
     if (lane == 0 && ncore) atomicAdd(&v.ctr->n_core, ncore);
 }
 
+// Cluster ids of core points, point-parallel (a cell can hold tens of thousands of points).
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_label_core(LowdView<T, D> v) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < v.g.n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        if (!v.core[j]) continue;
+        const uint32_t o = v.perm[j];
+        v.labels[o] = (int32_t)v.comp_min[v.parent[v.cell_of[j]]];
+        if (v.core_out) v.core_out[o] = 1;
+    }
+}
+
 // Algorithm 4 and Definition 5 with the canonical rule: core points take their cluster id;
 // a non-core point takes the smallest id among the clusters of the core points within eps
 // (the core points of its own cell qualify without a test, the cell's diagonal being at most
-// eps), else -1.  One warp per cell; neighbour cells are walked 32 at a time and a cell whose
-// box lies wholly within eps settles a point without per-point tests.  Writes labels in
-// input order.
+// eps), else -1.  One warp per cell; the neighbour cells that hold core points and a smaller
+// id are walked 32 at a time, one per lane; for each searching point a cell whose box lies
+// wholly within eps settles that point at once (warp minimum), one wholly beyond eps is
+// dropped, and the others are compared point by point.  Writes labels in input order.
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_labels(LowdView<T, D> v, int n_all) {
     const uint32_t C = v.ctr->n_cells;
@@ -930,6 +1019,7 @@ __global__ void __launch_bounds__(256) k_labels(LowdView<T, D> v, int n_all) {
     uint32_t noise = 0, chunks = 0;
     for (uint32_t A = global_warp(); A < C; A += total_warps()) {
         const uint32_t s = v.cell_start[A], e = v.cell_start[A + 1];
+        if (e - s >= v.g.min_pts) continue;  // dense: every point is core (k_label_core)
         const bool hasc = v.cell_core[A];
         const uint32_t clA = hasc ? v.comp_min[v.parent[A]] : kNoLabel;
         for (uint32_t base = s; base < e; base += 32) {
@@ -937,8 +1027,8 @@ __global__ void __launch_bounds__(256) k_labels(LowdView<T, D> v, int n_all) {
             const bool have = i < e;
             const bool isc = have && v.core[i];
             uint32_t best = clA;
-            const bool search = have && !isc;
-            if (__any_sync(0xffffffffu, search)) {
+            unsigned search = __ballot_sync(0xffffffffu, have && !isc);
+            if (search) {
                 const Pt<T, D> pa = have ? v.pts[i] : zero_pt<T, D>();
                 float ta[D];
                 band_coords<T, D>(pa, v.g, ta);
@@ -947,56 +1037,70 @@ __global__ void __launch_bounds__(256) k_labels(LowdView<T, D> v, int n_all) {
                     const uint2 rg = k < n_all ? v.ranges[(uint64_t)A * n_all + k] : make_uint2(0u, 0u);
                     const LaneRanges lr = lane_ranges(rg.x, rg.y);
                     for (uint32_t f0 = 0; f0 < lr.total; f0 += 32) {
-                        uint32_t worst = search ? best : 0u;
-                        for (int o = 16; o; o >>= 1) worst = max(worst, __shfl_xor_sync(0xffffffffu, worst, o));
                         const uint32_t f = f0 + lane;
                         const uint32_t B = flat_cell(lr, f < lr.total ? f : 0u);
-                        const bool vb = f < lr.total && B != A && v.cell_core[B];
-                        const uint32_t clB = vb ? v.comp_min[v.parent[B]] : kNoLabel;
-                        unsigned cm = __ballot_sync(0xffffffffu, vb && clB < worst);
-                        const uint64_t bkey = cm ? v.cell_key[B] : 0ull;
-                        while (cm) {
-                            const int t = __ffs(cm) - 1;
-                            cm &= cm - 1;
-                            const uint32_t B2 = __shfl_sync(0xffffffffu, B, t);
-                            const uint32_t cl2 = __shfl_sync(0xffffffffu, clB, t);
-                            int cb[D];
-                            unpack_key<D>(__shfl_sync(0xffffffffu, bkey, t), v.g, cb);
-                            bool want = search && best > cl2;
-                            if (want) {
-                                const int cls = box_class<D>(ta, cb, v.g);
-                                if (cls == 2) best = cl2;
-                                want = cls == 1;
-                            }
-                            const unsigned wm = __ballot_sync(0xffffffffu, want);
-                            if (!wm) continue;
-                            const uint32_t sb = v.cell_start[B2], eb = v.cell_start[B2 + 1];
-                            unsigned open = wm;
-                            for (uint32_t qb = sb; qb < eb && open; qb += 32) {
-                                const uint32_t q = qb + lane;
-                                const bool vq = q < eb && v.core[q];
-                                const Pt<T, D> pq = vq ? v.pts[q] : zero_pt<T, D>();
-                                ++chunks;
-                                unsigned rem = open;
-                                while (rem) {
-                                    const int jj = __ffs(rem) - 1;
-                                    rem &= rem - 1;
-                                    const Pt<T, D> aj = shfl_pt<T, D>(pa, jj);
-                                    if (__any_sync(0xffffffffu, vq && within_eps<D>(aj, pq, v.g))) {
-                                        if (lane == jj) best = cl2;
-                                        open &= ~(1u << jj);
+                        const bool okb = f < lr.total && B != A && v.cell_core[B];
+                        const uint32_t clB = okb ? v.comp_min[v.parent[B]] : kNoLabel;
+                        if (!__any_sync(0xffffffffu, okb)) continue;
+                        const uint32_t bs = okb ? v.cell_start[B] : 0u;
+                        const uint32_t be = okb ? v.cell_start[B + 1] : 0u;
+                        int cb[D];
+                        unpack_key<D>(okb ? v.cell_key[B] : 0ull, v.g, cb);
+                        unsigned rem = search;
+                        while (rem) {
+                            const int jj = __ffs(rem) - 1;
+                            rem &= rem - 1;
+                            uint32_t bj = __shfl_sync(0xffffffffu, best, jj);
+                            const bool cand = okb && clB < bj;
+                            if (!__any_sync(0xffffffffu, cand)) continue;
+                            float tj[D];
+#pragma unroll
+                            for (int k2 = 0; k2 < D; ++k2) tj[k2] = __shfl_sync(0xffffffffu, ta[k2], jj);
+                            const int cls = cand ? box_class<D>(tj, cb, v.g) : 0;
+                            uint32_t m2 = cls == 2 ? clB : kNoLabel;
+#pragma unroll
+                            for (int o = 16; o; o >>= 1) m2 = min(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+                            bj = min(bj, m2);
+                            unsigned partial = __ballot_sync(0xffffffffu, cls == 1 && clB < bj);
+                            if (partial) {
+                                const Pt<T, D> aj = shfl_pt<T, D>(pa, jj);
+                                while (partial) {
+                                    const int t = __ffs(partial) - 1;
+                                    partial &= partial - 1;
+                                    const uint32_t cl2 = __shfl_sync(0xffffffffu, clB, t);
+                                    if (cl2 >= bj) continue;
+                                    const uint32_t ps = __shfl_sync(0xffffffffu, bs, t);
+                                    const uint32_t pe = __shfl_sync(0xffffffffu, be, t);
+                                    for (uint32_t qb = ps; qb < pe; qb += 128) {
+                                        Pt<T, D> q4[4];
+                                        bool c4[4];
+#pragma unroll
+                                        for (int u = 0; u < 4; ++u) {
+                                            const uint32_t q = qb + 32 * u + lane;
+                                            c4[u] = q < pe && v.core[q];
+                                            q4[u] = q < pe ? v.pts[q] : zero_pt<T, D>();
+                                        }
+                                        bool hit = false;
+#pragma unroll
+                                        for (int u = 0; u < 4; ++u) hit |= c4[u] && within_eps<D>(aj, q4[u], v.g);
+                                        ++chunks;
+                                        if (__any_sync(0xffffffffu, hit)) {
+                                            bj = cl2;
+                                            break;
+                                        }
                                     }
                                 }
                             }
+                            if (lane == jj) best = bj;
                         }
                     }
                 }
             }
-            if (have) {
+            if (have && !isc) {
                 const int32_t lab = best == kNoLabel ? -1 : (int32_t)best;
                 const uint32_t o = v.perm[i];
                 v.labels[o] = lab;
-                if (v.core_out) v.core_out[o] = isc ? 1 : 0;
+                if (v.core_out) v.core_out[o] = 0;
                 noise += lab < 0;
             }
         }

@@ -264,7 +264,7 @@ int run_lowd(const RunArgs &a) {
     mark(0);
     cudaMemsetAsync(ctr, 0, sizeof(DevCounters), s);
     cudaMemsetAsync(ctr->minmax_enc, 0xff, sizeof(uint64_t) * kMaxD, s);
-    k_minmax<T, D><<<gpts, 256, 0, s>>>((const T *)a.d_points, n, ctr);
+    k_minmax<T, D><<<grid_for(n, 256, sms, 2), 256, 0, s>>>((const T *)a.d_points, n, ctr);
     ++launches;
     if (cudaMemcpyAsync(h, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) { rc = HCA_ECUDA; goto out; }
@@ -281,8 +281,10 @@ int run_lowd(const RunArgs &a) {
         if (rc) goto out;
         rc = make_stencil(D, a.eps, 1.0 / g.inv_side, tau, st);
         if (rc) goto out;
-        // neighbour ranges: one (lo, hi) pair per cell and stencil pencil
-        if (pool_alloc(&ws_ranges, sizeof(uint2) * (size_t)n * st.n_all, s) != cudaSuccess || !ws_ranges) {
+        // neighbour ranges (one (lo, hi) pair per cell and stencil pencil) and the coordinates
+        // of the representative points (ndir per cell)
+        if (pool_alloc(&ws_ranges, sizeof(uint2) * (size_t)n * st.n_all + sizeof(Pt<T, D>) * (size_t)n * ndir + 256,
+                       s) != cudaSuccess || !ws_ranges) {
             rc = HCA_ENOMEM;
             goto out;
         }
@@ -359,6 +361,7 @@ int run_lowd(const RunArgs &a) {
     v.reps = (uint64_t *)(b + o_reps);
     v.comp_min = (uint32_t *)(b + o_cmin);
     v.ranges = (uint2 *)ws_ranges;
+    v.rep_pts = (Pt<T, D> *)((char *)ws_ranges + align_up(sizeof(uint2) * (size_t)n * st.n_all));
     v.labels = a.d_labels;
     v.core_out = a.d_core;
     v.ctr = ctr;
@@ -371,19 +374,32 @@ int run_lowd(const RunArgs &a) {
     ++launches;
     mark(6);
     // ---- Algorithm 2: representative points ----
-    k_reps<T, D><<<grid_for((n + 255) / 256, 8, sms, 16), 256, 0, s>>>(v);
-    ++launches;
+    {
+        uint32_t *nch = (uint32_t *)(b + o_pflags), *choff = (uint32_t *)(b + o_pexcl);  // reused
+        k_rep_chunks<T, D><<<gpts, 256, 0, s>>>(v, nch);
+        exclusive_scan_u32(nch, choff, n, &ctr->n_cells, &ctr->n_chunks, (uint32_t *)(b + o_part), s, &launches);
+        v.chunk_off = choff;
+        v.chunk_cell = (uint32_t *)(b + o_excl);  // reused: free after the cell pass
+        k_chunk_cells<T, D><<<gpts, 256, 0, s>>>(v, nch, v.chunk_cell);
+        ++launches;
+        k_reps<T, D><<<grid_for(n / 256 + 1 + n / 8, 8, sms, 16), 256, 0, s>>>(v);
+        k_rep_pts<T, D><<<grid_for(n * (int64_t)ndir, 256, sms, 8), 256, 0, s>>>(v);
+        launches += 3;
+    }
     mark(7);
-    // ---- Algorithm 3: merge neighbouring cells (near offsets, then far ones) ----
-    k_merge<T, D><<<gwarp, 256, 0, s>>>(v, st.n_all, st.n_half, 0);
-    k_merge<T, D><<<gwarp, 256, 0, s>>>(v, st.n_all, st.n_half, 1);
-    k_compress<T, D><<<gpts, 256, 0, s>>>(v);
-    launches += 3;
+    // ---- Algorithm 3: first links, pointer jumping, then one merge pass over every pair ----
+    k_hook<T, D><<<gwarp, 256, 0, s>>>(v, st.n_all, st.n_half);
+    for (int r = 0; r < 5; ++r) k_jump<T, D><<<gpts, 256, 0, s>>>(v);
+    launches += 6;
+    k_merge<T, D><<<gwarp, 256, 0, s>>>(v, st.n_all, st.n_half, 2);
+    k_compress<T, D><<<gpts, 256, 0, s>>>(v, 1);
+    launches += 2;
     mark(8);
     // ---- Algorithm 4: cluster ids, border and noise ----
     k_comp_min<T, D><<<gpts, 256, 0, s>>>(v);
+    k_label_core<T, D><<<gpts, 256, 0, s>>>(v);
     k_labels<T, D><<<gwarp, 256, 0, s>>>(v, st.n_all);
-    launches += 2;
+    launches += 3;
     mark(9);
     if (cudaGetLastError() != cudaSuccess) { rc = HCA_ECUDA; goto out; }
     if (cudaMemcpyAsync(h, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

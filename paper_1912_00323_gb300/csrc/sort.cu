@@ -1,6 +1,6 @@
 // LSD radix sort of (key, uint32 value) pairs, 8 bits per pass.
 //
-// Each pass: (1) every block counts the digits of its tile of 4096 keys into a per-block
+// Each pass: (1) every block counts the digits of its tile of 2048 keys into a per-block
 // histogram, stored digit-major; (2) an exclusive scan of that array gives every
 // (digit, block) its first output position; (3) every block re-reads its tile, ranks each
 // key stably among the keys of its tile with the same digit (warp match + per-warp digit
@@ -15,7 +15,7 @@ namespace {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortItems = 16;  // per lane: a warp covers 512 consecutive keys
+constexpr int kSortItems = 8;   // per lane: a warp covers 256 consecutive keys
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kRadix = 256;
 
@@ -41,18 +41,27 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const K *__restrict_
     for (int i = threadIdx.x; i < kRadix; i += kSortThreads) hist[(int64_t)i * nb + blockIdx.x] = h[i];
 }
 
+// Scatter of one pass.  Keys are ranked stably inside the tile, written to shared memory in
+// digit order, and then copied out so that consecutive threads write consecutive positions of
+// each digit's output run (coalesced stores).
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
     const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, K *__restrict__ keys_out,
     uint32_t *__restrict__ vals_out, int64_t n, int shift, int mask_bits,
     const uint32_t *__restrict__ offsets, int nb) {
-    __shared__ uint32_t whist[kSortWarps][kRadix];
+    extern __shared__ __align__(16) unsigned char sm[];
+    uint32_t(*whist)[kRadix] = reinterpret_cast<uint32_t(*)[kRadix]>(sm);  // [warps][digits]
+    uint32_t *lstart = reinterpret_cast<uint32_t *>(sm) + kSortWarps * kRadix;
+    uint32_t *goff = lstart + kRadix;
+    K *skeys = reinterpret_cast<K *>(goff + kRadix);
+    uint32_t *svals = reinterpret_cast<uint32_t *>(skeys + kSortTile);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t mask = (1u << mask_bits) - 1u;
     for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&whist[0][0])[i] = 0;
     __syncthreads();
 
-    const int64_t wbase = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * (32 * kSortItems);
+    const int64_t tbase = (int64_t)blockIdx.x * kSortTile;
+    const int64_t wbase = tbase + (int64_t)warp * (32 * kSortItems);
     K k[kSortItems];
     uint32_t v[kSortItems];
     uint32_t rank[kSortItems];
@@ -71,27 +80,45 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
         rank[r] = before + __popc(peers & ((1u << lane) - 1u));
     }
     __syncthreads();
-    // exclusive scan of the per-warp counts across warps, per digit, plus the global offset
-    for (int dg = threadIdx.x; dg < kRadix; dg += kSortThreads) {
-        uint32_t sum = offsets[(int64_t)dg * nb + blockIdx.x];
+    // per digit: exclusive prefix across warps, the tile's count, and the global offset
+    uint32_t total = 0;
+    {
+        const int dg = threadIdx.x;  // kSortThreads == kRadix
 #pragma unroll
         for (int w = 0; w < kSortWarps; ++w) {
-            uint32_t t = whist[w][dg];
-            whist[w][dg] = sum;
-            sum += t;
+            const uint32_t t = whist[w][dg];
+            whist[w][dg] = total;
+            total += t;
         }
+        goff[dg] = offsets[(int64_t)dg * nb + blockIdx.x];
     }
+    uint32_t tile_count;
+    const uint32_t ls = block_exclusive_scan<kSortThreads>(total, &tile_count);
+    lstart[threadIdx.x] = ls;
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const int64_t i = wbase + r * 32 + lane;
         if (i < n) {
             const uint32_t dg = (uint32_t)(k[r] >> shift) & mask;
-            const uint32_t pos = whist[warp][dg] + rank[r];
-            keys_out[pos] = k[r];
-            vals_out[pos] = v[r];
+            const uint32_t lpos = lstart[dg] + whist[warp][dg] + rank[r];
+            skeys[lpos] = k[r];
+            svals[lpos] = v[r];
         }
     }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < tile_count; i += kSortThreads) {
+        const K key = skeys[i];
+        const uint32_t dg = (uint32_t)(key >> shift) & mask;
+        const uint32_t gpos = goff[dg] + (i - lstart[dg]);
+        keys_out[gpos] = key;
+        vals_out[gpos] = svals[i];
+    }
+}
+
+template <typename K>
+constexpr size_t scatter_smem() {
+    return sizeof(uint32_t) * (kSortWarps * kRadix + 2 * kRadix) + (sizeof(K) + sizeof(uint32_t)) * kSortTile;
 }
 
 }  // namespace
@@ -108,6 +135,9 @@ bool radix_sort_pairs(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt, 
                       cudaStream_t s, int *launches) {
     if (n <= 1 || end_bit <= begin_bit) return false;
     const int nb = (int)((n + kSortTile - 1) / kSortTile);
+    static_assert(kSortThreads == kRadix, "one thread per digit in the scatter's digit scan");
+    if (scatter_smem<K>() > 48 * 1024)
+        cudaFuncSetAttribute(k_sort_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scatter_smem<K>());
     bool flipped = false;
     K *kin = keys, *kout = keys_alt;
     uint32_t *vin = vals, *vout = vals_alt;
@@ -115,7 +145,7 @@ bool radix_sort_pairs(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt, 
         const int bits = (end_bit - shift) < 8 ? (end_bit - shift) : 8;
         k_sort_hist<K><<<nb, kSortThreads, 0, s>>>(kin, n, shift, bits, hist, nb);
         exclusive_scan_u32(hist, hist, (int64_t)nb * kRadix, nullptr, nullptr, partials, s, launches);
-        k_sort_scatter<K><<<nb, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift, bits, hist, nb);
+        k_sort_scatter<K><<<nb, kSortThreads, scatter_smem<K>(), s>>>(kin, vin, kout, vout, n, shift, bits, hist, nb);
         if (launches) *launches += 2;
         K *tk = kin; kin = kout; kout = tk;
         uint32_t *tv = vin; vin = vout; vout = tv;

@@ -19,8 +19,8 @@ namespace {
 
 constexpr int64_t kMaxPairs = HCA_SORT_NOALLOC_MAX_PAIRS;
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-// histogram entries for kMaxPairs (one 256-digit row per 4096-key tile)
-constexpr size_t kHistElems = ((kMaxPairs + 4095) / 4096) * 256;
+// histogram entries for kMaxPairs (one 256-digit row per 2048-key tile)
+constexpr size_t kHistElems = ((kMaxPairs + 2047) / 2048) * 256;
 constexpr size_t kPartElems = ((kMaxPairs > (int64_t)kHistElems ? kMaxPairs : (int64_t)kHistElems) + 2047) / 2048 + 2;
 constexpr size_t kOffVals = align256(sizeof(uint64_t) * kMaxPairs);
 constexpr size_t kOffHist = kOffVals + align256(sizeof(uint32_t) * kMaxPairs);
