@@ -155,7 +155,7 @@ HCA_API int hca_radix_sort_pairs(void *d_keys, uint32_t *d_vals, int64_t n, int3
  * owns all device memory, code that must not risk the synchronisation cudaMalloc / cudaFree
  * can cause).  Same arguments, result and stream semantics as hca_radix_sort_pairs.
  *   n  at most HCA_SORT_NOALLOC_MAX_PAIRS (2^18); larger n returns HCA_ETOOLARGE.
- * Scratch: a fixed array of about 3.1 MiB inside the library (a __device__ variable), held on
+ * Scratch: a fixed array of about 3.3 MiB inside the library (a __device__ variable), held on
  * every GPU that loads the library until the process exits.  The first call on a device looks
  * up that array's device address (cudaGetSymbolAddress) and caches it; make that first call
  * before any stream capture.  Calls no cudaMalloc, cudaFree or other allocating routine.

@@ -197,9 +197,13 @@ extern "C" int hca_radix_sort_pairs(void *d_keys, uint32_t *d_vals, int64_t n, i
             cudaMemcpyAsync(d_vals, valt, (size_t)n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             rc = HCA_ECUDA;
     }
+    uint32_t status = 0;
+    if (cudaMemcpyAsync(&status, sort_status_word(h, n), sizeof(status), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        rc = HCA_ECUDA;
     if (cudaGetLastError() != cudaSuccess) rc = HCA_ECUDA;
     pool_free(ws, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) rc = HCA_ECUDA;
+    if (rc == HCA_OK && status) rc = HCA_EDEVICE;
     return rc;
 }
 

@@ -35,6 +35,7 @@ struct DevCounters {
     uint32_t n_chunks;     // 32-point chunks of the coarse cells (high-dimensional path)
     uint32_t pad[2];
     unsigned long long work[8];  // work counters (see hca_stats)
+    uint32_t digit_counts[8 * 256];  // radix digit counts per pass, filled while binning
 };
 
 // Grid of hypercubes (Algorithm 1) and everything a kernel needs to bin, pack and compare.
@@ -98,12 +99,18 @@ void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t m_max, const 
 
 // LSD radix sort of (key, value) pairs by bits [begin_bit, end_bit), 8 bits per pass.
 // Ping-pongs between (keys, vals) and (keys_alt, vals_alt); returns true when the sorted
-// result ends up in the alternate buffers.  hist: sort_hist_size(n) uint32 of scratch.
+// result ends up in the alternate buffers.  hist: sort_hist_size(n) uint32 of scratch
+// (8-byte aligned; cleared by the sort itself).  A bounded look-back wait that ran out sets
+// bit 2 of *err_out (device word; NULL: the status word inside hist, sort_status_word).
 size_t sort_hist_size(int64_t n);
+uint32_t *sort_status_word(uint32_t *hist, int64_t n);
+// digit_counts (optional, device): counts of every 8-bit digit of every pass, [pass][256],
+// already computed by the caller.
 template <typename K>
 bool radix_sort_pairs(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt, int64_t n,
                       int begin_bit, int end_bit, uint32_t *hist, uint32_t *partials,
-                      cudaStream_t s, int *launches);
+                      cudaStream_t s, int *launches, uint32_t *err_out = nullptr,
+                      const uint32_t *digit_counts = nullptr);
 
 // Pool allocation (stream ordered) used by api.cu and the pipelines.
 cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s);

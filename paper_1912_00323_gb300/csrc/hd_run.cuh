@@ -175,7 +175,7 @@ int run_hd(const RunArgs &a) {
             uint32_t *ka = (uint32_t *)(b + o_ka), *kb = (uint32_t *)(b + o_kb);
             k_bin_proj<T, uint32_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, d, sel, g, ka, ia);
             mark(2);
-            flipped = radix_sort_pairs<uint32_t>(ka, ia, kb, ib, n, 0, g.key_bits, hist, part, s, &launches);
+            flipped = radix_sort_pairs<uint32_t>(ka, ia, kb, ib, n, 0, g.key_bits, hist, part, s, &launches, &ctr->status);
             mark(3);
             k_gather_hd<T, DP, uint32_t><<<grid_for(n, 8, sms, 16), 256, 0, s>>>(
                 (const T *)a.d_points, d, flipped ? kb : ka, flipped ? ib : ia, n, (T *)(b + o_pts),
@@ -184,7 +184,7 @@ int run_hd(const RunArgs &a) {
             uint64_t *ka = (uint64_t *)(b + o_ka), *kb = (uint64_t *)(b + o_kb);
             k_bin_proj<T, uint64_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, d, sel, g, ka, ia);
             mark(2);
-            flipped = radix_sort_pairs<uint64_t>(ka, ia, kb, ib, n, 0, g.key_bits, hist, part, s, &launches);
+            flipped = radix_sort_pairs<uint64_t>(ka, ia, kb, ib, n, 0, g.key_bits, hist, part, s, &launches, &ctr->status);
             mark(3);
             k_gather_hd<T, DP, uint64_t><<<grid_for(n, 8, sms, 16), 256, 0, s>>>(
                 (const T *)a.d_points, d, flipped ? kb : ka, flipped ? ib : ia, n, (T *)(b + o_pts),

@@ -429,7 +429,13 @@ __global__ void __launch_bounds__(256) k_minmax(const T *__restrict__ in, int64_
 // key whose order is lexicographic in (c_0, ..., c_{d-1}).
 template <typename T, int D, typename K>
 __global__ void __launch_bounds__(256) k_bin(const T *__restrict__ in, GridParams g,
-                                            K *__restrict__ keys, uint32_t *__restrict__ idx) {
+                                            K *__restrict__ keys, uint32_t *__restrict__ idx,
+                                            uint32_t *__restrict__ digit_counts) {
+    // digit counts of every radix pass, for the sort that follows
+    __shared__ uint32_t h[8][256];
+    const int passes = (g.key_bits + 7) / 8;
+    for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+    __syncthreads();
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < g.n;
          j += (int64_t)gridDim.x * blockDim.x) {
         uint64_t key = 0;
@@ -449,6 +455,12 @@ __global__ void __launch_bounds__(256) k_bin(const T *__restrict__ in, GridParam
         }
         keys[j] = (K)key;
         idx[j] = (uint32_t)j;
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(uint32_t)(key >> (8 * p)) & 0xffu], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
+        const uint32_t c = (&h[0][0])[i];
+        if (c) atomicAdd(&digit_counts[i], c);
     }
 }
 

@@ -297,20 +297,20 @@ int run_lowd(const RunArgs &a) {
         const bool use32 = g.key_bits <= 32;
         if (use32) {
             uint32_t *ka = (uint32_t *)(b + o_ka), *kb = (uint32_t *)(b + o_kb);
-            k_bin<T, D, uint32_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, g, ka, ia);
+            k_bin<T, D, uint32_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, g, ka, ia, ctr->digit_counts);
             ++launches;
             mark(2);
-            flipped = radix_sort_pairs<uint32_t>(ka, ia, kb, ib, n, 0, g.key_bits, hist, part, s, &launches);
+            flipped = radix_sort_pairs<uint32_t>(ka, ia, kb, ib, n, 0, g.key_bits, hist, part, s, &launches, &ctr->status, ctr->digit_counts);
             mark(3);
             k_gather<T, D, uint32_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, flipped ? kb : ka,
                                                           flipped ? ib : ia, n, (Pt<T, D> *)(b + o_pts),
                                                           (uint32_t *)(b + o_flags));
         } else {
             uint64_t *ka = (uint64_t *)(b + o_ka), *kb = (uint64_t *)(b + o_kb);
-            k_bin<T, D, uint64_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, g, ka, ia);
+            k_bin<T, D, uint64_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, g, ka, ia, ctr->digit_counts);
             ++launches;
             mark(2);
-            flipped = radix_sort_pairs<uint64_t>(ka, ia, kb, ib, n, 0, g.key_bits, hist, part, s, &launches);
+            flipped = radix_sort_pairs<uint64_t>(ka, ia, kb, ib, n, 0, g.key_bits, hist, part, s, &launches, &ctr->status, ctr->digit_counts);
             mark(3);
             k_gather<T, D, uint64_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, flipped ? kb : ka,
                                                           flipped ? ib : ia, n, (Pt<T, D> *)(b + o_pts),

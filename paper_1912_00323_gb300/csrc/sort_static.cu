@@ -7,7 +7,7 @@
 // entry point takes the caller's keys and values and uses only the array below.
 //
 // The array is a file-scope __device__ variable: every GPU on which the library is loaded
-// holds its HCA_SORT_NOALLOC_MAX_PAIRS * 12 bytes (plus histogram space, about 3.1 MiB in all)
+// holds its HCA_SORT_NOALLOC_MAX_PAIRS * 12 bytes (plus look-back space, about 3.3 MiB in all)
 // until the process exits.  In host code its name is only a stand-in: the device address is
 // looked up once per device with cudaGetSymbolAddress, by the first call on that device.
 #include <mutex>
@@ -19,8 +19,9 @@ namespace {
 
 constexpr int64_t kMaxPairs = HCA_SORT_NOALLOC_MAX_PAIRS;
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-// histogram entries for kMaxPairs (one 256-digit row per 2048-key tile)
-constexpr size_t kHistElems = ((kMaxPairs + 2047) / 2048) * 256;
+// sort scratch words for kMaxPairs: look-back words (2 per 2048-key tile and digit), digit
+// counts of up to 8 passes, tickets and a status word
+constexpr size_t kHistElems = 2 * ((kMaxPairs + 2047) / 2048) * 256 + 8 * 256 + 10;
 constexpr size_t kPartElems = ((kMaxPairs > (int64_t)kHistElems ? kMaxPairs : (int64_t)kHistElems) + 2047) / 2048 + 2;
 constexpr size_t kOffVals = align256(sizeof(uint64_t) * kMaxPairs);
 constexpr size_t kOffHist = kOffVals + align256(sizeof(uint32_t) * kMaxPairs);
@@ -74,8 +75,9 @@ extern "C" int hca_radix_sort_pairs_noalloc(void *d_keys, uint32_t *d_vals, int6
     uint32_t *valt = (uint32_t *)(b + kOffVals);
     uint32_t *hist = (uint32_t *)(b + kOffHist);
     uint32_t *part = (uint32_t *)(b + kOffPart);
-    // Every scratch word a pass reads is written earlier in the same pass (histograms, tile
-    // sums, alternate buffers), so nothing left by a previous call needs clearing.
+    // The sort clears its counters, tickets and look-back words itself at the start of every
+    // call; every other scratch word is written before it is read, so nothing left by an
+    // earlier call is used.
     bool flipped;
     if (key_bytes == 4)
         flipped = radix_sort_pairs<uint32_t>((uint32_t *)d_keys, d_vals, (uint32_t *)b, valt, n,
@@ -89,7 +91,11 @@ extern "C" int hca_radix_sort_pairs_noalloc(void *d_keys, uint32_t *d_vals, int6
             cudaMemcpyAsync(d_vals, valt, (size_t)n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             rc = HCA_ECUDA;
     }
+    uint32_t status = 0;
+    if (cudaMemcpyAsync(&status, sort_status_word(hist, n), sizeof(status), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        rc = HCA_ECUDA;
     if (cudaGetLastError() != cudaSuccess) rc = HCA_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) rc = HCA_ECUDA;
+    if (rc == HCA_OK && status) rc = HCA_EDEVICE;
     return rc;
 }
