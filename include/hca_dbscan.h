@@ -137,6 +137,24 @@ HCA_API int hca_dbscan_device_ex(const void *d_points, int32_t dtype, int64_t n,
                          hca_stats *stats, int32_t flags);
 
 /*
+ * hca_dbscan_batched -- cluster many independent point sets in one call.
+ *   d_points  device, the sets' points concatenated: set s is rows [offsets[s], offsets[s+1])
+ *             of a row-major (offsets[n_sets] x d) array of `dtype`.
+ *   offsets   host, n_sets + 1 non-decreasing int64, offsets[0] = 0; empty sets are allowed.
+ *   eps, min_pts  host, n_sets values: each set's own parameters (Definitions 1-2).
+ *   d_labels  device, offsets[n_sets] int32: each set's labels, with cluster ids that are
+ *             indices WITHIN the set (the same values a separate call on that set returns).
+ *   d_core    device, optional core flags; stats host, optional (totals over the sets).
+ * For 1 <= d <= 4 all sets go through one pipeline: the set id sits above the cell key, so
+ * one sort, one pencil hash and one launch of each kernel serve every set, and cells never
+ * mix sets.  For d >= 5 the sets are clustered one after another.  Returns after the labels
+ * are complete on `stream`.  One d per call: group sets of different d into separate calls.
+ */
+HCA_API int hca_dbscan_batched(const void *d_points, int32_t dtype, int32_t n_sets, const int64_t *offsets,
+                               int32_t d, const double *eps, const int32_t *min_pts, int32_t *d_labels,
+                               uint8_t *d_core, void *stream, hca_stats *stats, int32_t flags);
+
+/*
  * hca_radix_sort_pairs -- stable ascending sort of (key, value) pairs on the device, by key
  * bits [begin_bit, end_bit) (the pre-sort of Sec. 2 is done with this sort on cell keys).
  *   d_keys     device, n keys of key_bytes (4 or 8) bytes, 8-byte aligned; sorted in place.

@@ -7,6 +7,7 @@ CPU fallback: if the library is missing or cannot be loaded, every call raises.
 Names follow include/hca_dbscan.h:
   hca_dbscan(points, eps, min_pts)               host numpy array in, int32 labels out
   hca_dbscan_device(points, eps, min_pts, ...)   CUDA torch tensor in, CUDA labels out
+  hca_dbscan_batched(points, offsets, eps, min_pts)  many sets, one call
   hca_radix_sort_pairs(keys, vals, begin, end)   in-place device sort (the Sec. 2 pre-sort)
   hca_strerror(code), hca_version()
 """
@@ -25,8 +26,8 @@ HCA_OK, HCA_EINVAL, HCA_ENOMEM, HCA_ECUDA, HCA_ERANGE, HCA_ENOTIMPL, HCA_EDEVICE
 HCA_FLAG_TIMING, HCA_FLAG_FP64_ONLY = 1, 2
 STAGES = ("minmax", "bin", "sort", "cells", "hash", "core", "reps", "merge", "labels")
 
-ABI_FUNCTIONS = ("hca_dbscan", "hca_dbscan_device", "hca_dbscan_device_ex", "hca_radix_sort_pairs",
-                 "hca_strerror", "hca_version")
+ABI_FUNCTIONS = ("hca_dbscan", "hca_dbscan_device", "hca_dbscan_device_ex", "hca_dbscan_batched",
+                 "hca_radix_sort_pairs", "hca_strerror", "hca_version")
 
 
 class HcaStats(ctypes.Structure):
@@ -70,6 +71,9 @@ def load():
     lib.hca_dbscan_device_ex.argtypes = [vp, i32, i64, i32, dbl, i32, vp, vp, vp,
                                          ctypes.POINTER(HcaStats), i32]
     lib.hca_radix_sort_pairs.argtypes = [vp, vp, i64, i32, i32, i32, vp]
+    lib.hca_dbscan_batched.argtypes = [vp, i32, i32, vp, i32, vp, vp, vp, vp, vp,
+                                       ctypes.POINTER(HcaStats), i32]
+    lib.hca_dbscan_batched.restype = ctypes.c_int
     lib.hca_strerror.argtypes = [ctypes.c_int]
     lib.hca_strerror.restype = ctypes.c_char_p
     lib.hca_version.restype = i32
@@ -154,6 +158,38 @@ def hca_dbscan_device(points, eps: float, min_pts: int, labels=None, core=None, 
                                   _stream_ptr(stream), ctypes.byref(st), flags)
     if rc != HCA_OK:
         raise HcaError(rc, "hca_dbscan_device")
+    if stats or timing:
+        return labels, st.as_dict()
+    return labels
+
+
+def hca_dbscan_batched(points, offsets, eps, min_pts, labels=None, core=None, stream=None,
+                       stats: bool = False, timing: bool = False, fp64_only: bool = False):
+    """Cluster the sets points[offsets[s]:offsets[s+1]] (a CUDA tensor (N, d)), each with its
+    own eps[s] and min_pts[s] (host sequences).  Labels are per set (ids are indices within the
+    set).  Returns the label tensor, or (labels, stats_dict) when stats or timing is requested."""
+    import torch
+    lib = load()
+    if not points.is_cuda:
+        raise ValueError("hca_dbscan_batched takes a CUDA tensor")
+    pts = points.contiguous()
+    n = pts.shape[0]
+    d = pts.shape[1] if pts.dim() == 2 else 1
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    e = np.ascontiguousarray(np.asarray(eps, dtype=np.float64))
+    m = np.ascontiguousarray(np.asarray(min_pts, dtype=np.int32))
+    if off.ndim != 1 or len(off) != len(e) + 1 or len(e) != len(m) or off[-1] != n:
+        raise ValueError("offsets must have n_sets + 1 entries ending at len(points); eps, min_pts n_sets")
+    if labels is None:
+        labels = torch.empty(n, dtype=torch.int32, device=pts.device)
+    flags = (HCA_FLAG_TIMING if timing else 0) | (HCA_FLAG_FP64_ONLY if fp64_only else 0)
+    st = HcaStats()
+    rc = lib.hca_dbscan_batched(pts.data_ptr(), _dtype_code(pts.dtype), len(e), off.ctypes.data, d,
+                                e.ctypes.data, m.ctypes.data, labels.data_ptr(),
+                                core.data_ptr() if core is not None else None, _stream_ptr(stream),
+                                ctypes.byref(st), flags)
+    if rc != HCA_OK:
+        raise HcaError(rc, "hca_dbscan_batched")
     if stats or timing:
         return labels, st.as_dict()
     return labels

@@ -131,6 +131,65 @@ extern "C" int hca_dbscan_device_ex(const void *d_points, int32_t dtype, int64_t
     return dispatch(a, dtype);
 }
 
+extern "C" int hca_dbscan_batched(const void *d_points, int32_t dtype, int32_t n_sets, const int64_t *offsets,
+                                  int32_t d, const double *eps, const int32_t *min_pts, int32_t *d_labels,
+                                  uint8_t *d_core, void *stream, hca_stats *stats, int32_t flags) {
+    if (n_sets < 1 || !offsets || !eps || !min_pts) return HCA_EINVAL;
+    if (offsets[0] != 0) return HCA_EINVAL;
+    for (int32_t i = 0; i < n_sets; ++i) {
+        if (offsets[i + 1] < offsets[i]) return HCA_EINVAL;
+        if (!finite_positive(eps[i]) || min_pts[i] < 1) return HCA_EINVAL;
+    }
+    const int64_t n = offsets[n_sets];
+    int rc = check_common(d_points, dtype, n, d, 1.0, 1, d_labels);
+    if (rc) return rc;
+    if (stats) {
+        hca_stats z = {};
+        *stats = z;
+    }
+    if (n == 0) return HCA_OK;
+    const size_t esz = dtype == HCA_F32 ? 4 : 8;
+    if (((uintptr_t)d_points) % esz || ((uintptr_t)d_labels) % 4) return HCA_EINVAL;
+    if (d <= kMaxD) {
+        RunArgs a;
+        a.d_points = d_points;
+        a.n = n;
+        a.d = d;
+        a.eps = eps[0];
+        a.min_pts = min_pts[0];
+        a.d_labels = d_labels;
+        a.d_core = d_core;
+        a.stream = (cudaStream_t)stream;
+        a.stats = stats;
+        a.flags = flags;
+        a.nsets = n_sets;
+        a.h_off = offsets;
+        a.h_eps = eps;
+        a.h_minpts = min_pts;
+        return dispatch(a, dtype);
+    }
+    // d >= 5: one call per set, totals summed into stats
+    for (int32_t i = 0; i < n_sets; ++i) {
+        const int64_t m = offsets[i + 1] - offsets[i];
+        if (m == 0) continue;
+        hca_stats one = {};
+        rc = hca_dbscan_device_ex((const char *)d_points + (size_t)offsets[i] * d * esz, dtype, m, d, eps[i],
+                                  min_pts[i], d_labels + offsets[i], d_core ? d_core + offsets[i] : nullptr,
+                                  stream, stats ? &one : nullptr, flags & ~HCA_FLAG_TIMING);
+        if (rc) return rc;
+        if (stats) {
+            stats->n_points += one.n_points;
+            stats->n_cells += one.n_cells;
+            stats->n_pencils += one.n_pencils;
+            stats->n_core_points += one.n_core_points;
+            stats->n_clusters += one.n_clusters;
+            stats->n_noise += one.n_noise;
+            stats->kernel_launches += one.kernel_launches;
+        }
+    }
+    return HCA_OK;
+}
+
 extern "C" int hca_dbscan_device(const void *d_points, int32_t dtype, int64_t n, int32_t d, double eps,
                                  int32_t min_pts, int32_t *d_labels, void *stream) {
     return hca_dbscan_device_ex(d_points, dtype, n, d, eps, min_pts, d_labels, nullptr, stream, nullptr, 0);

@@ -130,6 +130,11 @@ struct RunArgs {
     cudaStream_t stream;
     hca_stats *stats;
     int flags;
+    // batched calls (n_sets > 0): sets of consecutive points, each with its own eps and MINPTS
+    int nsets = 0;
+    const int64_t *h_off = nullptr;      // host, nsets + 1 point offsets
+    const double *h_eps = nullptr;       // host, nsets
+    const int32_t *h_minpts = nullptr;   // host, nsets
 };
 template <typename T, int D>
 int run_lowd(const RunArgs &a);

@@ -22,7 +22,9 @@ namespace hca {
 
 template <typename T, int D>
 struct LowdView {
-    GridParams g;
+    GridParams g;                 // key layout, and the parameters of a single-instance call
+    const GridParams *gtab;       // batched calls: parameters of every set (same key layout)
+    const int64_t *set_off;       // batched calls: first point of every set (n_sets + 1)
     const T *in;                  // input points, row-major n x D
     const Pt<T, D> *pts;          // sorted, padded
     const uint32_t *perm;
@@ -72,6 +74,16 @@ __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
 __device__ __forceinline__ void set_error(DevCounters *ctr, uint32_t bit) {
     atomicOr(&ctr->status, bit);
+}
+
+// Batched calls put the set id above the cell key bits; cells never mix sets.
+template <typename V>
+__device__ __forceinline__ uint32_t set_of_key(const V &v, uint64_t key) {
+    return v.gtab ? (uint32_t)(key >> v.g.key_bits) : 0u;
+}
+template <typename V>
+__device__ __forceinline__ const GridParams &params_of(const V &v, uint32_t set) {
+    return v.gtab ? v.gtab[set] : v.g;
 }
 
 // Number of representative directions kept per cell: all 3^D - 1 for D <= 3 (Sec. 2), the
@@ -201,9 +213,9 @@ __device__ __forceinline__ uint32_t hash_lookup(const uint64_t *hkeys, const uin
 // half: for the zero offset only cells after `a` along the last coordinate.
 template <typename T, int D>
 __device__ __forceinline__ bool pencil_range(const LowdView<T, D> &v, const Stencil &st, int k,
-                                             const int *ac, bool half, uint32_t &lo, uint32_t &hi) {
-    const GridParams &g = v.g;
-    uint64_t pkey = 0;
+                                             const int *ac, bool half, uint32_t &lo, uint32_t &hi,
+                                             const GridParams &g, uint32_t set) {
+    uint64_t pkey = v.gtab ? (uint64_t)set << (g.key_bits - g.prefix_shift) : 0ull;
 #pragma unroll
     for (int i = 0; i < D - 1; ++i) {
         int c = ac[i] + (int)st.off[k][i];
@@ -219,7 +231,7 @@ __device__ __forceinline__ bool pencil_range(const LowdView<T, D> &v, const Sten
     if (llo < 0) llo = 0;
     if (lhi > (int)g.ncell[D - 1] - 1) lhi = (int)g.ncell[D - 1] - 1;
     if (llo > lhi) return false;
-    const uint64_t base = (D > 1) ? (pkey << g.prefix_shift) : 0ull;
+    const uint64_t base = pkey << g.prefix_shift;  // set id and all coordinates but the last
     const uint64_t klo = base | (uint64_t)llo, khi = base | (uint64_t)lhi;
     // lower bound of klo, then upper bound of khi, inside the pencil
     uint32_t a = ps, b = pe;
@@ -562,9 +574,11 @@ __global__ void __launch_bounds__(256) k_ranges(LowdView<T, D> v, Stencil st_in)
         const uint32_t c = (uint32_t)(idx / na);
         const int k = (int)(idx - (uint64_t)c * na);
         int ac[D];
-        unpack_key<D>(v.cell_key[c], v.g, ac);
+        const uint64_t key = v.cell_key[c];
+        unpack_key<D>(key, v.g, ac);
+        const uint32_t set = set_of_key(v, key);
         uint32_t lo = 0, hi = 0;
-        if (!pencil_range<T, D>(v, st, k, ac, false, lo, hi)) lo = hi = 0;
+        if (!pencil_range<T, D>(v, st, k, ac, false, lo, hi, params_of(v, set), set)) lo = hi = 0;
         v.ranges[idx] = make_uint2(lo, hi);
     }
 }
@@ -580,10 +594,11 @@ __global__ void __launch_bounds__(256) k_ranges(LowdView<T, D> v, Stencil st_in)
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_core(LowdView<T, D> v, int n_all) {
     const uint32_t C = v.ctr->n_cells;
-    const uint32_t min_pts = v.g.min_pts;
     const int lane = lane_id();
     uint32_t dense_cells = 0, chunks = 0;
     for (uint32_t A = global_warp(); A < C; A += total_warps()) {
+        const GridParams &G = params_of(v, set_of_key(v, v.cell_key[A]));
+        const uint32_t min_pts = G.min_pts;
         const uint32_t s = v.cell_start[A], e = v.cell_start[A + 1], m = e - s;
         if (lane == 0) {
             v.parent[A] = A;
@@ -602,7 +617,7 @@ __global__ void __launch_bounds__(256) k_core(LowdView<T, D> v, int n_all) {
             const bool have = i < e;
             const Pt<T, D> pa = have ? v.pts[i] : zero_pt<T, D>();
             float ta[D];
-            band_coords<T, D>(pa, v.g, ta);
+            band_coords<T, D>(pa, G, ta);
             uint32_t cnt = m;  // the own cell: every point within eps
             unsigned open = __ballot_sync(0xffffffffu, have && cnt < min_pts);
             for (int g0 = 0; g0 < n_all && open; g0 += 32) {
@@ -624,7 +639,7 @@ __global__ void __launch_bounds__(256) k_core(LowdView<T, D> v, int n_all) {
                         float tj[D];
 #pragma unroll
                         for (int k2 = 0; k2 < D; ++k2) tj[k2] = __shfl_sync(0xffffffffu, ta[k2], jj);
-                        const int cls = okb ? box_class<D>(tj, cb, v.g) : 0;
+                        const int cls = okb ? box_class<D>(tj, cb, G) : 0;
                         uint32_t full = cls == 2 ? be - bs : 0u;
 #pragma unroll
                         for (int o = 16; o; o >>= 1) full += __shfl_xor_sync(0xffffffffu, full, o);
@@ -648,7 +663,7 @@ __global__ void __launch_bounds__(256) k_core(LowdView<T, D> v, int n_all) {
 #pragma unroll
                                     for (int u = 0; u < 4; ++u) {
                                         const uint32_t q = qb + 32 * u + lane;
-                                        const bool hit = q < pe && within_eps<D>(aj, q4[u], v.g);
+                                        const bool hit = q < pe && within_eps<D>(aj, q4[u], G);
                                         cj += __popc(__ballot_sync(0xffffffffu, hit));
                                     }
                                     ++chunks;
@@ -713,6 +728,7 @@ __global__ void __launch_bounds__(256) k_reps(LowdView<T, D> v) {
     (void)C;
     for (uint32_t t = global_warp(); t < NC; t += total_warps()) {
         const uint32_t A = v.chunk_cell[t];
+        const GridParams &G = params_of(v, set_of_key(v, v.cell_key[A]));
         const uint32_t s = v.cell_start[A], e = v.cell_start[A + 1];
         const uint32_t j0 = s + kChunk * (t - v.chunk_off[A]);
         const uint32_t j1 = min(j0 + kChunk, e);
@@ -725,7 +741,7 @@ __global__ void __launch_bounds__(256) k_reps(LowdView<T, D> v) {
         for (uint32_t j = j0 + lane; j < j1; j += 32) {
             if (!v.core[j]) continue;
             float u[D], lo2[D], hi2[D];
-            band_coords<T, D>(v.pts[j], v.g, u);
+            band_coords<T, D>(v.pts[j], G, u);
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 const float x = u[k] - (float)ac[k];
@@ -792,7 +808,7 @@ __global__ void __launch_bounds__(256) k_rep_pts(LowdView<T, D> v) {
 // whose distance to the whole other box is below eps settles it at once (B holds core points).
 template <typename T, int D>
 __device__ bool warp_core_pair(const LowdView<T, D> &v, uint32_t A, uint32_t B, const int *ac,
-                               const int *bc, uint32_t &chunks) {
+                               const int *bc, uint32_t &chunks, const GridParams &G) {
     const int lane = lane_id();
     const uint32_t sa = v.cell_start[A], ea = v.cell_start[A + 1];
     const uint32_t sb = v.cell_start[B], eb = v.cell_start[B + 1];
@@ -803,8 +819,8 @@ __device__ bool warp_core_pair(const LowdView<T, D> &v, uint32_t A, uint32_t B, 
         int cls = 0;
         if (va) {
             float t[D];
-            band_coords<T, D>(pa, v.g, t);
-            cls = box_class<D>(t, bc, v.g);
+            band_coords<T, D>(pa, G, t);
+            cls = box_class<D>(t, bc, G);
         }
         if (__any_sync(0xffffffffu, cls == 2)) return true;
         va = cls != 0;
@@ -815,8 +831,8 @@ __device__ bool warp_core_pair(const LowdView<T, D> &v, uint32_t A, uint32_t B, 
             const Pt<T, D> pb = vb ? v.pts[j] : zero_pt<T, D>();
             if (vb) {
                 float t[D];
-                band_coords<T, D>(pb, v.g, t);
-                vb = box_class<D>(t, ac, v.g) != 0;
+                band_coords<T, D>(pb, G, t);
+                vb = box_class<D>(t, ac, G) != 0;
             }
             const unsigned bm = __ballot_sync(0xffffffffu, vb);
             if (!bm) continue;
@@ -826,7 +842,7 @@ __device__ bool warp_core_pair(const LowdView<T, D> &v, uint32_t A, uint32_t B, 
                 const int t = __ffs(rem) - 1;
                 rem &= rem - 1;
                 const Pt<T, D> q = shfl_pt<T, D>(pb, t);
-                if (__any_sync(0xffffffffu, va && within_eps<D>(pa, q, v.g))) return true;
+                if (__any_sync(0xffffffffu, va && within_eps<D>(pa, q, G))) return true;
             }
         }
     }
@@ -846,7 +862,9 @@ __global__ void __launch_bounds__(256) k_hook(LowdView<T, D> v, int n_all, int n
     for (uint32_t A = global_warp(); A < C; A += total_warps()) {
         if (!v.cell_core[A]) continue;
         int ac[D];
-        unpack_key<D>(v.cell_key[A], v.g, ac);
+        const uint64_t akey = v.cell_key[A];
+        unpack_key<D>(akey, v.g, ac);
+        const GridParams &G = params_of(v, set_of_key(v, akey));
         bool linked = false;
         for (int g0 = 0; g0 < n_all && !linked; g0 += 32) {
             const int k = g0 + lane;
@@ -865,7 +883,7 @@ __global__ void __launch_bounds__(256) k_hook(LowdView<T, D> v, int n_all, int n
                     for (int i = 0; i < D; ++i) delta[i] = bc[i] - ac[i];
                     const int ra = rep_dir_of<D>(delta);
                     const int rb = rep_dir_complement<D>(ra);
-                    hit = within_eps<D>(v.rep_pts[(uint64_t)A * ndir + ra], v.rep_pts[(uint64_t)B * ndir + rb], v.g);
+                    hit = within_eps<D>(v.rep_pts[(uint64_t)A * ndir + ra], v.rep_pts[(uint64_t)B * ndir + rb], G);
                 }
                 const unsigned hm = __ballot_sync(0xffffffffu, hit);
                 if (hm) {
@@ -905,7 +923,9 @@ __global__ void __launch_bounds__(256) k_merge(LowdView<T, D> v, int n_all, int 
     for (uint32_t A = global_warp(); A < C; A += total_warps()) {
         if (!v.cell_core[A]) continue;
         int ac[D];
-        unpack_key<D>(v.cell_key[A], v.g, ac);
+        const uint64_t akey = v.cell_key[A];
+        unpack_key<D>(akey, v.g, ac);
+        const GridParams &G = params_of(v, set_of_key(v, akey));
         for (int g0 = 0; g0 < n_half; g0 += 32) {
             const int k = g0 + lane;
             uint2 rg = k < n_half ? v.ranges[(uint64_t)A * n_all + k] : make_uint2(0u, 0u);
@@ -931,7 +951,7 @@ __global__ void __launch_bounds__(256) k_merge(LowdView<T, D> v, int n_all, int 
                     const int ra = rep_dir_of<D>(delta);
                     const int rb = rep_dir_complement<D>(ra);
                     ++rep_tests;
-                    if (within_eps<D>(v.rep_pts[(uint64_t)A * ndir + ra], v.rep_pts[(uint64_t)B * ndir + rb], v.g)) {
+                    if (within_eps<D>(v.rep_pts[(uint64_t)A * ndir + ra], v.rep_pts[(uint64_t)B * ndir + rb], G)) {
                         uf_union(v.parent, A, B, v.ctr);
                         pending = false;
                         ++rep_hits;
@@ -950,7 +970,7 @@ __global__ void __launch_bounds__(256) k_merge(LowdView<T, D> v, int n_all, int 
                     same = __shfl_sync(0xffffffffu, same, 0);
                     if (same) continue;
                     ++exhaustive;
-                    if (warp_core_pair<T, D>(v, A, B2, ac, bc2, chunks) && lane == 0)
+                    if (warp_core_pair<T, D>(v, A, B2, ac, bc2, chunks, G) && lane == 0)
                         uf_union(v.parent, A, B2, v.ctr);
                 }
             }
@@ -1012,7 +1032,9 @@ __global__ void __launch_bounds__(256) k_label_core(LowdView<T, D> v) {
          j += (int64_t)gridDim.x * blockDim.x) {
         if (!v.core[j]) continue;
         const uint32_t o = v.perm[j];
-        v.labels[o] = (int32_t)v.comp_min[v.parent[v.cell_of[j]]];
+        const uint32_t c = v.cell_of[j];
+        const uint32_t base = v.gtab ? (uint32_t)v.set_off[set_of_key(v, v.cell_key[c])] : 0u;
+        v.labels[o] = (int32_t)(v.comp_min[v.parent[c]] - base);
         if (v.core_out) v.core_out[o] = 1;
     }
 }
@@ -1031,7 +1053,11 @@ __global__ void __launch_bounds__(256) k_labels(LowdView<T, D> v, int n_all) {
     uint32_t noise = 0, chunks = 0;
     for (uint32_t A = global_warp(); A < C; A += total_warps()) {
         const uint32_t s = v.cell_start[A], e = v.cell_start[A + 1];
-        if (e - s >= v.g.min_pts) continue;  // dense: every point is core (k_label_core)
+        const uint64_t akey = v.cell_key[A];
+        const uint32_t aset = set_of_key(v, akey);
+        const GridParams &G = params_of(v, aset);
+        if (e - s >= G.min_pts) continue;  // dense: every point is core (k_label_core)
+        const uint32_t base_label = v.gtab ? (uint32_t)v.set_off[aset] : 0u;
         const bool hasc = v.cell_core[A];
         const uint32_t clA = hasc ? v.comp_min[v.parent[A]] : kNoLabel;
         for (uint32_t base = s; base < e; base += 32) {
@@ -1043,7 +1069,7 @@ __global__ void __launch_bounds__(256) k_labels(LowdView<T, D> v, int n_all) {
             if (search) {
                 const Pt<T, D> pa = have ? v.pts[i] : zero_pt<T, D>();
                 float ta[D];
-                band_coords<T, D>(pa, v.g, ta);
+                band_coords<T, D>(pa, G, ta);
                 for (int g0 = 0; g0 < n_all; g0 += 32) {
                     const int k = g0 + lane;
                     const uint2 rg = k < n_all ? v.ranges[(uint64_t)A * n_all + k] : make_uint2(0u, 0u);
@@ -1068,7 +1094,7 @@ __global__ void __launch_bounds__(256) k_labels(LowdView<T, D> v, int n_all) {
                             float tj[D];
 #pragma unroll
                             for (int k2 = 0; k2 < D; ++k2) tj[k2] = __shfl_sync(0xffffffffu, ta[k2], jj);
-                            const int cls = cand ? box_class<D>(tj, cb, v.g) : 0;
+                            const int cls = cand ? box_class<D>(tj, cb, G) : 0;
                             uint32_t m2 = cls == 2 ? clB : kNoLabel;
 #pragma unroll
                             for (int o = 16; o; o >>= 1) m2 = min(m2, __shfl_xor_sync(0xffffffffu, m2, o));
@@ -1094,7 +1120,7 @@ __global__ void __launch_bounds__(256) k_labels(LowdView<T, D> v, int n_all) {
                                         }
                                         bool hit = false;
 #pragma unroll
-                                        for (int u = 0; u < 4; ++u) hit |= c4[u] && within_eps<D>(aj, q4[u], v.g);
+                                        for (int u = 0; u < 4; ++u) hit |= c4[u] && within_eps<D>(aj, q4[u], G);
                                         ++chunks;
                                         if (__any_sync(0xffffffffu, hit)) {
                                             bj = cl2;
@@ -1109,7 +1135,7 @@ __global__ void __launch_bounds__(256) k_labels(LowdView<T, D> v, int n_all) {
                 }
             }
             if (have && !isc) {
-                const int32_t lab = best == kNoLabel ? -1 : (int32_t)best;
+                const int32_t lab = best == kNoLabel ? -1 : (int32_t)(best - base_label);
                 const uint32_t o = v.perm[i];
                 v.labels[o] = lab;
                 if (v.core_out) v.core_out[o] = 0;
@@ -1120,6 +1146,97 @@ __global__ void __launch_bounds__(256) k_labels(LowdView<T, D> v, int n_all) {
     for (int o = 16; o; o >>= 1) noise += __shfl_xor_sync(0xffffffffu, noise, o);
     if (lane == 0 && noise) atomicAdd(&v.ctr->n_noise, noise);
     add_counter(&v.ctr->work[5], lane == 0 ? chunks : 0u);
+}
+
+
+// ------------------------------------------------------------------------------------------
+// Batched calls: per-set origin shift and binning
+// ------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t set_of_point(const int64_t *set_off, int nsets, int64_t j) {
+    int lo = 0, hi = nsets;  // last s with set_off[s] <= j
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(set_off + mid) <= j) lo = mid; else hi = mid;
+    }
+    return (uint32_t)lo;
+}
+
+// Per-set min / max (origin shift, Sec. 2) and NaN check; mm[set * kMaxD + i] = min encoding,
+// mm[(nsets + set) * kMaxD + i] = max encoding.  A warp whose points share one set reduces first.
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_minmax_seg(const T *__restrict__ in, int64_t n, const int64_t *set_off,
+                                                   int nsets, unsigned long long *mm, DevCounters *ctr) {
+    const int lane = lane_id();
+    bool nan = false;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = base + lane;
+        const bool valid = j < n;
+        const uint32_t set = valid ? set_of_point(set_off, nsets, j) : 0xffffffffu;
+        const uint32_t s0 = __shfl_sync(0xffffffffu, set, 0);
+        const bool uniform = __all_sync(0xffffffffu, !valid || set == s0);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const double x = valid ? (double)in[j * D + i] : 0.0;
+            nan |= valid && (x != x);
+            if (uniform) {
+                double a = valid ? x : DBL_MAX, b = valid ? x : -DBL_MAX;
+                for (int o = 16; o; o >>= 1) {
+                    a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+                    b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+                }
+                if (lane == 0) {
+                    atomicMin(&mm[(uint64_t)s0 * kMaxD + i], (unsigned long long)enc_double(a));
+                    atomicMax(&mm[((uint64_t)nsets + s0) * kMaxD + i], (unsigned long long)enc_double(b));
+                }
+            } else if (valid) {
+                atomicMin(&mm[(uint64_t)set * kMaxD + i], (unsigned long long)enc_double(x));
+                atomicMax(&mm[((uint64_t)nsets + set) * kMaxD + i], (unsigned long long)enc_double(x));
+            }
+        }
+    }
+    if (__any_sync(0xffffffffu, nan) && lane == 0) atomicOr(&ctr->nan_seen, 1u);
+}
+
+// Algorithm 1 per set, with the set id above the cell key bits.
+template <typename T, int D, typename K>
+__global__ void __launch_bounds__(256) k_bin_seg(const T *__restrict__ in, int64_t n, const int64_t *set_off,
+                                                int nsets, const GridParams *gtab, int key_bits,
+                                                K *__restrict__ keys, uint32_t *__restrict__ idx,
+                                                uint32_t *__restrict__ digit_counts, int total_bits) {
+    __shared__ uint32_t h[8][256];
+    const int passes = (total_bits + 7) / 8;
+    for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+    __syncthreads();
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t set = set_of_point(set_off, nsets, j);
+        const GridParams &g = gtab[set];
+        uint64_t key = (uint64_t)set << key_bits;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const T x = in[j * D + i];
+            uint32_t c;
+            if (sizeof(T) == 4 && !g.bin_fp64) {
+                float t = __fmul_rn(__fsub_rn((float)x, g.origin_f[i]), g.inv_side_f);
+                c = (uint32_t)floorf(t);
+            } else {
+                double t = __dmul_rn(__dsub_rn((double)x, g.origin[i]), g.inv_side);
+                c = (uint32_t)floor(t);
+            }
+            if (c > g.ncell[i] - 1) c = g.ncell[i] - 1;
+            key |= (uint64_t)c << g.shift[i];
+        }
+        keys[j] = (K)key;
+        idx[j] = (uint32_t)j;
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(uint32_t)(key >> (8 * p)) & 0xffu], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
+        const uint32_t c = (&h[0][0])[i];
+        if (c) atomicAdd(&digit_counts[i], c);
+    }
 }
 
 }  // namespace hca

@@ -130,8 +130,51 @@ inline int make_grid(int D, bool input_f32, double eps, int min_pts, int64_t n,
 // largest k that still passes.  Entry 0 is the zero pencil offset, then the offsets that are
 // lexicographically positive (the upper half, used to visit each pair of cells once), then
 // the negative ones.
-inline int make_stencil(int D, double eps, double side, double tau, Stencil &st) {
+struct StencilEntry { int off[kMaxD]; int reach; int cls; };
+
+inline void collect_stencil(int D, double eps, double side, double tau, std::vector<StencilEntry> &out);
+
+// Union of the stencils of several grids (batched calls): every pencil offset any grid needs,
+// with the largest reach.
+inline int make_stencil_union(int D, const std::vector<double> &eps, const std::vector<double> &side,
+                              const std::vector<double> &tau, Stencil &st) {
+    std::vector<StencilEntry> all;
+    for (size_t i = 0; i < eps.size(); ++i) {
+        std::vector<StencilEntry> one;
+        collect_stencil(D, eps[i], side[i], tau[i], one);
+        for (const StencilEntry &e : one) {
+            bool found = false;
+            for (StencilEntry &a : all) {
+                if (memcmp(a.off, e.off, sizeof(a.off)) == 0) {
+                    a.reach = a.reach > e.reach ? a.reach : e.reach;
+                    found = true;
+                    break;
+                }
+            }
+            if (!found) all.push_back(e);
+        }
+    }
     memset(&st, 0, sizeof(st));
+    if ((int)all.size() > kMaxPencils) return HCA_ENOTIMPL;
+    int k = 0;
+    for (int cls = 0; cls < 3; ++cls) {
+        for (const StencilEntry &e : all) {
+            if (e.cls != cls) continue;
+            for (int i = 0; i < D - 1; ++i) st.off[k][i] = (int8_t)e.off[i];
+            st.reach[k] = (int8_t)e.reach;
+            ++k;
+        }
+        if (cls == 1) st.n_half = k;
+    }
+    st.n_all = k;
+    return HCA_OK;
+}
+
+inline int make_stencil(int D, double eps, double side, double tau, Stencil &st) {
+    return make_stencil_union(D, std::vector<double>{eps}, std::vector<double>{side}, std::vector<double>{tau}, st);
+}
+
+inline void collect_stencil(int D, double eps, double side, double tau, std::vector<StencilEntry> &all) {
     const double bound = eps * eps * (1.0 + ldexp(1.0, -20));
     auto gap2 = [&](int k) {
         double gg = (double)k - 1.0 - 2.0 * tau;
@@ -141,8 +184,6 @@ inline int make_stencil(int D, double eps, double side, double tau, Stencil &st)
     };
     int R = 1;
     while (gap2(R + 1) <= bound) ++R;
-    struct Entry { int off[kMaxD]; int reach; int cls; };
-    std::vector<Entry> all;
     const int P = D - 1;
     std::vector<int> delta(P > 0 ? P : 1, -R);
     for (;;) {
@@ -155,7 +196,7 @@ inline int make_stencil(int D, double eps, double side, double tau, Stencil &st)
             if (delta[i] != 0 && zero) { zero = false; first = delta[i]; }
         }
         if (gp <= bound) {
-            Entry e;
+            StencilEntry e;
             memset(&e, 0, sizeof(e));
             for (int i = 0; i < P; ++i) e.off[i] = delta[i];
             int r = 1;
@@ -169,19 +210,6 @@ inline int make_stencil(int D, double eps, double side, double tau, Stencil &st)
         if (i >= P) break;
         ++delta[i];
     }
-    if ((int)all.size() > kMaxPencils) return HCA_ENOTIMPL;
-    int k = 0;
-    for (int cls = 0; cls < 3; ++cls) {
-        for (const Entry &e : all) {
-            if (e.cls != cls) continue;
-            for (int i = 0; i < P; ++i) st.off[k][i] = (int8_t)e.off[i];
-            st.reach[k] = (int8_t)e.reach;
-            ++k;
-        }
-        if (cls == 1) st.n_half = k;
-    }
-    st.n_all = k;
-    return HCA_OK;
 }
 
 struct HostCounters {
@@ -238,6 +266,11 @@ int run_lowd(const RunArgs &a) {
     const size_t o_core = take(n), o_ccore = take(n);
     const size_t o_parent = take(4 * n), o_cmin = take(4 * n);
     const size_t o_reps = take(8 * (size_t)n * ndir);
+    const bool batched = a.nsets > 0;
+    const int nsets = batched ? a.nsets : 1;
+    const size_t o_mm = take(sizeof(uint64_t) * 2 * kMaxD * (size_t)nsets);
+    const size_t o_gtab = take(sizeof(GridParams) * (size_t)nsets);
+    const size_t o_setoff = take(sizeof(int64_t) * ((size_t)nsets + 1));
     void *ws = nullptr, *ws_ranges = nullptr;
     if (pool_alloc(&ws, off, s) != cudaSuccess || !ws) return HCA_ENOMEM;
     char *b = (char *)ws;
@@ -259,16 +292,78 @@ int run_lowd(const RunArgs &a) {
     LowdView<T, D> v;
     memset(&v, 0, sizeof(v));
     bool flipped = false;
+    int sort_bits = 0;
+    std::vector<GridParams> gsets;
+    std::vector<uint64_t> hmm;
+    GridParams *d_gtab = (GridParams *)(b + o_gtab);
+    int64_t *d_setoff = (int64_t *)(b + o_setoff);
+    uint64_t *d_mm = (uint64_t *)(b + o_mm);
 
     if (!h) { rc = HCA_ECUDA; goto out; }
     mark(0);
     cudaMemsetAsync(ctr, 0, sizeof(DevCounters), s);
     cudaMemsetAsync(ctr->minmax_enc, 0xff, sizeof(uint64_t) * kMaxD, s);
-    k_minmax<T, D><<<grid_for(n, 256, sms, 2), 256, 0, s>>>((const T *)a.d_points, n, ctr);
+    if (!batched) {
+        k_minmax<T, D><<<grid_for(n, 256, sms, 2), 256, 0, s>>>((const T *)a.d_points, n, ctr);
+    } else {
+        cudaMemsetAsync(d_mm, 0xff, sizeof(uint64_t) * kMaxD * nsets, s);
+        cudaMemsetAsync(d_mm + (size_t)kMaxD * nsets, 0, sizeof(uint64_t) * kMaxD * nsets, s);
+        cudaMemcpyAsync(d_setoff, a.h_off, sizeof(int64_t) * (nsets + 1), cudaMemcpyHostToDevice, s);
+        k_minmax_seg<T, D><<<grid_for(n, 256, sms, 4), 256, 0, s>>>((const T *)a.d_points, n, d_setoff, nsets,
+                                                                  (unsigned long long *)d_mm, ctr);
+        hmm.resize((size_t)2 * kMaxD * nsets);
+        cudaMemcpyAsync(hmm.data(), d_mm, sizeof(uint64_t) * hmm.size(), cudaMemcpyDeviceToHost, s);
+    }
     ++launches;
     if (cudaMemcpyAsync(h, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) { rc = HCA_ECUDA; goto out; }
-    {
+    if (batched) {
+        if (h->nan_seen) { rc = HCA_EINVAL; goto out; }
+        // a grid per set, then one key layout for all (per dimension the largest bit count)
+        gsets.resize(nsets);
+        std::vector<double> e_eps(nsets), e_side(nsets), e_tau(nsets);
+        uint32_t bits[kMaxD] = {};
+        for (int st_i = 0; st_i < nsets; ++st_i) {
+            double mn[kMaxD], mx[kMaxD];
+            const bool empty = a.h_off[st_i + 1] == a.h_off[st_i];
+            for (int i = 0; i < D; ++i) {
+                mn[i] = empty ? 0.0 : dec_double(hmm[(size_t)st_i * kMaxD + i]);
+                mx[i] = empty ? 0.0 : dec_double(hmm[(size_t)kMaxD * nsets + (size_t)st_i * kMaxD + i]);
+                if (!isfinite(mn[i]) || !isfinite(mx[i])) { rc = HCA_EINVAL; goto out; }
+            }
+            double tau_s = 0.0;
+            rc = make_grid(D, sizeof(T) == 4, a.h_eps[st_i], a.h_minpts[st_i], n, mn, mx, a.flags, gsets[st_i], tau_s);
+            if (rc) goto out;
+            e_eps[st_i] = a.h_eps[st_i];
+            e_side[st_i] = 1.0 / gsets[st_i].inv_side;
+            e_tau[st_i] = tau_s;
+            for (int i = 0; i < D; ++i) bits[i] = bits[i] > gsets[st_i].bits[i] ? bits[i] : gsets[st_i].bits[i];
+        }
+        int key_bits = 0, set_bits = 1;
+        for (int i = 0; i < D; ++i) key_bits += (int)bits[i];
+        while ((1ll << set_bits) < nsets) ++set_bits;
+        if (key_bits + set_bits > 63) { rc = HCA_ERANGE; goto out; }
+        for (GridParams &gp : gsets) {
+            int sh = 0;
+            for (int i = D - 1; i >= 0; --i) {
+                gp.bits[i] = bits[i];
+                gp.shift[i] = (uint32_t)sh;
+                sh += (int)bits[i];
+            }
+            gp.key_bits = key_bits;
+            gp.prefix_shift = (int)bits[D - 1];
+        }
+        g = gsets[0];
+        sort_bits = key_bits + set_bits;
+        rc = make_stencil_union(D, e_eps, e_side, e_tau, st);
+        if (rc) goto out;
+        cudaMemcpyAsync(d_gtab, gsets.data(), sizeof(GridParams) * nsets, cudaMemcpyHostToDevice, s);
+        if (pool_alloc(&ws_ranges, sizeof(uint2) * (size_t)n * st.n_all + sizeof(Pt<T, D>) * (size_t)n * ndir + 256,
+                       s) != cudaSuccess || !ws_ranges) {
+            rc = HCA_ENOMEM;
+            goto out;
+        }
+    } else {
         if (h->nan_seen) { rc = HCA_EINVAL; goto out; }
         const uint64_t *mm = reinterpret_cast<const uint64_t *>(h->minmax_enc);
         double mn[kMaxD], mx[kMaxD];
@@ -281,6 +376,7 @@ int run_lowd(const RunArgs &a) {
         if (rc) goto out;
         rc = make_stencil(D, a.eps, 1.0 / g.inv_side, tau, st);
         if (rc) goto out;
+        sort_bits = g.key_bits;
         // neighbour ranges (one (lo, hi) pair per cell and stencil pencil) and the coordinates
         // of the representative points (ndir per cell)
         if (pool_alloc(&ws_ranges, sizeof(uint2) * (size_t)n * st.n_all + sizeof(Pt<T, D>) * (size_t)n * ndir + 256,
@@ -294,23 +390,31 @@ int run_lowd(const RunArgs &a) {
     {
         uint32_t *ia = (uint32_t *)(b + o_ia), *ib = (uint32_t *)(b + o_ib);
         uint32_t *hist = (uint32_t *)(b + o_hist), *part = (uint32_t *)(b + o_part);
-        const bool use32 = g.key_bits <= 32;
+        const bool use32 = sort_bits <= 32;
         if (use32) {
             uint32_t *ka = (uint32_t *)(b + o_ka), *kb = (uint32_t *)(b + o_kb);
-            k_bin<T, D, uint32_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, g, ka, ia, ctr->digit_counts);
+            if (batched)
+                k_bin_seg<T, D, uint32_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, n, d_setoff, nsets, d_gtab,
+                                                               g.key_bits, ka, ia, ctr->digit_counts, sort_bits);
+            else
+                k_bin<T, D, uint32_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, g, ka, ia, ctr->digit_counts);
             ++launches;
             mark(2);
-            flipped = radix_sort_pairs<uint32_t>(ka, ia, kb, ib, n, 0, g.key_bits, hist, part, s, &launches, &ctr->status, ctr->digit_counts);
+            flipped = radix_sort_pairs<uint32_t>(ka, ia, kb, ib, n, 0, sort_bits, hist, part, s, &launches, &ctr->status, ctr->digit_counts);
             mark(3);
             k_gather<T, D, uint32_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, flipped ? kb : ka,
                                                           flipped ? ib : ia, n, (Pt<T, D> *)(b + o_pts),
                                                           (uint32_t *)(b + o_flags));
         } else {
             uint64_t *ka = (uint64_t *)(b + o_ka), *kb = (uint64_t *)(b + o_kb);
-            k_bin<T, D, uint64_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, g, ka, ia, ctr->digit_counts);
+            if (batched)
+                k_bin_seg<T, D, uint64_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, n, d_setoff, nsets, d_gtab,
+                                                               g.key_bits, ka, ia, ctr->digit_counts, sort_bits);
+            else
+                k_bin<T, D, uint64_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, g, ka, ia, ctr->digit_counts);
             ++launches;
             mark(2);
-            flipped = radix_sort_pairs<uint64_t>(ka, ia, kb, ib, n, 0, g.key_bits, hist, part, s, &launches, &ctr->status, ctr->digit_counts);
+            flipped = radix_sort_pairs<uint64_t>(ka, ia, kb, ib, n, 0, sort_bits, hist, part, s, &launches, &ctr->status, ctr->digit_counts);
             mark(3);
             k_gather<T, D, uint64_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, flipped ? kb : ka,
                                                           flipped ? ib : ia, n, (Pt<T, D> *)(b + o_pts),
@@ -347,6 +451,8 @@ int run_lowd(const RunArgs &a) {
         launches += 3;
     }
     v.g = g;
+    v.gtab = batched ? d_gtab : nullptr;
+    v.set_off = batched ? d_setoff : nullptr;
     v.in = (const T *)a.d_points;
     v.pts = (const Pt<T, D> *)(b + o_pts);
     v.cell_of = (const uint32_t *)(b + o_flags);
@@ -414,8 +520,8 @@ int run_lowd(const RunArgs &a) {
         st_out->n_core_points = h->n_core;
         st_out->n_clusters = h->n_clusters;
         st_out->n_noise = h->n_noise;
-        st_out->key_bits = g.key_bits;
-        st_out->sort_passes = (g.key_bits + 7) / 8;
+        st_out->key_bits = sort_bits;
+        st_out->sort_passes = (sort_bits + 7) / 8;
         st_out->kernel_launches = launches;
         st_out->n_count_chunks = (int64_t)h->work[0];
         st_out->n_rep_tests = (int64_t)h->work[1];

@@ -23,6 +23,9 @@ Recipes (sizes are parameters so the same recipe can be run small):
             random rotation, centres U[10,90]^16) holding 90% of the points and 10% uniform
             noise over [0,100]^16; coordinates on multiples of 2^-12; eps 4, minPts 20.
             Default n = 1,000,000.
+  batched   4096 independent sets: n log-uniform in [1,000, 200,000], d from {2, 3, 8}, 5 blobs
+            (sigma 2 eps / sqrt(d)) + 10% noise in [0,100]^d, eps U[0.5, 3] on 2^-12, MINPTS
+            U{4..16}, float32 on the 2^-12 lattice (sizes are parameters).
   lattice   any d: points on the integer lattice times `step` (default 0.25) drawn from a few
             small blobs plus noise, so that many pairs sit at exactly eps; for tie tests.
 """
@@ -132,6 +135,30 @@ def lattice(n: int, d: int, seed: int, step: float = 0.25, eps_steps: int = 4,
     X = X[r.permutation(len(X))]
     X = np.round(X / step) * step
     return np.ascontiguousarray(X, dtype=dtype), eps_steps * step, min_pts
+
+
+def batched_sets(n_sets: int = 4096, seed: int = SEED_BASE + 3, n_min: int = 1_000,
+                 n_max: int = 200_000, dims=(2, 3, 8)):
+    """Many independent point sets: n log-uniform in [n_min, n_max], d drawn from `dims`, 5
+    Gaussian blobs (sigma = c_d * eps) plus 10% uniform noise in [0,100]^d, eps uniform in
+    [0.5, 3] and rounded to 2^-12, MINPTS uniform in {4..16}, float32 coordinates on the 2^-12
+    lattice.  c_d = 2 / sqrt(d) keeps roughly half of the points core at every d.
+    Returns a list of (X, eps, min_pts)."""
+    r = _rng(seed)
+    out = []
+    for _ in range(n_sets):
+        n = int(round(np.exp(r.uniform(np.log(n_min), np.log(n_max)))))
+        d = int(r.choice(dims))
+        eps = float(np.round(r.uniform(0.5, 3.0) * 4096) / 4096)
+        min_pts = int(r.integers(4, 17))
+        sigma = 2.0 / np.sqrt(d) * eps
+        n_noise = n // 10
+        parts = [r.normal(r.uniform(10.0, 90.0, size=d), sigma, size=(m, d)) for m in _even(n - n_noise, 5)]
+        parts.append(r.uniform(0.0, 100.0, size=(n_noise, d)))
+        X = np.concatenate(parts, axis=0)
+        X = X[r.permutation(n)]
+        out.append((np.ascontiguousarray(_round_lattice(X, 12).astype(np.float32)), eps, min_pts))
+    return out
 
 
 WORKLOADS = {

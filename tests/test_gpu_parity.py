@@ -288,3 +288,80 @@ def test_aniso16d_full_sampled(env):
         else:
             cl = lab[nb & (core == 1)]
             assert lab[p] == (cl.min() if len(cl) else -1), f"border/noise label of {p}"
+
+
+# ---------------------------------------------------------------------------------------------
+# Batched calls: many sets, each with its own eps and MINPTS, labels local to each set
+# ---------------------------------------------------------------------------------------------
+
+def _sets_for(d, seed, count, dtype):
+    r = np.random.Generator(np.random.PCG64(seed))
+    sets = []
+    for k in range(count):
+        n = int(r.choice([0, 1, 2, 37, 500, 1500, 4000]))
+        X, eps, mp = workloads.lattice(max(n, 1), d, seed=seed * 1000 + k, spread=2.0 + d,
+                                       box=6.0 + 3 * d, eps_steps=int(r.integers(3, 7)),
+                                       min_pts=int(r.integers(1, 12)))
+        sets.append((X[:n].astype(dtype), eps, mp))
+    return sets
+
+
+def _run_batched(env, sets, **kw):
+    torch, pkg, _ = env
+    d = sets[0][0].shape[1]
+    X = np.concatenate([s[0].reshape(-1, d) for s in sets], axis=0)
+    off = np.zeros(len(sets) + 1, np.int64)
+    off[1:] = np.cumsum([len(s[0]) for s in sets])
+    t = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    core = torch.empty(len(X), dtype=torch.uint8, device="cuda")
+    out = pkg.hca_dbscan_batched(t, off, [s[1] for s in sets], [s[2] for s in sets], core=core, **kw)
+    lab = out[0] if isinstance(out, tuple) else out
+    return lab.cpu().numpy(), core.cpu().numpy(), off, (out[1] if isinstance(out, tuple) else None)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_batched_matches_oracle_per_set(env, d, dtype):
+    _, _, oracle = env
+    sets = _sets_for(d, 70 + d, 40, dtype)
+    lab, core, off, st = _run_batched(env, sets, stats=True)
+    for s, (X, eps, mp) in enumerate(sets):
+        if len(X) == 0:
+            continue
+        want = oracle.grid(X.astype(np.float64), eps, mp)
+        np.testing.assert_array_equal(lab[off[s]:off[s + 1]], want[0], err_msg=f"set {s}")
+        np.testing.assert_array_equal(core[off[s]:off[s + 1]], want[1], err_msg=f"set {s}")
+
+
+def test_batched_high_d_sets(env):
+    _, _, oracle = env
+    sets = _sets_for(8, 88, 12, np.float32)
+    lab, core, off, _ = _run_batched(env, sets)
+    for s, (X, eps, mp) in enumerate(sets):
+        if len(X):
+            want = oracle.grid(X.astype(np.float64), eps, mp)
+            np.testing.assert_array_equal(lab[off[s]:off[s + 1]], want[0], err_msg=f"set {s}")
+
+
+@pytest.mark.parametrize("dims", [(2,), (3,)])
+def test_batched_recipe_equals_separate_calls(env, dims):
+    """The batched recipe (blobs + noise, per-set eps and MINPTS): one batched call gives each
+    set exactly the labels of a separate call on that set, and the oracle's."""
+    torch, pkg, oracle = env
+    sets = workloads.batched_sets(n_sets=200, n_min=100, n_max=20000, dims=dims, seed=dims[0])
+    lab, core, off, st = _run_batched(env, sets, stats=True)
+    assert st["n_points"] == off[-1]
+    for s, (X, eps, mp) in enumerate(sets):
+        single = pkg.hca_dbscan_device(torch.from_numpy(X).cuda(), eps, mp).cpu().numpy()
+        np.testing.assert_array_equal(lab[off[s]:off[s + 1]], single, err_msg=f"set {s}")
+        if s % 20 == 0:
+            want = oracle.grid(X.astype(np.float64), eps, mp)
+            np.testing.assert_array_equal(single, want[0], err_msg=f"set {s} vs oracle")
+
+
+def test_batched_rejects_bad_offsets(env):
+    torch, pkg, _ = env
+    X = torch.zeros((10, 2), device="cuda")
+    for off in ([0, 5, 4, 10], [1, 5, 10]):
+        with pytest.raises((pkg.HcaError, ValueError)):
+            pkg.hca_dbscan_batched(X, off, [1.0] * (len(off) - 1), [2] * (len(off) - 1))
