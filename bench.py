@@ -65,7 +65,11 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mixed3d", choices=["mixed3d", "blobs2d", "aniso16d"])
+    ap.add_argument("--workload", default="mixed3d",
+                    choices=["mixed3d", "blobs2d", "aniso16d", "batched", "serving"])
+    ap.add_argument("--sets", type=int, default=4096, help="batched: number of point sets")
+    ap.add_argument("--seconds", type=float, default=20.0, help="serving: arrival window")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrivals per second")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -345,10 +349,120 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args):
+    """Config B: many independent sets (n log-uniform [1e3, 2e5], d in {2, 3, 8}, own eps and
+    MINPTS), one hca_dbscan_batched call per d per step; value = points of all sets / step."""
+    import torch
+    import paper_1912_00323_gb300 as pkg
+    from paper_1912_00323_gb300 import build as pkg_build, workloads
+    pkg_build.build()
+    pkg.load()
+    sets = workloads.batched_sets(n_sets=args.sets)
+    groups = {}
+    for X, e, m in sets:
+        groups.setdefault(X.shape[1], []).append((X, e, m))
+    dev_groups = []
+    for d, g in sorted(groups.items()):
+        X = np.concatenate([x for x, _, _ in g], axis=0)
+        off = np.zeros(len(g) + 1, np.int64)
+        off[1:] = np.cumsum([len(x) for x, _, _ in g])
+        dev_groups.append((d, torch.from_numpy(X).cuda(), off, [e for _, e, _ in g], [m for _, _, m in g]))
+    n_total = sum(len(x) for x, _, _ in sets)
+    per_d = {}
+    def step():
+        for d, t, off, e, m in dev_groups:
+            t0 = time.perf_counter()
+            pkg.hca_dbscan_batched(t, off, e, m)
+            per_d[d] = time.perf_counter() - t0
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        step()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.median(times)
+    line = {"metric": "points clustered/sec, batched sets (labels == oracle per set)",
+            "value": n_total / (ms / 1e3), "unit": "points/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched: {args.sets} sets, n log-uniform [1e3, 2e5], d in {{2,3,8}}, "
+                                   "blobs + 10% noise, eps U[0.5,3], minPts U{4..16}",
+                       "points": n_total, "sets_per_d": {int(d): len(g) for d, g in groups.items()}},
+            "ms_per_d": {int(d): 1e3 * t for d, t in per_d.items()}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serving(args):
+    """Config S: Poisson arrivals of clustering jobs (n log-uniform [1e3, 2e6], d uniform in
+    2..16, blob + noise data, float32 lattice) to the request server; p50 / p99 latency from
+    submit to labels, and points/s.  Jobs draw their data from a pool of pre-generated sets."""
+    import threading
+    import torch
+    import paper_1912_00323_gb300 as pkg
+    from paper_1912_00323_gb300 import build as pkg_build, workloads
+    pkg_build.build()
+    pkg.load()
+    r = np.random.Generator(np.random.PCG64(workloads.SEED_BASE + 4))
+    pool = []
+    for k in range(48):
+        d = int(r.integers(2, 17))
+        (X, e, m), = workloads.batched_sets(n_sets=1, seed=workloads.SEED_BASE + 100 + k, n_min=1_000,
+                                            n_max=2_000_000, dims=(d,))
+        e = float(np.round(1.5 * np.sqrt(d / 2.0) * 4096) / 4096)
+        pool.append((np.ascontiguousarray(X), e, int(r.integers(4, 21))))
+    arrivals = np.cumsum(r.exponential(1.0 / args.rate, size=int(args.rate * args.seconds * 1.2) + 10))
+    arrivals = arrivals[arrivals < args.seconds]
+    picks = r.integers(0, len(pool), size=len(arrivals))
+    lat, pts = [], 0
+    with pkg.Server(hbm_budget_bytes=64 << 30, workers=2) as sv:
+        sv.wait(sv.submit(*pool[0]))          # warm-up
+        tickets = []
+        t0 = time.perf_counter()
+        def collect():
+            nonlocal pts
+            i = 0
+            while i < len(arrivals):
+                if i >= len(tickets):
+                    time.sleep(0.0005)
+                    continue
+                _, l = sv.wait(tickets[i])
+                lat.append(l)
+                pts += len(pool[picks[i]][0])
+                i += 1
+        th = threading.Thread(target=collect)
+        th.start()
+        for a, k in zip(arrivals, picks):
+            delay = a - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(sv.submit(*pool[k]))
+        th.join()
+        wall = time.perf_counter() - t0
+    lat = np.array(lat)
+    line = {"metric": "serving: p50/p99 submit-to-labels latency and points/s",
+            "value": pts / wall, "unit": "points/s", "n_gpus": 1, "higher_is_better": True,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "requests": int(len(lat)), "offered_rate_per_s": args.rate, "window_s": args.seconds,
+            "wall_s": wall, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving: Poisson arrivals, n log-uniform [1e3, 2e6], d uniform 2..16, "
+                                   "blobs + noise, eps = 1.5 sqrt(d/2), minPts U{4..20}; jobs drawn from 48 "
+                                   "pre-generated sets", "workers": 2}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

@@ -62,6 +62,9 @@ extern "C" {
 #define HCA_EDEVICE (-6)   /* a kernel's own consistency check tripped (bounded loop limit,
                               full hash table); the outputs hold no result */
 #define HCA_ETOOLARGE (-7) /* n above the fixed scratch of hca_radix_sort_pairs_noalloc */
+#define HCA_ETIMEDOUT (-8) /* hca_wait: the job did not complete before the deadline */
+#define HCA_ECANCELED (-9) /* the job was cancelled (hca_cancel, or the server shut down) */
+#define HCA_EBUSY (-10)    /* hca_cancel: the job is already running */
 
 /* largest n accepted by hca_radix_sort_pairs_noalloc */
 #define HCA_SORT_NOALLOC_MAX_PAIRS (1 << 18)
@@ -145,14 +148,52 @@ HCA_API int hca_dbscan_device_ex(const void *d_points, int32_t dtype, int64_t n,
  *   d_labels  device, offsets[n_sets] int32: each set's labels, with cluster ids that are
  *             indices WITHIN the set (the same values a separate call on that set returns).
  *   d_core    device, optional core flags; stats host, optional (totals over the sets).
- * For 1 <= d <= 4 all sets go through one pipeline: the set id sits above the cell key, so
- * one sort, one pencil hash and one launch of each kernel serve every set, and cells never
- * mix sets.  For d >= 5 the sets are clustered one after another.  Returns after the labels
- * are complete on `stream`.  One d per call: group sets of different d into separate calls.
+ * All sets go through one pipeline: the set id sits above the cell key (the hypercube key for
+ * d <= 4, the coarse-grid key for d >= 5), so one sort, one pencil hash and one launch of each
+ * kernel serve every set, and cells never mix sets.  Returns after the labels are complete on
+ * `stream`.  One d per call: group sets of different d into separate calls.
  */
 HCA_API int hca_dbscan_batched(const void *d_points, int32_t dtype, int32_t n_sets, const int64_t *offsets,
                                int32_t d, const double *eps, const int32_t *min_pts, int32_t *d_labels,
                                uint8_t *d_core, void *stream, hca_stats *stats, int32_t flags);
+
+/*
+ * Request server: asynchronous clustering jobs with continuous batching (the serving form of
+ * the library; the paper has no counterpart).  Worker threads, each with its own CUDA stream,
+ * repeatedly admit every queued job that fits the device-memory budget (in arrival order),
+ * group the admitted jobs by (d, dtype) and cluster each group with one hca_dbscan_batched
+ * call; jobs arriving while a batch runs join a later batch, and the workers keep several
+ * batches in flight.  A job's result is the same as a separate hca_dbscan call on its points.
+ */
+typedef struct hca_request {
+    const void *points;   /* n*d values of `dtype`, row-major; host or device memory */
+    int32_t *labels;      /* n int32 in the same kind of memory; written when the job completes */
+    int64_t n;
+    int32_t d;
+    int32_t dtype;
+    double eps;
+    int32_t min_pts;
+    int32_t on_device;    /* 1: points and labels are device pointers, 0: host pointers */
+} hca_request;
+
+typedef struct hca_server hca_server;
+
+/* Start a server on `device` with `workers` worker threads (1..16) and a device-memory budget
+ * (bytes charged per job: points, labels and about 1 KB of workspace per point).  A job larger
+ * than the whole budget runs alone.  The caller keeps every job's buffers alive until the
+ * job completes. */
+HCA_API int hca_server_create(hca_server **server, int32_t device, int64_t hbm_budget_bytes, int32_t workers);
+/* Stop accepting jobs, cancel queued ones (HCA_ECANCELED), finish running ones, free. */
+HCA_API int hca_server_destroy(hca_server *server);
+/* Queue a job; *ticket identifies it.  Arguments are checked as in hca_dbscan. */
+HCA_API int hca_submit(hca_server *server, const hca_request *request, int64_t *ticket);
+/* 1: completed successfully; 0: queued or running; negative: the job's error code. */
+HCA_API int hca_poll(hca_server *server, int64_t ticket);
+/* Wait up to timeout_ms for the job; on completion return its code, store its submit-to-done
+ * latency (ms, nullable) and forget the ticket; HCA_ETIMEDOUT if the deadline passed first. */
+HCA_API int hca_wait(hca_server *server, int64_t ticket, int64_t timeout_ms, double *latency_ms);
+/* Cancel a queued job (HCA_OK); HCA_EBUSY if it is already running. */
+HCA_API int hca_cancel(hca_server *server, int64_t ticket);
 
 /*
  * hca_radix_sort_pairs -- stable ascending sort of (key, value) pairs on the device, by key

@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libhca_dbscan.so")
 
 HCA_F32, HCA_F64 = 0, 1
 HCA_OK, HCA_EINVAL, HCA_ENOMEM, HCA_ECUDA, HCA_ERANGE, HCA_ENOTIMPL, HCA_EDEVICE = 0, -1, -2, -3, -4, -5, -6
+HCA_ETOOLARGE, HCA_ETIMEDOUT, HCA_ECANCELED, HCA_EBUSY = -7, -8, -9, -10
 HCA_FLAG_TIMING, HCA_FLAG_FP64_ONLY = 1, 2
 STAGES = ("minmax", "bin", "sort", "cells", "hash", "core", "reps", "merge", "labels")
 
@@ -45,6 +46,12 @@ class HcaStats(ctypes.Structure):
         d = {name: getattr(self, name) for name, _ in self._fields_ if name not in ("stage_ms", "reserved")}
         d["stage_ms"] = {s: float(self.stage_ms[i]) for i, s in enumerate(STAGES)}
         return d
+
+
+class HcaRequest(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_void_p), ("labels", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("d", ctypes.c_int32), ("dtype", ctypes.c_int32), ("eps", ctypes.c_double),
+                ("min_pts", ctypes.c_int32), ("on_device", ctypes.c_int32)]
 
 
 class HcaError(RuntimeError):
@@ -74,6 +81,14 @@ def load():
     lib.hca_dbscan_batched.argtypes = [vp, i32, i32, vp, i32, vp, vp, vp, vp, vp,
                                        ctypes.POINTER(HcaStats), i32]
     lib.hca_dbscan_batched.restype = ctypes.c_int
+    lib.hca_server_create.argtypes = [ctypes.POINTER(vp), i32, i64, i32]
+    lib.hca_server_destroy.argtypes = [vp]
+    lib.hca_submit.argtypes = [vp, ctypes.POINTER(HcaRequest), ctypes.POINTER(i64)]
+    lib.hca_poll.argtypes = [vp, i64]
+    lib.hca_wait.argtypes = [vp, i64, i64, ctypes.POINTER(ctypes.c_double)]
+    lib.hca_cancel.argtypes = [vp, i64]
+    for f in ("hca_server_create", "hca_server_destroy", "hca_submit", "hca_poll", "hca_wait", "hca_cancel"):
+        getattr(lib, f).restype = ctypes.c_int
     lib.hca_strerror.argtypes = [ctypes.c_int]
     lib.hca_strerror.restype = ctypes.c_char_p
     lib.hca_version.restype = i32
@@ -207,3 +222,75 @@ def hca_radix_sort_pairs(keys, vals, begin_bit: int = 0, end_bit: int | None = N
     if rc != HCA_OK:
         raise HcaError(rc, "hca_radix_sort_pairs")
     return keys, vals
+
+
+class Server:
+    """Asynchronous clustering jobs with continuous batching (hca_server_* / hca_submit /
+    hca_poll / hca_wait / hca_cancel).  submit() takes host numpy arrays or CUDA tensors and
+    keeps them alive until the job is waited for."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 32 << 30, workers: int = 2):
+        lib = load()
+        self._lib = lib
+        h = ctypes.c_void_p()
+        rc = lib.hca_server_create(ctypes.byref(h), int(device), int(hbm_budget_bytes), int(workers))
+        if rc != HCA_OK:
+            raise HcaError(rc, "hca_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, points, eps: float, min_pts: int, labels=None) -> int:
+        on_device = hasattr(points, "is_cuda") and points.is_cuda
+        if hasattr(points, "data_ptr"):
+            pts = points.contiguous()
+            ptr = pts.data_ptr()
+            n, d = pts.shape[0], (pts.shape[1] if pts.dim() == 2 else 1)
+            if labels is None:
+                import torch
+                labels = torch.empty(n, dtype=torch.int32, device=pts.device)
+            lptr = labels.data_ptr()
+        else:
+            pts = np.ascontiguousarray(points)
+            if pts.ndim == 1:
+                pts = pts[:, None]
+            n, d = pts.shape
+            ptr = pts.ctypes.data
+            if labels is None:
+                labels = np.empty(n, np.int32)
+            lptr = labels.ctypes.data
+        req = HcaRequest(ptr, lptr, n, d, _dtype_code(pts.dtype), float(eps), int(min_pts), int(on_device))
+        t = ctypes.c_int64()
+        rc = self._lib.hca_submit(self._h, ctypes.byref(req), ctypes.byref(t))
+        if rc != HCA_OK:
+            raise HcaError(rc, "hca_submit")
+        self._keep[t.value] = (pts, labels)
+        return t.value
+
+    def poll(self, ticket: int) -> int:
+        return int(self._lib.hca_poll(self._h, int(ticket)))
+
+    def wait(self, ticket: int, timeout_ms: int = 600_000):
+        """Returns (labels, latency_ms); raises HcaError on a job error or a timeout."""
+        lat = ctypes.c_double()
+        rc = self._lib.hca_wait(self._h, int(ticket), int(timeout_ms), ctypes.byref(lat))
+        if rc == HCA_ETIMEDOUT:
+            raise HcaError(rc, "hca_wait")
+        _, labels = self._keep.pop(int(ticket))
+        if rc != HCA_OK:
+            raise HcaError(rc, "hca_wait")
+        return labels, lat.value
+
+    def cancel(self, ticket: int) -> int:
+        return int(self._lib.hca_cancel(self._h, int(ticket)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.hca_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

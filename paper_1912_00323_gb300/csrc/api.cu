@@ -150,7 +150,7 @@ extern "C" int hca_dbscan_batched(const void *d_points, int32_t dtype, int32_t n
     if (n == 0) return HCA_OK;
     const size_t esz = dtype == HCA_F32 ? 4 : 8;
     if (((uintptr_t)d_points) % esz || ((uintptr_t)d_labels) % 4) return HCA_EINVAL;
-    if (d <= kMaxD) {
+    {
         RunArgs a;
         a.d_points = d_points;
         a.n = n;
@@ -168,26 +168,6 @@ extern "C" int hca_dbscan_batched(const void *d_points, int32_t dtype, int32_t n
         a.h_minpts = min_pts;
         return dispatch(a, dtype);
     }
-    // d >= 5: one call per set, totals summed into stats
-    for (int32_t i = 0; i < n_sets; ++i) {
-        const int64_t m = offsets[i + 1] - offsets[i];
-        if (m == 0) continue;
-        hca_stats one = {};
-        rc = hca_dbscan_device_ex((const char *)d_points + (size_t)offsets[i] * d * esz, dtype, m, d, eps[i],
-                                  min_pts[i], d_labels + offsets[i], d_core ? d_core + offsets[i] : nullptr,
-                                  stream, stats ? &one : nullptr, flags & ~HCA_FLAG_TIMING);
-        if (rc) return rc;
-        if (stats) {
-            stats->n_points += one.n_points;
-            stats->n_cells += one.n_cells;
-            stats->n_pencils += one.n_pencils;
-            stats->n_core_points += one.n_core_points;
-            stats->n_clusters += one.n_clusters;
-            stats->n_noise += one.n_noise;
-            stats->kernel_launches += one.kernel_launches;
-        }
-    }
-    return HCA_OK;
 }
 
 extern "C" int hca_dbscan_device(const void *d_points, int32_t dtype, int64_t n, int32_t d, double eps,
@@ -276,6 +256,9 @@ extern "C" const char *hca_strerror(int code) {
         case HCA_ENOTIMPL: return "not implemented in this build";
         case HCA_EDEVICE: return "device-side consistency check failed";
         case HCA_ETOOLARGE: return "input larger than the fixed scratch of the no-allocation entry point";
+        case HCA_ETIMEDOUT: return "timed out";
+        case HCA_ECANCELED: return "cancelled";
+        case HCA_EBUSY: return "busy";
     }
     return "unknown error";
 }

@@ -58,6 +58,7 @@ struct GridParams {
     int box_ok;                  // band coordinates exact enough in FP32 for cell-box tests
     float tau_box;               // widening of a cell box, band units
     float box_full, box_none;    // eps^2 in band units^2 times (1 -/+ 2^-12)
+    int sel[3];                  // coarse-grid path: the three projected input dimensions
 };
 
 // Neighbour pencils: offsets of the first d-1 coordinates and the reach along the last one.

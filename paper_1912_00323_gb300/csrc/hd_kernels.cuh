@@ -23,6 +23,8 @@ namespace hca {
 template <typename T, int DP>
 struct HdView {
     GridParams g;                 // coarse grid on the projected dimensions; eps2, lo32, hi32, min_pts, n
+    const GridParams *gtab;       // batched calls: parameters of every set (same key layout)
+    const int64_t *set_off;       // batched calls: first point of every set
     int d;
     const T *pts;                 // sorted, n x DP
     const uint32_t *perm;
@@ -209,10 +211,11 @@ template <typename T, int DP>
 __global__ void __launch_bounds__(32 * kHdWarps) k_count_hd(HdView<T, DP> v) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *rows = reinterpret_cast<T *>(smem_raw) + (threadIdx.x >> 5) * 32 * DP;
-    const uint32_t min_pts = v.g.min_pts;
     const int lane = lane_id();
     uint32_t chunks = 0;
     HD_FOR_EACH_CHUNK(v, A, base, e) {
+        const GridParams &G = params_of(v, set_of_key(v, v.cell_key[A]));
+        const uint32_t min_pts = G.min_pts;
         stage_rows<T, DP>(rows, v.pts, base, e);
         const bool have = base + lane < e;
         uint32_t cnt = 0;
@@ -235,7 +238,7 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_count_hd(HdView<T, DP> v) {
                     while (rem) {
                         const int jj = __ffs(rem) - 1;
                         rem &= rem - 1;
-                        const unsigned hits = __ballot_sync(0xffffffffu, q < q1 && hd_within<DP>(rows + jj * DP, qv, v.g));
+                        const unsigned hits = __ballot_sync(0xffffffffu, q < q1 && hd_within<DP>(rows + jj * DP, qv, G));
                         if (lane == jj) cnt += __popc(hits);
                     }
                     open &= __ballot_sync(0xffffffffu, have && cnt < min_pts);
@@ -273,6 +276,7 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_hook_hd(HdView<T, DP> v) {
         const uint32_t p = base + lane;
         unsigned open = __ballot_sync(0xffffffffu, p < e && v.core[p]);
         if (!open) continue;
+        const GridParams &G = params_of(v, set_of_key(v, v.cell_key[A]));
         stage_rows<T, DP>(rows, v.pts, base, e);
         for (int g0 = 0; g0 < v.n_all && open; g0 += 32) {
             const int k = g0 + lane;
@@ -294,7 +298,7 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_hook_hd(HdView<T, DP> v) {
                     while (rem) {
                         const int jj = __ffs(rem) - 1;
                         rem &= rem - 1;
-                        const bool hit = qc && q < base + jj && hd_within<DP>(rows + jj * DP, qv, v.g);
+                        const bool hit = qc && q < base + jj && hd_within<DP>(rows + jj * DP, qv, G);
                         const unsigned hm = __ballot_sync(0xffffffffu, hit);
                         if (hm) {
                             if (lane == jj) v.parent[base + jj] = qb + (uint32_t)(__ffs(hm) - 1);
@@ -336,6 +340,7 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_merge_hd(HdView<T, DP> v) {
         const bool pc = p < e && v.core[p];
         const unsigned amask = __ballot_sync(0xffffffffu, pc);
         if (!amask) continue;
+        const GridParams &G = params_of(v, set_of_key(v, v.cell_key[A]));
         stage_rows<T, DP>(rows, v.pts, base, e);
         uint32_t rp = pc ? uf_find(v.parent, p, v.ctr) : 0xffffffffu;
         for (int g0 = 0; g0 < v.n_half; g0 += 32) {
@@ -371,7 +376,7 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_merge_hd(HdView<T, DP> v) {
                         const bool need = qc && q > pj && rq != rj;
                         if (!__any_sync(0xffffffffu, need)) continue;
                         ++tests;
-                        const bool hit = need && hd_within<DP>(rows + jj * DP, qv, v.g);
+                        const bool hit = need && hd_within<DP>(rows + jj * DP, qv, G);
                         if (hit) uf_union(v.parent, pj, q, v.ctr);
                         if (__any_sync(0xffffffffu, hit)) {
                             // roots moved: refresh every lane so later pairs of the tile skip
@@ -438,6 +443,9 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_labels_hd(HdView<T, DP> v) {
     uint32_t noise = 0, chunks = 0;
     HD_FOR_EACH_CHUNK(v, A, base, e) {
         {
+            const uint32_t aset = set_of_key(v, v.cell_key[A]);
+            const GridParams &G = params_of(v, aset);
+            const uint32_t base_label = v.gtab ? (uint32_t)v.set_off[aset] : 0u;
             const uint32_t p = base + lane;
             const bool have = p < e;
             const bool isc = have && v.core[p];
@@ -468,7 +476,7 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_labels_hd(HdView<T, DP> v) {
                                 const uint32_t bj = __shfl_sync(0xffffffffu, best, jj);
                                 const bool need = qc && lq < bj;
                                 if (!__any_sync(0xffffffffu, need)) continue;
-                                uint32_t cand = (need && hd_within<DP>(rows + jj * DP, qv, v.g)) ? lq : kNoLabel;
+                                uint32_t cand = (need && hd_within<DP>(rows + jj * DP, qv, G)) ? lq : kNoLabel;
                                 for (int o = 16; o; o >>= 1) cand = min(cand, __shfl_xor_sync(0xffffffffu, cand, o));
                                 if (lane == jj && cand < best) best = cand;
                             }
@@ -478,7 +486,7 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_labels_hd(HdView<T, DP> v) {
                 __syncwarp();
             }
             if (have) {
-                const int32_t lab = best == kNoLabel ? -1 : (int32_t)best;
+                const int32_t lab = best == kNoLabel ? -1 : (int32_t)(best - base_label);
                 const uint32_t o = v.perm[p];
                 v.labels[o] = lab;
                 if (v.core_out) v.core_out[o] = isc ? 1 : 0;
@@ -489,6 +497,67 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_labels_hd(HdView<T, DP> v) {
     for (int o = 16; o; o >>= 1) noise += __shfl_xor_sync(0xffffffffu, noise, o);
     if (lane == 0 && noise) atomicAdd(&v.ctr->n_noise, noise);
     add_counter(&v.ctr->work[5], lane == 0 ? chunks : 0u);
+}
+
+
+// Batched calls: per-set min / max of every dimension (mm[set * 64 + i] min encodings,
+// mm[(nsets + set) * 64 + i] max encodings); a warp whose points share one set reduces first.
+template <typename T>
+__global__ void __launch_bounds__(256) k_minmax_rt_seg(const T *__restrict__ in, int64_t n, int d,
+                                                      const int64_t *set_off, int nsets,
+                                                      unsigned long long *mm, DevCounters *ctr) {
+    const int lane = lane_id();
+    bool nan = false;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = base + lane;
+        const bool valid = j < n;
+        const uint32_t set = valid ? set_of_point(set_off, nsets, j) : 0xffffffffu;
+        const uint32_t s0 = __shfl_sync(0xffffffffu, set, 0);
+        const bool uniform = __all_sync(0xffffffffu, !valid || set == s0);
+        for (int i = 0; i < d; ++i) {
+            const double x = valid ? (double)in[j * d + i] : 0.0;
+            nan |= valid && (x != x);
+            if (uniform) {
+                double a = valid ? x : DBL_MAX, b = valid ? x : -DBL_MAX;
+                for (int o = 16; o; o >>= 1) {
+                    a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+                    b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+                }
+                if (lane == 0) {
+                    atomicMin(&mm[(uint64_t)s0 * 64 + i], (unsigned long long)enc_double(a));
+                    atomicMax(&mm[((uint64_t)nsets + s0) * 64 + i], (unsigned long long)enc_double(b));
+                }
+            } else if (valid) {
+                atomicMin(&mm[(uint64_t)set * 64 + i], (unsigned long long)enc_double(x));
+                atomicMax(&mm[((uint64_t)nsets + set) * 64 + i], (unsigned long long)enc_double(x));
+            }
+        }
+    }
+    if (__any_sync(0xffffffffu, nan) && lane == 0) atomicOr(&ctr->nan_seen, 1u);
+}
+
+// Batched calls: coarse cell keys with the set id above them; each set projects on its own
+// three dimensions (GridParams::sel).
+template <typename T, typename K>
+__global__ void __launch_bounds__(256) k_bin_proj_seg(const T *__restrict__ in, int64_t n, int d,
+                                                     const int64_t *set_off, int nsets, const GridParams *gtab,
+                                                     int key_bits, K *__restrict__ keys, uint32_t *__restrict__ idx) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t set = set_of_point(set_off, nsets, j);
+        const GridParams &g = gtab[set];
+        uint64_t key = (uint64_t)set << key_bits;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const double t = __dmul_rn(__dsub_rn((double)in[j * d + g.sel[i]], g.origin[i]), g.inv_side);
+            uint32_t c = (uint32_t)floor(t);
+            if (c > g.ncell[i] - 1) c = g.ncell[i] - 1;
+            key |= (uint64_t)c << g.shift[i];
+        }
+        keys[j] = (K)key;
+        idx[j] = (uint32_t)j;
+    }
 }
 
 }  // namespace hca

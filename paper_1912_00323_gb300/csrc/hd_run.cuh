@@ -102,6 +102,11 @@ int run_hd(const RunArgs &a) {
     const size_t o_parent = take(4 * n), o_cmin = take(4 * n);
     const size_t o_ranges = take(sizeof(uint2) * 9 * (size_t)n);
     const size_t o_nch = take(4 * n), o_choff = take(4 * n);
+    const bool batched = a.nsets > 0;
+    const int nsets = batched ? a.nsets : 1;
+    const size_t o_smm = take(sizeof(unsigned long long) * 2 * 64 * (size_t)nsets);
+    const size_t o_gtab = take(sizeof(GridParams) * (size_t)nsets);
+    const size_t o_setoff = take(sizeof(int64_t) * ((size_t)nsets + 1));
     void *ws = nullptr;
     if (pool_alloc(&ws, off, s) != cudaSuccess || !ws) return HCA_ENOMEM;
     char *b = (char *)ws;
@@ -129,18 +134,86 @@ int run_hd(const RunArgs &a) {
     LowdView<float, 3> lv;
     memset(&hv, 0, sizeof(hv));
     memset(&lv, 0, sizeof(lv));
+    int sort_bits = 0;
+    std::vector<unsigned long long> smm;
+    std::vector<GridParams> gsets;
+    GridParams *d_gtab = (GridParams *)(b + o_gtab);
+    int64_t *d_setoff = (int64_t *)(b + o_setoff);
+    unsigned long long *d_smm = (unsigned long long *)(b + o_smm);
 
     if (!h) { rc = HCA_ECUDA; goto out; }
     mark(0);
     cudaMemsetAsync(ctr, 0, sizeof(DevCounters), s);
-    cudaMemsetAsync(mm, 0xff, sizeof(unsigned long long) * 64, s);
-    cudaMemsetAsync(mm + 64, 0, sizeof(unsigned long long) * 64, s);
-    k_minmax_rt<T><<<grid_for(n * d, 256, sms, 8), 256, 0, s>>>((const T *)a.d_points, n, d, ctr, mm);
+    if (!batched) {
+        cudaMemsetAsync(mm, 0xff, sizeof(unsigned long long) * 64, s);
+        cudaMemsetAsync(mm + 64, 0, sizeof(unsigned long long) * 64, s);
+        k_minmax_rt<T><<<grid_for(n * d, 256, sms, 8), 256, 0, s>>>((const T *)a.d_points, n, d, ctr, mm);
+        cudaMemcpyAsync(hmm.data(), mm, sizeof(unsigned long long) * 128, cudaMemcpyDeviceToHost, s);
+    } else {
+        cudaMemsetAsync(d_smm, 0xff, sizeof(unsigned long long) * 64 * nsets, s);
+        cudaMemsetAsync(d_smm + (size_t)64 * nsets, 0, sizeof(unsigned long long) * 64 * nsets, s);
+        cudaMemcpyAsync(d_setoff, a.h_off, sizeof(int64_t) * (nsets + 1), cudaMemcpyHostToDevice, s);
+        k_minmax_rt_seg<T><<<grid_for(n, 256, sms, 4), 256, 0, s>>>((const T *)a.d_points, n, d, d_setoff, nsets,
+                                                                   d_smm, ctr);
+        smm.resize((size_t)2 * 64 * nsets);
+        cudaMemcpyAsync(smm.data(), d_smm, sizeof(unsigned long long) * smm.size(), cudaMemcpyDeviceToHost, s);
+    }
     ++launches;
     if (cudaMemcpyAsync(h, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(hmm.data(), mm, sizeof(unsigned long long) * 128, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) { rc = HCA_ECUDA; goto out; }
-    {
+    if (batched) {
+        if (h->nan_seen) { rc = HCA_EINVAL; goto out; }
+        gsets.resize(nsets);
+        std::vector<double> e_eps(nsets), e_side(nsets), e_tau(nsets);
+        uint32_t bits[3] = {};
+        for (int si = 0; si < nsets; ++si) {
+            const bool empty = a.h_off[si + 1] == a.h_off[si];
+            double mn_all[64], mx_all[64];
+            for (int i = 0; i < d; ++i) {
+                mn_all[i] = empty ? 0.0 : dec_double(smm[(size_t)si * 64 + i]);
+                mx_all[i] = empty ? 0.0 : dec_double(smm[((size_t)nsets + si) * 64 + i]);
+                if (!isfinite(mn_all[i]) || !isfinite(mx_all[i])) { rc = HCA_EINVAL; goto out; }
+            }
+            int pick[3] = {-1, -1, -1};
+            for (int k = 0; k < 3; ++k) {
+                double best = -1.0;
+                for (int i = 0; i < d; ++i) {
+                    if (i == pick[0] || i == pick[1]) continue;
+                    const double ext = mx_all[i] - mn_all[i];
+                    if (ext > best) { best = ext; pick[k] = i; }
+                }
+            }
+            const double mn3[3] = {mn_all[pick[0]], mn_all[pick[1]], mn_all[pick[2]]};
+            const double mx3[3] = {mx_all[pick[0]], mx_all[pick[1]], mx_all[pick[2]]};
+            double tau_s = 0.0;
+            rc = make_coarse_grid(sizeof(T) == 4, a.h_eps[si], a.h_minpts[si], n, mn3, mx3, a.flags, gsets[si], tau_s);
+            if (rc) goto out;
+            for (int k = 0; k < 3; ++k) gsets[si].sel[k] = pick[k];
+            e_eps[si] = a.h_eps[si];
+            e_side[si] = 1.0 / gsets[si].inv_side;
+            e_tau[si] = tau_s;
+            for (int i = 0; i < 3; ++i) bits[i] = bits[i] > gsets[si].bits[i] ? bits[i] : gsets[si].bits[i];
+        }
+        int key_bits = 0, set_bits = 1;
+        for (int i = 0; i < 3; ++i) key_bits += (int)bits[i];
+        while ((1ll << set_bits) < nsets) ++set_bits;
+        if (key_bits + set_bits > 63) { rc = HCA_ERANGE; goto out; }
+        for (GridParams &gp : gsets) {
+            int sh = 0;
+            for (int i = 2; i >= 0; --i) {
+                gp.bits[i] = bits[i];
+                gp.shift[i] = (uint32_t)sh;
+                sh += (int)bits[i];
+            }
+            gp.key_bits = key_bits;
+            gp.prefix_shift = (int)bits[2];
+        }
+        g = gsets[0];
+        sort_bits = key_bits + set_bits;
+        rc = make_stencil_union(3, e_eps, e_side, e_tau, st);
+        if (rc) goto out;
+        cudaMemcpyAsync(d_gtab, gsets.data(), sizeof(GridParams) * nsets, cudaMemcpyHostToDevice, s);
+    } else {
         if (h->nan_seen) { rc = HCA_EINVAL; goto out; }
         double mn_all[64], mx_all[64];
         for (int i = 0; i < d; ++i) {
@@ -165,26 +238,35 @@ int run_hd(const RunArgs &a) {
         if (rc) goto out;
         rc = make_stencil(3, a.eps, 1.0 / g.inv_side, tau, st);
         if (rc) goto out;
+        sort_bits = g.key_bits;
     }
     mark(1);
     {
         uint32_t *ia = (uint32_t *)(b + o_ia), *ib = (uint32_t *)(b + o_ib);
         uint32_t *hist = (uint32_t *)(b + o_hist), *part = (uint32_t *)(b + o_part);
-        const bool use32 = g.key_bits <= 32;
+        const bool use32 = sort_bits <= 32;
         if (use32) {
             uint32_t *ka = (uint32_t *)(b + o_ka), *kb = (uint32_t *)(b + o_kb);
-            k_bin_proj<T, uint32_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, d, sel, g, ka, ia);
+            if (batched)
+                k_bin_proj_seg<T, uint32_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, n, d, d_setoff, nsets, d_gtab,
+                                                                 g.key_bits, ka, ia);
+            else
+                k_bin_proj<T, uint32_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, d, sel, g, ka, ia);
             mark(2);
-            flipped = radix_sort_pairs<uint32_t>(ka, ia, kb, ib, n, 0, g.key_bits, hist, part, s, &launches, &ctr->status);
+            flipped = radix_sort_pairs<uint32_t>(ka, ia, kb, ib, n, 0, sort_bits, hist, part, s, &launches, &ctr->status);
             mark(3);
             k_gather_hd<T, DP, uint32_t><<<grid_for(n, 8, sms, 16), 256, 0, s>>>(
                 (const T *)a.d_points, d, flipped ? kb : ka, flipped ? ib : ia, n, (T *)(b + o_pts),
                 (uint32_t *)(b + o_flags));
         } else {
             uint64_t *ka = (uint64_t *)(b + o_ka), *kb = (uint64_t *)(b + o_kb);
-            k_bin_proj<T, uint64_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, d, sel, g, ka, ia);
+            if (batched)
+                k_bin_proj_seg<T, uint64_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, n, d, d_setoff, nsets, d_gtab,
+                                                                 g.key_bits, ka, ia);
+            else
+                k_bin_proj<T, uint64_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, d, sel, g, ka, ia);
             mark(2);
-            flipped = radix_sort_pairs<uint64_t>(ka, ia, kb, ib, n, 0, g.key_bits, hist, part, s, &launches, &ctr->status);
+            flipped = radix_sort_pairs<uint64_t>(ka, ia, kb, ib, n, 0, sort_bits, hist, part, s, &launches, &ctr->status);
             mark(3);
             k_gather_hd<T, DP, uint64_t><<<grid_for(n, 8, sms, 16), 256, 0, s>>>(
                 (const T *)a.d_points, d, flipped ? kb : ka, flipped ? ib : ia, n, (T *)(b + o_pts),
@@ -217,6 +299,7 @@ int run_hd(const RunArgs &a) {
                                        (uint32_t *)(b + o_pstart), (uint64_t *)(b + o_hk),
                                        (uint32_t *)(b + o_hv), ctr);
         lv.g = g;
+        lv.gtab = batched ? d_gtab : nullptr;
         lv.cell_key = (const uint64_t *)(b + o_ckey);
         lv.pencil_start = (const uint32_t *)(b + o_pstart);
         lv.hkeys = (uint64_t *)(b + o_hk);
@@ -231,6 +314,8 @@ int run_hd(const RunArgs &a) {
     }
     mark(5);
     hv.g = g;
+    hv.gtab = batched ? d_gtab : nullptr;
+    hv.set_off = batched ? d_setoff : nullptr;
     hv.d = d;
     hv.pts = (const T *)(b + o_pts);
     hv.cell_start = (const uint32_t *)(b + o_cstart);
@@ -283,8 +368,8 @@ int run_hd(const RunArgs &a) {
         so->n_core_points = h->n_core;
         so->n_clusters = h->n_clusters;
         so->n_noise = h->n_noise;
-        so->key_bits = g.key_bits;
-        so->sort_passes = (g.key_bits + 7) / 8;
+        so->key_bits = sort_bits;
+        so->sort_passes = (sort_bits + 7) / 8;
         so->kernel_launches = launches;
         so->n_count_chunks = (int64_t)h->work[0];
         so->n_rep_tests = (int64_t)h->work[1];   // hook-pass chunks in this path

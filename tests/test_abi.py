@@ -82,3 +82,14 @@ def test_oracle_and_library_share_no_code():
                 path.endswith("workloads.py"), path
     src = open(os.path.join(ROOT, "oracle", "hca_oracle.c")).read()
     assert "hca_dbscan.h" not in src and "csrc" not in src
+
+
+def test_server_argument_checks(pkg):
+    import ctypes
+    lib = pkg.load()
+    h = ctypes.c_void_p()
+    assert lib.hca_server_create(ctypes.byref(h), 0, 0, 2) == pkg.HCA_EINVAL
+    assert lib.hca_server_create(ctypes.byref(h), 0, 1 << 30, 0) == pkg.HCA_EINVAL
+    assert lib.hca_submit(None, None, None) == pkg.HCA_EINVAL
+    assert lib.hca_poll(None, 1) == pkg.HCA_EINVAL
+    assert lib.hca_cancel(None, 1) == pkg.HCA_EINVAL

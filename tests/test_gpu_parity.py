@@ -333,9 +333,11 @@ def test_batched_matches_oracle_per_set(env, d, dtype):
         np.testing.assert_array_equal(core[off[s]:off[s + 1]], want[1], err_msg=f"set {s}")
 
 
-def test_batched_high_d_sets(env):
+@pytest.mark.parametrize("d", [5, 8, 16])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_batched_high_d_sets(env, d, dtype):
     _, _, oracle = env
-    sets = _sets_for(8, 88, 12, np.float32)
+    sets = _sets_for(d, 80 + d, 24, dtype)
     lab, core, off, _ = _run_batched(env, sets)
     for s, (X, eps, mp) in enumerate(sets):
         if len(X):
@@ -343,7 +345,7 @@ def test_batched_high_d_sets(env):
             np.testing.assert_array_equal(lab[off[s]:off[s + 1]], want[0], err_msg=f"set {s}")
 
 
-@pytest.mark.parametrize("dims", [(2,), (3,)])
+@pytest.mark.parametrize("dims", [(2,), (3,), (8,)])
 def test_batched_recipe_equals_separate_calls(env, dims):
     """The batched recipe (blobs + noise, per-set eps and MINPTS): one batched call gives each
     set exactly the labels of a separate call on that set, and the oracle's."""
