@@ -368,12 +368,16 @@ def run_batched(args):
         off[1:] = np.cumsum([len(x) for x, _, _ in g])
         dev_groups.append((d, torch.from_numpy(X).cuda(), off, [e for _, e, _ in g], [m for _, _, m in g]))
     n_total = sum(len(x) for x, _, _ in sets)
-    per_d = {}
+    per_d, stages, work = {}, {}, {}
     def step():
         for d, t, off, e, m in dev_groups:
             t0 = time.perf_counter()
-            pkg.hca_dbscan_batched(t, off, e, m)
+            _, st = pkg.hca_dbscan_batched(t, off, e, m, timing=True)
             per_d[d] = time.perf_counter() - t0
+            stages[int(d)] = {k: round(v, 3) for k, v in st["stage_ms"].items()}
+            work[int(d)] = {k: st[k] for k in ("n_cells", "n_core_points", "n_count_chunks", "n_rep_tests",
+                                               "n_rep_hits", "n_exhaustive_pairs", "n_exhaustive_chunks",
+                                               "n_border_chunks")}
     for _ in range(max(args.warmup, 1)):
         step()
     torch.cuda.synchronize()
@@ -391,7 +395,8 @@ def run_batched(args):
             "config": {"workload": f"batched: {args.sets} sets, n log-uniform [1e3, 2e5], d in {{2,3,8}}, "
                                    "blobs + 10% noise, eps U[0.5,3], minPts U{4..16}",
                        "points": n_total, "sets_per_d": {int(d): len(g) for d, g in groups.items()}},
-            "ms_per_d": {int(d): 1e3 * t for d, t in per_d.items()}}
+            "ms_per_d": {int(d): 1e3 * t for d, t in per_d.items()}, "stage_ms_per_d": stages,
+            "work_per_d": work}
     print(json.dumps(line), flush=True)
     return 0
 
