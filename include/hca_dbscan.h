@@ -72,6 +72,8 @@ extern "C" {
 /* flags for hca_dbscan_device_ex */
 #define HCA_FLAG_TIMING 1     /* record CUDA events around each stage into stats->stage_ms */
 #define HCA_FLAG_FP64_ONLY 2  /* decide every distance in FP64 (no FP32 filter); same result */
+#define HCA_FLAG_NO_TENSOR_CORES 4  /* d >= 5, float input: compare pairs on the CUDA cores
+                                       instead of the tensor-core distance tiles; same result */
 
 /* stages timed with HCA_FLAG_TIMING (index into hca_stats.stage_ms) */
 #define HCA_STAGE_MINMAX 0    /* origin shift: per-dimension min / max (Sec. 2) */
@@ -107,6 +109,11 @@ typedef struct hca_stats {
     int64_t n_exhaustive_pairs;
     int64_t n_exhaustive_chunks;
     int64_t n_border_chunks;
+    /* d >= 5, float input: 128 x 128 tensor-core distance tiles computed (counts, unions and
+       labels together) and the pairs of those tiles that fell in the guard band and were
+       decided by the exact predicate */
+    int64_t n_tc_tiles;
+    int64_t n_tc_rechecks;
 } hca_stats;
 
 /*

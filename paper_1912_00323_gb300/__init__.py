@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "libhca_dbscan.so")
 HCA_F32, HCA_F64 = 0, 1
 HCA_OK, HCA_EINVAL, HCA_ENOMEM, HCA_ECUDA, HCA_ERANGE, HCA_ENOTIMPL, HCA_EDEVICE = 0, -1, -2, -3, -4, -5, -6
 HCA_ETOOLARGE, HCA_ETIMEDOUT, HCA_ECANCELED, HCA_EBUSY = -7, -8, -9, -10
-HCA_FLAG_TIMING, HCA_FLAG_FP64_ONLY = 1, 2
+HCA_FLAG_TIMING, HCA_FLAG_FP64_ONLY, HCA_FLAG_NO_TENSOR_CORES = 1, 2, 4
 STAGES = ("minmax", "bin", "sort", "cells", "hash", "core", "reps", "merge", "labels")
 
 ABI_FUNCTIONS = ("hca_dbscan", "hca_dbscan_device", "hca_dbscan_device_ex", "hca_dbscan_batched",
@@ -40,7 +40,8 @@ class HcaStats(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("stage_ms", ctypes.c_float * len(STAGES)),
                 ("n_count_chunks", ctypes.c_int64), ("n_rep_tests", ctypes.c_int64),
                 ("n_rep_hits", ctypes.c_int64), ("n_exhaustive_pairs", ctypes.c_int64),
-                ("n_exhaustive_chunks", ctypes.c_int64), ("n_border_chunks", ctypes.c_int64)]
+                ("n_exhaustive_chunks", ctypes.c_int64), ("n_border_chunks", ctypes.c_int64),
+                ("n_tc_tiles", ctypes.c_int64), ("n_tc_rechecks", ctypes.c_int64)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_ if name not in ("stage_ms", "reserved")}
@@ -152,10 +153,12 @@ def _stream_ptr(stream):
 
 
 def hca_dbscan_device(points, eps: float, min_pts: int, labels=None, core=None, stream=None,
-                      stats: bool = False, timing: bool = False, fp64_only: bool = False):
+                      stats: bool = False, timing: bool = False, fp64_only: bool = False,
+                      tensor_cores: bool = True):
     """Cluster a CUDA tensor of shape (n, d).  Returns the int32 label tensor, or
     (labels, stats_dict) when stats or timing is requested.  `core`, if given, is a uint8
-    CUDA tensor of length n that receives the core flags."""
+    CUDA tensor of length n that receives the core flags.  tensor_cores=False keeps the d >= 5
+    float path on the CUDA cores (same labels)."""
     import torch
     lib = load()
     if not points.is_cuda:
@@ -166,7 +169,8 @@ def hca_dbscan_device(points, eps: float, min_pts: int, labels=None, core=None, 
     code = _dtype_code(pts.dtype)
     if labels is None:
         labels = torch.empty(n, dtype=torch.int32, device=pts.device)
-    flags = (HCA_FLAG_TIMING if timing else 0) | (HCA_FLAG_FP64_ONLY if fp64_only else 0)
+    flags = ((HCA_FLAG_TIMING if timing else 0) | (HCA_FLAG_FP64_ONLY if fp64_only else 0)
+             | (0 if tensor_cores else HCA_FLAG_NO_TENSOR_CORES))
     st = HcaStats()
     rc = lib.hca_dbscan_device_ex(pts.data_ptr(), code, n, d, float(eps), int(min_pts),
                                   labels.data_ptr(), core.data_ptr() if core is not None else None,
@@ -179,7 +183,8 @@ def hca_dbscan_device(points, eps: float, min_pts: int, labels=None, core=None, 
 
 
 def hca_dbscan_batched(points, offsets, eps, min_pts, labels=None, core=None, stream=None,
-                       stats: bool = False, timing: bool = False, fp64_only: bool = False):
+                       stats: bool = False, timing: bool = False, fp64_only: bool = False,
+                       tensor_cores: bool = True):
     """Cluster the sets points[offsets[s]:offsets[s+1]] (a CUDA tensor (N, d)), each with its
     own eps[s] and min_pts[s] (host sequences).  Labels are per set (ids are indices within the
     set).  Returns the label tensor, or (labels, stats_dict) when stats or timing is requested."""
@@ -197,7 +202,8 @@ def hca_dbscan_batched(points, offsets, eps, min_pts, labels=None, core=None, st
         raise ValueError("offsets must have n_sets + 1 entries ending at len(points); eps, min_pts n_sets")
     if labels is None:
         labels = torch.empty(n, dtype=torch.int32, device=pts.device)
-    flags = (HCA_FLAG_TIMING if timing else 0) | (HCA_FLAG_FP64_ONLY if fp64_only else 0)
+    flags = ((HCA_FLAG_TIMING if timing else 0) | (HCA_FLAG_FP64_ONLY if fp64_only else 0)
+             | (0 if tensor_cores else HCA_FLAG_NO_TENSOR_CORES))
     st = HcaStats()
     rc = lib.hca_dbscan_batched(pts.data_ptr(), _dtype_code(pts.dtype), len(e), off.ctypes.data, d,
                                 e.ctypes.data, m.ctypes.data, labels.data_ptr(),

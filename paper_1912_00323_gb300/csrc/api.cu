@@ -263,4 +263,4 @@ extern "C" const char *hca_strerror(int code) {
     return "unknown error";
 }
 
-extern "C" int32_t hca_version(void) { return 100; }
+extern "C" int32_t hca_version(void) { return 101; }

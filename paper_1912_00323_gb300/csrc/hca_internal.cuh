@@ -33,7 +33,9 @@ struct DevCounters {
     uint32_t minmax_enc[2 * kMaxD * 2];  // order-preserving encodings of min / max per dim
     uint32_t nan_seen;
     uint32_t n_chunks;     // 32-point chunks of the coarse cells (high-dimensional path)
-    uint32_t pad[2];
+    uint32_t n_tc_chunks[3];  // 128-row chunks of the tensor-core phases: counts, unions, labels
+    uint32_t tc_next[3];      // next unclaimed chunk of each tensor-core phase
+    uint32_t pad;
     unsigned long long work[8];  // work counters (see hca_stats)
     uint32_t digit_counts[8 * 256];  // radix digit counts per pass, filled while binning
 };

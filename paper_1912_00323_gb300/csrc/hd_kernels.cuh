@@ -40,6 +40,10 @@ struct HdView {
     uint8_t *core_out;
     DevCounters *ctr;
     int n_all, n_half;
+    // cells left to the tensor-core kernels (float input): those with at least tc_min_rows rows
+    // of a phase (0: none); cx = exclusive scan of the core flags, for the per-cell core counts
+    uint32_t tc_min_rows;
+    const uint32_t *cx;
 };
 
 constexpr int kHdWarps = 4;   // warps per block in the point kernels of this path
@@ -214,12 +218,15 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_count_hd(HdView<T, DP> v) {
     const int lane = lane_id();
     uint32_t chunks = 0;
     HD_FOR_EACH_CHUNK(v, A, base, e) {
+        // a cell counted on the tensor cores leaves here only the rows it handed over (core = 2)
+        const bool tc_cell = v.tc_min_rows && e - v.cell_start[A] >= v.tc_min_rows;
+        const bool have = base + lane < e && (!tc_cell || v.core[base + lane] == 2);
+        unsigned open = __ballot_sync(0xffffffffu, have);
+        if (!open) continue;
         const GridParams &G = params_of(v, set_of_key(v, v.cell_key[A]));
         const uint32_t min_pts = G.min_pts;
         stage_rows<T, DP>(rows, v.pts, base, e);
-        const bool have = base + lane < e;
         uint32_t cnt = 0;
-        unsigned open = __ballot_sync(0xffffffffu, have);
         for (int g0 = 0; g0 < v.n_all && open; g0 += 32) {
             const int k = g0 + lane;
             const uint2 rg = k < v.n_all ? v.ranges[(uint64_t)A * v.n_all + k] : make_uint2(0u, 0u);
@@ -336,6 +343,7 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_merge_hd(HdView<T, DP> v) {
     uint32_t chunks = 0, tests = 0, skipped = 0;
     HD_FOR_EACH_CHUNK(v, A, base, e) {
         if (!v.cell_core[A]) continue;
+        if (v.tc_min_rows && v.cx[e] - v.cx[v.cell_start[A]] >= v.tc_min_rows) continue;  // tensor-core cell
         const uint32_t p = base + lane;
         const bool pc = p < e && v.core[p];
         const unsigned amask = __ballot_sync(0xffffffffu, pc);
@@ -442,6 +450,10 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_labels_hd(HdView<T, DP> v) {
     const int lane = lane_id();
     uint32_t noise = 0, chunks = 0;
     HD_FOR_EACH_CHUNK(v, A, base, e) {
+        if (v.tc_min_rows) {  // non-core rows of a tensor-core cell: labelled there
+            const uint32_t s0 = v.cell_start[A];
+            if (e - s0 - (v.cx[e] - v.cx[s0]) >= v.tc_min_rows) continue;
+        }
         {
             const uint32_t aset = set_of_key(v, v.cell_key[A]);
             const GridParams &G = params_of(v, aset);

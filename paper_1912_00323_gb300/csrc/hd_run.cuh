@@ -1,8 +1,11 @@
 // Host orchestration of the high-dimensional path (5 <= d <= 64) for one call.
 #pragma once
 
+#include <type_traits>
+
 #include "hd_kernels.cuh"
 #include "lowd_run.cuh"
+#include "tc_kernels.cuh"
 
 namespace hca {
 
@@ -70,7 +73,116 @@ inline void allow_smem(Kern k, size_t bytes) {
     if (bytes > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// The tensor-core filter's error bound needs finite FP32 norms and products: d * extent^2 <=
+// 2^100 in every dimension and the FP32 filter enabled (eps^2 in [2^-100, 2^100]).
+inline bool tc_magnitude_ok(int d, const double *mn, const double *mx, const GridParams &g) {
+    if (!(g.lo32 >= 0.0f)) return false;
+    for (int i = 0; i < d; ++i) {
+        const double ext = mx[i] - mn[i];
+        if (!(d * ext * ext <= ldexp(1.0, 100))) return false;
+    }
+    return true;
+}
+
+// Launch shape of the tensor-core kernels: their own shared memory, raised until a fifth CTA
+// no longer fits on an SM (each CTA holds 128 of the SM's 512 tensor-memory columns, so four
+// resident CTAs never wait in tcgen05.alloc), and the resident CTAs per SM (0: do not use).
+template <int DP>
+inline int tc_launch_shape(size_t &smem) {
+    int dev = 0, sm_bytes = 0, reserved = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess)
+        return 0;
+    size_t need = tc::smem_bytes<DP>();
+    const size_t floor5 = (size_t)sm_bytes / 5 - (size_t)reserved + 16;  // 5 (floor5 + reserved) > sm_bytes
+    if (need < floor5) need = floor5;
+    smem = (need + 127) & ~(size_t)127;
+    auto setup = [&](auto k) {
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    };
+    setup(tc::k_tc_hd<DP, tc::kCount>);
+    setup(tc::k_tc_hd<DP, tc::kMerge>);
+    setup(tc::k_tc_hd<DP, tc::kLabels>);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tc::k_tc_hd<DP, tc::kCount>, tc::kTile, smem) !=
+            cudaSuccess ||
+        occ < 1)
+        return 0;
+    // CTAs per SM that the shared memory admits (at most 4); more launched than can be resident
+    // only wait for a slot, and find the chunk counter exhausted
+    const int fit = (int)((size_t)sm_bytes / (smem + (size_t)reserved));
+    return fit < 1 ? 0 : (fit > 4 ? 4 : fit);
+}
+
 }  // namespace detail
+
+// Rows of a phase from which a coarse cell goes to the tensor-core kernels.
+inline uint32_t tc_min_rows() {
+    static const uint32_t v = [] {
+        const char *e = getenv("HCA_TC_MIN_ROWS");
+        const int x = e ? atoi(e) : 64;
+        return (uint32_t)(x < 1 ? 1 : x);
+    }();
+    return v;
+}
+
+// Workspace offsets of the tensor-core phases.
+struct TcOffsets {
+    size_t nch, nch2, ch0, ch1, ch2, flags, cx, clist, nclist, clab;
+};
+
+inline uint32_t *part_of(char *b, size_t o) { return (uint32_t *)(b + o); }
+
+// The three point phases with tensor-core tiles for the cells holding at least min_rows rows
+// of a phase and the CUDA-core kernels for the rest (float input): counts (Definition 2),
+// first links + pointer jumping + unions (Definitions 3-5) and labels (Algorithm 4).
+template <int DP, typename Mark>
+void run_tc_phases(HdView<float, DP> &hv, cudaStream_t s, char *b, int64_t n, int grid_tc, size_t tc_smem,
+                   int gpts, int gcell, size_t smem, uint32_t *part, const TcOffsets &o, int nsets,
+                   DevCounters *ctr, uint32_t min_rows, Mark &mark, int &launches) {
+    uint32_t *nch = (uint32_t *)(b + o.nch), *nch2 = (uint32_t *)(b + o.nch2);
+    uint32_t *ch0 = (uint32_t *)(b + o.ch0), *ch1 = (uint32_t *)(b + o.ch1), *ch2 = (uint32_t *)(b + o.ch2);
+    uint32_t *flags = (uint32_t *)(b + o.flags), *cx = (uint32_t *)(b + o.cx);
+    uint32_t *clist = (uint32_t *)(b + o.clist), *nclist = (uint32_t *)(b + o.nclist);
+    uint32_t *clab = (uint32_t *)(b + o.clab);
+    hv.tc_min_rows = min_rows;
+    hv.cx = cx;
+    // ---- Definition 2: exact counts over the neighbouring coarse cells ----
+    cudaMemsetAsync(hv.cell_core, 0, (size_t)n, s);
+    tc::k_tc_chunks_count<<<gpts, 256, 0, s>>>(hv.cell_start, ctr, min_rows, nch);
+    exclusive_scan_u32(nch, ch0, n, &ctr->n_cells, &ctr->n_tc_chunks[tc::kCount], part, s, &launches);
+    tc::k_tc_hd<DP, tc::kCount><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch0, cx, clist, nclist, clab});
+    k_count_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
+    launches += 3;
+    mark(6);
+    // core numbering, core and non-core lists, chunk tables of the unions and the labels
+    tc::k_tc_core_flags<<<gpts, 256, 0, s>>>(hv.core, n, flags);
+    exclusive_scan_u32(flags, cx, n, nullptr, cx + n, part, s, &launches);
+    tc::k_tc_partition<<<gpts, 256, 0, s>>>(hv.core, cx, n, clist, nclist);
+    tc::k_tc_chunks_split<<<gpts, 256, 0, s>>>(hv.cell_start, cx, ctr, min_rows, nch, nch2);
+    exclusive_scan_u32(nch, ch1, n, &ctr->n_cells, &ctr->n_tc_chunks[tc::kMerge], part, s, &launches);
+    exclusive_scan_u32(nch2, ch2, n, &ctr->n_cells, &ctr->n_tc_chunks[tc::kLabels], part, s, &launches);
+    launches += 3;
+    mark(7);
+    // ---- Definitions 3-5: first links, pointer jumping, then the remaining unions ----
+    k_uf_init_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
+    k_hook_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
+    for (int r = 0; r < 6; ++r) k_jump_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
+    tc::k_tc_hd<DP, tc::kMerge><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch1, cx, clist, nclist, clab});
+    k_merge_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
+    k_compress_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
+    launches += 11;
+    mark(8);
+    // ---- Algorithm 4: canonical ids, core labels, border and noise points ----
+    k_comp_min_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
+    tc::k_tc_core_labels<DP><<<gpts, 256, 0, s>>>(hv, tc::Tables{ch2, cx, clist, nclist, clab}, nsets, clab);
+    tc::k_tc_hd<DP, tc::kLabels><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch2, cx, clist, nclist, clab});
+    k_labels_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
+    launches += 4;
+    mark(9);
+}
 
 template <typename T, int DP>
 int run_hd(const RunArgs &a) {
@@ -107,6 +219,17 @@ int run_hd(const RunArgs &a) {
     const size_t o_smm = take(sizeof(unsigned long long) * 2 * 64 * (size_t)nsets);
     const size_t o_gtab = take(sizeof(GridParams) * (size_t)nsets);
     const size_t o_setoff = take(sizeof(int64_t) * ((size_t)nsets + 1));
+    // tensor-core phases (float input): chunk tables, core numbering, core / non-core lists
+    size_t tc_smem = 0;
+    int tc_occ = 0;
+    if constexpr (std::is_same<T, float>::value)
+        if (!(a.flags & (HCA_FLAG_FP64_ONLY | HCA_FLAG_NO_TENSOR_CORES))) tc_occ = tc_launch_shape<DP>(tc_smem);
+    const size_t tc_n = tc_occ ? (size_t)n : 0;
+    const size_t o_tnch = take(4 * tc_n), o_tnch2 = take(4 * tc_n);
+    const size_t o_tch0 = take(4 * tc_n), o_tch1 = take(4 * tc_n), o_tch2 = take(4 * tc_n);
+    const size_t o_tflags = take(4 * tc_n), o_cx = take(4 * (tc_n + 1));
+    const size_t o_clist = take(4 * tc_n), o_nclist = take(4 * tc_n), o_clab = take(4 * tc_n);
+    bool use_tc = tc_occ > 0;
     void *ws = nullptr;
     if (pool_alloc(&ws, off, s) != cudaSuccess || !ws) return HCA_ENOMEM;
     char *b = (char *)ws;
@@ -188,6 +311,7 @@ int run_hd(const RunArgs &a) {
             double tau_s = 0.0;
             rc = make_coarse_grid(sizeof(T) == 4, a.h_eps[si], a.h_minpts[si], n, mn3, mx3, a.flags, gsets[si], tau_s);
             if (rc) goto out;
+            if (!tc_magnitude_ok(d, mn_all, mx_all, gsets[si])) use_tc = false;
             for (int k = 0; k < 3; ++k) gsets[si].sel[k] = pick[k];
             e_eps[si] = a.h_eps[si];
             e_side[si] = 1.0 / gsets[si].inv_side;
@@ -236,6 +360,7 @@ int run_hd(const RunArgs &a) {
         const double mx3[3] = {mx_all[pick[0]], mx_all[pick[1]], mx_all[pick[2]]};
         rc = make_coarse_grid(sizeof(T) == 4, a.eps, a.min_pts, n, mn3, mx3, a.flags, g, tau);
         if (rc) goto out;
+        if (!tc_magnitude_ok(d, mn_all, mx_all, g)) use_tc = false;
         rc = make_stencil(3, a.eps, 1.0 / g.inv_side, tau, st);
         if (rc) goto out;
         sort_bits = g.key_bits;
@@ -335,6 +460,15 @@ int run_hd(const RunArgs &a) {
     allow_smem(k_hook_hd<T, DP>, smem);
     allow_smem(k_merge_hd<T, DP>, smem);
     allow_smem(k_labels_hd<T, DP>, smem);
+    if constexpr (std::is_same<T, float>::value) {
+        if (use_tc && st.n_all <= tc::kMaxRng) {
+            run_tc_phases<DP>(hv, s, b, n, sms * tc_occ, tc_smem, gpts, gcell, smem, part_of(b, o_part),
+                              TcOffsets{o_tnch, o_tnch2, o_tch0, o_tch1, o_tch2, o_tflags, o_cx, o_clist, o_nclist,
+                                        o_clab},
+                              batched ? nsets : 0, ctr, tc_min_rows(), mark, launches);
+            goto done_phases;
+        }
+    }
     // ---- Definition 2: exact counts over the neighbouring coarse cells ----
     cudaMemsetAsync(hv.cell_core, 0, (size_t)n, s);
     k_count_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
@@ -355,6 +489,7 @@ int run_hd(const RunArgs &a) {
     k_labels_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
     launches += 2;
     mark(9);
+done_phases:
     if (cudaGetLastError() != cudaSuccess) { rc = HCA_ECUDA; goto out; }
     if (cudaMemcpyAsync(h, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) { rc = HCA_ECUDA; goto out; }
@@ -377,6 +512,8 @@ int run_hd(const RunArgs &a) {
         so->n_exhaustive_pairs = (int64_t)h->work[3];
         so->n_exhaustive_chunks = (int64_t)h->work[4];
         so->n_border_chunks = (int64_t)h->work[5];
+        so->n_tc_tiles = (int64_t)h->work[6];
+        so->n_tc_rechecks = (int64_t)h->work[7];
         for (int i = 0; i < HCA_NUM_STAGES; ++i) {
             float ms = 0.f;
             if (timing) cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);

@@ -1,0 +1,588 @@
+// Tensor-core distance tiles for the high-dimensional path (float input, DP = 8, 16, 32, 64).
+//
+// The three point phases of the coarse-grid path (the counts of Definition 2, the unions of
+// Definitions 3-5 and the labels of Algorithm 4) all test point pairs of neighbouring coarse
+// cells against eps.  Here a CTA of 128 threads takes up to 128 rows of one coarse cell (all
+// its points for the counts, its core points for the unions, its non-core points for the
+// labels) and streams the candidate points of the neighbouring cells (all points for the
+// counts, the core points otherwise) in blocks of 128.  Rows and candidates are centred on
+// the chunk's first row, c, and staged in shared memory in the K-major, unswizzled operand
+// layout of tcgen05; one thread issues tcgen05.mma kind::tf32 (K = 8 per instruction) into a
+// 128 x 128 FP32 accumulator in tensor memory, and every thread reads its row back with
+// tcgen05.ld and classifies its 128 pairs.
+//
+// Filter and error bound.  With x = a - c and y = b - c rounded to FP32, S = |x|^2 + |y|^2 and
+// dot the tensor-core value of x.y, d2 = S - 2 dot approximates |a - b|^2.  The tensor core
+// reads FP32 operands as TF32 (relative error below 2^-10 each), forms exact products and
+// accumulates in FP32, so |dot - x.y| <= (2^-9 + 2^-20 + K 2^-23) sum |x_i y_i| with
+// sum |x_i y_i| <= S / 2; the FP32 norms add at most 2^-18 S, and the rounding of the
+// centring at most 2^-21 S to |a - b|^2.  Everything together stays below 0.52 * 2^-8 S, so
+// with E = 2^-8 S
+//   d2 + E < eps^2 (1 - 2^-20)  =>  |a - b|^2 < eps^2 (1 - 2^-22)  (pair within eps),
+//   d2 - E > eps^2 (1 + 2^-20)  =>  |a - b|^2 > eps^2 (1 + 2^-21)  (pair outside eps),
+// both far enough from eps^2 that the FP64 sum of the exact predicate lands on the same side;
+// every other pair is decided by the exact predicate on the original coordinates (FP32
+// filter, FP64 recheck).  The labels are therefore the exact ones.  The two tests are written
+// as dot > rowA + colA and dot < rowR + colR with per-row and per-column halves of
+// ((1 +- 2^-8) S - eps^2 (1 -+ 2^-20)) / 2; their FP32 rounding (a few 2^-24 of S or eps^2)
+// stays inside the unused half of E, because a pair near eps has S >= eps^2 / 2.  The host
+// enables these kernels only when every extent satisfies d * extent^2 <= 2^100 and eps^2 lies
+// in [2^-100, 2^100], so no FP32 value above overflows or loses the bound to underflow.
+//
+// Residency: each CTA holds 128 of the 512 tensor-memory columns of an SM; the dynamic
+// shared memory of at least 48 KB per CTA keeps at most four CTAs of these kernels on an SM,
+// so tcgen05.alloc never waits for a CTA that is not running.  Every wait on the MMA's
+// mbarrier is bounded; a wait that runs out sets the status word, and the CTA stops, waits
+// once more (bounded) for the outstanding MMA and frees its tensor memory.
+#pragma once
+
+#include "hd_kernels.cuh"
+
+namespace hca {
+namespace tc {
+
+constexpr int kTile = 128;                 // rows per chunk (MMA M) and candidates per block (MMA N)
+constexpr uint32_t kLBO = 128;             // bytes between core matrices along K
+constexpr uint32_t kWaitLimit = 1u << 22;  // mbarrier polls before a wait gives up
+constexpr size_t kMinSmem = 48 * 1024;     // per CTA: at most 4 CTAs (4 x 128 TMEM columns) per SM
+constexpr int kMaxRng = 32;                // neighbour ranges per cell (the coarse grid has 9)
+constexpr int kHandOff = 8;                // open count rows at which a chunk hands over to the CUDA cores
+enum { kCount = 0, kMerge = 1, kLabels = 2 };
+
+// Row and candidate lists of the three phases.
+struct Tables {
+    const uint32_t *choff;      // first 128-row chunk of every coarse cell (this phase)
+    const uint32_t *cx;         // exclusive scan of the core flags over sorted points (n + 1)
+    const uint32_t *core_list;  // core points, ascending
+    const uint32_t *nc_list;    // non-core points, ascending
+    const uint32_t *core_lab;   // cluster id of every core point, by core-list index (labels phase)
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Byte offset of element (row, k) in the K-major canonical layout: 8 x 16-byte core matrices,
+// consecutive along K every kLBO bytes, 8-row groups every DP / 4 core matrices.
+template <int DP>
+__device__ __forceinline__ uint32_t op_offset(int row, int k) {
+    constexpr uint32_t sbo = (DP / 4) * 128;
+    return (uint32_t)(row >> 3) * sbo + (uint32_t)(k >> 2) * kLBO + (uint32_t)(row & 7) * 16 + (uint32_t)(k & 3) * 4;
+}
+
+// Shared-memory matrix descriptor: start address >> 4, leading and stride byte offsets >> 4,
+// descriptor version 1 (bit 46), no swizzle.
+template <int DP>
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    constexpr uint32_t sbo = (DP / 4) * 128;
+    uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)(kLBO >> 4) << 16;
+    d |= (uint64_t)(sbo >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::tf32: D F32 (bit 4), A and B TF32 (bits 7, 10), both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24.
+__device__ __forceinline__ uint32_t idesc_tf32() {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTile >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+// Bounded wait for the completion of the given phase of an mbarrier; false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+    uint32_t done = 0;
+    for (uint32_t it = 0; it < kWaitLimit && !done; ++it) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+    }
+    return done != 0;
+}
+
+// 32 consecutive accumulator columns of this warp's 32 lanes (lane i of warp w = row 32 w + i).
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int DP>
+struct Smem {
+    float a[kTile * DP];       // rows, centred, operand layout
+    float b[kTile * DP];       // candidates, centred, operand layout
+    float a_orig[kTile * DP];  // rows, original coordinates, row-major
+    float b_orig[kTile * DP];  // candidates, original coordinates, row-major
+    float2 cth[kTile];         // per candidate: (1 + 2^-8) |y|^2 / 2, (1 - 2^-8) |y|^2 / 2; inf if empty
+    uint32_t cpay[kTile];      // per candidate: tree node (unions) or cluster id (labels)
+    uint32_t cidx[kTile];      // per candidate: list index
+    uint32_t rq0[kMaxRng];     // first list index of each neighbour range
+    uint32_t rpre[kMaxRng + 1];  // stream offset of each range; [kMaxRng] = stream length
+    uint64_t mbar;
+    uint32_t taddr, ref, next, pad;
+};
+
+template <int DP>
+inline size_t smem_bytes() {
+    return sizeof(Smem<DP>) > kMinSmem ? sizeof(Smem<DP>) : kMinSmem;
+}
+
+// Copy row j of pts (or zeros) into row `row` of a row-major staging array.
+template <int DP>
+__device__ __forceinline__ void stage_orig(float *rows, int row, const float *pts, uint32_t j, bool valid) {
+    const float4 *src = reinterpret_cast<const float4 *>(pts + (uint64_t)j * DP);
+    float4 *dst = reinterpret_cast<float4 *>(rows + row * DP);
+#pragma unroll
+    for (int k = 0; k < DP / 4; ++k) dst[k] = valid ? src[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Centre staged row `row` on c (FP32 subtraction), store it in the operand layout and return
+// its squared norm (FP32); an invalid row becomes the zero row.
+template <int DP>
+__device__ __forceinline__ float stage_centred(float *op, int row, const float *orig, const float *c, bool valid) {
+    float nrm = 0.f;
+#pragma unroll
+    for (int k = 0; k < DP; k += 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(orig + row * DP + k);
+        const float4 cc = *reinterpret_cast<const float4 *>(c + k);
+        float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (valid) {
+            w.x = __fsub_rn(q.x, cc.x);
+            w.y = __fsub_rn(q.y, cc.y);
+            w.z = __fsub_rn(q.z, cc.z);
+            w.w = __fsub_rn(q.w, cc.w);
+        }
+        nrm = __fmaf_rn(w.x, w.x, nrm);
+        nrm = __fmaf_rn(w.y, w.y, nrm);
+        nrm = __fmaf_rn(w.z, w.z, nrm);
+        nrm = __fmaf_rn(w.w, w.w, nrm);
+        *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(op) + op_offset<DP>(row, k)) = w;
+    }
+    return nrm;
+}
+
+// The exact predicate on two staged rows: FP32 filter with the guard band of GridParams, FP64
+// sum in dimension order in the band.
+template <int DP>
+__device__ __forceinline__ bool within_rows(const float *a, const float *b, const GridParams &g) {
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < DP; i += 4) {
+        const float4 av = *reinterpret_cast<const float4 *>(a + i);
+        const float4 bv = *reinterpret_cast<const float4 *>(b + i);
+        float t = __fsub_rn(av.x, bv.x);  s = __fmaf_rn(t, t, s);
+        t = __fsub_rn(av.y, bv.y);        s = __fmaf_rn(t, t, s);
+        t = __fsub_rn(av.z, bv.z);        s = __fmaf_rn(t, t, s);
+        t = __fsub_rn(av.w, bv.w);        s = __fmaf_rn(t, t, s);
+    }
+    if (s < g.lo32) return true;
+    if (s > g.hi32) return false;
+    double e = 0.0;
+#pragma unroll
+    for (int i = 0; i < DP; ++i) {
+        const double t = __dsub_rn((double)a[i], (double)b[i]);
+        e = __dadd_rn(e, __dmul_rn(t, t));
+    }
+    return e <= g.eps2;
+}
+
+template <int MODE>
+__device__ __forceinline__ uint32_t row_point(const Tables &tt, uint32_t k) {
+    return MODE == kCount ? k : MODE == kMerge ? __ldg(tt.core_list + k) : __ldg(tt.nc_list + k);
+}
+
+// Candidate u of the chunk's stream: the neighbour ranges laid end to end (list indices
+// rq0[g] .. rq0[g] + (rpre[g + 1] - rpre[g])).  Returns the list index.
+__device__ __forceinline__ uint32_t stream_index(const uint32_t *rpre, const uint32_t *rq0, int n_rng, uint32_t u) {
+    int lo = 0, hi = n_rng;  // last g with rpre[g] <= u
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (rpre[mid] <= u) lo = mid; else hi = mid;
+    }
+    return rq0[lo] + (u - rpre[lo]);
+}
+
+// One phase over tensor-core tiles (MODE = kCount, kMerge or kLabels) for the coarse cells
+// with at least tc_min_rows rows of that phase (the other cells are left to the CUDA-core
+// kernels); persistent CTAs take 128-row chunks from a counter.  The candidates of a chunk
+// (its neighbour ranges laid end to end) stream through in blocks of 128; the next block's
+// rows are loaded into registers while the current block is multiplied and classified.
+//   kCount:  rows = every point of the cell, candidates = every point of the 27 neighbouring
+//            cells; core[p] = (|N_eps(p)| >= MINPTS).  A row stops at MINPTS; once at most
+//            kHandOff rows of a chunk are still open the chunk stops and marks them core[p] = 2,
+//            and the CUDA-core count finishes them.
+//   kMerge:  rows = core points, candidates = core points of the upper half of the
+//            neighbourhood after the row (each unordered pair once); a pair within eps whose
+//            trees differ is joined.  A block whose rows and candidates all share one tree
+//            node is skipped before the MMA.
+//   kLabels: rows = non-core points, candidates = core points of the 27 cells; the row takes
+//            the smallest cluster id among the candidates within eps, else -1.
+template <int DP, int MODE>
+__global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    Smem<DP> &S = *reinterpret_cast<Smem<DP> *>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t mbar = smem_u32(&S.mbar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.taddr)),
+                     "r"(kTile));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t taddr = S.taddr;
+    const uint32_t t_lane = taddr + ((uint32_t)(warp * 32) << 16);
+    const uint32_t idesc = idesc_tf32();
+    const uint32_t C = v.ctr->n_cells, NC = v.ctr->n_tc_chunks[MODE];
+    const int n_rng = MODE == kMerge ? v.n_half : v.n_all;
+    uint32_t phase = 0;
+    bool failed = false;  // CTA-uniform
+    uint32_t n_tiles = 0, n_skip = 0, n_re = 0, n_noise = 0;
+
+    for (;;) {
+        __syncthreads();  // every thread is done with the shared memory of the previous chunk
+        if (tid == 0) S.next = failed ? NC : atomicAdd(&v.ctr->tc_next[MODE], 1u);
+        __syncthreads();
+        const uint32_t t = S.next;
+        if (t >= NC) break;
+        const uint32_t A = chunk_cell(tt.choff, C, t);
+        const uint32_t aset = set_of_key(v, v.cell_key[A]);
+        const GridParams &G = params_of(v, aset);
+        const uint32_t cs0 = v.cell_start[A], cs1 = v.cell_start[A + 1];
+        uint32_t rbeg, rend;
+        if (MODE == kCount) {
+            rbeg = cs0;
+            rend = cs1;
+        } else if (MODE == kMerge) {
+            rbeg = tt.cx[cs0];
+            rend = tt.cx[cs1];
+        } else {
+            rbeg = cs0 - tt.cx[cs0];
+            rend = cs1 - tt.cx[cs1];
+        }
+        const uint32_t k0 = rbeg + (uint32_t)kTile * (t - tt.choff[A]);  // list index of row 0
+        const uint32_t rk = k0 + (uint32_t)tid;
+        const bool have = rk < rend;
+        const uint32_t p = have ? row_point<MODE>(tt, rk) : 0u;
+        stage_orig<DP>(S.a_orig, tid, v.pts, p, have);
+        // the candidate stream: one range per warp-0 lane, then a prefix over the ranges
+        if (warp == 0) {
+            uint32_t q0 = 0, len = 0;
+            if (tid < n_rng) {
+                uint2 rg = v.ranges[(uint64_t)A * v.n_all + tid];
+                if (MODE == kMerge && tid == 0) rg.x = A;  // own pencil: this cell and the ones after it
+                if (rg.x < rg.y) {
+                    q0 = v.cell_start[rg.x];
+                    uint32_t q1 = v.cell_start[rg.y];
+                    if (MODE != kCount) {
+                        q0 = tt.cx[q0];
+                        q1 = tt.cx[q1];
+                    }
+                    if (MODE == kMerge && tid == 0) q0 = max(q0, k0);  // earlier rows pair from their side
+                    len = q1 > q0 ? q1 - q0 : 0u;
+                }
+            }
+            uint32_t incl = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (tid >= o) incl += y;
+            }
+            if (tid < n_rng) {
+                S.rq0[tid] = q0;
+                S.rpre[tid] = incl - len;
+            }
+            if (tid == 31) S.rpre[kMaxRng] = incl;  // stream length
+        }
+        __syncthreads();
+        const uint32_t L = S.rpre[kMaxRng];
+        const float *c = S.a_orig;  // the centre: row 0, present in every chunk
+        const float na = stage_centred<DP>(S.a, tid, S.a_orig, c, have);
+        const float lo = (float)(G.eps2 * (1.0 - 0x1p-20));
+        const float hi = (float)(G.eps2 * (1.0 + 0x1p-20));
+        const float rowA = 0.5f * __fsub_rn(__fmul_rn(na, 1.00390625f), lo);
+        const float rowR = 0.5f * __fsub_rn(__fmul_rn(na, 0.99609375f), hi);
+        uint32_t cnt = 0, rp = 0, best = kNoLabel;
+        if (MODE == kMerge && have) rp = uf_find(v.parent, p, v.ctr);
+        bool done = !have;  // counts: the row has reached MINPTS
+        bool handed = false;  // counts: left to the CUDA-core kernel
+        // registers of the next candidate block (loaded one block ahead)
+        float4 pre[DP / 4];
+        uint32_t pre_k = 0, pre_pay = 0;
+        bool pre_in = false;
+        auto prefetch = [&](uint32_t ub) {
+            const uint32_t u = ub + (uint32_t)tid;
+            pre_in = u < L;
+            pre_k = pre_in ? stream_index(S.rpre, S.rq0, n_rng, u) : 0u;
+            const uint32_t qp = pre_in ? (MODE == kCount ? pre_k : __ldg(tt.core_list + pre_k)) : 0u;
+            const float4 *src = reinterpret_cast<const float4 *>(v.pts + (uint64_t)qp * DP);
+#pragma unroll
+            for (int k = 0; k < DP / 4; ++k) pre[k] = pre_in ? src[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (MODE == kMerge) pre_pay = pre_in ? __ldcg(v.parent + qp) : 0xffffffffu;  // an ancestor of qp
+            if (MODE == kLabels) pre_pay = pre_in ? __ldg(tt.core_lab + pre_k) : kNoLabel;
+        };
+        if (L > 0) prefetch(0);
+        for (uint32_t ub = 0; ub < L; ub += kTile) {
+            // stage the prefetched block
+            {
+                float4 *dst = reinterpret_cast<float4 *>(S.b_orig + tid * DP);
+                float nb = 0.f;
+#pragma unroll
+                for (int k = 0; k < DP / 4; ++k) {
+                    dst[k] = pre[k];
+                    const float4 cc = *reinterpret_cast<const float4 *>(c + 4 * k);
+                    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (pre_in) {
+                        w.x = __fsub_rn(pre[k].x, cc.x);
+                        w.y = __fsub_rn(pre[k].y, cc.y);
+                        w.z = __fsub_rn(pre[k].z, cc.z);
+                        w.w = __fsub_rn(pre[k].w, cc.w);
+                    }
+                    nb = __fmaf_rn(w.x, w.x, nb);
+                    nb = __fmaf_rn(w.y, w.y, nb);
+                    nb = __fmaf_rn(w.z, w.z, nb);
+                    nb = __fmaf_rn(w.w, w.w, nb);
+                    *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(S.b) + op_offset<DP>(tid, 4 * k)) = w;
+                }
+                S.cth[tid] = pre_in ? make_float2(0.5f * __fmul_rn(nb, 1.00390625f), 0.5f * __fmul_rn(nb, 0.99609375f))
+                                    : make_float2(INFINITY, INFINITY);
+                S.cidx[tid] = pre_k;
+            }
+            const bool cin = pre_in;
+            uint32_t rq = 0xffffffffu;
+            if (MODE == kMerge) {
+                if (cin) rq = __ldcg(v.parent + pre_pay);  // one more step towards the root
+                S.cpay[tid] = rq;
+                if (have) {
+                    rp = __ldcg(v.parent + rp);
+                    S.ref = rp;  // any row's tree node; all rows write before the barrier
+                }
+            } else if (MODE == kLabels) {
+                S.cpay[tid] = pre_pay;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            bool skip = false;
+            if (MODE == kMerge) {
+                __syncthreads();
+                const uint32_t ref = S.ref;
+                skip = __syncthreads_and((!have || rp == ref) && (!cin || rq == ref)) != 0;
+            } else {
+                __syncthreads();
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t nq = min((uint32_t)kTile, L - ub);
+            if (skip) {
+                ++n_skip;
+                if (ub + kTile < L) prefetch(ub + kTile);
+                continue;
+            }
+            if (tid == 0) {
+                const uint32_t a0 = smem_u32(S.a), b0 = smem_u32(S.b);
+#pragma unroll
+                for (int ks = 0; ks < DP / 8; ++ks)
+                    mma_tf32(taddr, smem_desc<DP>(a0 + ks * 2 * kLBO), smem_desc<DP>(b0 + ks * 2 * kLBO), idesc,
+                             ks > 0 ? 1u : 0u);
+                mma_commit(mbar);
+            }
+            if (ub + kTile < L) prefetch(ub + kTile);  // overlaps the MMA and the classification
+            const bool ok = mbar_wait(mbar, phase);
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                if (tid == 0) set_error(v.ctr, kErrLoop);
+                break;
+            }
+            phase ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            ++n_tiles;
+            bool need = have && (MODE != kCount || !done);
+            if (__any_sync(0xffffffffu, need)) {
+                for (uint32_t c0 = 0; c0 < nq; c0 += 32) {
+                    uint32_t dv[32];
+                    tmem_ld32(t_lane + c0, dv);
+                    if (!need) continue;
+                    // classify 32 pairs: inside (the filter accepts), band (the exact predicate decides)
+                    uint32_t in_m = 0, band_m = 0;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float dot = __uint_as_float(dv[j]);
+                        const float2 ct = S.cth[c0 + j];
+                        const bool out = dot < rowR + ct.y;  // outside eps, or an empty column
+                        const bool in = dot > rowA + ct.x;
+                        in_m |= (uint32_t)in << j;
+                        band_m |= (uint32_t)(!out && !in) << j;
+                    }
+                    if (MODE == kCount) {
+                        cnt += (uint32_t)__popc(in_m);
+                        while (band_m) {
+                            const uint32_t col = c0 + (uint32_t)(__ffs(band_m) - 1);
+                            band_m &= band_m - 1;
+                            ++n_re;
+                            cnt += within_rows<DP>(S.a_orig + tid * DP, S.b_orig + col * DP, G) ? 1u : 0u;
+                        }
+                        if (cnt >= G.min_pts) need = false;
+                    } else {
+                        uint32_t m = in_m | band_m;
+                        while (m) {
+                            const int j = __ffs(m) - 1;
+                            m &= m - 1;
+                            const uint32_t col = c0 + (uint32_t)j;
+                            const bool inside = (in_m >> j) & 1u;
+                            if (MODE == kMerge) {
+                                const uint32_t ck2 = S.cidx[col];
+                                if (ck2 <= rk || S.cpay[col] == rp) continue;
+                                bool hit = inside;
+                                if (!hit) {
+                                    ++n_re;
+                                    hit = within_rows<DP>(S.a_orig + tid * DP, S.b_orig + col * DP, G);
+                                }
+                                if (hit) {
+                                    uf_union(v.parent, p, __ldg(tt.core_list + ck2), v.ctr);
+                                    rp = uf_find(v.parent, p, v.ctr);
+                                }
+                            } else {
+                                const uint32_t lq = S.cpay[col];
+                                if (lq >= best) continue;
+                                bool hit = inside;
+                                if (!hit) {
+                                    ++n_re;
+                                    hit = within_rows<DP>(S.a_orig + tid * DP, S.b_orig + col * DP, G);
+                                }
+                                if (hit) best = lq;
+                            }
+                        }
+                    }
+                }
+            }
+            if (MODE == kCount) done = done || cnt >= G.min_pts;
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            if (MODE == kCount) {
+                const int open = __syncthreads_count(!done);
+                if (open == 0) break;
+                if (open <= kHandOff && ub + 2 * kTile < L) {
+                    // few rows left and more than one block to go: the CUDA-core count takes them
+                    handed = !done;
+                    break;
+                }
+            } else {
+                __syncthreads();
+            }
+        }
+        if (failed) continue;  // the loop head ends this CTA
+        if (MODE == kCount) {
+            const bool is_core = have && !handed && cnt >= G.min_pts;
+            if (have) v.core[p] = handed ? 2 : (is_core ? 1 : 0);
+            // the unions of a cell may run on the CUDA cores (fewer core rows than points)
+            if (__syncthreads_or(is_core) && tid == 0) v.cell_core[A] = 1;
+        } else if (MODE == kLabels) {
+            if (have) {
+                const uint32_t base_label = v.gtab ? (uint32_t)v.set_off[aset] : 0u;
+                const int32_t lab = best == kNoLabel ? -1 : (int32_t)(best - base_label);
+                const uint32_t o = v.perm[p];
+                v.labels[o] = lab;
+                if (v.core_out) v.core_out[o] = 0;
+                n_noise += lab < 0 ? 1u : 0u;
+            }
+        }
+    }
+    if (failed) mbar_wait(mbar, phase);  // the MMA that did not complete in time, bounded again
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTile));
+    add_counter(&v.ctr->work[6], tid == 0 ? n_tiles : 0u);
+    add_counter(&v.ctr->work[7], n_re);
+    if (MODE == kMerge) add_counter(&v.ctr->work[2], tid == 0 ? n_skip : 0u);
+    if (MODE == kLabels) {
+        for (int o = 16; o; o >>= 1) n_noise += __shfl_xor_sync(0xffffffffu, n_noise, o);
+        if ((tid & 31) == 0 && n_noise) atomicAdd(&v.ctr->n_noise, n_noise);
+    }
+}
+
+__device__ __forceinline__ uint32_t tc_chunks(uint32_t rows, uint32_t min_rows) {
+    return rows >= min_rows ? (rows + (uint32_t)kTile - 1u) / (uint32_t)kTile : 0u;
+}
+
+// 128-row chunks of the counts for every coarse cell with at least min_rows points.
+static __global__ void __launch_bounds__(256) k_tc_chunks_count(const uint32_t *__restrict__ cell_start,
+                                                               const DevCounters *ctr, uint32_t min_rows,
+                                                               uint32_t *__restrict__ nch) {
+    const uint32_t C = ctr->n_cells;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x)
+        nch[c] = tc_chunks(cell_start[c + 1] - cell_start[c], min_rows);
+}
+
+// Core flags as uint32 for the scan that numbers the core points.
+static __global__ void __launch_bounds__(256) k_tc_core_flags(const uint8_t *__restrict__ core, int64_t n,
+                                                             uint32_t *__restrict__ f) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        f[j] = core[j];
+}
+
+// Core and non-core point lists (ascending) from the scan cx of the core flags.
+static __global__ void __launch_bounds__(256) k_tc_partition(const uint8_t *__restrict__ core,
+                                                            const uint32_t *__restrict__ cx, int64_t n,
+                                                            uint32_t *__restrict__ core_list,
+                                                            uint32_t *__restrict__ nc_list) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t x = cx[j];
+        if (core[j]) core_list[x] = (uint32_t)j;
+        else nc_list[(uint32_t)j - x] = (uint32_t)j;
+    }
+}
+
+// 128-row chunks of every coarse cell for the unions (core rows) and the labels (non-core rows).
+static __global__ void __launch_bounds__(256) k_tc_chunks_split(const uint32_t *__restrict__ cell_start,
+                                                               const uint32_t *__restrict__ cx, const DevCounters *ctr,
+                                                               uint32_t min_rows, uint32_t *__restrict__ nch_core,
+                                                               uint32_t *__restrict__ nch_nc) {
+    const uint32_t C = ctr->n_cells;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+        const uint32_t s = cell_start[c], e = cell_start[c + 1];
+        const uint32_t nc = cx[e] - cx[s];
+        nch_core[c] = tc_chunks(nc, min_rows);
+        nch_nc[c] = tc_chunks(e - s - nc, min_rows);
+    }
+}
+
+// Cluster id of every core point (by core-list index, for the labels phase), its label and
+// the core flag output.
+template <int DP>
+__global__ void __launch_bounds__(256) k_tc_core_labels(HdView<float, DP> v, Tables tt, int nsets,
+                                                       uint32_t *__restrict__ core_lab) {
+    const uint32_t n_core = tt.cx[v.g.n];
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n_core; k += gridDim.x * blockDim.x) {
+        const uint32_t j = tt.core_list[k];
+        const uint32_t lab = v.comp_min[v.parent[j]];
+        core_lab[k] = lab;
+        const uint32_t o = v.perm[j];
+        const uint32_t base_label = v.gtab ? (uint32_t)v.set_off[set_of_point(v.set_off, nsets, o)] : 0u;
+        v.labels[o] = (int32_t)(lab - base_label);
+        if (v.core_out) v.core_out[o] = 1;
+    }
+}
+
+}  // namespace tc
+}  // namespace hca
