@@ -6,34 +6,42 @@
 // its points for the counts, its core points for the unions, its non-core points for the
 // labels) and streams the candidate points of the neighbouring cells (all points for the
 // counts, the core points otherwise) in blocks of 128.  Rows and candidates are centred on
-// the chunk's first row, c, and staged in shared memory in the K-major, unswizzled operand
-// layout of tcgen05; one thread issues tcgen05.mma kind::tf32 (K = 8 per instruction) into a
-// 128 x 128 FP32 accumulator in tensor memory, and every thread reads its row back with
-// tcgen05.ld and classifies its 128 pairs.
+// the chunk's first row, c, split into TF32 pairs (hi + lo) and staged in shared memory in the
+// K-major, unswizzled operand layout of tcgen05; one thread issues tcgen05.mma kind::tf32
+// (K = 8 per instruction, three products per K step: hi.hi + hi.lo + lo.hi) into a 128 x 128
+// FP32 accumulator in tensor memory, and every thread reads its row back with tcgen05.ld and
+// classifies its 128 pairs.  The rows carry 8 extra K columns (1, 1, 0, ...) and the
+// candidates (-hi, -lo, 0, ...) of colA, so the accumulator holds D = x.y - colA directly.
 //
-// Filter and error bound.  With x = a - c and y = b - c rounded to FP32, S = |x|^2 + |y|^2 and
-// dot the tensor-core value of x.y, d2 = S - 2 dot approximates |a - b|^2.  The tensor core
-// reads FP32 operands as TF32 (relative error below 2^-10 each), forms exact products and
-// accumulates in FP32, so |dot - x.y| <= (2^-9 + 2^-20 + K 2^-23) sum |x_i y_i| with
-// sum |x_i y_i| <= S / 2; the FP32 norms add at most 2^-18 S, and the rounding of the
-// centring at most 2^-21 S to |a - b|^2.  Everything together stays below 0.52 * 2^-8 S, so
-// with E = 2^-8 S
+// Filter and error bound.  With x = a - c and y = b - c rounded to FP32 and S = |x|^2 + |y|^2,
+// d2 = S - 2 x.y is |a - b|^2 up to the centring's rounding (at most 2^-21 S).  The split
+// operands represent x and y to 2^-20 relative, the dropped lo.lo product is below 2^-20 of
+// |x_i y_i|, every product of TF32 values is exact in FP32, and the accumulation of the
+// 3 KP products and the two colA terms adds at most 3 KP 2^-23 of their absolute sum (KP =
+// DP + 8 <= 72); with sum |x_i y_i| <= S / 2 and the FP32 norms (2^-18 S) the error of d2 stays
+// below 2^-14 S.  With E = 2^-12 S
 //   d2 + E < eps^2 (1 - 2^-20)  =>  |a - b|^2 < eps^2 (1 - 2^-22)  (pair within eps),
 //   d2 - E > eps^2 (1 + 2^-20)  =>  |a - b|^2 > eps^2 (1 + 2^-21)  (pair outside eps),
-// both far enough from eps^2 that the FP64 sum of the exact predicate lands on the same side;
-// every other pair is decided by the exact predicate on the original coordinates (FP32
-// filter, FP64 recheck).  The labels are therefore the exact ones.  The two tests are written
-// as dot > rowA + colA and dot < rowR + colR with per-row and per-column halves of
-// ((1 +- 2^-8) S - eps^2 (1 -+ 2^-20)) / 2; their FP32 rounding (a few 2^-24 of S or eps^2)
-// stays inside the unused half of E, because a pair near eps has S >= eps^2 / 2.  The host
-// enables these kernels only when every extent satisfies d * extent^2 <= 2^100 and eps^2 lies
-// in [2^-100, 2^100], so no FP32 value above overflows or loses the bound to underflow.
+// both far enough from eps^2 that the FP64 sum of the exact predicate lands on the same side.
+// In terms of D: accept when D > rowA = ((1 + 2^-12) |x|^2 - eps^2 (1 - 2^-20)) / 2 with
+// colA = (1 + 2^-12) |y|^2 / 2.  Rejection uses row quantities only: a pair within eps has
+// |y|^2 <= 2 |x|^2 + 2 eps^2, so S <= 3 |x|^2 + 2 eps^2 and D >= (|x|^2 - eps^2) / 2 -
+// 2^-12 (1.6 |x|^2 + 1.5 eps^2); D < thr_near = (|x|^2 - eps^2) / 2 - 2^-11 (|x|^2 + eps^2)
+// (eps^2 taken as eps^2 (1 + 2^-20)) therefore proves the pair outside.  The FP32 rounding
+// of these thresholds (a few 2^-24 of S or eps^2) fits in the unused part of the margins,
+// because a pair near eps has S >= eps^2 / 2.  Pairs between the two tests are decided by the
+// exact predicate on the original coordinates (FP32 filter, FP64 recheck); the counts keep
+// two tallies instead (surely within, not proved outside) and leave a row whose MINPTS falls
+// between them to the exact CUDA-core count.  The labels are therefore the exact ones.  An
+// empty candidate column carries colA = 2^110, so D = -2^110 rejects it.  The host enables these
+// kernels only when every extent satisfies d * extent^2 <= 2^100 and eps^2 lies in
+// [2^-100, 2^100], so no FP32 value above overflows or loses the bound to underflow.
 //
 // Residency: each CTA holds 128 of the 512 tensor-memory columns of an SM; the dynamic
-// shared memory of at least 48 KB per CTA keeps at most four CTAs of these kernels on an SM,
-// so tcgen05.alloc never waits for a CTA that is not running.  Every wait on the MMA's
-// mbarrier is bounded; a wait that runs out sets the status word, and the CTA stops, waits
-// once more (bounded) for the outstanding MMA and frees its tensor memory.
+// shared memory of these kernels keeps at most four of their CTAs on an SM, so
+// tcgen05.alloc never waits for a CTA that is not running.  Every wait on the MMA's mbarrier
+// is bounded; a wait that runs out sets the status word, and the CTA stops, waits once more
+// (bounded) for the outstanding MMA and frees its tensor memory.
 #pragma once
 
 #include "hd_kernels.cuh"
@@ -60,19 +68,19 @@ struct Tables {
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Byte offset of element (row, k) in the K-major canonical layout: 8 x 16-byte core matrices,
-// consecutive along K every kLBO bytes, 8-row groups every DP / 4 core matrices.
-template <int DP>
+// Byte offset of element (row, k) in the K-major canonical layout with KP columns: 8 x 16-byte
+// core matrices, consecutive along K every kLBO bytes, 8-row groups every KP / 4 core matrices.
+template <int KP>
 __device__ __forceinline__ uint32_t op_offset(int row, int k) {
-    constexpr uint32_t sbo = (DP / 4) * 128;
+    constexpr uint32_t sbo = (KP / 4) * 128;
     return (uint32_t)(row >> 3) * sbo + (uint32_t)(k >> 2) * kLBO + (uint32_t)(row & 7) * 16 + (uint32_t)(k & 3) * 4;
 }
 
 // Shared-memory matrix descriptor: start address >> 4, leading and stride byte offsets >> 4,
 // descriptor version 1 (bit 46), no swizzle.
-template <int DP>
+template <int KP>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-    constexpr uint32_t sbo = (DP / 4) * 128;
+    constexpr uint32_t sbo = (KP / 4) * 128;
     uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
     d |= (uint64_t)(kLBO >> 4) << 16;
     d |= (uint64_t)(sbo >> 4) << 32;
@@ -126,11 +134,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&v)[32]) {
 
 template <int DP>
 struct Smem {
-    float a[kTile * DP];       // rows, centred, operand layout
-    float b[kTile * DP];       // candidates, centred, operand layout
-    float a_orig[kTile * DP];  // rows, original coordinates, row-major
-    float b_orig[kTile * DP];  // candidates, original coordinates, row-major
-    float2 cth[kTile];         // per candidate: (1 + 2^-8) |y|^2 / 2, (1 - 2^-8) |y|^2 / 2; inf if empty
+    static constexpr int KP = DP + 8;  // K of the MMA: coordinates and the threshold columns
+    float a_hi[kTile * KP];    // rows: centred coordinates (TF32 hi part), (1, 1, 0, ...)
+    float a_lo[kTile * KP];    // rows: the lo parts, zeros
+    float b_hi[kTile * KP];    // candidates: centred coordinates (hi), (-colA_hi, -colA_lo, 0, ...)
+    float b_lo[kTile * KP];    // candidates: the lo parts, zeros
+    float cen[DP];             // the centre c (row 0 of the chunk, original coordinates)
     uint32_t cpay[kTile];      // per candidate: tree node (unions) or cluster id (labels)
     uint32_t cidx[kTile];      // per candidate: list index
     uint32_t rq0[kMaxRng];     // first list index of each neighbour range
@@ -144,60 +153,75 @@ inline size_t smem_bytes() {
     return sizeof(Smem<DP>) > kMinSmem ? sizeof(Smem<DP>) : kMinSmem;
 }
 
-// Copy row j of pts (or zeros) into row `row` of a row-major staging array.
-template <int DP>
-__device__ __forceinline__ void stage_orig(float *rows, int row, const float *pts, uint32_t j, bool valid) {
-    const float4 *src = reinterpret_cast<const float4 *>(pts + (uint64_t)j * DP);
-    float4 *dst = reinterpret_cast<float4 *>(rows + row * DP);
-#pragma unroll
-    for (int k = 0; k < DP / 4; ++k) dst[k] = valid ? src[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-}
+// FP32 value truncated to TF32 (10 stored mantissa bits); x - tf32_trunc(x) is exact in FP32.
+__device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
-// Centre staged row `row` on c (FP32 subtraction), store it in the operand layout and return
-// its squared norm (FP32); an invalid row becomes the zero row.
-template <int DP>
-__device__ __forceinline__ float stage_centred(float *op, int row, const float *orig, const float *c, bool valid) {
+// Centre a row (4 coordinates per float4) on c, split it into TF32 hi and lo parts, store both
+// in the operand layout (columns [0, DP) of KP) and return the squared norm (FP32) of the
+// centred row; an invalid row becomes the zero row.
+template <int DP, int KP>
+__device__ __forceinline__ float stage_split(float *hi_op, float *lo_op, int row, const float4 (&q)[DP / 4],
+                                             const float *c, bool valid) {
     float nrm = 0.f;
 #pragma unroll
-    for (int k = 0; k < DP; k += 4) {
-        const float4 q = *reinterpret_cast<const float4 *>(orig + row * DP + k);
-        const float4 cc = *reinterpret_cast<const float4 *>(c + k);
+    for (int k = 0; k < DP / 4; ++k) {
+        const float4 cc = *reinterpret_cast<const float4 *>(c + 4 * k);
         float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
         if (valid) {
-            w.x = __fsub_rn(q.x, cc.x);
-            w.y = __fsub_rn(q.y, cc.y);
-            w.z = __fsub_rn(q.z, cc.z);
-            w.w = __fsub_rn(q.w, cc.w);
+            w.x = __fsub_rn(q[k].x, cc.x);
+            w.y = __fsub_rn(q[k].y, cc.y);
+            w.z = __fsub_rn(q[k].z, cc.z);
+            w.w = __fsub_rn(q[k].w, cc.w);
         }
         nrm = __fmaf_rn(w.x, w.x, nrm);
         nrm = __fmaf_rn(w.y, w.y, nrm);
         nrm = __fmaf_rn(w.z, w.z, nrm);
         nrm = __fmaf_rn(w.w, w.w, nrm);
-        *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(op) + op_offset<DP>(row, k)) = w;
+        const float4 h = make_float4(tf32_trunc(w.x), tf32_trunc(w.y), tf32_trunc(w.z), tf32_trunc(w.w));
+        const float4 l = make_float4(__fsub_rn(w.x, h.x), __fsub_rn(w.y, h.y), __fsub_rn(w.z, h.z), __fsub_rn(w.w, h.w));
+        const uint32_t off = op_offset<KP>(row, 4 * k);
+        *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(hi_op) + off) = h;
+        *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(lo_op) + off) = l;
     }
     return nrm;
 }
 
-// The exact predicate on two staged rows: FP32 filter with the guard band of GridParams, FP64
-// sum in dimension order in the band.
+// Columns [DP, DP + 8) of an operand row pair: w0 in the hi part, zeros elsewhere.
+template <int DP, int KP>
+__device__ __forceinline__ void stage_extra(float *hi_op, float *lo_op, int row, float4 w0) {
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint32_t o0 = op_offset<KP>(row, DP), o1 = op_offset<KP>(row, DP + 4);
+    *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(hi_op) + o0) = w0;
+    *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(hi_op) + o1) = z;
+    *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(lo_op) + o0) = z;
+    *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(lo_op) + o1) = z;
+}
+
+// The exact predicate on two points of the sorted rows: FP32 filter with the guard band of
+// GridParams, FP64 sum in dimension order in the band.
 template <int DP>
-__device__ __forceinline__ bool within_rows(const float *a, const float *b, const GridParams &g) {
+__device__ __forceinline__ bool within_pts(const float *pts, uint32_t i, uint32_t j, const GridParams &g) {
+    const float4 *a = reinterpret_cast<const float4 *>(pts + (uint64_t)i * DP);
+    const float4 *b = reinterpret_cast<const float4 *>(pts + (uint64_t)j * DP);
+    float av[DP], bv[DP];
+#pragma unroll
+    for (int k = 0; k < DP / 4; ++k) {
+        const float4 x = a[k], y = b[k];
+        av[4 * k] = x.x; av[4 * k + 1] = x.y; av[4 * k + 2] = x.z; av[4 * k + 3] = x.w;
+        bv[4 * k] = y.x; bv[4 * k + 1] = y.y; bv[4 * k + 2] = y.z; bv[4 * k + 3] = y.w;
+    }
     float s = 0.f;
 #pragma unroll
-    for (int i = 0; i < DP; i += 4) {
-        const float4 av = *reinterpret_cast<const float4 *>(a + i);
-        const float4 bv = *reinterpret_cast<const float4 *>(b + i);
-        float t = __fsub_rn(av.x, bv.x);  s = __fmaf_rn(t, t, s);
-        t = __fsub_rn(av.y, bv.y);        s = __fmaf_rn(t, t, s);
-        t = __fsub_rn(av.z, bv.z);        s = __fmaf_rn(t, t, s);
-        t = __fsub_rn(av.w, bv.w);        s = __fmaf_rn(t, t, s);
+    for (int i2 = 0; i2 < DP; ++i2) {
+        const float t = __fsub_rn(av[i2], bv[i2]);
+        s = __fmaf_rn(t, t, s);
     }
     if (s < g.lo32) return true;
     if (s > g.hi32) return false;
     double e = 0.0;
 #pragma unroll
-    for (int i = 0; i < DP; ++i) {
-        const double t = __dsub_rn((double)a[i], (double)b[i]);
+    for (int i2 = 0; i2 < DP; ++i2) {
+        const double t = __dsub_rn((double)av[i2], (double)bv[i2]);
         e = __dadd_rn(e, __dmul_rn(t, t));
     }
     return e <= g.eps2;
@@ -225,9 +249,10 @@ __device__ __forceinline__ uint32_t stream_index(const uint32_t *rpre, const uin
 // (its neighbour ranges laid end to end) stream through in blocks of 128; the next block's
 // rows are loaded into registers while the current block is multiplied and classified.
 //   kCount:  rows = every point of the cell, candidates = every point of the 27 neighbouring
-//            cells; core[p] = (|N_eps(p)| >= MINPTS).  A row stops at MINPTS; once at most
-//            kHandOff rows of a chunk are still open the chunk stops and marks them core[p] = 2,
-//            and the CUDA-core count finishes them.
+//            cells; core[p] = (|N_eps(p)| >= MINPTS).  A row stops once surely MINPTS
+//            candidates are within eps.  A row that ends between the two tallies, and the
+//            rows still open when at most kHandOff rows of a chunk are, get core[p] = 2, and
+//            the CUDA-core count decides them exactly.
 //   kMerge:  rows = core points, candidates = core points of the upper half of the
 //            neighbourhood after the row (each unordered pair once); a pair within eps whose
 //            trees differ is joined.  A block whose rows and candidates all share one tree
@@ -236,6 +261,7 @@ __device__ __forceinline__ uint32_t stream_index(const uint32_t *rpre, const uin
 //            the smallest cluster id among the candidates within eps, else -1.
 template <int DP, int MODE>
 __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt) {
+    constexpr int KP = Smem<DP>::KP;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     Smem<DP> &S = *reinterpret_cast<Smem<DP> *>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -286,7 +312,16 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
         const uint32_t rk = k0 + (uint32_t)tid;
         const bool have = rk < rend;
         const uint32_t p = have ? row_point<MODE>(tt, rk) : 0u;
-        stage_orig<DP>(S.a_orig, tid, v.pts, p, have);
+        float4 q[DP / 4];
+        {
+            const float4 *src = reinterpret_cast<const float4 *>(v.pts + (uint64_t)p * DP);
+#pragma unroll
+            for (int k = 0; k < DP / 4; ++k) q[k] = have ? src[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (tid == 0) {
+#pragma unroll
+                for (int k = 0; k < DP / 4; ++k) *reinterpret_cast<float4 *>(S.cen + 4 * k) = q[k];
+            }
+        }
         // the candidate stream: one range per warp-0 lane, then a prefix over the ranges
         if (warp == 0) {
             uint32_t q0 = 0, len = 0;
@@ -318,18 +353,17 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
         }
         __syncthreads();
         const uint32_t L = S.rpre[kMaxRng];
-        const float *c = S.a_orig;  // the centre: row 0, present in every chunk
-        const float na = stage_centred<DP>(S.a, tid, S.a_orig, c, have);
+        const float na = stage_split<DP, KP>(S.a_hi, S.a_lo, tid, q, S.cen, have);
+        stage_extra<DP, KP>(S.a_hi, S.a_lo, tid, make_float4(1.f, 1.f, 0.f, 0.f));
         const float lo = (float)(G.eps2 * (1.0 - 0x1p-20));
         const float hi = (float)(G.eps2 * (1.0 + 0x1p-20));
-        const float rowA = 0.5f * __fsub_rn(__fmul_rn(na, 1.00390625f), lo);
-        const float rowR = 0.5f * __fsub_rn(__fmul_rn(na, 0.99609375f), hi);
-        uint32_t cnt = 0, rp = 0, best = kNoLabel;
+        const float rowA = 0.5f * __fsub_rn(__fmul_rn(na, 1.000244140625f), lo);  // (1 + 2^-12) |x|^2
+        const float thr_near = __fsub_rn(0.5f * __fsub_rn(na, hi), 0x1p-11f * __fadd_rn(na, hi));
+        uint32_t cnt = 0, cnt_hi = 0, rp = 0, best = kNoLabel;
         if (MODE == kMerge && have) rp = uf_find(v.parent, p, v.ctr);
-        bool done = !have;  // counts: the row has reached MINPTS
+        bool done = !have;    // counts: the row surely has MINPTS neighbours
         bool handed = false;  // counts: left to the CUDA-core kernel
         // registers of the next candidate block (loaded one block ahead)
-        float4 pre[DP / 4];
         uint32_t pre_k = 0, pre_pay = 0;
         bool pre_in = false;
         auto prefetch = [&](uint32_t ub) {
@@ -339,7 +373,7 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
             const uint32_t qp = pre_in ? (MODE == kCount ? pre_k : __ldg(tt.core_list + pre_k)) : 0u;
             const float4 *src = reinterpret_cast<const float4 *>(v.pts + (uint64_t)qp * DP);
 #pragma unroll
-            for (int k = 0; k < DP / 4; ++k) pre[k] = pre_in ? src[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int k = 0; k < DP / 4; ++k) q[k] = pre_in ? src[k] : make_float4(0.f, 0.f, 0.f, 0.f);
             if (MODE == kMerge) pre_pay = pre_in ? __ldcg(v.parent + qp) : 0xffffffffu;  // an ancestor of qp
             if (MODE == kLabels) pre_pay = pre_in ? __ldg(tt.core_lab + pre_k) : kNoLabel;
         };
@@ -347,27 +381,10 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
         for (uint32_t ub = 0; ub < L; ub += kTile) {
             // stage the prefetched block
             {
-                float4 *dst = reinterpret_cast<float4 *>(S.b_orig + tid * DP);
-                float nb = 0.f;
-#pragma unroll
-                for (int k = 0; k < DP / 4; ++k) {
-                    dst[k] = pre[k];
-                    const float4 cc = *reinterpret_cast<const float4 *>(c + 4 * k);
-                    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (pre_in) {
-                        w.x = __fsub_rn(pre[k].x, cc.x);
-                        w.y = __fsub_rn(pre[k].y, cc.y);
-                        w.z = __fsub_rn(pre[k].z, cc.z);
-                        w.w = __fsub_rn(pre[k].w, cc.w);
-                    }
-                    nb = __fmaf_rn(w.x, w.x, nb);
-                    nb = __fmaf_rn(w.y, w.y, nb);
-                    nb = __fmaf_rn(w.z, w.z, nb);
-                    nb = __fmaf_rn(w.w, w.w, nb);
-                    *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(S.b) + op_offset<DP>(tid, 4 * k)) = w;
-                }
-                S.cth[tid] = pre_in ? make_float2(0.5f * __fmul_rn(nb, 1.00390625f), 0.5f * __fmul_rn(nb, 0.99609375f))
-                                    : make_float2(INFINITY, INFINITY);
+                const float nb = stage_split<DP, KP>(S.b_hi, S.b_lo, tid, q, S.cen, pre_in);
+                const float colA = pre_in ? 0.5f * __fmul_rn(nb, 1.000244140625f) : 0x1p110f;
+                const float chi = tf32_trunc(colA);
+                stage_extra<DP, KP>(S.b_hi, S.b_lo, tid, make_float4(-chi, -__fsub_rn(colA, chi), 0.f, 0.f));
                 S.cidx[tid] = pre_k;
             }
             const bool cin = pre_in;
@@ -400,11 +417,17 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
                 continue;
             }
             if (tid == 0) {
-                const uint32_t a0 = smem_u32(S.a), b0 = smem_u32(S.b);
+                const uint32_t ah = smem_u32(S.a_hi), al = smem_u32(S.a_lo);
+                const uint32_t bh = smem_u32(S.b_hi), bl = smem_u32(S.b_lo);
 #pragma unroll
-                for (int ks = 0; ks < DP / 8; ++ks)
-                    mma_tf32(taddr, smem_desc<DP>(a0 + ks * 2 * kLBO), smem_desc<DP>(b0 + ks * 2 * kLBO), idesc,
-                             ks > 0 ? 1u : 0u);
+                for (int ks = 0; ks < KP / 8; ++ks) {
+                    const uint32_t o = ks * 2 * kLBO;
+                    mma_tf32(taddr, smem_desc<KP>(ah + o), smem_desc<KP>(bh + o), idesc, ks > 0 ? 1u : 0u);
+                    if (ks < DP / 8) {  // the threshold columns have no lo parts
+                        mma_tf32(taddr, smem_desc<KP>(ah + o), smem_desc<KP>(bl + o), idesc, 1u);
+                        mma_tf32(taddr, smem_desc<KP>(al + o), smem_desc<KP>(bh + o), idesc, 1u);
+                    }
+                }
                 mma_commit(mbar);
             }
             if (ub + kTile < L) prefetch(ub + kTile);  // overlaps the MMA and the classification
@@ -423,43 +446,41 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
                     uint32_t dv[32];
                     tmem_ld32(t_lane + c0, dv);
                     if (!need) continue;
-                    // classify 32 pairs: inside (the filter accepts), band (the exact predicate decides)
-                    uint32_t in_m = 0, band_m = 0;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float dot = __uint_as_float(dv[j]);
-                        const float2 ct = S.cth[c0 + j];
-                        const bool out = dot < rowR + ct.y;  // outside eps, or an empty column
-                        const bool in = dot > rowA + ct.x;
-                        in_m |= (uint32_t)in << j;
-                        band_m |= (uint32_t)(!out && !in) << j;
-                    }
                     if (MODE == kCount) {
-                        cnt += (uint32_t)__popc(in_m);
-                        while (band_m) {
-                            const uint32_t col = c0 + (uint32_t)(__ffs(band_m) - 1);
-                            band_m &= band_m - 1;
-                            ++n_re;
-                            cnt += within_rows<DP>(S.a_orig + tid * DP, S.b_orig + col * DP, G) ? 1u : 0u;
+                        // cnt: pairs surely within eps (D > rowA); cnt_hi: pairs not proved outside
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float dd = __uint_as_float(dv[j]);
+                            cnt += dd > rowA ? 1u : 0u;
+                            cnt_hi += dd < thr_near ? 0u : 1u;
                         }
                         if (cnt >= G.min_pts) need = false;
                     } else {
-                        uint32_t m = in_m | band_m;
+                        uint32_t in_m = 0, near_m = 0;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float dd = __uint_as_float(dv[j]);
+                            const bool in = dd > rowA;
+                            in_m |= (uint32_t)in << j;
+                            near_m |= (uint32_t)(!in && !(dd < thr_near)) << j;
+                        }
+                        uint32_t m = in_m | near_m;  // near: decided by the exact predicate
                         while (m) {
                             const int j = __ffs(m) - 1;
                             m &= m - 1;
                             const uint32_t col = c0 + (uint32_t)j;
                             const bool inside = (in_m >> j) & 1u;
+                            const uint32_t ck2 = S.cidx[col];
                             if (MODE == kMerge) {
-                                const uint32_t ck2 = S.cidx[col];
                                 if (ck2 <= rk || S.cpay[col] == rp) continue;
+                                const uint32_t qp = __ldg(tt.core_list + ck2);
                                 bool hit = inside;
                                 if (!hit) {
                                     ++n_re;
-                                    hit = within_rows<DP>(S.a_orig + tid * DP, S.b_orig + col * DP, G);
+                                    hit = within_pts<DP>(v.pts, p, qp, G);
                                 }
                                 if (hit) {
-                                    uf_union(v.parent, p, __ldg(tt.core_list + ck2), v.ctr);
+                                    uf_union(v.parent, p, qp, v.ctr);
                                     rp = uf_find(v.parent, p, v.ctr);
                                 }
                             } else {
@@ -468,7 +489,7 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
                                 bool hit = inside;
                                 if (!hit) {
                                     ++n_re;
-                                    hit = within_rows<DP>(S.a_orig + tid * DP, S.b_orig + col * DP, G);
+                                    hit = within_pts<DP>(v.pts, p, __ldg(tt.core_list + ck2), G);
                                 }
                                 if (hit) best = lq;
                             }
@@ -492,6 +513,8 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
         }
         if (failed) continue;  // the loop head ends this CTA
         if (MODE == kCount) {
+            // every candidate seen: a row with cnt < MINPTS <= cnt_hi needs the exact count
+            handed = handed || (have && cnt < G.min_pts && cnt_hi >= G.min_pts);
             const bool is_core = have && !handed && cnt >= G.min_pts;
             if (have) v.core[p] = handed ? 2 : (is_core ? 1 : 0);
             // the unions of a cell may run on the CUDA cores (fewer core rows than points)
