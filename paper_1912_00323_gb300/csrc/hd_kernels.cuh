@@ -40,10 +40,15 @@ struct HdView {
     uint8_t *core_out;
     DevCounters *ctr;
     int n_all, n_half;
-    // cells left to the tensor-core kernels (float input): those with at least tc_min_rows rows
-    // of a phase (0: none); cx = exclusive scan of the core flags, for the per-cell core counts
-    uint32_t tc_min_rows;
+    // cells left to the tensor-core kernels (float input): those with at least tc_min[phase] rows
+    // of a phase (counts, unions, labels; 0: none); cx = exclusive scan of the core flags, for
+    // the per-cell core counts; tc_hook: first links also in cells whose unions run there
+    uint32_t tc_min[3];
+    uint32_t tc_hook;
     const uint32_t *cx;
+    // rows the tensor-core count handed over: count so far and candidate-stream position
+    uint32_t *tc_cnt;
+    uint32_t *tc_pos;
 };
 
 constexpr int kHdWarps = 4;   // warps per block in the point kernels of this path
@@ -219,14 +224,18 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_count_hd(HdView<T, DP> v) {
     uint32_t chunks = 0;
     HD_FOR_EACH_CHUNK(v, A, base, e) {
         // a cell counted on the tensor cores leaves here only the rows it handed over (core = 2)
-        const bool tc_cell = v.tc_min_rows && e - v.cell_start[A] >= v.tc_min_rows;
+        const bool tc_cell = v.tc_min[0] && e - v.cell_start[A] >= v.tc_min[0];
         const bool have = base + lane < e && (!tc_cell || v.core[base + lane] == 2);
         unsigned open = __ballot_sync(0xffffffffu, have);
         if (!open) continue;
         const GridParams &G = params_of(v, set_of_key(v, v.cell_key[A]));
         const uint32_t min_pts = G.min_pts;
         stage_rows<T, DP>(rows, v.pts, base, e);
-        uint32_t cnt = 0;
+        uint32_t cnt = 0, skip = 0;
+        if (tc_cell) {  // resume where the tensor-core count stopped (same candidate order)
+            if (have) cnt = v.tc_cnt[base + lane];
+            skip = __shfl_sync(0xffffffffu, have ? v.tc_pos[base + lane] : 0u, __ffs(open) - 1);
+        }
         for (int g0 = 0; g0 < v.n_all && open; g0 += 32) {
             const int k = g0 + lane;
             const uint2 rg = k < v.n_all ? v.ranges[(uint64_t)A * v.n_all + k] : make_uint2(0u, 0u);
@@ -235,7 +244,16 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_count_hd(HdView<T, DP> v) {
                 const uint32_t lo = __shfl_sync(0xffffffffu, rg.x, kk);
                 const uint32_t hi = __shfl_sync(0xffffffffu, rg.y, kk);
                 if (lo >= hi) continue;
-                const uint32_t q0 = v.cell_start[lo], q1 = v.cell_start[hi];
+                uint32_t q0 = v.cell_start[lo];
+                const uint32_t q1 = v.cell_start[hi];
+                if (skip) {
+                    if (skip >= q1 - q0) {
+                        skip -= q1 - q0;
+                        continue;
+                    }
+                    q0 += skip;
+                    skip = 0;
+                }
                 for (uint32_t qb = q0; qb < q1 && open; qb += 32) {
                     const uint32_t q = qb + lane;
                     T qv[DP];
@@ -280,6 +298,7 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_hook_hd(HdView<T, DP> v) {
     const int lane = lane_id();
     uint32_t chunks = 0;
     HD_FOR_EACH_CHUNK(v, A, base, e) {
+        if (v.tc_min[1] && !v.tc_hook && v.cx[e] - v.cx[v.cell_start[A]] >= v.tc_min[1]) continue;
         const uint32_t p = base + lane;
         unsigned open = __ballot_sync(0xffffffffu, p < e && v.core[p]);
         if (!open) continue;
@@ -343,7 +362,7 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_merge_hd(HdView<T, DP> v) {
     uint32_t chunks = 0, tests = 0, skipped = 0;
     HD_FOR_EACH_CHUNK(v, A, base, e) {
         if (!v.cell_core[A]) continue;
-        if (v.tc_min_rows && v.cx[e] - v.cx[v.cell_start[A]] >= v.tc_min_rows) continue;  // tensor-core cell
+        if (v.tc_min[1] && v.cx[e] - v.cx[v.cell_start[A]] >= v.tc_min[1]) continue;  // tensor-core cell
         const uint32_t p = base + lane;
         const bool pc = p < e && v.core[p];
         const unsigned amask = __ballot_sync(0xffffffffu, pc);
@@ -450,9 +469,9 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_labels_hd(HdView<T, DP> v) {
     const int lane = lane_id();
     uint32_t noise = 0, chunks = 0;
     HD_FOR_EACH_CHUNK(v, A, base, e) {
-        if (v.tc_min_rows) {  // non-core rows of a tensor-core cell: labelled there
+        if (v.tc_min[2]) {  // non-core rows of a tensor-core cell: labelled there
             const uint32_t s0 = v.cell_start[A];
-            if (e - s0 - (v.cx[e] - v.cx[s0]) >= v.tc_min_rows) continue;
+            if (e - s0 - (v.cx[e] - v.cx[s0]) >= v.tc_min[2]) continue;
         }
         {
             const uint32_t aset = set_of_key(v, v.cell_key[A]);

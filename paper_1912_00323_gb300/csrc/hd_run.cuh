@@ -118,15 +118,17 @@ inline int tc_launch_shape(size_t &smem) {
 
 }  // namespace detail
 
-// Rows of a phase from which a coarse cell goes to the tensor-core kernels.
-inline uint32_t tc_min_rows() {
-    static const uint32_t v = [] {
-        const char *e = getenv("HCA_TC_MIN_ROWS");
-        const int x = e ? atoi(e) : 64;
-        return (uint32_t)(x < 1 ? 1 : x);
-    }();
-    return v;
-}
+// Rows of a phase (counts, unions, labels) from which a coarse cell goes to the tensor-core
+// kernels, and whether the first links also run in cells whose unions are on tensor cores.
+// A 128-row chunk with r rows of a phase costs about the same per 128 candidates as r rows on
+// the CUDA cores at r ~ 2 (labels: non-core rows, compacted), r ~ 8 (unions: core rows) and
+// r ~ 32 (counts: all rows of the cell, not compacted); the first links shorten the union
+// chains enough to pay for themselves on dense clusters.
+struct TcTuning {
+    uint32_t min[3];
+    uint32_t hook;
+};
+constexpr TcTuning kTcTuning = {{32u, 8u, 2u}, 1u};
 
 // Workspace offsets of the tensor-core phases.
 struct TcOffsets {
@@ -141,17 +143,20 @@ inline uint32_t *part_of(char *b, size_t o) { return (uint32_t *)(b + o); }
 template <int DP, typename Mark>
 void run_tc_phases(HdView<float, DP> &hv, cudaStream_t s, char *b, int64_t n, int grid_tc, size_t tc_smem,
                    int gpts, int gcell, size_t smem, uint32_t *part, const TcOffsets &o, int nsets,
-                   DevCounters *ctr, uint32_t min_rows, Mark &mark, int &launches) {
+                   DevCounters *ctr, const TcTuning &tune, Mark &mark, int &launches) {
     uint32_t *nch = (uint32_t *)(b + o.nch), *nch2 = (uint32_t *)(b + o.nch2);
     uint32_t *ch0 = (uint32_t *)(b + o.ch0), *ch1 = (uint32_t *)(b + o.ch1), *ch2 = (uint32_t *)(b + o.ch2);
     uint32_t *flags = (uint32_t *)(b + o.flags), *cx = (uint32_t *)(b + o.cx);
     uint32_t *clist = (uint32_t *)(b + o.clist), *nclist = (uint32_t *)(b + o.nclist);
     uint32_t *clab = (uint32_t *)(b + o.clab);
-    hv.tc_min_rows = min_rows;
+    for (int i = 0; i < 3; ++i) hv.tc_min[i] = tune.min[i];
+    hv.tc_hook = tune.hook;
     hv.cx = cx;
+    hv.tc_cnt = clab;   // free until the labels phase
+    hv.tc_pos = flags;  // free until the core numbering
     // ---- Definition 2: exact counts over the neighbouring coarse cells ----
     cudaMemsetAsync(hv.cell_core, 0, (size_t)n, s);
-    tc::k_tc_chunks_count<<<gpts, 256, 0, s>>>(hv.cell_start, ctr, min_rows, nch);
+    tc::k_tc_chunks_count<<<gpts, 256, 0, s>>>(hv.cell_start, ctr, tune.min[0], nch);
     exclusive_scan_u32(nch, ch0, n, &ctr->n_cells, &ctr->n_tc_chunks[tc::kCount], part, s, &launches);
     tc::k_tc_hd<DP, tc::kCount><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch0, cx, clist, nclist, clab});
     k_count_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
@@ -161,7 +166,7 @@ void run_tc_phases(HdView<float, DP> &hv, cudaStream_t s, char *b, int64_t n, in
     tc::k_tc_core_flags<<<gpts, 256, 0, s>>>(hv.core, n, flags);
     exclusive_scan_u32(flags, cx, n, nullptr, cx + n, part, s, &launches);
     tc::k_tc_partition<<<gpts, 256, 0, s>>>(hv.core, cx, n, clist, nclist);
-    tc::k_tc_chunks_split<<<gpts, 256, 0, s>>>(hv.cell_start, cx, ctr, min_rows, nch, nch2);
+    tc::k_tc_chunks_split<<<gpts, 256, 0, s>>>(hv.cell_start, cx, ctr, tune.min[1], tune.min[2], nch, nch2);
     exclusive_scan_u32(nch, ch1, n, &ctr->n_cells, &ctr->n_tc_chunks[tc::kMerge], part, s, &launches);
     exclusive_scan_u32(nch2, ch2, n, &ctr->n_cells, &ctr->n_tc_chunks[tc::kLabels], part, s, &launches);
     launches += 3;
@@ -465,7 +470,7 @@ int run_hd(const RunArgs &a) {
             run_tc_phases<DP>(hv, s, b, n, sms * tc_occ, tc_smem, gpts, gcell, smem, part_of(b, o_part),
                               TcOffsets{o_tnch, o_tnch2, o_tch0, o_tch1, o_tch2, o_tflags, o_cx, o_clist, o_nclist,
                                         o_clab},
-                              batched ? nsets : 0, ctr, tc_min_rows(), mark, launches);
+                              batched ? nsets : 0, ctr, kTcTuning, mark, launches);
             goto done_phases;
         }
     }

@@ -30,9 +30,9 @@
 // (eps^2 taken as eps^2 (1 + 2^-20)) therefore proves the pair outside.  The FP32 rounding
 // of these thresholds (a few 2^-24 of S or eps^2) fits in the unused part of the margins,
 // because a pair near eps has S >= eps^2 / 2.  Pairs between the two tests are decided by the
-// exact predicate on the original coordinates (FP32 filter, FP64 recheck); the counts keep
-// two tallies instead (surely within, not proved outside) and leave a row whose MINPTS falls
-// between them to the exact CUDA-core count.  The labels are therefore the exact ones.  An
+// exact predicate on the original coordinates (FP32 filter, FP64 recheck); the counts keep two
+// tallies and leave a row that the tallies do not decide to the exact CUDA-core count.  The
+// labels are therefore the exact ones.  An
 // empty candidate column carries colA = 2^110, so D = -2^110 rejects it.  The host enables these
 // kernels only when every extent satisfies d * extent^2 <= 2^100 and eps^2 lies in
 // [2^-100, 2^100], so no FP32 value above overflows or loses the bound to underflow.
@@ -244,15 +244,17 @@ __device__ __forceinline__ uint32_t stream_index(const uint32_t *rpre, const uin
 }
 
 // One phase over tensor-core tiles (MODE = kCount, kMerge or kLabels) for the coarse cells
-// with at least tc_min_rows rows of that phase (the other cells are left to the CUDA-core
+// with at least tc_min[MODE] rows of that phase (the other cells are left to the CUDA-core
 // kernels); persistent CTAs take 128-row chunks from a counter.  The candidates of a chunk
 // (its neighbour ranges laid end to end) stream through in blocks of 128; the next block's
 // rows are loaded into registers while the current block is multiplied and classified.
 //   kCount:  rows = every point of the cell, candidates = every point of the 27 neighbouring
-//            cells; core[p] = (|N_eps(p)| >= MINPTS).  A row stops once surely MINPTS
-//            candidates are within eps.  A row that ends between the two tallies, and the
-//            rows still open when at most kHandOff rows of a chunk are, get core[p] = 2, and
-//            the CUDA-core count decides them exactly.
+//            cells; core[p] = (|N_eps(p)| >= MINPTS).  Two tallies per row: pairs surely within
+//            eps and pairs not proved outside; a row stops once the first reaches MINPTS.  Once
+//            at most kHandOff rows of a chunk are open the chunk stops, and those rows get
+//            core[p] = 2 with their count and the next stream position (or zero and zero for
+//            all of them if one saw an undecided pair); a row that ends with MINPTS between the tallies gets core[p] =
+//            2, zero and zero.  The CUDA-core count continues them exactly.
 //   kMerge:  rows = core points, candidates = core points of the upper half of the
 //            neighbourhood after the row (each unordered pair once); a pair within eps whose
 //            trees differ is joined.  A block whose rows and candidates all share one tree
@@ -447,7 +449,8 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
                     tmem_ld32(t_lane + c0, dv);
                     if (!need) continue;
                     if (MODE == kCount) {
-                        // cnt: pairs surely within eps (D > rowA); cnt_hi: pairs not proved outside
+                        // cnt: pairs surely within eps (D > rowA); cnt_hi: pairs not proved
+                        // outside (D >= thr_near)
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
                             const float dd = __uint_as_float(dv[j]);
@@ -503,8 +506,16 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
                 const int open = __syncthreads_count(!done);
                 if (open == 0) break;
                 if (open <= kHandOff && ub + 2 * kTile < L) {
-                    // few rows left and more than one block to go: the CUDA-core count takes them
+                    // few rows left and more than one block to go: the CUDA-core count continues
+                    // them from the next candidate on
+                    // the rows resume from the next block if none saw an undecided pair, else
+                    // all start over (one start position per chunk)
                     handed = !done;
+                    const bool exact = __syncthreads_and(!handed || cnt_hi == cnt) != 0;
+                    if (handed) {
+                        v.tc_cnt[p] = exact ? cnt : 0u;
+                        v.tc_pos[p] = exact ? ub + kTile : 0u;
+                    }
                     break;
                 }
             } else {
@@ -513,8 +524,12 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
         }
         if (failed) continue;  // the loop head ends this CTA
         if (MODE == kCount) {
-            // every candidate seen: a row with cnt < MINPTS <= cnt_hi needs the exact count
-            handed = handed || (have && cnt < G.min_pts && cnt_hi >= G.min_pts);
+            // every candidate seen: a row with cnt < MINPTS <= cnt_hi is counted exactly there
+            if (have && !handed && cnt < G.min_pts && cnt_hi >= G.min_pts) {
+                handed = true;
+                v.tc_cnt[p] = 0u;
+                v.tc_pos[p] = 0u;
+            }
             const bool is_core = have && !handed && cnt >= G.min_pts;
             if (have) v.core[p] = handed ? 2 : (is_core ? 1 : 0);
             // the unions of a cell may run on the CUDA cores (fewer core rows than points)
@@ -579,14 +594,15 @@ static __global__ void __launch_bounds__(256) k_tc_partition(const uint8_t *__re
 // 128-row chunks of every coarse cell for the unions (core rows) and the labels (non-core rows).
 static __global__ void __launch_bounds__(256) k_tc_chunks_split(const uint32_t *__restrict__ cell_start,
                                                                const uint32_t *__restrict__ cx, const DevCounters *ctr,
-                                                               uint32_t min_rows, uint32_t *__restrict__ nch_core,
+                                                               uint32_t min_core, uint32_t min_nc,
+                                                               uint32_t *__restrict__ nch_core,
                                                                uint32_t *__restrict__ nch_nc) {
     const uint32_t C = ctr->n_cells;
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
         const uint32_t s = cell_start[c], e = cell_start[c + 1];
         const uint32_t nc = cx[e] - cx[s];
-        nch_core[c] = tc_chunks(nc, min_rows);
-        nch_nc[c] = tc_chunks(e - s - nc, min_rows);
+        nch_core[c] = tc_chunks(nc, min_core);
+        nch_nc[c] = tc_chunks(e - s - nc, min_nc);
     }
 }
 
