@@ -41,6 +41,7 @@ L2_FLUSH_BYTES = 256 << 20
 #   sort:  per 8-bit pass read and write key + value (16)
 #   cells: read index (4) + the point (4 d), write the padded point (16 for d = 3) + cell id (4);
 #          per cell write start (4) + key (8)
+#   reps:  see below (the stage is the k_reps kernel alone)
 def stage_bytes(stage, n, d, C, P, passes, key_bytes):
     pt = 4 * d
     pad = 16 if d == 3 else pt
@@ -55,7 +56,10 @@ def stage_bytes(stage, n, d, C, P, passes, key_bytes):
     if stage == "hash":
         return C * 8 + P * 16
     if stage == "reps":
-        return n * (pad + 4 + 1) + C * 8 * (26 if d == 3 else 8)
+        # k_reps: read every point and its core flag, per cell its key and start, write the
+        # 64-bit (distance, index) word of every representative direction
+        ndir = {1: 2, 2: 8, 3: 26, 4: 8}.get(d, 0)
+        return n * (pad + 1) + C * (12 + 8 * ndir)
     return None
 
 

@@ -81,8 +81,9 @@ extern "C" {
 #define HCA_STAGE_SORT 2      /* radix sort of (key, index) (the pre-sort of Sec. 2) */
 #define HCA_STAGE_CELLS 3     /* gather into cell order, run-length cell offsets */
 #define HCA_STAGE_HASH 4      /* neighbour lookup table */
-#define HCA_STAGE_CORE 5      /* dense cells and exact counts (Definition 2) */
-#define HCA_STAGE_REPS 6      /* representative points (Algorithm 2) */
+#define HCA_STAGE_CORE 5      /* dense cells and exact counts (Definition 2); d <= 4: with the
+                                 chunk table of the representative pass */
+#define HCA_STAGE_REPS 6      /* representative points (Algorithm 2): the selection kernel alone */
 #define HCA_STAGE_MERGE 7     /* merging neighbouring cells, union-find (Algorithm 3) */
 #define HCA_STAGE_LABELS 8    /* cluster ids, border and noise points (Algorithm 4) */
 #define HCA_NUM_STAGES 9

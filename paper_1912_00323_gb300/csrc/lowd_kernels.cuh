@@ -712,20 +712,48 @@ __device__ __forceinline__ float rep_dist(int r, const float *lo2, const float *
 }
 
 // Algorithm 2: for every cell with core points and every direction delta, the core point
-// nearest to the ideal position of delta; ties go to the smaller sorted index.  The work is
-// split into chunks of at most 256 points of one cell (chunk_off[c] = first chunk of cell c),
-// one warp per chunk, so a cell of any size is shared out evenly.  Each lane keeps its own
-// minima over its points of the chunk, the warp reduces once per direction, and a cell of
-// several chunks combines them by 64-bit atomicMin of (distance bits, index) (non-negative
-// float bits order like the floats).  Among equal distances any holder may be kept: the
-// representative only decides which pair is tested first, never a label.
+// nearest to the ideal position of delta.  The work is split into chunks of at most 256
+// points of one cell (chunk_off[c] = first chunk of cell c), one warp per chunk, so a cell of
+// any size is shared out evenly.  A chunk of at most 32 points (most cells) is staged in
+// shared memory, one point per lane, and then lane r scans its points for direction r: no
+// reduction.  A larger chunk keeps per-lane minima over its points and reduces once per
+// direction.  A cell of several chunks combines them by 64-bit atomicMin of (distance bits,
+// index) (non-negative float bits order like the floats).  Among equal distances any holder
+// may be kept: the representative only decides which pair is tested first, never a label.
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_reps(LowdView<T, D> v) {
     constexpr int ndir = RepDirs<D>::value;
     constexpr uint32_t kChunk = 256;
+    __shared__ float2 s_lh[8][32][D];  // per warp: (lo2, hi2) of every dimension of its 32 points
     const uint32_t C = v.ctr->n_cells, NC = v.ctr->n_chunks;
-    const int lane = lane_id();
+    const int lane = lane_id(), wib = threadIdx.x >> 5;
     (void)C;
+    // this lane's direction in the transposed scan: weights of lo2 / hi2 per dimension
+    float wlo[D], whi[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        wlo[k] = 0.f;
+        whi[k] = 0.f;
+    }
+    if (lane < ndir) {
+        if (D <= 3) {
+            int code = lane < (ndir / 2) ? lane : lane + 1;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const int sgn = code % 3 - 1;
+                code /= 3;
+                if (sgn > 0) whi[k] = 1.f;
+                if (sgn < 0) wlo[k] = 1.f;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+                if (k == (lane >> 1)) {
+                    if (lane & 1) whi[k] = 1.f;
+                    else wlo[k] = 1.f;
+                }
+        }
+    }
     for (uint32_t t = global_warp(); t < NC; t += total_warps()) {
         const uint32_t A = v.chunk_cell[t];
         const GridParams &G = params_of(v, set_of_key(v, v.cell_key[A]));
@@ -734,14 +762,67 @@ __global__ void __launch_bounds__(256) k_reps(LowdView<T, D> v) {
         const uint32_t j1 = min(j0 + kChunk, e);
         int ac[D];
         unpack_key<D>(v.cell_key[A], v.g, ac);
+        const bool single = e - s <= kChunk;
+        if (j1 - j0 <= 32) {
+            const uint32_t j = j0 + lane;
+            const bool ok = j < j1 && v.core[j];
+            if (ok) {
+                float u[D];
+                band_coords<T, D>(v.pts[j], G, u);
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const float x = u[k] - (float)ac[k];
+                    s_lh[wib][lane][k] = make_float2(x * x, (1.f - x) * (1.f - x));
+                }
+            }
+            unsigned m = __ballot_sync(0xffffffffu, ok);
+            __syncwarp();
+            if (lane < ndir && m) {
+                float best = FLT_MAX;
+                uint32_t bi = 0xffffffffu;
+                while (m) {
+                    const int k = __ffs(m) - 1;
+                    m &= m - 1;
+                    float dd = 0.f;
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        const float2 lh = s_lh[wib][k][i];
+                        dd = __fmaf_rn(wlo[i], lh.x, dd);
+                        dd = __fmaf_rn(whi[i], lh.y, dd);
+                    }
+                    if (dd < best) {
+                        best = dd;
+                        bi = j0 + (uint32_t)k;
+                    }
+                }
+                const uint64_t val = ((uint64_t)__float_as_uint(best) << 32) | bi;
+                if (single) v.reps[(uint64_t)A * ndir + lane] = val;
+                else atomicMin((unsigned long long *)&v.reps[(uint64_t)A * ndir + lane], (unsigned long long)val);
+            }
+            __syncwarp();
+            continue;
+        }
         float best[ndir];
         uint32_t bidx[ndir];
 #pragma unroll
         for (int r = 0; r < ndir; ++r) { best[r] = FLT_MAX; bidx[r] = 0xffffffffu; }
-        for (uint32_t j = j0 + lane; j < j1; j += 32) {
-            if (!v.core[j]) continue;
+        // every load of this lane's points (at most kChunk / 32) is issued before any is used
+        constexpr int kPer = (int)(kChunk / 32);
+        Pt<T, D> pp[kPer];
+        bool pc[kPer];
+#pragma unroll
+        for (int it = 0; it < kPer; ++it) {
+            const uint32_t j = j0 + lane + 32u * it;
+            const bool ok = j < j1;
+            pc[it] = ok && v.core[j];
+            pp[it] = ok ? v.pts[j] : zero_pt<T, D>();
+        }
+#pragma unroll
+        for (int it = 0; it < kPer; ++it) {
+            if (!pc[it]) continue;
+            const uint32_t j = j0 + lane + 32u * it;
             float u[D], lo2[D], hi2[D];
-            band_coords<T, D>(v.pts[j], G, u);
+            band_coords<T, D>(pp[it], G, u);
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 const float x = u[k] - (float)ac[k];
@@ -754,7 +835,6 @@ __global__ void __launch_bounds__(256) k_reps(LowdView<T, D> v) {
                 if (dd < best[r]) { best[r] = dd; bidx[r] = j; }
             }
         }
-        const bool single = e - s <= kChunk;
 #pragma unroll
         for (int r = 0; r < ndir; ++r) {
             // warp minimum of the distance, then the lowest lane holding it supplies the index

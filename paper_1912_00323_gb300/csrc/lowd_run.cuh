@@ -478,8 +478,9 @@ int run_lowd(const RunArgs &a) {
     // ---- Definition 2: dense cells and exact counts ----
     k_core<T, D><<<gwarp, 256, 0, s>>>(v, st.n_all);
     ++launches;
-    mark(6);
-    // ---- Algorithm 2: representative points ----
+    // ---- Algorithm 2: representative points (the stage times k_reps alone; its chunk table
+    // is counted with the core stage and the gather of the representatives' coordinates with
+    // the merge stage) ----
     {
         uint32_t *nch = (uint32_t *)(b + o_pflags), *choff = (uint32_t *)(b + o_pexcl);  // reused
         k_rep_chunks<T, D><<<gpts, 256, 0, s>>>(v, nch);
@@ -488,11 +489,12 @@ int run_lowd(const RunArgs &a) {
         v.chunk_cell = (uint32_t *)(b + o_excl);  // reused: free after the cell pass
         k_chunk_cells<T, D><<<gpts, 256, 0, s>>>(v, nch, v.chunk_cell);
         ++launches;
+        mark(6);
         k_reps<T, D><<<grid_for(n / 256 + 1 + n / 8, 8, sms, 16), 256, 0, s>>>(v);
+        mark(7);
         k_rep_pts<T, D><<<grid_for(n * (int64_t)ndir, 256, sms, 8), 256, 0, s>>>(v);
         launches += 3;
     }
-    mark(7);
     // ---- Algorithm 3: first links, pointer jumping, then one merge pass over every pair ----
     k_hook<T, D><<<gwarp, 256, 0, s>>>(v, st.n_all, st.n_half);
     for (int r = 0; r < 5; ++r) k_jump<T, D><<<gpts, 256, 0, s>>>(v);
