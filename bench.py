@@ -300,6 +300,32 @@ def run_ours(args):
     if not np.array_equal(host_lab.numpy(), labels.cpu().numpy()):
         raise RuntimeError("host and device entry points disagree")
 
+    # the plain per-instance path on the same GPU: every distance decided in FP64, no FP32
+    # filter and no tensor cores (labels must be identical)
+    plain_lab = torch.empty_like(labels)
+    def plain_step():
+        pkg.hca_dbscan_device(pts, eps, min_pts, labels=plain_lab, stream=stream, fp64_only=True,
+                              tensor_cores=False)
+    for _ in range(2):
+        plain_step()
+    plain_ms = []
+    for _ in range(max(3, min(args.steps, 20))):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plain_step()
+        e1.record(stream)
+        e1.synchronize()
+        plain_ms.append(e0.elapsed_time(e1))
+    if not torch.equal(plain_lab, labels):
+        raise RuntimeError("plain FP64 path and tuned path disagree")
+    plain = statistics.median(plain_ms)
+    if dist:
+        t = torch.tensor([plain], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        plain = float(t.item())
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -342,7 +368,12 @@ def run_ours(args):
                    "core_points": stats["n_core_points"], "clusters": stats["n_clusters"],
                    "noise": stats["n_noise"]},
         "work": {k: stats[k] for k in ("n_count_chunks", "n_rep_tests", "n_rep_hits",
-                                       "n_exhaustive_pairs", "n_exhaustive_chunks", "n_border_chunks")},
+                                       "n_exhaustive_pairs", "n_exhaustive_chunks", "n_border_chunks",
+                                       "n_tc_tiles", "n_tc_rechecks")},
+        "plain_fp64_gpu": {"ms_per_step": plain, "value": n * ws / (plain / 1e3), "unit": "points/s",
+                           "speedup_of_tuned": plain / ms,
+                           "path": "same library, HCA_FLAG_FP64_ONLY | HCA_FLAG_NO_TENSOR_CORES, "
+                                   "labels identical"},
         "wall_s": wall,
     }
     if not args.no_cpu_baseline and ws == 1:
@@ -381,7 +412,7 @@ def run_batched(args):
             stages[int(d)] = {k: round(v, 3) for k, v in st["stage_ms"].items()}
             work[int(d)] = {k: st[k] for k in ("n_cells", "n_core_points", "n_count_chunks", "n_rep_tests",
                                                "n_rep_hits", "n_exhaustive_pairs", "n_exhaustive_chunks",
-                                               "n_border_chunks")}
+                                               "n_border_chunks", "n_tc_tiles", "n_tc_rechecks")}
     for _ in range(max(args.warmup, 1)):
         step()
     torch.cuda.synchronize()
@@ -392,6 +423,33 @@ def run_batched(args):
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
     ms = 1e3 * statistics.median(times)
+
+    # the same batched calls on the CUDA cores only, and the plain per-instance path: one
+    # hca_dbscan_device call per set, every distance in FP64 (labels must be identical)
+    def cuda_core_step():
+        for d, t, off, e, m in dev_groups:
+            pkg.hca_dbscan_batched(t, off, e, m, tensor_cores=False)
+    cuda_core_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cuda_core_step()
+    torch.cuda.synchronize()
+    cc_ms = 1e3 * (time.perf_counter() - t0)
+    ref_labels = [pkg.hca_dbscan_batched(t, off, e, m) for d, t, off, e, m in dev_groups]
+    singles = []
+    for (d, t, off, e, m), lab in zip(dev_groups, ref_labels):
+        for s in range(len(e)):
+            singles.append((t[off[s]:off[s + 1]], e[s], m[s], lab[off[s]:off[s + 1]]))
+    for x, e, m, _ in singles[:8]:
+        pkg.hca_dbscan_device(x, e, m, fp64_only=True, tensor_cores=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    outs = [pkg.hca_dbscan_device(x, e, m, fp64_only=True, tensor_cores=False) for x, e, m, _ in singles]
+    torch.cuda.synchronize()
+    plain_ms = 1e3 * (time.perf_counter() - t0)
+    if not all(torch.equal(o, lab) for o, (_, _, _, lab) in zip(outs, singles)):
+        raise RuntimeError("per-set plain FP64 calls and the batched call disagree")
+
     line = {"metric": "points clustered/sec, batched sets (labels == oracle per set)",
             "value": n_total / (ms / 1e3), "unit": "points/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -400,7 +458,13 @@ def run_batched(args):
                                    "blobs + 10% noise, eps U[0.5,3], minPts U{4..16}",
                        "points": n_total, "sets_per_d": {int(d): len(g) for d, g in groups.items()}},
             "ms_per_d": {int(d): 1e3 * t for d, t in per_d.items()}, "stage_ms_per_d": stages,
-            "work_per_d": work}
+            "work_per_d": work,
+            "cuda_cores_only": {"ms_per_step": cc_ms, "value": n_total / (cc_ms / 1e3),
+                                "speedup_of_tuned": cc_ms / ms},
+            "plain_fp64_per_set": {"ms_per_step": plain_ms, "value": n_total / (plain_ms / 1e3),
+                                   "speedup_of_tuned": plain_ms / ms,
+                                   "path": "one hca_dbscan_device call per set, HCA_FLAG_FP64_ONLY | "
+                                           "HCA_FLAG_NO_TENSOR_CORES, labels identical"}}
     print(json.dumps(line), flush=True)
     return 0
 

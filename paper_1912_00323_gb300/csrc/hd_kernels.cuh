@@ -204,9 +204,18 @@ __device__ __forceinline__ uint32_t chunk_cell(const uint32_t *chunk_off, uint32
     return lo;
 }
 
-#define HD_FOR_EACH_CHUNK(v, A, base, e)                                                     \
+// The next chunk for this warp from a per-kernel counter (chunks differ in cost by orders of
+// magnitude, so they are handed out dynamically).  Warp-uniform.
+__device__ __forceinline__ uint32_t next_chunk(uint32_t *counter) {
+    uint32_t t = 0;
+    if (lane_id() == 0) t = atomicAdd(counter, 1u);
+    return __shfl_sync(0xffffffffu, t, 0);
+}
+
+#define HD_FOR_EACH_CHUNK(v, A, base, e, slot)                                                \
     const uint32_t C_ = (v).ctr->n_cells, NC_ = (v).ctr->n_chunks;                           \
-    for (uint32_t t_ = global_warp(); t_ < NC_; t_ += total_warps())                         \
+    for (uint32_t t_ = next_chunk(&(v).ctr->hd_next[slot]); t_ < NC_;                        \
+         t_ = next_chunk(&(v).ctr->hd_next[slot]))                                           \
         for (uint32_t A = chunk_cell((v).chunk_off, C_, t_), once_ = 1; once_; once_ = 0)    \
             for (uint32_t e = (v).cell_start[A + 1],                                         \
                           base = (v).cell_start[A] + 32u * (t_ - (v).chunk_off[A]), o2_ = 1; \
@@ -222,7 +231,7 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_count_hd(HdView<T, DP> v) {
     T *rows = reinterpret_cast<T *>(smem_raw) + (threadIdx.x >> 5) * 32 * DP;
     const int lane = lane_id();
     uint32_t chunks = 0;
-    HD_FOR_EACH_CHUNK(v, A, base, e) {
+    HD_FOR_EACH_CHUNK(v, A, base, e, 0) {
         // a cell counted on the tensor cores leaves here only the rows it handed over (core = 2)
         const bool tc_cell = v.tc_min[0] && e - v.cell_start[A] >= v.tc_min[0];
         const bool have = base + lane < e && (!tc_cell || v.core[base + lane] == 2);
@@ -297,7 +306,7 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_hook_hd(HdView<T, DP> v) {
     T *rows = reinterpret_cast<T *>(smem_raw) + (threadIdx.x >> 5) * 32 * DP;
     const int lane = lane_id();
     uint32_t chunks = 0;
-    HD_FOR_EACH_CHUNK(v, A, base, e) {
+    HD_FOR_EACH_CHUNK(v, A, base, e, 1) {
         if (v.tc_min[1] && !v.tc_hook && v.cx[e] - v.cx[v.cell_start[A]] >= v.tc_min[1]) continue;
         const uint32_t p = base + lane;
         unsigned open = __ballot_sync(0xffffffffu, p < e && v.core[p]);
@@ -360,7 +369,7 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_merge_hd(HdView<T, DP> v) {
     T *rows = reinterpret_cast<T *>(smem_raw) + (threadIdx.x >> 5) * 32 * DP;
     const int lane = lane_id();
     uint32_t chunks = 0, tests = 0, skipped = 0;
-    HD_FOR_EACH_CHUNK(v, A, base, e) {
+    HD_FOR_EACH_CHUNK(v, A, base, e, 2) {
         if (!v.cell_core[A]) continue;
         if (v.tc_min[1] && v.cx[e] - v.cx[v.cell_start[A]] >= v.tc_min[1]) continue;  // tensor-core cell
         const uint32_t p = base + lane;
@@ -468,7 +477,7 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_labels_hd(HdView<T, DP> v) {
     T *rows = reinterpret_cast<T *>(smem_raw) + (threadIdx.x >> 5) * 32 * DP;
     const int lane = lane_id();
     uint32_t noise = 0, chunks = 0;
-    HD_FOR_EACH_CHUNK(v, A, base, e) {
+    HD_FOR_EACH_CHUNK(v, A, base, e, 3) {
         if (v.tc_min[2]) {  // non-core rows of a tensor-core cell: labelled there
             const uint32_t s0 = v.cell_start[A];
             if (e - s0 - (v.cx[e] - v.cx[s0]) >= v.tc_min[2]) continue;

@@ -121,14 +121,14 @@ inline int tc_launch_shape(size_t &smem) {
 // Rows of a phase (counts, unions, labels) from which a coarse cell goes to the tensor-core
 // kernels, and whether the first links also run in cells whose unions are on tensor cores.
 // A 128-row chunk with r rows of a phase costs about the same per 128 candidates as r rows on
-// the CUDA cores at r ~ 2 (labels: non-core rows, compacted), r ~ 8 (unions: core rows) and
-// r ~ 32 (counts: all rows of the cell, not compacted); the first links shorten the union
-// chains enough to pay for themselves on dense clusters.
+// the CUDA cores at r ~ 2 (labels: non-core rows) and r ~ 8 (unions: core rows; counts: all
+// rows), measured on the 16-D workload and the batched d = 8 sets; the first links shorten the
+// union chains enough to pay for themselves on dense clusters.
 struct TcTuning {
     uint32_t min[3];
     uint32_t hook;
 };
-constexpr TcTuning kTcTuning = {{32u, 8u, 2u}, 1u};
+constexpr TcTuning kTcTuning = {{8u, 8u, 2u}, 1u};
 
 // Workspace offsets of the tensor-core phases.
 struct TcOffsets {

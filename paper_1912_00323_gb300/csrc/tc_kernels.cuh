@@ -142,6 +142,8 @@ struct Smem {
     float cen[DP];             // the centre c (row 0 of the chunk, original coordinates)
     uint32_t cpay[kTile];      // per candidate: tree node (unions) or cluster id (labels)
     uint32_t cidx[kTile];      // per candidate: list index
+    uint32_t gsum[4];          // per 32 candidates: unions: bit mask of the candidates whose tree node
+                               // differs from ref; labels: the smallest cluster id
     uint32_t rq0[kMaxRng];     // first list index of each neighbour range
     uint32_t rpre[kMaxRng + 1];  // stream offset of each range; [kMaxRng] = stream length
     uint64_t mbar;
@@ -400,13 +402,20 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
                 }
             } else if (MODE == kLabels) {
                 S.cpay[tid] = pre_pay;
+                uint32_t gm = pre_pay;
+#pragma unroll
+                for (int o = 16; o; o >>= 1) gm = min(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+                if ((tid & 31) == 0) S.gsum[warp] = gm;
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;");
             bool skip = false;
+            uint32_t ref = 0xffffffffu;
             if (MODE == kMerge) {
                 __syncthreads();
-                const uint32_t ref = S.ref;
+                ref = S.ref;
+                const unsigned dm = __ballot_sync(0xffffffffu, cin && rq != ref);
+                if ((tid & 31) == 0) S.gsum[warp] = dm;  // read after the barrier of the MMA wait
                 skip = __syncthreads_and((!have || rp == ref) && (!cin || rq == ref)) != 0;
             } else {
                 __syncthreads();
@@ -468,6 +477,10 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
                             near_m |= (uint32_t)(!in && !(dd < thr_near)) << j;
                         }
                         uint32_t m = in_m | near_m;  // near: decided by the exact predicate
+                        // candidates sharing the row's tree node need no test; nor do ids that
+                        // cannot lower the row's label
+                        if (MODE == kMerge && rp == ref) m &= S.gsum[c0 >> 5];
+                        if (MODE == kLabels && S.gsum[c0 >> 5] >= best) m = 0;
                         while (m) {
                             const int j = __ffs(m) - 1;
                             m &= m - 1;
