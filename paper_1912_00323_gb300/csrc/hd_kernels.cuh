@@ -204,14 +204,6 @@ __device__ __forceinline__ uint32_t chunk_cell(const uint32_t *chunk_off, uint32
     return lo;
 }
 
-// The next chunk for this warp from a per-kernel counter (chunks differ in cost by orders of
-// magnitude, so they are handed out dynamically).  Warp-uniform.
-__device__ __forceinline__ uint32_t next_chunk(uint32_t *counter) {
-    uint32_t t = 0;
-    if (lane_id() == 0) t = atomicAdd(counter, 1u);
-    return __shfl_sync(0xffffffffu, t, 0);
-}
-
 #define HD_FOR_EACH_CHUNK(v, A, base, e, slot)                                                \
     const uint32_t C_ = (v).ctr->n_cells, NC_ = (v).ctr->n_chunks;                           \
     for (uint32_t t_ = next_chunk(&(v).ctr->hd_next[slot]); t_ < NC_;                        \

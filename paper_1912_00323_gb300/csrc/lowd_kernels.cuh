@@ -76,6 +76,21 @@ __device__ __forceinline__ void set_error(DevCounters *ctr, uint32_t bit) {
     atomicOr(&ctr->status, bit);
 }
 
+// The next work item for this warp from a per-kernel counter (warp-uniform): cells and chunks
+// differ in cost by orders of magnitude, so they are handed out dynamically.
+__device__ __forceinline__ uint32_t next_chunk(uint32_t *counter) {
+    uint32_t t = 0;
+    if (lane_id() == 0) t = atomicAdd(counter, 1u);
+    return __shfl_sync(0xffffffffu, t, 0);
+}
+
+// Items [0, N) to warps in batches of kItemBatch taken from counter ctr->lowd_next[slot].
+constexpr uint32_t kItemBatch = 4;
+#define LOWD_FOR_EACH(v, X, N, slot)                                                                  \
+    for (uint32_t b_ = next_chunk(&(v).ctr->lowd_next[slot]) * kItemBatch; b_ < (N);                \
+         b_ = next_chunk(&(v).ctr->lowd_next[slot]) * kItemBatch)                                   \
+        for (uint32_t X = b_, xe_ = min(b_ + kItemBatch, (uint32_t)(N)); X < xe_; ++X)
+
 // Batched calls put the set id above the cell key bits; cells never mix sets.
 template <typename V>
 __device__ __forceinline__ uint32_t set_of_key(const V &v, uint64_t key) {
@@ -754,7 +769,7 @@ __global__ void __launch_bounds__(256) k_reps(LowdView<T, D> v) {
                 }
         }
     }
-    for (uint32_t t = global_warp(); t < NC; t += total_warps()) {
+    LOWD_FOR_EACH(v, t, NC, 1) {
         const uint32_t A = v.chunk_cell[t];
         const GridParams &G = params_of(v, set_of_key(v, v.cell_key[A]));
         const uint32_t s = v.cell_start[A], e = v.cell_start[A + 1];
@@ -1131,7 +1146,7 @@ __global__ void __launch_bounds__(256) k_labels(LowdView<T, D> v, int n_all) {
     const uint32_t C = v.ctr->n_cells;
     const int lane = lane_id();
     uint32_t noise = 0, chunks = 0;
-    for (uint32_t A = global_warp(); A < C; A += total_warps()) {
+    LOWD_FOR_EACH(v, A, C, 4) {
         const uint32_t s = v.cell_start[A], e = v.cell_start[A + 1];
         const uint64_t akey = v.cell_key[A];
         const uint32_t aset = set_of_key(v, akey);
