@@ -234,6 +234,55 @@ HCA_API int hca_radix_sort_pairs_noalloc(void *d_keys, uint32_t *d_vals, int64_t
                                          int32_t key_bytes, int32_t begin_bit, int32_t end_bit,
                                          void *stream);
 
+/*
+ * Tuning of the neighbour search and of the tensor-core tiles, per dimension d (process-wide,
+ * all devices).  The paper has no counterpart: these choose how the same exact result is
+ * computed (Sec. 2's hypercube neighbour enumeration, or the coarse grid of the d >= 5 path;
+ * which cells use tensor-core tiles), never what is computed.
+ *   path           0: by d (hypercube stencil for d <= 4, coarse grid for d >= 5);
+ *                  1: hypercube stencil (d <= 4 only); 2: coarse grid (d >= 3 only).
+ *   tc_min_count, tc_min_merge, tc_min_labels
+ *                  coarse grid, float input: rows of a phase (all points / core points /
+ *                  non-core points of a cell) from which that cell's counts / unions / labels
+ *                  use tensor-core tiles; >= 1.
+ *   tc_handoff     open rows at which a tensor-core count chunk hands them to the CUDA cores;
+ *                  0..127.
+ *   first_links    1: first-link pass in every coarse cell; 0: only in cells whose unions run
+ *                  on the CUDA cores.
+ */
+typedef struct hca_tuning {
+    int32_t path;
+    int32_t tc_min_count;
+    int32_t tc_min_merge;
+    int32_t tc_min_labels;
+    int32_t tc_handoff;
+    int32_t first_links;
+} hca_tuning;
+
+/* The tuning used for dimension d (1..64); HCA_EINVAL for a bad d or NULL out. */
+HCA_API int hca_tuning_get(int32_t d, hca_tuning *out);
+/* Set the tuning of dimension d; NULL restores the defaults.  HCA_EINVAL for a bad d or a
+ * field out of range (nothing changes).  Takes effect for calls that start afterwards. */
+HCA_API int hca_tuning_set(int32_t d, const hca_tuning *t);
+
+/*
+ * hca_autotune -- time candidate tunings for dimension d on the caller's device-resident points
+ * (same arguments as hca_dbscan_device; the points are only read) and keep the fastest as the
+ * tuning of d.  Each candidate runs once untimed and then `repeats` times (1..16) timed with CUDA
+ * events on `stream`, keeping its minimum.  Candidates: both neighbour searches for d = 3, 4;
+ * for the coarse grid with float input, first links on / off and several row thresholds.
+ *   out       host, nullable: the tuning kept.   best_ms  host, nullable: its time.
+ * Synchronous.  Returns HCA_OK, or the first error of a candidate run (nothing is changed).
+ */
+HCA_API int hca_autotune(const void *d_points, int32_t dtype, int64_t n, int32_t d, double eps,
+                         int32_t min_pts, void *stream, int32_t repeats, hca_tuning *out,
+                         double *best_ms);
+/* hca_autotune for the sets of a batched call (arguments as hca_dbscan_batched). */
+HCA_API int hca_autotune_batched(const void *d_points, int32_t dtype, int32_t n_sets,
+                                 const int64_t *offsets, int32_t d, const double *eps,
+                                 const int32_t *min_pts, void *stream, int32_t repeats,
+                                 hca_tuning *out, double *best_ms);
+
 /* Static description of a return code; never NULL. */
 HCA_API const char *hca_strerror(int code);
 

@@ -28,7 +28,8 @@ HCA_FLAG_TIMING, HCA_FLAG_FP64_ONLY, HCA_FLAG_NO_TENSOR_CORES = 1, 2, 4
 STAGES = ("minmax", "bin", "sort", "cells", "hash", "core", "reps", "merge", "labels")
 
 ABI_FUNCTIONS = ("hca_dbscan", "hca_dbscan_device", "hca_dbscan_device_ex", "hca_dbscan_batched",
-                 "hca_radix_sort_pairs", "hca_strerror", "hca_version")
+                 "hca_radix_sort_pairs", "hca_tuning_get", "hca_tuning_set", "hca_autotune",
+                 "hca_autotune_batched", "hca_strerror", "hca_version")
 
 
 class HcaStats(ctypes.Structure):
@@ -47,6 +48,15 @@ class HcaStats(ctypes.Structure):
         d = {name: getattr(self, name) for name, _ in self._fields_ if name not in ("stage_ms", "reserved")}
         d["stage_ms"] = {s: float(self.stage_ms[i]) for i, s in enumerate(STAGES)}
         return d
+
+
+class HcaTuning(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("tc_min_count", ctypes.c_int32),
+                ("tc_min_merge", ctypes.c_int32), ("tc_min_labels", ctypes.c_int32),
+                ("tc_handoff", ctypes.c_int32), ("first_links", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
 
 
 class HcaRequest(ctypes.Structure):
@@ -89,6 +99,14 @@ def load():
     lib.hca_wait.argtypes = [vp, i64, i64, ctypes.POINTER(ctypes.c_double)]
     lib.hca_cancel.argtypes = [vp, i64]
     for f in ("hca_server_create", "hca_server_destroy", "hca_submit", "hca_poll", "hca_wait", "hca_cancel"):
+        getattr(lib, f).restype = ctypes.c_int
+    lib.hca_tuning_get.argtypes = [i32, ctypes.POINTER(HcaTuning)]
+    lib.hca_tuning_set.argtypes = [i32, ctypes.POINTER(HcaTuning)]
+    lib.hca_autotune.argtypes = [vp, i32, i64, i32, dbl, i32, vp, i32, ctypes.POINTER(HcaTuning),
+                                 ctypes.POINTER(ctypes.c_double)]
+    lib.hca_autotune_batched.argtypes = [vp, i32, i32, vp, i32, vp, vp, vp, i32, ctypes.POINTER(HcaTuning),
+                                         ctypes.POINTER(ctypes.c_double)]
+    for f in ("hca_tuning_get", "hca_tuning_set", "hca_autotune", "hca_autotune_batched"):
         getattr(lib, f).restype = ctypes.c_int
     lib.hca_strerror.argtypes = [ctypes.c_int]
     lib.hca_strerror.restype = ctypes.c_char_p
@@ -228,6 +246,63 @@ def hca_radix_sort_pairs(keys, vals, begin_bit: int = 0, end_bit: int | None = N
     if rc != HCA_OK:
         raise HcaError(rc, "hca_radix_sort_pairs")
     return keys, vals
+
+
+def hca_tuning_get(d: int) -> dict:
+    """The tuning used for dimension d (neighbour search, tensor-core split)."""
+    t = HcaTuning()
+    rc = load().hca_tuning_get(int(d), ctypes.byref(t))
+    if rc != HCA_OK:
+        raise HcaError(rc, "hca_tuning_get")
+    return t.as_dict()
+
+
+def hca_tuning_set(d: int, tuning: dict | None = None):
+    """Set the tuning of dimension d from a dict with the fields of hca_tuning (missing fields
+    keep their current values); None restores the defaults."""
+    lib = load()
+    if tuning is None:
+        rc = lib.hca_tuning_set(int(d), None)
+    else:
+        cur = hca_tuning_get(d)
+        cur.update(tuning)
+        t = HcaTuning(**{k: int(v) for k, v in cur.items()})
+        rc = lib.hca_tuning_set(int(d), ctypes.byref(t))
+    if rc != HCA_OK:
+        raise HcaError(rc, "hca_tuning_set")
+
+
+def hca_autotune(points, eps: float, min_pts: int, stream=None, repeats: int = 2):
+    """Time candidate tunings for points.shape[1] on a CUDA tensor of points and keep the fastest;
+    returns (tuning dict, best ms)."""
+    lib = load()
+    pts = points.contiguous()
+    d = pts.shape[1] if pts.dim() == 2 else 1
+    t, ms = HcaTuning(), ctypes.c_double()
+    rc = lib.hca_autotune(pts.data_ptr(), _dtype_code(pts.dtype), pts.shape[0], d, float(eps), int(min_pts),
+                          _stream_ptr(stream), int(repeats), ctypes.byref(t), ctypes.byref(ms))
+    if rc != HCA_OK:
+        raise HcaError(rc, "hca_autotune")
+    return t.as_dict(), ms.value
+
+
+def hca_autotune_batched(points, offsets, eps, min_pts, stream=None, repeats: int = 2):
+    """hca_autotune for the sets of a batched call; returns (tuning dict, best ms)."""
+    lib = load()
+    pts = points.contiguous()
+    d = pts.shape[1] if pts.dim() == 2 else 1
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    e = np.ascontiguousarray(np.asarray(eps, dtype=np.float64))
+    m = np.ascontiguousarray(np.asarray(min_pts, dtype=np.int32))
+    if off.ndim != 1 or len(off) != len(e) + 1 or len(e) != len(m) or off[-1] != pts.shape[0]:
+        raise ValueError("offsets must have n_sets + 1 entries ending at len(points); eps, min_pts n_sets")
+    t, ms = HcaTuning(), ctypes.c_double()
+    rc = lib.hca_autotune_batched(pts.data_ptr(), _dtype_code(pts.dtype), len(e), off.ctypes.data, d,
+                                  e.ctypes.data, m.ctypes.data, _stream_ptr(stream), int(repeats),
+                                  ctypes.byref(t), ctypes.byref(ms))
+    if rc != HCA_OK:
+        raise HcaError(rc, "hca_autotune_batched")
+    return t.as_dict(), ms.value
 
 
 class Server:

@@ -64,7 +64,7 @@ int device_sm_count() {
     return g_sms[dev];
 }
 
-static int check_common(const void *pts, int32_t dtype, int64_t n, int32_t d, double eps,
+int check_common(const void *pts, int32_t dtype, int64_t n, int32_t d, double eps,
                         int32_t min_pts, const void *labels) {
     if (n < 0 || n >= ((int64_t)1 << 31)) return HCA_EINVAL;
     if (d < 1 || d > 64) return HCA_EINVAL;
@@ -74,40 +74,35 @@ static int check_common(const void *pts, int32_t dtype, int64_t n, int32_t d, do
     return HCA_OK;
 }
 
-static int dispatch(const RunArgs &a, int32_t dtype) {
-    if (dtype == HCA_F32) {
+template <typename T>
+static int dispatch_t(const RunArgs &a) {
+    // the hypercube stencil path exists for d <= 4, the coarse grid for d >= 3
+    const int path = a.tune.path == 0 ? (a.d <= 4 ? 1 : 2) : a.tune.path;
+    if (path == 1) {
         switch (a.d) {
-            case 1: return run_lowd<float, 1>(a);
-            case 2: return run_lowd<float, 2>(a);
-            case 3: return run_lowd<float, 3>(a);
-            case 4: return run_lowd<float, 4>(a);
+            case 1: return run_lowd<T, 1>(a);
+            case 2: return run_lowd<T, 2>(a);
+            case 3: return run_lowd<T, 3>(a);
+            case 4: return run_lowd<T, 4>(a);
         }
-        if (a.d <= 8) return run_hd<float, 8>(a);
-        if (a.d <= 16) return run_hd<float, 16>(a);
-        if (a.d <= 32) return run_hd<float, 32>(a);
-        if (a.d <= 64) return run_hd<float, 64>(a);
-    } else {
-        switch (a.d) {
-            case 1: return run_lowd<double, 1>(a);
-            case 2: return run_lowd<double, 2>(a);
-            case 3: return run_lowd<double, 3>(a);
-            case 4: return run_lowd<double, 4>(a);
-        }
-        if (a.d <= 8) return run_hd<double, 8>(a);
-        if (a.d <= 16) return run_hd<double, 16>(a);
-        if (a.d <= 32) return run_hd<double, 32>(a);
-        if (a.d <= 64) return run_hd<double, 64>(a);
+        return HCA_EINVAL;
+    }
+    if (path == 2 && a.d >= 3) {
+        if (a.d <= 8) return run_hd<T, 8>(a);
+        if (a.d <= 16) return run_hd<T, 16>(a);
+        if (a.d <= 32) return run_hd<T, 32>(a);
+        if (a.d <= 64) return run_hd<T, 64>(a);
     }
     return HCA_EINVAL;
 }
 
-}  // namespace hca
+int dispatch(const RunArgs &a, int32_t dtype) {
+    return dtype == HCA_F32 ? dispatch_t<float>(a) : dispatch_t<double>(a);
+}
 
-using namespace hca;
-
-extern "C" int hca_dbscan_device_ex(const void *d_points, int32_t dtype, int64_t n, int32_t d,
-                                    double eps, int32_t min_pts, int32_t *d_labels, uint8_t *d_core,
-                                    void *stream, hca_stats *stats, int32_t flags) {
+int device_ex_tuned(const void *d_points, int32_t dtype, int64_t n, int32_t d, double eps, int32_t min_pts,
+                    int32_t *d_labels, uint8_t *d_core, void *stream, hca_stats *stats, int32_t flags,
+                    const hca_tuning &tune) {
     int rc = check_common(d_points, dtype, n, d, eps, min_pts, d_labels);
     if (rc) return rc;
     if (stats) {
@@ -128,12 +123,13 @@ extern "C" int hca_dbscan_device_ex(const void *d_points, int32_t dtype, int64_t
     a.stream = (cudaStream_t)stream;
     a.stats = stats;
     a.flags = flags;
+    a.tune = tune;
     return dispatch(a, dtype);
 }
 
-extern "C" int hca_dbscan_batched(const void *d_points, int32_t dtype, int32_t n_sets, const int64_t *offsets,
-                                  int32_t d, const double *eps, const int32_t *min_pts, int32_t *d_labels,
-                                  uint8_t *d_core, void *stream, hca_stats *stats, int32_t flags) {
+int batched_tuned(const void *d_points, int32_t dtype, int32_t n_sets, const int64_t *offsets, int32_t d,
+                  const double *eps, const int32_t *min_pts, int32_t *d_labels, uint8_t *d_core, void *stream,
+                  hca_stats *stats, int32_t flags, const hca_tuning &tune) {
     if (n_sets < 1 || !offsets || !eps || !min_pts) return HCA_EINVAL;
     if (offsets[0] != 0) return HCA_EINVAL;
     for (int32_t i = 0; i < n_sets; ++i) {
@@ -150,24 +146,41 @@ extern "C" int hca_dbscan_batched(const void *d_points, int32_t dtype, int32_t n
     if (n == 0) return HCA_OK;
     const size_t esz = dtype == HCA_F32 ? 4 : 8;
     if (((uintptr_t)d_points) % esz || ((uintptr_t)d_labels) % 4) return HCA_EINVAL;
-    {
-        RunArgs a;
-        a.d_points = d_points;
-        a.n = n;
-        a.d = d;
-        a.eps = eps[0];
-        a.min_pts = min_pts[0];
-        a.d_labels = d_labels;
-        a.d_core = d_core;
-        a.stream = (cudaStream_t)stream;
-        a.stats = stats;
-        a.flags = flags;
-        a.nsets = n_sets;
-        a.h_off = offsets;
-        a.h_eps = eps;
-        a.h_minpts = min_pts;
-        return dispatch(a, dtype);
-    }
+    RunArgs a;
+    a.d_points = d_points;
+    a.n = n;
+    a.d = d;
+    a.eps = eps[0];
+    a.min_pts = min_pts[0];
+    a.d_labels = d_labels;
+    a.d_core = d_core;
+    a.stream = (cudaStream_t)stream;
+    a.stats = stats;
+    a.flags = flags;
+    a.nsets = n_sets;
+    a.h_off = offsets;
+    a.h_eps = eps;
+    a.h_minpts = min_pts;
+    a.tune = tune;
+    return dispatch(a, dtype);
+}
+
+}  // namespace hca
+
+using namespace hca;
+
+extern "C" int hca_dbscan_device_ex(const void *d_points, int32_t dtype, int64_t n, int32_t d,
+                                    double eps, int32_t min_pts, int32_t *d_labels, uint8_t *d_core,
+                                    void *stream, hca_stats *stats, int32_t flags) {
+    return device_ex_tuned(d_points, dtype, n, d, eps, min_pts, d_labels, d_core, stream, stats, flags,
+                           tuning_for(d));
+}
+
+extern "C" int hca_dbscan_batched(const void *d_points, int32_t dtype, int32_t n_sets, const int64_t *offsets,
+                                  int32_t d, const double *eps, const int32_t *min_pts, int32_t *d_labels,
+                                  uint8_t *d_core, void *stream, hca_stats *stats, int32_t flags) {
+    return batched_tuned(d_points, dtype, n_sets, offsets, d, eps, min_pts, d_labels, d_core, stream, stats,
+                         flags, tuning_for(d));
 }
 
 extern "C" int hca_dbscan_device(const void *d_points, int32_t dtype, int64_t n, int32_t d, double eps,

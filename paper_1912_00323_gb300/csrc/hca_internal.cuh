@@ -20,6 +20,13 @@ constexpr uint32_t kLoopLimit = 1u << 22;  // cap of every loop that reads concu
 constexpr uint32_t kErrHashFull = 1u;
 constexpr uint32_t kErrLoop = 2u;
 
+// Default tuning (include/hca_dbscan.h): dimension-chosen neighbour search; tensor-core tiles
+// from 8 rows (counts, unions) and 2 non-core rows (labels); hand-off at 8 open count rows;
+// first links everywhere.  A 128-row chunk with r rows of a phase costs about the same per 128
+// candidates as r rows on the CUDA cores at r ~ 2 (labels) and r ~ 8 (counts, unions),
+// measured on the 16-D workload and the batched d = 8 sets.
+constexpr hca_tuning kDefaultTuning = {0, 8, 8, 2, 8, 1};
+
 // Device counters and status, one struct per call in the workspace.
 struct DevCounters {
     uint32_t n_cells;      // C: non-empty cells
@@ -139,7 +146,21 @@ struct RunArgs {
     const int64_t *h_off = nullptr;      // host, nsets + 1 point offsets
     const double *h_eps = nullptr;       // host, nsets
     const int32_t *h_minpts = nullptr;   // host, nsets
+    hca_tuning tune = kDefaultTuning;    // neighbour search and tensor-core split of this call
 };
+
+// The tuning in effect for dimension d (tune.cu).
+hca_tuning tuning_for(int d);
+
+// api.cu: argument checks and the clustering calls with an explicit tuning.
+int check_common(const void *pts, int32_t dtype, int64_t n, int32_t d, double eps, int32_t min_pts,
+                 const void *labels);
+int device_ex_tuned(const void *d_points, int32_t dtype, int64_t n, int32_t d, double eps, int32_t min_pts,
+                    int32_t *d_labels, uint8_t *d_core, void *stream, hca_stats *stats, int32_t flags,
+                    const hca_tuning &tune);
+int batched_tuned(const void *d_points, int32_t dtype, int32_t n_sets, const int64_t *offsets, int32_t d,
+                  const double *eps, const int32_t *min_pts, int32_t *d_labels, uint8_t *d_core, void *stream,
+                  hca_stats *stats, int32_t flags, const hca_tuning &tune);
 template <typename T, int D>
 int run_lowd(const RunArgs &a);
 template <typename T, int DP>

@@ -45,6 +45,7 @@ struct HdView {
     // the per-cell core counts; tc_hook: first links also in cells whose unions run there
     uint32_t tc_min[3];
     uint32_t tc_hook;
+    uint32_t tc_handoff;  // open count rows at which a tensor-core chunk hands over
     const uint32_t *cx;
     // rows the tensor-core count handed over: count so far and candidate-stream position
     uint32_t *tc_cnt;

@@ -119,16 +119,13 @@ inline int tc_launch_shape(size_t &smem) {
 }  // namespace detail
 
 // Rows of a phase (counts, unions, labels) from which a coarse cell goes to the tensor-core
-// kernels, and whether the first links also run in cells whose unions are on tensor cores.
-// A 128-row chunk with r rows of a phase costs about the same per 128 candidates as r rows on
-// the CUDA cores at r ~ 2 (labels: non-core rows) and r ~ 8 (unions: core rows; counts: all
-// rows), measured on the 16-D workload and the batched d = 8 sets; the first links shorten the
-// union chains enough to pay for themselves on dense clusters.
+// kernels, whether the first links also run in cells whose unions are on tensor cores, and the
+// open count rows at which a tensor-core chunk hands over (from the call's hca_tuning).
 struct TcTuning {
     uint32_t min[3];
     uint32_t hook;
+    uint32_t handoff;
 };
-constexpr TcTuning kTcTuning = {{8u, 8u, 2u}, 1u};
 
 // Workspace offsets of the tensor-core phases.
 struct TcOffsets {
@@ -151,6 +148,7 @@ void run_tc_phases(HdView<float, DP> &hv, cudaStream_t s, char *b, int64_t n, in
     uint32_t *clab = (uint32_t *)(b + o.clab);
     for (int i = 0; i < 3; ++i) hv.tc_min[i] = tune.min[i];
     hv.tc_hook = tune.hook;
+    hv.tc_handoff = tune.handoff;
     hv.cx = cx;
     hv.tc_cnt = clab;   // free until the labels phase
     hv.tc_pos = flags;  // free until the core numbering
@@ -470,7 +468,11 @@ int run_hd(const RunArgs &a) {
             run_tc_phases<DP>(hv, s, b, n, sms * tc_occ, tc_smem, gpts, gcell, smem, part_of(b, o_part),
                               TcOffsets{o_tnch, o_tnch2, o_tch0, o_tch1, o_tch2, o_tflags, o_cx, o_clist, o_nclist,
                                         o_clab},
-                              batched ? nsets : 0, ctr, kTcTuning, mark, launches);
+                              batched ? nsets : 0, ctr,
+                              TcTuning{{(uint32_t)a.tune.tc_min_count, (uint32_t)a.tune.tc_min_merge,
+                                        (uint32_t)a.tune.tc_min_labels},
+                                       (uint32_t)a.tune.first_links, (uint32_t)a.tune.tc_handoff},
+                              mark, launches);
             goto done_phases;
         }
     }

@@ -54,7 +54,6 @@ constexpr uint32_t kLBO = 128;             // bytes between core matrices along 
 constexpr uint32_t kWaitLimit = 1u << 22;  // mbarrier polls before a wait gives up
 constexpr size_t kMinSmem = 48 * 1024;     // per CTA: at most 4 CTAs (4 x 128 TMEM columns) per SM
 constexpr int kMaxRng = 32;                // neighbour ranges per cell (the coarse grid has 9)
-constexpr int kHandOff = 8;                // open count rows at which a chunk hands over to the CUDA cores
 enum { kCount = 0, kMerge = 1, kLabels = 2 };
 
 // Row and candidate lists of the three phases.
@@ -253,7 +252,7 @@ __device__ __forceinline__ uint32_t stream_index(const uint32_t *rpre, const uin
 //   kCount:  rows = every point of the cell, candidates = every point of the 27 neighbouring
 //            cells; core[p] = (|N_eps(p)| >= MINPTS).  Two tallies per row: pairs surely within
 //            eps and pairs not proved outside; a row stops once the first reaches MINPTS.  Once
-//            at most kHandOff rows of a chunk are open the chunk stops, and those rows get
+//            at most tc_handoff rows of a chunk are open the chunk stops, and those rows get
 //            core[p] = 2 with their count and the next stream position (or zero and zero for
 //            all of them if one saw an undecided pair); a row that ends with MINPTS between the tallies gets core[p] =
 //            2, zero and zero.  The CUDA-core count continues them exactly.
@@ -518,7 +517,7 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
             if (MODE == kCount) {
                 const int open = __syncthreads_count(!done);
                 if (open == 0) break;
-                if (open <= kHandOff && ub + 2 * kTile < L) {
+                if (open <= (int)v.tc_handoff && ub + 2 * kTile < L) {
                     // few rows left and more than one block to go: the CUDA-core count continues
                     // them from the next candidate on
                     // the rows resume from the next block if none saw an undecided pair, else
