@@ -235,6 +235,37 @@ HCA_API int hca_radix_sort_pairs_noalloc(void *d_keys, uint32_t *d_vals, int64_t
                                          void *stream);
 
 /*
+ * Plans: one clustering call of the hypercube path (1 <= d <= 4) whose buffers and point
+ * extents are fixed up front, captured once into a CUDA graph and replayed.  The paper has no
+ * counterpart; the result is the one hca_dbscan_device / hca_dbscan_batched give.  With the
+ * extents declared, the grid, the stencil and the workspace are fixed before the first launch,
+ * so a launch never waits for the host: the whole call is one graph launch.
+ *   d_points, d_labels, d_core  device buffers bound to the plan (as in hca_dbscan_device_ex;
+ *              d_core nullable); the caller may rewrite d_points between launches.
+ *   box_min, box_max  host, d values (batched: n_sets x d, set-major): every coordinate of
+ *              every launch's points must lie in [box_min, box_max]; a launch whose points do
+ *              not makes hca_plan_wait return HCA_ERANGE (its labels are then undefined).  A
+ *              larger box gives the same labels (the grid origin does not change a label).
+ * hca_plan_create[_batched] synchronises (it sizes and allocates the workspace and captures
+ * the graph; no kernel runs).  hca_plan_launch enqueues one clustering on `stream` and returns.
+ * hca_plan_wait synchronises `stream` and returns the launch's code: HCA_OK, HCA_ERANGE (a
+ * point outside its box), HCA_EINVAL (a NaN coordinate) or HCA_EDEVICE; `stats` (nullable)
+ * receives its counts (n_cells, n_pencils, n_dense_cells, n_core_points, n_clusters, n_noise).
+ * Launches of one plan share its workspace: order them (one stream, or wait in between).
+ */
+typedef struct hca_plan hca_plan;
+HCA_API int hca_plan_create(hca_plan **out, const void *d_points, int32_t dtype, int64_t n, int32_t d,
+                            double eps, int32_t min_pts, const double *box_min, const double *box_max,
+                            int32_t *d_labels, uint8_t *d_core);
+HCA_API int hca_plan_create_batched(hca_plan **out, const void *d_points, int32_t dtype, int32_t n_sets,
+                                    const int64_t *offsets, int32_t d, const double *eps,
+                                    const int32_t *min_pts, const double *box_min,
+                                    const double *box_max, int32_t *d_labels, uint8_t *d_core);
+HCA_API int hca_plan_launch(hca_plan *plan, void *stream);
+HCA_API int hca_plan_wait(hca_plan *plan, void *stream, hca_stats *stats);
+HCA_API int hca_plan_destroy(hca_plan *plan);
+
+/*
  * Tuning of the neighbour search and of the tensor-core tiles, per dimension d (process-wide,
  * all devices).  The paper has no counterpart: these choose how the same exact result is
  * computed (Sec. 2's hypercube neighbour enumeration, or the coarse grid of the d >= 5 path;

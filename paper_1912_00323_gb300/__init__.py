@@ -29,7 +29,8 @@ STAGES = ("minmax", "bin", "sort", "cells", "hash", "core", "reps", "merge", "la
 
 ABI_FUNCTIONS = ("hca_dbscan", "hca_dbscan_device", "hca_dbscan_device_ex", "hca_dbscan_batched",
                  "hca_radix_sort_pairs", "hca_tuning_get", "hca_tuning_set", "hca_autotune",
-                 "hca_autotune_batched", "hca_strerror", "hca_version")
+                 "hca_autotune_batched", "hca_plan_create", "hca_plan_create_batched", "hca_plan_launch",
+                 "hca_plan_wait", "hca_plan_destroy", "hca_strerror", "hca_version")
 
 
 class HcaStats(ctypes.Structure):
@@ -107,6 +108,13 @@ def load():
     lib.hca_autotune_batched.argtypes = [vp, i32, i32, vp, i32, vp, vp, vp, i32, ctypes.POINTER(HcaTuning),
                                          ctypes.POINTER(ctypes.c_double)]
     for f in ("hca_tuning_get", "hca_tuning_set", "hca_autotune", "hca_autotune_batched"):
+        getattr(lib, f).restype = ctypes.c_int
+    lib.hca_plan_create.argtypes = [ctypes.POINTER(vp), vp, i32, i64, i32, dbl, i32, vp, vp, vp, vp]
+    lib.hca_plan_create_batched.argtypes = [ctypes.POINTER(vp), vp, i32, i32, vp, i32, vp, vp, vp, vp, vp, vp]
+    lib.hca_plan_launch.argtypes = [vp, vp]
+    lib.hca_plan_wait.argtypes = [vp, vp, ctypes.POINTER(HcaStats)]
+    lib.hca_plan_destroy.argtypes = [vp]
+    for f in ("hca_plan_create", "hca_plan_create_batched", "hca_plan_launch", "hca_plan_wait", "hca_plan_destroy"):
         getattr(lib, f).restype = ctypes.c_int
     lib.hca_strerror.argtypes = [ctypes.c_int]
     lib.hca_strerror.restype = ctypes.c_char_p
@@ -303,6 +311,75 @@ def hca_autotune_batched(points, offsets, eps, min_pts, stream=None, repeats: in
     if rc != HCA_OK:
         raise HcaError(rc, "hca_autotune_batched")
     return t.as_dict(), ms.value
+
+
+class Plan:
+    """One clustering call of the hypercube path (d <= 4) captured as a CUDA graph (hca_plan_*).
+    Bound to the CUDA tensors `points` (n, d) and `labels` (n,) (and `core`, optional); the
+    points may be rewritten between launches as long as they stay inside the declared box
+    (box_min, box_max: d values, or n_sets x d for a batched plan)."""
+
+    def __init__(self, points, eps, min_pts, box_min, box_max, labels=None, core=None, offsets=None):
+        import torch
+        lib = load()
+        if not points.is_cuda or not points.is_contiguous():
+            raise ValueError("Plan takes a contiguous CUDA tensor")
+        self.points = points
+        n = points.shape[0]
+        d = points.shape[1] if points.dim() == 2 else 1
+        self.labels = labels if labels is not None else torch.empty(n, dtype=torch.int32, device=points.device)
+        self.core = core
+        self._bmn = np.ascontiguousarray(np.asarray(box_min, dtype=np.float64).ravel())
+        self._bmx = np.ascontiguousarray(np.asarray(box_max, dtype=np.float64).ravel())
+        h = ctypes.c_void_p()
+        cp = core.data_ptr() if core is not None else None
+        if offsets is None:
+            rc = lib.hca_plan_create(ctypes.byref(h), points.data_ptr(), _dtype_code(points.dtype), n, d,
+                                     float(eps), int(min_pts), self._bmn.ctypes.data, self._bmx.ctypes.data,
+                                     self.labels.data_ptr(), cp)
+        else:
+            self._off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+            self._eps = np.ascontiguousarray(np.asarray(eps, dtype=np.float64))
+            self._mp = np.ascontiguousarray(np.asarray(min_pts, dtype=np.int32))
+            if len(self._off) != len(self._eps) + 1 or self._off[-1] != n:
+                raise ValueError("offsets must have n_sets + 1 entries ending at len(points)")
+            rc = lib.hca_plan_create_batched(ctypes.byref(h), points.data_ptr(), _dtype_code(points.dtype),
+                                             len(self._eps), self._off.ctypes.data, d, self._eps.ctypes.data,
+                                             self._mp.ctypes.data, self._bmn.ctypes.data, self._bmx.ctypes.data,
+                                             self.labels.data_ptr(), cp)
+        if rc != HCA_OK:
+            raise HcaError(rc, "hca_plan_create")
+        self._h = h
+
+    def launch(self, stream=None):
+        rc = load().hca_plan_launch(self._h, _stream_ptr(stream))
+        if rc != HCA_OK:
+            raise HcaError(rc, "hca_plan_launch")
+
+    def wait(self, stream=None):
+        st = HcaStats()
+        rc = load().hca_plan_wait(self._h, _stream_ptr(stream), ctypes.byref(st))
+        if rc != HCA_OK:
+            raise HcaError(rc, "hca_plan_wait")
+        return {k: st.as_dict()[k] for k in ("n_cells", "n_pencils", "n_dense_cells", "n_core_points",
+                                              "n_clusters", "n_noise")}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().hca_plan_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

@@ -19,6 +19,7 @@ constexpr uint32_t kLoopLimit = 1u << 22;  // cap of every loop that reads concu
 // device-side status word bits (HCA_EDEVICE when non-zero)
 constexpr uint32_t kErrHashFull = 1u;
 constexpr uint32_t kErrLoop = 2u;
+constexpr uint32_t kErrBox = 8u;   // a point lies outside the extents a plan declared
 
 // Default tuning (include/hca_dbscan.h): dimension-chosen neighbour search; tensor-core tiles
 // from 8 rows (counts, unions) and 2 non-core rows (labels); hand-off at 8 open count rows;
@@ -147,12 +148,24 @@ struct RunArgs {
     const double *h_eps = nullptr;       // host, nsets
     const int32_t *h_minpts = nullptr;   // host, nsets
     hca_tuning tune = kDefaultTuning;    // neighbour search and tensor-core split of this call
+    // Plans (d <= 4): declared extents box_mn / box_mx (host, D values per set, set-major) size
+    // the grids instead of the measured ones, so nothing in the call waits for the host; a
+    // device kernel flags a point outside its box (status kErrBox).
+    const double *box_mn = nullptr, *box_mx = nullptr;
+    size_t *ws_query = nullptr;          // set: store the workspace bytes needed, launch nothing
+    void *ws_ext = nullptr;              // caller-owned workspace (nullptr: the call allocates)
+    size_t ws_ext_bytes = 0;
+    DevCounters *h_ext = nullptr;        // pinned host copy of the counters (nullptr: the thread's)
+    void *h_stage = nullptr;             // pinned staging of the batched tables (deferred calls)
+    bool deferred = false;               // no host synchronisation: the caller checks the status
 };
 
 // The tuning in effect for dimension d (tune.cu).
 hca_tuning tuning_for(int d);
 
-// api.cu: argument checks and the clustering calls with an explicit tuning.
+// api.cu: argument checks, dispatch to the pipelines, and the clustering calls with an
+// explicit tuning.
+int dispatch(const RunArgs &a, int32_t dtype);
 int check_common(const void *pts, int32_t dtype, int64_t n, int32_t d, double eps, int32_t min_pts,
                  const void *labels);
 int device_ex_tuned(const void *d_points, int32_t dtype, int64_t n, int32_t d, double eps, int32_t min_pts,

@@ -57,6 +57,11 @@ __device__ __forceinline__ uint64_t enc_double(double f) {
     return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 
+__device__ __forceinline__ double dec_double_dev(uint64_t e) {
+    const uint64_t b = (e >> 63) ? (e & 0x7fffffffffffffffull) : ~e;
+    return __longlong_as_double((long long)b);
+}
+
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
     x ^= x >> 30;
     x *= 0xbf58476d1ce4e5b9ull;
@@ -1255,6 +1260,36 @@ __device__ __forceinline__ uint32_t set_of_point(const int64_t *set_off, int nse
         if (__ldg(set_off + mid) <= j) lo = mid; else hi = mid;
     }
     return (uint32_t)lo;
+}
+
+// Declared extents of a plan (one set: box in `single`, measured extents in ctr->minmax_enc;
+// sets: boxes and measured extents per set in `mm`, set-major): a measured minimum below or
+// maximum above the box, or a NaN, sets status bit kErrBox.
+struct BoxArgs {
+    double mn[kMaxD], mx[kMaxD];
+};
+template <int D>
+__global__ void __launch_bounds__(256) k_box_check(BoxArgs single, const double *__restrict__ boxes, int nsets,
+                                                  const int64_t *__restrict__ set_off,
+                                                  const unsigned long long *__restrict__ mm, DevCounters *ctr) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && ctr->nan_seen) atomicOr(&ctr->status, kErrBox);
+    if (!boxes) {
+        if (blockIdx.x != 0 || threadIdx.x >= D) return;
+        const int i = threadIdx.x;
+        const uint64_t *enc = reinterpret_cast<const uint64_t *>(ctr->minmax_enc);
+        if (dec_double_dev(enc[i]) < single.mn[i] || dec_double_dev(enc[kMaxD + i]) > single.mx[i])
+            atomicOr(&ctr->status, kErrBox);
+        return;
+    }
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < (int64_t)nsets * D;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int set = (int)(k / D), i = (int)(k % D);
+        if (set_off[set + 1] == set_off[set]) continue;
+        const double lo = dec_double_dev(mm[(size_t)set * kMaxD + i]);
+        const double hi = dec_double_dev(mm[(size_t)kMaxD * nsets + (size_t)set * kMaxD + i]);
+        if (lo < boxes[(size_t)set * D + i] || hi > boxes[(size_t)(nsets + set) * D + i])
+            atomicOr(&ctr->status, kErrBox);
+    }
 }
 
 // Per-set min / max (origin shift, Sec. 2) and NaN check; mm[set * kMaxD + i] = min encoding,

@@ -271,17 +271,19 @@ int run_lowd(const RunArgs &a) {
     const size_t o_mm = take(sizeof(uint64_t) * 2 * kMaxD * (size_t)nsets);
     const size_t o_gtab = take(sizeof(GridParams) * (size_t)nsets);
     const size_t o_setoff = take(sizeof(int64_t) * ((size_t)nsets + 1));
+    const size_t o_box = take(sizeof(double) * 2 * D * (size_t)nsets);
+    const size_t main_bytes = off;
     void *ws = nullptr, *ws_ranges = nullptr;
-    if (pool_alloc(&ws, off, s) != cudaSuccess || !ws) return HCA_ENOMEM;
-    char *b = (char *)ws;
-    DevCounters *ctr = (DevCounters *)(b + o_ctr);
-    DevCounters *h = host_counters();
+    const bool boxed = a.box_mn != nullptr;
+    const bool own_ws = a.ws_ext == nullptr;
+    char *b = nullptr;
+    DevCounters *ctr = nullptr;
+    DevCounters *h = a.h_ext ? a.h_ext : host_counters();
     int rc = HCA_OK;
+    size_t ranges_bytes = 0;
 
     cudaEvent_t ev[HCA_NUM_STAGES + 1] = {};
-    const bool timing = (a.flags & HCA_FLAG_TIMING) && a.stats;
-    if (timing)
-        for (int i = 0; i <= HCA_NUM_STAGES; ++i) cudaEventCreate(&ev[i]);
+    const bool timing = (a.flags & HCA_FLAG_TIMING) && a.stats && !a.deferred;
     auto mark = [&](int i) { if (timing) cudaEventRecord(ev[i], s); };
 
     GridParams g;
@@ -295,31 +297,27 @@ int run_lowd(const RunArgs &a) {
     int sort_bits = 0;
     std::vector<GridParams> gsets;
     std::vector<uint64_t> hmm;
-    GridParams *d_gtab = (GridParams *)(b + o_gtab);
-    int64_t *d_setoff = (int64_t *)(b + o_setoff);
-    uint64_t *d_mm = (uint64_t *)(b + o_mm);
+    GridParams *d_gtab = nullptr;
+    int64_t *d_setoff = nullptr;
+    uint64_t *d_mm = nullptr;
 
-    if (!h) { rc = HCA_ECUDA; goto out; }
-    mark(0);
-    cudaMemsetAsync(ctr, 0, sizeof(DevCounters), s);
-    cudaMemsetAsync(ctr->minmax_enc, 0xff, sizeof(uint64_t) * kMaxD, s);
-    if (!batched) {
-        k_minmax<T, D><<<grid_for(n, 256, sms, 2), 256, 0, s>>>((const T *)a.d_points, n, ctr);
-    } else {
-        cudaMemsetAsync(d_mm, 0xff, sizeof(uint64_t) * kMaxD * nsets, s);
-        cudaMemsetAsync(d_mm + (size_t)kMaxD * nsets, 0, sizeof(uint64_t) * kMaxD * nsets, s);
-        cudaMemcpyAsync(d_setoff, a.h_off, sizeof(int64_t) * (nsets + 1), cudaMemcpyHostToDevice, s);
-        k_minmax_seg<T, D><<<grid_for(n, 256, sms, 4), 256, 0, s>>>((const T *)a.d_points, n, d_setoff, nsets,
-                                                                  (unsigned long long *)d_mm, ctr);
-        hmm.resize((size_t)2 * kMaxD * nsets);
-        cudaMemcpyAsync(hmm.data(), d_mm, sizeof(uint64_t) * hmm.size(), cudaMemcpyDeviceToHost, s);
-    }
-    ++launches;
-    if (cudaMemcpyAsync(h, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) { rc = HCA_ECUDA; goto out; }
-    if (batched) {
-        if (h->nan_seen) { rc = HCA_EINVAL; goto out; }
-        // a grid per set, then one key layout for all (per dimension the largest bit count)
+    // the grids (one per set, one key layout for all) and the stencil, from the extents of
+    // every set: the measured ones, or a plan's declared boxes
+    auto build_grids = [&](auto mn_of, auto mx_of) -> int {
+        if (!batched) {
+            double mn[kMaxD], mx[kMaxD];
+            for (int i = 0; i < D; ++i) {
+                mn[i] = mn_of(0, i);
+                mx[i] = mx_of(0, i);
+                if (!isfinite(mn[i]) || !isfinite(mx[i]) || mx[i] < mn[i]) return HCA_EINVAL;
+            }
+            int r = make_grid(D, sizeof(T) == 4, a.eps, a.min_pts, n, mn, mx, a.flags, g, tau);
+            if (r) return r;
+            r = make_stencil(D, a.eps, 1.0 / g.inv_side, tau, st);
+            if (r) return r;
+            sort_bits = g.key_bits;
+            return HCA_OK;
+        }
         gsets.resize(nsets);
         std::vector<double> e_eps(nsets), e_side(nsets), e_tau(nsets);
         uint32_t bits[kMaxD] = {};
@@ -327,13 +325,14 @@ int run_lowd(const RunArgs &a) {
             double mn[kMaxD], mx[kMaxD];
             const bool empty = a.h_off[st_i + 1] == a.h_off[st_i];
             for (int i = 0; i < D; ++i) {
-                mn[i] = empty ? 0.0 : dec_double(hmm[(size_t)st_i * kMaxD + i]);
-                mx[i] = empty ? 0.0 : dec_double(hmm[(size_t)kMaxD * nsets + (size_t)st_i * kMaxD + i]);
-                if (!isfinite(mn[i]) || !isfinite(mx[i])) { rc = HCA_EINVAL; goto out; }
+                mn[i] = empty ? 0.0 : mn_of(st_i, i);
+                mx[i] = empty ? 0.0 : mx_of(st_i, i);
+                if (!isfinite(mn[i]) || !isfinite(mx[i]) || mx[i] < mn[i]) return HCA_EINVAL;
             }
             double tau_s = 0.0;
-            rc = make_grid(D, sizeof(T) == 4, a.h_eps[st_i], a.h_minpts[st_i], n, mn, mx, a.flags, gsets[st_i], tau_s);
-            if (rc) goto out;
+            const int r = make_grid(D, sizeof(T) == 4, a.h_eps[st_i], a.h_minpts[st_i], n, mn, mx, a.flags,
+                                    gsets[st_i], tau_s);
+            if (r) return r;
             e_eps[st_i] = a.h_eps[st_i];
             e_side[st_i] = 1.0 / gsets[st_i].inv_side;
             e_tau[st_i] = tau_s;
@@ -342,7 +341,7 @@ int run_lowd(const RunArgs &a) {
         int key_bits = 0, set_bits = 1;
         for (int i = 0; i < D; ++i) key_bits += (int)bits[i];
         while ((1ll << set_bits) < nsets) ++set_bits;
-        if (key_bits + set_bits > 63) { rc = HCA_ERANGE; goto out; }
+        if (key_bits + set_bits > 63) return HCA_ERANGE;
         for (GridParams &gp : gsets) {
             int sh = 0;
             for (int i = D - 1; i >= 0; --i) {
@@ -355,28 +354,98 @@ int run_lowd(const RunArgs &a) {
         }
         g = gsets[0];
         sort_bits = key_bits + set_bits;
-        rc = make_stencil_union(D, e_eps, e_side, e_tau, st);
-        if (rc) goto out;
-        cudaMemcpyAsync(d_gtab, gsets.data(), sizeof(GridParams) * nsets, cudaMemcpyHostToDevice, s);
-        if (pool_alloc(&ws_ranges, sizeof(uint2) * (size_t)n * st.n_all + sizeof(Pt<T, D>) * (size_t)n * ndir + 256,
-                       s) != cudaSuccess || !ws_ranges) {
-            rc = HCA_ENOMEM;
-            goto out;
+        return make_stencil_union(D, e_eps, e_side, e_tau, st);
+    };
+    // per-set tables to the device: from pinned staging when the call is deferred (a graph
+    // replays the copy), else straight from the host arrays
+    auto upload = [&](void *dst, const void *src, size_t bytes, size_t stage_off) {
+        if (a.deferred && a.h_stage) {
+            memcpy((char *)a.h_stage + stage_off, src, bytes);
+            src = (char *)a.h_stage + stage_off;
         }
+        cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+    };
+    const size_t stage_setoff = 0, stage_gtab = align_up(sizeof(int64_t) * ((size_t)nsets + 1));
+    const size_t stage_box = stage_gtab + align_up(sizeof(GridParams) * (size_t)nsets);
+
+    if (!h) return HCA_ECUDA;
+    if (boxed) {
+        rc = build_grids([&](int set, int i) { return a.box_mn[(size_t)set * D + i]; },
+                         [&](int set, int i) { return a.box_mx[(size_t)set * D + i]; });
+        if (rc) return rc;
+        ranges_bytes = sizeof(uint2) * (size_t)n * st.n_all + sizeof(Pt<T, D>) * (size_t)n * ndir + 256;
+    }
+    if (a.ws_query) {  // plans size their workspace first (declared extents only)
+        if (!boxed) return HCA_EINVAL;
+        *a.ws_query = main_bytes + ranges_bytes;
+        return HCA_OK;
+    }
+    if (!own_ws) {
+        if (!boxed || a.ws_ext_bytes < main_bytes + ranges_bytes) return HCA_EINVAL;
+        ws = a.ws_ext;
+        ws_ranges = (char *)a.ws_ext + main_bytes;
     } else {
-        if (h->nan_seen) { rc = HCA_EINVAL; goto out; }
-        const uint64_t *mm = reinterpret_cast<const uint64_t *>(h->minmax_enc);
-        double mn[kMaxD], mx[kMaxD];
-        for (int i = 0; i < D; ++i) {
-            mn[i] = dec_double(mm[i]);
-            mx[i] = dec_double(mm[kMaxD + i]);
-            if (!isfinite(mn[i]) || !isfinite(mx[i])) { rc = HCA_EINVAL; goto out; }
+        if (pool_alloc(&ws, main_bytes + ranges_bytes, s) != cudaSuccess || !ws) return HCA_ENOMEM;
+        if (boxed) ws_ranges = (char *)ws + main_bytes;
+    }
+    b = (char *)ws;
+    ctr = (DevCounters *)(b + o_ctr);
+    d_gtab = (GridParams *)(b + o_gtab);
+    d_setoff = (int64_t *)(b + o_setoff);
+    d_mm = (uint64_t *)(b + o_mm);
+    if (timing)
+        for (int i = 0; i <= HCA_NUM_STAGES; ++i) cudaEventCreate(&ev[i]);
+
+    mark(0);
+    cudaMemsetAsync(ctr, 0, sizeof(DevCounters), s);
+    cudaMemsetAsync(ctr->minmax_enc, 0xff, sizeof(uint64_t) * kMaxD, s);
+    if (!batched) {
+        k_minmax<T, D><<<grid_for(n, 256, sms, 2), 256, 0, s>>>((const T *)a.d_points, n, ctr);
+    } else {
+        cudaMemsetAsync(d_mm, 0xff, sizeof(uint64_t) * kMaxD * nsets, s);
+        cudaMemsetAsync(d_mm + (size_t)kMaxD * nsets, 0, sizeof(uint64_t) * kMaxD * nsets, s);
+        upload(d_setoff, a.h_off, sizeof(int64_t) * (nsets + 1), stage_setoff);
+        k_minmax_seg<T, D><<<grid_for(n, 256, sms, 4), 256, 0, s>>>((const T *)a.d_points, n, d_setoff, nsets,
+                                                                  (unsigned long long *)d_mm, ctr);
+        if (!boxed) {
+            hmm.resize((size_t)2 * kMaxD * nsets);
+            cudaMemcpyAsync(hmm.data(), d_mm, sizeof(uint64_t) * hmm.size(), cudaMemcpyDeviceToHost, s);
         }
-        rc = make_grid(D, sizeof(T) == 4, a.eps, a.min_pts, n, mn, mx, a.flags, g, tau);
+    }
+    ++launches;
+    if (boxed) {
+        // declared extents: check them on the device, no host round trip
+        BoxArgs one;
+        memset(&one, 0, sizeof(one));
+        double *d_box = nullptr;
+        if (!batched) {
+            for (int i = 0; i < D; ++i) {
+                one.mn[i] = a.box_mn[i];
+                one.mx[i] = a.box_mx[i];
+            }
+        } else {
+            std::vector<double> boxes((size_t)2 * D * nsets);
+            memcpy(boxes.data(), a.box_mn, sizeof(double) * D * nsets);
+            memcpy(boxes.data() + (size_t)D * nsets, a.box_mx, sizeof(double) * D * nsets);
+            d_box = (double *)(b + o_box);
+            upload(d_box, boxes.data(), sizeof(double) * boxes.size(), stage_box);
+            upload(d_gtab, gsets.data(), sizeof(GridParams) * nsets, stage_gtab);
+        }
+        k_box_check<D><<<grid_for((int64_t)nsets * D, 256, sms, 1), 256, 0, s>>>(
+            one, d_box, nsets, d_setoff, (const unsigned long long *)d_mm, ctr);
+        ++launches;
+    } else {
+        if (cudaMemcpyAsync(h, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) { rc = HCA_ECUDA; goto out; }
+        if (h->nan_seen) { rc = HCA_EINVAL; goto out; }
+        if (batched)
+            rc = build_grids([&](int set, int i) { return dec_double(hmm[(size_t)set * kMaxD + i]); },
+                             [&](int set, int i) { return dec_double(hmm[(size_t)kMaxD * nsets + (size_t)set * kMaxD + i]); });
+        else
+            rc = build_grids([&](int, int i) { return dec_double(reinterpret_cast<const uint64_t *>(h->minmax_enc)[i]); },
+                             [&](int, int i) { return dec_double(reinterpret_cast<const uint64_t *>(h->minmax_enc)[kMaxD + i]); });
         if (rc) goto out;
-        rc = make_stencil(D, a.eps, 1.0 / g.inv_side, tau, st);
-        if (rc) goto out;
-        sort_bits = g.key_bits;
+        if (batched) cudaMemcpyAsync(d_gtab, gsets.data(), sizeof(GridParams) * nsets, cudaMemcpyHostToDevice, s);
         // neighbour ranges (one (lo, hi) pair per cell and stencil pencil) and the coordinates
         // of the representative points (ndir per cell)
         if (pool_alloc(&ws_ranges, sizeof(uint2) * (size_t)n * st.n_all + sizeof(Pt<T, D>) * (size_t)n * ndir + 256,
@@ -510,9 +579,14 @@ int run_lowd(const RunArgs &a) {
     launches += 3;
     mark(9);
     if (cudaGetLastError() != cudaSuccess) { rc = HCA_ECUDA; goto out; }
-    if (cudaMemcpyAsync(h, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) { rc = HCA_ECUDA; goto out; }
-    if (h->status) { rc = HCA_EDEVICE; goto out; }
+    if (cudaMemcpyAsync(h, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+        rc = HCA_ECUDA;
+        goto out;
+    }
+    if (a.deferred) goto out;  // the caller synchronises and reads the status from h
+    if (cudaStreamSynchronize(s) != cudaSuccess) { rc = HCA_ECUDA; goto out; }
+    if (boxed && h->nan_seen) { rc = HCA_EINVAL; goto out; }
+    if (h->status) { rc = (h->status & kErrBox) ? HCA_ERANGE : HCA_EDEVICE; goto out; }
     if (a.stats) {
         hca_stats *st_out = a.stats;
         st_out->n_points = n;
@@ -541,9 +615,9 @@ out:
     if (timing)
         for (int i = 0; i <= HCA_NUM_STAGES; ++i)
             if (ev[i]) cudaEventDestroy(ev[i]);
-    pool_free(ws_ranges, s);
-    pool_free(ws, s);
-    if (rc != HCA_OK) cudaStreamSynchronize(s);
+    if (!boxed) pool_free(ws_ranges, s);  // with declared extents it is part of ws
+    if (own_ws) pool_free(ws, s);
+    if (rc != HCA_OK && !a.deferred) cudaStreamSynchronize(s);
     return rc;
 }
 
