@@ -497,6 +497,7 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
                                 if (hit) {
                                     uf_union(v.parent, p, qp, v.ctr);
                                     rp = uf_find(v.parent, p, v.ctr);
+                                    S.cpay[col] = rp;  // now an ancestor of qp too: later rows skip it
                                 }
                             } else {
                                 const uint32_t lq = S.cpay[col];
