@@ -466,12 +466,13 @@ def run_batched(args):
     groups = {}
     for X, e, m in sets:
         groups.setdefault(X.shape[1], []).append((X, e, m))
-    dev_groups = []
+    dev_groups, group_arrays = [], []
     for d, g in sorted(groups.items()):
         X = np.concatenate([x for x, _, _ in g], axis=0)
         off = np.zeros(len(g) + 1, np.int64)
         off[1:] = np.cumsum([len(x) for x, _, _ in g])
         dev_groups.append((d, torch.from_numpy(X).cuda(), off, [e for _, e, _ in g], [m for _, _, m in g]))
+        group_arrays.append((X, None, None))
     n_total = sum(len(x) for x, _, _ in sets)
     per_d, stages, work = {}, {}, {}
     def step():
@@ -508,6 +509,29 @@ def run_batched(args):
         times.append(time.perf_counter() - t0)
     ms = 1e3 * statistics.median(times)
 
+    # the same step as one CUDA graph per d group (plans with the sets' extents, captured with
+    # the autotuned tuning): three graph launches on one stream, one wait
+    plans = []
+    for (d, t, off, e, m), (X_g, _, _) in zip(dev_groups, group_arrays):
+        lo = np.stack([X_g[off[s]:off[s + 1]].min(axis=0) for s in range(len(e))])
+        hi = np.stack([X_g[off[s]:off[s + 1]].max(axis=0) for s in range(len(e))])
+        plans.append(pkg.Plan(t, e, m, lo, hi, offsets=off))
+    def plan_step():
+        for pl in plans:
+            pl.launch()
+        for pl in plans:
+            pl.wait()
+    plan_step()
+    g_times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        plan_step()
+        g_times.append(time.perf_counter() - t0)
+    graph_ms = 1e3 * statistics.median(g_times)
+    for pl, (d, t, off, e, m) in zip(plans, dev_groups):
+        if not torch.equal(pl.labels, pkg.hca_dbscan_batched(t, off, e, m)):
+            raise RuntimeError("batched plan and batched call disagree")
+        pl.close()
     for d, *_ in dev_groups:
         pkg.hca_tuning_set(int(d), None)   # the comparisons below run the default tuning
     # the same batched calls on the CUDA cores only, and the plain per-instance path: one
@@ -549,6 +573,10 @@ def run_batched(args):
                                 "speedup_of_tuned": cc_ms / ms},
             "autotune": {"tuning_per_d": tunings, "tuning_seconds": tune_s,
                          "default_tuning_ms_per_step": default_ms},
+            "graph_plans": {"ms_per_step": graph_ms, "value": n_total / (graph_ms / 1e3),
+                            "path": "one hca_plan per d group (declared per-set extents, autotuned), "
+                                    "captured as a CUDA graph: three graph launches and one wait per step",
+                            "labels": "identical to the batched calls"},
             "plain_fp64_per_set": {"ms_per_step": plain_ms, "value": n_total / (plain_ms / 1e3),
                                    "speedup_of_tuned": plain_ms / ms,
                                    "path": "one hca_dbscan_device call per set, HCA_FLAG_FP64_ONLY | "

@@ -235,8 +235,8 @@ HCA_API int hca_radix_sort_pairs_noalloc(void *d_keys, uint32_t *d_vals, int64_t
                                          void *stream);
 
 /*
- * Plans: one clustering call of the hypercube path (1 <= d <= 4) whose buffers and point
- * extents are fixed up front, captured once into a CUDA graph and replayed.  The paper has no
+ * Plans: one clustering call (1 <= d <= 64; the tuning of d at creation is fixed into it) whose
+ * buffers and point extents are fixed up front, captured once into a CUDA graph and replayed.  The paper has no
  * counterpart; the result is the one hca_dbscan_device / hca_dbscan_batched give.  With the
  * extents declared, the grid, the stencil and the workspace are fixed before the first launch,
  * so a launch never waits for the host: the whole call is one graph launch.

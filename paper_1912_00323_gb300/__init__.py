@@ -314,7 +314,7 @@ def hca_autotune_batched(points, offsets, eps, min_pts, stream=None, repeats: in
 
 
 class Plan:
-    """One clustering call of the hypercube path (d <= 4) captured as a CUDA graph (hca_plan_*).
+    """One clustering call captured as a CUDA graph (hca_plan_*), with the tuning of d at creation.
     Bound to the CUDA tensors `points` (n, d) and `labels` (n,) (and `core`, optional); the
     points may be rewritten between launches as long as they stay inside the declared box
     (box_min, box_max: d values, or n_sets x d for a batched plan)."""

@@ -107,6 +107,25 @@ __device__ __forceinline__ void hd_load(const T *pts, uint32_t j, bool valid, T 
     }
 }
 
+// Declared extents of a plan against the measured ones (encoded min of dimension i of set s at
+// mm[s * 64 + i], max at mm[(nsets + s) * 64 + i]; boxes: mins [s * d + i], maxes
+// [(nsets + s) * d + i]): a point outside its box, or a NaN, sets status bit kErrBox.
+static __global__ void __launch_bounds__(256) k_box_check_hd(const double *__restrict__ boxes, int nsets, int d,
+                                                            const int64_t *__restrict__ set_off,
+                                                            const unsigned long long *__restrict__ mm,
+                                                            DevCounters *ctr) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && ctr->nan_seen) atomicOr(&ctr->status, kErrBox);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < (int64_t)nsets * d;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int set = (int)(k / d), i = (int)(k % d);
+        if (set_off && set_off[set + 1] == set_off[set]) continue;
+        const double lo = dec_double_dev(mm[(size_t)set * 64 + i]);
+        const double hi = dec_double_dev(mm[((size_t)nsets + set) * 64 + i]);
+        if (lo < boxes[(size_t)set * d + i] || hi > boxes[((size_t)nsets + set) * d + i])
+            atomicOr(&ctr->status, kErrBox);
+    }
+}
+
 // Per-dimension min / max of row-major n x d input (origin shift, Sec. 2).  Each thread keeps
 // one dimension (the stride is a multiple of d).
 template <typename T>

@@ -232,17 +232,30 @@ int run_hd(const RunArgs &a) {
     const size_t o_tch0 = take(4 * tc_n), o_tch1 = take(4 * tc_n), o_tch2 = take(4 * tc_n);
     const size_t o_tflags = take(4 * tc_n), o_cx = take(4 * (tc_n + 1));
     const size_t o_clist = take(4 * tc_n), o_nclist = take(4 * tc_n), o_clab = take(4 * tc_n);
+    const size_t o_box = take(sizeof(double) * 2 * (size_t)d * nsets);
     bool use_tc = tc_occ > 0;
+    const bool boxed = a.box_mn != nullptr;
+    const bool own_ws = a.ws_ext == nullptr;
     void *ws = nullptr;
-    if (pool_alloc(&ws, off, s) != cudaSuccess || !ws) return HCA_ENOMEM;
+    if (a.ws_query) {  // plans size their workspace first (declared extents only)
+        if (!boxed) return HCA_EINVAL;
+        *a.ws_query = off;
+        return HCA_OK;
+    }
+    if (!own_ws) {
+        if (!boxed || a.ws_ext_bytes < off) return HCA_EINVAL;
+        ws = a.ws_ext;
+    } else if (pool_alloc(&ws, off, s) != cudaSuccess || !ws) {
+        return HCA_ENOMEM;
+    }
     char *b = (char *)ws;
     DevCounters *ctr = (DevCounters *)(b + o_ctr);
     unsigned long long *mm = (unsigned long long *)(b + o_mm);
-    DevCounters *h = host_counters();
+    DevCounters *h = a.h_ext ? a.h_ext : host_counters();
     int rc = HCA_OK;
 
     cudaEvent_t ev[HCA_NUM_STAGES + 1] = {};
-    const bool timing = (a.flags & HCA_FLAG_TIMING) && a.stats;
+    const bool timing = (a.flags & HCA_FLAG_TIMING) && a.stats && !a.deferred;
     if (timing)
         for (int i = 0; i <= HCA_NUM_STAGES; ++i) cudaEventCreate(&ev[i]);
     auto mark = [&](int i) { if (timing) cudaEventRecord(ev[i], s); };
@@ -266,56 +279,61 @@ int run_hd(const RunArgs &a) {
     GridParams *d_gtab = (GridParams *)(b + o_gtab);
     int64_t *d_setoff = (int64_t *)(b + o_setoff);
     unsigned long long *d_smm = (unsigned long long *)(b + o_smm);
+    const size_t stage_setoff = 0, stage_gtab = align_up(sizeof(int64_t) * ((size_t)nsets + 1));
+    const size_t stage_box = stage_gtab + align_up(sizeof(GridParams) * (size_t)nsets);
 
-    if (!h) { rc = HCA_ECUDA; goto out; }
-    mark(0);
-    cudaMemsetAsync(ctr, 0, sizeof(DevCounters), s);
-    if (!batched) {
-        cudaMemsetAsync(mm, 0xff, sizeof(unsigned long long) * 64, s);
-        cudaMemsetAsync(mm + 64, 0, sizeof(unsigned long long) * 64, s);
-        k_minmax_rt<T><<<grid_for(n * d, 256, sms, 8), 256, 0, s>>>((const T *)a.d_points, n, d, ctr, mm);
-        cudaMemcpyAsync(hmm.data(), mm, sizeof(unsigned long long) * 128, cudaMemcpyDeviceToHost, s);
-    } else {
-        cudaMemsetAsync(d_smm, 0xff, sizeof(unsigned long long) * 64 * nsets, s);
-        cudaMemsetAsync(d_smm + (size_t)64 * nsets, 0, sizeof(unsigned long long) * 64 * nsets, s);
-        cudaMemcpyAsync(d_setoff, a.h_off, sizeof(int64_t) * (nsets + 1), cudaMemcpyHostToDevice, s);
-        k_minmax_rt_seg<T><<<grid_for(n, 256, sms, 4), 256, 0, s>>>((const T *)a.d_points, n, d, d_setoff, nsets,
-                                                                   d_smm, ctr);
-        smm.resize((size_t)2 * 64 * nsets);
-        cudaMemcpyAsync(smm.data(), d_smm, sizeof(unsigned long long) * smm.size(), cudaMemcpyDeviceToHost, s);
-    }
-    ++launches;
-    if (cudaMemcpyAsync(h, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) { rc = HCA_ECUDA; goto out; }
-    if (batched) {
-        if (h->nan_seen) { rc = HCA_EINVAL; goto out; }
+    // the coarse grid of one set from its extents: the three dimensions of largest extent
+    // (ties: lower index), cells of side eps (1 + 2^-10) over them
+    auto grid_of = [&](const double *mn_all, const double *mx_all, double set_eps, int set_minpts, GridParams &gp,
+                       double &tau_s) -> int {
+        for (int i = 0; i < d; ++i)
+            if (!isfinite(mn_all[i]) || !isfinite(mx_all[i]) || mx_all[i] < mn_all[i]) return HCA_EINVAL;
+        int pick[3] = {-1, -1, -1};
+        for (int k = 0; k < 3; ++k) {
+            double best = -1.0;
+            for (int i = 0; i < d; ++i) {
+                if (i == pick[0] || i == pick[1]) continue;
+                const double ext = mx_all[i] - mn_all[i];
+                if (ext > best) { best = ext; pick[k] = i; }
+            }
+        }
+        const double mn3[3] = {mn_all[pick[0]], mn_all[pick[1]], mn_all[pick[2]]};
+        const double mx3[3] = {mx_all[pick[0]], mx_all[pick[1]], mx_all[pick[2]]};
+        const int r = make_coarse_grid(sizeof(T) == 4, set_eps, set_minpts, n, mn3, mx3, a.flags, gp, tau_s);
+        if (r) return r;
+        if (!tc_magnitude_ok(d, mn_all, mx_all, gp)) use_tc = false;
+        for (int k = 0; k < 3; ++k) gp.sel[k] = pick[k];
+        return HCA_OK;
+    };
+    // every set's grid, one key layout for all, the stencil; extents of set si, dimension i
+    // from mn_of / mx_of (measured, or a plan's declared boxes)
+    auto build_grids = [&](auto mn_of, auto mx_of) -> int {
+        double mn_all[64], mx_all[64];
+        if (!batched) {
+            for (int i = 0; i < d; ++i) {
+                mn_all[i] = mn_of(0, i);
+                mx_all[i] = mx_of(0, i);
+            }
+            int r = grid_of(mn_all, mx_all, a.eps, a.min_pts, g, tau);
+            if (r) return r;
+            sel = make_int3(g.sel[0], g.sel[1], g.sel[2]);
+            r = make_stencil(3, a.eps, 1.0 / g.inv_side, tau, st);
+            if (r) return r;
+            sort_bits = g.key_bits;
+            return HCA_OK;
+        }
         gsets.resize(nsets);
         std::vector<double> e_eps(nsets), e_side(nsets), e_tau(nsets);
         uint32_t bits[3] = {};
         for (int si = 0; si < nsets; ++si) {
             const bool empty = a.h_off[si + 1] == a.h_off[si];
-            double mn_all[64], mx_all[64];
             for (int i = 0; i < d; ++i) {
-                mn_all[i] = empty ? 0.0 : dec_double(smm[(size_t)si * 64 + i]);
-                mx_all[i] = empty ? 0.0 : dec_double(smm[((size_t)nsets + si) * 64 + i]);
-                if (!isfinite(mn_all[i]) || !isfinite(mx_all[i])) { rc = HCA_EINVAL; goto out; }
+                mn_all[i] = empty ? 0.0 : mn_of(si, i);
+                mx_all[i] = empty ? 0.0 : mx_of(si, i);
             }
-            int pick[3] = {-1, -1, -1};
-            for (int k = 0; k < 3; ++k) {
-                double best = -1.0;
-                for (int i = 0; i < d; ++i) {
-                    if (i == pick[0] || i == pick[1]) continue;
-                    const double ext = mx_all[i] - mn_all[i];
-                    if (ext > best) { best = ext; pick[k] = i; }
-                }
-            }
-            const double mn3[3] = {mn_all[pick[0]], mn_all[pick[1]], mn_all[pick[2]]};
-            const double mx3[3] = {mx_all[pick[0]], mx_all[pick[1]], mx_all[pick[2]]};
             double tau_s = 0.0;
-            rc = make_coarse_grid(sizeof(T) == 4, a.h_eps[si], a.h_minpts[si], n, mn3, mx3, a.flags, gsets[si], tau_s);
-            if (rc) goto out;
-            if (!tc_magnitude_ok(d, mn_all, mx_all, gsets[si])) use_tc = false;
-            for (int k = 0; k < 3; ++k) gsets[si].sel[k] = pick[k];
+            const int r = grid_of(mn_all, mx_all, a.h_eps[si], a.h_minpts[si], gsets[si], tau_s);
+            if (r) return r;
             e_eps[si] = a.h_eps[si];
             e_side[si] = 1.0 / gsets[si].inv_side;
             e_tau[si] = tau_s;
@@ -324,7 +342,7 @@ int run_hd(const RunArgs &a) {
         int key_bits = 0, set_bits = 1;
         for (int i = 0; i < 3; ++i) key_bits += (int)bits[i];
         while ((1ll << set_bits) < nsets) ++set_bits;
-        if (key_bits + set_bits > 63) { rc = HCA_ERANGE; goto out; }
+        if (key_bits + set_bits > 63) return HCA_ERANGE;
         for (GridParams &gp : gsets) {
             int sh = 0;
             for (int i = 2; i >= 0; --i) {
@@ -337,36 +355,64 @@ int run_hd(const RunArgs &a) {
         }
         g = gsets[0];
         sort_bits = key_bits + set_bits;
-        rc = make_stencil_union(3, e_eps, e_side, e_tau, st);
+        return make_stencil_union(3, e_eps, e_side, e_tau, st);
+    };
+    auto upload = [&](void *dst, const void *src, size_t bytes, size_t stage_off) {
+        if (a.deferred && a.h_stage) {
+            memcpy((char *)a.h_stage + stage_off, src, bytes);
+            src = (char *)a.h_stage + stage_off;
+        }
+        cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+    };
+
+    if (!h) { rc = HCA_ECUDA; goto out; }
+    if (boxed) {
+        rc = build_grids([&](int set, int i) { return a.box_mn[(size_t)set * d + i]; },
+                         [&](int set, int i) { return a.box_mx[(size_t)set * d + i]; });
         if (rc) goto out;
-        cudaMemcpyAsync(d_gtab, gsets.data(), sizeof(GridParams) * nsets, cudaMemcpyHostToDevice, s);
+    }
+    mark(0);
+    cudaMemsetAsync(ctr, 0, sizeof(DevCounters), s);
+    if (!batched) {
+        cudaMemsetAsync(mm, 0xff, sizeof(unsigned long long) * 64, s);
+        cudaMemsetAsync(mm + 64, 0, sizeof(unsigned long long) * 64, s);
+        k_minmax_rt<T><<<grid_for(n * d, 256, sms, 8), 256, 0, s>>>((const T *)a.d_points, n, d, ctr, mm);
+        if (!boxed) cudaMemcpyAsync(hmm.data(), mm, sizeof(unsigned long long) * 128, cudaMemcpyDeviceToHost, s);
     } else {
+        cudaMemsetAsync(d_smm, 0xff, sizeof(unsigned long long) * 64 * nsets, s);
+        cudaMemsetAsync(d_smm + (size_t)64 * nsets, 0, sizeof(unsigned long long) * 64 * nsets, s);
+        upload(d_setoff, a.h_off, sizeof(int64_t) * (nsets + 1), stage_setoff);
+        k_minmax_rt_seg<T><<<grid_for(n, 256, sms, 4), 256, 0, s>>>((const T *)a.d_points, n, d, d_setoff, nsets,
+                                                                   d_smm, ctr);
+        if (!boxed) {
+            smm.resize((size_t)2 * 64 * nsets);
+            cudaMemcpyAsync(smm.data(), d_smm, sizeof(unsigned long long) * smm.size(), cudaMemcpyDeviceToHost, s);
+        }
+    }
+    ++launches;
+    if (boxed) {
+        // declared extents: check them on the device, no host round trip
+        std::vector<double> boxes((size_t)2 * d * nsets);
+        memcpy(boxes.data(), a.box_mn, sizeof(double) * d * nsets);
+        memcpy(boxes.data() + (size_t)d * nsets, a.box_mx, sizeof(double) * d * nsets);
+        double *d_box = (double *)(b + o_box);
+        upload(d_box, boxes.data(), sizeof(double) * boxes.size(), stage_box);
+        if (batched) upload(d_gtab, gsets.data(), sizeof(GridParams) * nsets, stage_gtab);
+        k_box_check_hd<<<grid_for((int64_t)nsets * d, 256, sms, 1), 256, 0, s>>>(
+            d_box, nsets, d, batched ? d_setoff : nullptr, batched ? d_smm : mm, ctr);
+        ++launches;
+    } else {
+        if (cudaMemcpyAsync(h, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) { rc = HCA_ECUDA; goto out; }
         if (h->nan_seen) { rc = HCA_EINVAL; goto out; }
-        double mn_all[64], mx_all[64];
-        for (int i = 0; i < d; ++i) {
-            mn_all[i] = dec_double(hmm[i]);
-            mx_all[i] = dec_double(hmm[64 + i]);
-            if (!isfinite(mn_all[i]) || !isfinite(mx_all[i])) { rc = HCA_EINVAL; goto out; }
-        }
-        // the three dimensions of largest extent (ties: lower index)
-        int pick[3] = {-1, -1, -1};
-        for (int k = 0; k < 3; ++k) {
-            double best = -1.0;
-            for (int i = 0; i < d; ++i) {
-                if (i == pick[0] || i == pick[1]) continue;
-                const double ext = mx_all[i] - mn_all[i];
-                if (ext > best) { best = ext; pick[k] = i; }
-            }
-        }
-        sel = make_int3(pick[0], pick[1], pick[2]);
-        const double mn3[3] = {mn_all[pick[0]], mn_all[pick[1]], mn_all[pick[2]]};
-        const double mx3[3] = {mx_all[pick[0]], mx_all[pick[1]], mx_all[pick[2]]};
-        rc = make_coarse_grid(sizeof(T) == 4, a.eps, a.min_pts, n, mn3, mx3, a.flags, g, tau);
+        if (batched)
+            rc = build_grids([&](int set, int i) { return dec_double(smm[(size_t)set * 64 + i]); },
+                             [&](int set, int i) { return dec_double(smm[((size_t)nsets + set) * 64 + i]); });
+        else
+            rc = build_grids([&](int, int i) { return dec_double(hmm[i]); },
+                             [&](int, int i) { return dec_double(hmm[64 + i]); });
         if (rc) goto out;
-        if (!tc_magnitude_ok(d, mn_all, mx_all, g)) use_tc = false;
-        rc = make_stencil(3, a.eps, 1.0 / g.inv_side, tau, st);
-        if (rc) goto out;
-        sort_bits = g.key_bits;
+        if (batched) cudaMemcpyAsync(d_gtab, gsets.data(), sizeof(GridParams) * nsets, cudaMemcpyHostToDevice, s);
     }
     mark(1);
     {
@@ -498,9 +544,14 @@ int run_hd(const RunArgs &a) {
     mark(9);
 done_phases:
     if (cudaGetLastError() != cudaSuccess) { rc = HCA_ECUDA; goto out; }
-    if (cudaMemcpyAsync(h, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) { rc = HCA_ECUDA; goto out; }
-    if (h->status) { rc = HCA_EDEVICE; goto out; }
+    if (cudaMemcpyAsync(h, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+        rc = HCA_ECUDA;
+        goto out;
+    }
+    if (a.deferred) goto out;  // the caller synchronises and reads the status from h
+    if (cudaStreamSynchronize(s) != cudaSuccess) { rc = HCA_ECUDA; goto out; }
+    if (boxed && h->nan_seen) { rc = HCA_EINVAL; goto out; }
+    if (h->status) { rc = (h->status & kErrBox) ? HCA_ERANGE : HCA_EDEVICE; goto out; }
     if (a.stats) {
         hca_stats *so = a.stats;
         so->n_points = n;
@@ -531,8 +582,8 @@ out:
     if (timing)
         for (int i = 0; i <= HCA_NUM_STAGES; ++i)
             if (ev[i]) cudaEventDestroy(ev[i]);
-    pool_free(ws, s);
-    if (rc != HCA_OK) cudaStreamSynchronize(s);
+    if (own_ws) pool_free(ws, s);
+    if (rc != HCA_OK && !a.deferred) cudaStreamSynchronize(s);
     return rc;
 }
 

@@ -1,6 +1,7 @@
 // Plans (include/hca_dbscan.h: hca_plan_create, hca_plan_create_batched, hca_plan_launch,
-// hca_plan_wait, hca_plan_destroy): one clustering call of the hypercube path (d <= 4) whose
-// buffers and point extents are fixed up front, captured once into a CUDA graph and replayed.
+// hca_plan_wait, hca_plan_destroy): one clustering call (either neighbour search, with the
+// tuning of its d) whose buffers and point extents are fixed up front, captured once into a
+// CUDA graph and replayed.
 // With the extents declared, the grids, the stencil and the workspace are known before the
 // first launch, so the call never waits for the host and the whole launch sequence is one
 // graph; a kernel in the graph checks every launch's points against the declared boxes.
@@ -45,7 +46,7 @@ int create(hca_plan **out, const void *d_points, int32_t dtype, int32_t n_sets, 
     using namespace hca;
     if (!out || !box_min || !box_max || !eps || !min_pts) return HCA_EINVAL;
     *out = nullptr;
-    if (d < 1 || d > 4) return HCA_EINVAL;  // the hypercube path only
+    if (d < 1 || d > 64) return HCA_EINVAL;
     int rc = check_common(d_points, dtype, n, d, eps[0], min_pts[0], d_labels);
     if (rc) return rc;
     if (n == 0) return HCA_EINVAL;
@@ -66,7 +67,7 @@ int create(hca_plan **out, const void *d_points, int32_t dtype, int32_t n_sets, 
     a.min_pts = p->min_pts[0];
     a.d_labels = d_labels;
     a.d_core = d_core;
-    a.tune.path = 1;
+    a.tune = tuning_for(d);  // fixed into the graph
     a.box_mn = p->box_mn.data();
     a.box_mx = p->box_mx.data();
     if (n_sets > 0) {

@@ -106,3 +106,56 @@ def test_batched_plan(env, d):
         for s in range(0, len(sets), 6):
             want = oracle.grid(sets[s][0].astype(np.float64), eps[s], mp[s])
             np.testing.assert_array_equal(lab[off[s]:off[s + 1]], want[0], err_msg=f"set {s}")
+
+
+@pytest.mark.parametrize("d", [5, 8, 16])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_plan_coarse_grid(env, d, dtype):
+    """d >= 5 (coarse grid, tensor-core tiles for float input) as a plan, relaunched on new points."""
+    torch, pkg, oracle = env
+    import math
+    mk = lambda seed: workloads.lattice(2500, d, seed=seed, step=0.25,
+                                        eps_steps=int(round(math.sqrt(2 * d) * 1.8)), spread=2.0,
+                                        box=2.0 * d, n_blobs=3)
+    X1, eps, _ = mk(300 + d)
+    X2, _, _ = mk(400 + d)
+    lo = np.minimum(X1.min(0), X2.min(0))
+    hi = np.maximum(X1.max(0), X2.max(0))
+    pts = torch.from_numpy(X1.astype(dtype)).cuda()
+    core = torch.empty(len(X1), dtype=torch.uint8, device="cuda")
+    with pkg.Plan(pts, eps, 5, lo, hi, core=core) as plan:
+        for X in (X1, X2):
+            pts.copy_(torch.from_numpy(X.astype(dtype)))
+            plan.launch()
+            plan.wait()
+            want = oracle.grid(X, eps, 5)
+            np.testing.assert_array_equal(plan.labels.cpu().numpy(), want[0])
+            np.testing.assert_array_equal(core.cpu().numpy(), want[1])
+
+
+def test_batched_plan_d8_and_outside(env):
+    torch, pkg, oracle = env
+    sets = workloads.batched_sets(n_sets=24, n_min=200, n_max=6000, dims=(8,), seed=48)
+    X = np.concatenate([s[0] for s in sets], axis=0)
+    off = np.zeros(len(sets) + 1, np.int64)
+    off[1:] = np.cumsum([len(s[0]) for s in sets])
+    lo = np.stack([s[0].min(0) for s in sets])
+    hi = np.stack([s[0].max(0) for s in sets])
+    eps = [s[1] for s in sets]
+    mp = [s[2] for s in sets]
+    pts = torch.from_numpy(X).cuda()
+    with pkg.Plan(pts, eps, mp, lo, hi, offsets=off) as plan:
+        plan.launch()
+        plan.wait()
+        lab = plan.labels.cpu().numpy()
+        np.testing.assert_array_equal(lab, pkg.hca_dbscan_batched(pts, off, eps, mp).cpu().numpy())
+        for s in range(0, len(sets), 6):
+            want = oracle.grid(sets[s][0].astype(np.float64), eps[s], mp[s])
+            np.testing.assert_array_equal(lab[off[s]:off[s + 1]], want[0], err_msg=f"set {s}")
+        Y = X.copy()
+        Y[off[5] + 1, 3] = hi[5, 3] + 0.5          # one point of set 5 leaves its box
+        pts.copy_(torch.from_numpy(Y))
+        plan.launch()
+        with pytest.raises(pkg.HcaError) as e:
+            plan.wait()
+        assert e.value.code == pkg.HCA_ERANGE

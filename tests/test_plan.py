@@ -21,7 +21,7 @@ def test_create_refuses_bad_arguments(lib):
     assert L.hca_plan_create(None, None, 0, 10, 2, 1.0, 4, box, box, None, None) == E          # no out
     assert L.hca_plan_create(ctypes.byref(h), None, 0, 0, 2, 1.0, 4, box, box, None, None) == E  # n = 0
     assert L.hca_plan_create(ctypes.byref(h), None, 0, 10, 2, 1.0, 4, None, box, None, None) == E
-    assert L.hca_plan_create(ctypes.byref(h), None, 0, 10, 5, 1.0, 4, box, box, None, None) == E  # d > 4
+    assert L.hca_plan_create(ctypes.byref(h), None, 0, 10, 65, 1.0, 4, box, box, None, None) == E  # d > 64
     assert L.hca_plan_create(ctypes.byref(h), None, 0, 10, 2, -1.0, 4, box, box, None, None) == E
     assert L.hca_plan_create(ctypes.byref(h), None, 0, 10, 2, 1.0, 0, box, box, None, None) == E
     assert h.value is None
