@@ -79,6 +79,7 @@ def parse_args():
     ap.add_argument("--sets", type=int, default=4096, help="batched: number of point sets")
     ap.add_argument("--seconds", type=float, default=20.0, help="serving: arrival window")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrivals per second")
+    ap.add_argument("--workers", type=int, default=4, help="serving: server worker threads (streams)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -607,7 +608,7 @@ def run_serving(args):
     arrivals = arrivals[arrivals < args.seconds]
     picks = r.integers(0, len(pool), size=len(arrivals))
     lat, pts = [], 0
-    with pkg.Server(hbm_budget_bytes=64 << 30, workers=2) as sv:
+    with pkg.Server(hbm_budget_bytes=64 << 30, workers=args.workers) as sv:
         sv.wait(sv.submit(*pool[0]))          # warm-up
         tickets = []
         t0 = time.perf_counter()
@@ -639,7 +640,7 @@ def run_serving(args):
             "wall_s": wall, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "serving: Poisson arrivals, n log-uniform [1e3, 2e6], d uniform 2..16, "
                                    "blobs + noise, eps = 1.5 sqrt(d/2), minPts U{4..20}; jobs drawn from 48 "
-                                   "pre-generated sets", "workers": 2}}
+                                   "pre-generated sets", "workers": args.workers}}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -387,7 +387,7 @@ class Server:
     hca_poll / hca_wait / hca_cancel).  submit() takes host numpy arrays or CUDA tensors and
     keeps them alive until the job is waited for."""
 
-    def __init__(self, device: int = 0, hbm_budget_bytes: int = 32 << 30, workers: int = 2):
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 32 << 30, workers: int = 4):
         lib = load()
         self._lib = lib
         h = ctypes.c_void_p()
