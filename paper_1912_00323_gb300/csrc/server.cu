@@ -4,7 +4,7 @@
 // take every queued job that fits the device-memory budget, group them by (d, dtype), stage
 // each group's points into one device buffer, cluster the group with one hca_dbscan_batched
 // call, copy each job's labels to its destination, and complete the jobs.  Jobs that arrive
-// while a batch is on the GPU join the next batch of a free worker, and two workers keep two
+// while a batch is on the GPU join the next batch of a free worker, and the workers keep as many
 // batches in flight.  All waits on the host are condition-variable waits with deadlines.
 #include <algorithm>
 #include <chrono>
