@@ -193,14 +193,20 @@ extern "C" int hca_dbscan(const void *points, int32_t dtype, int64_t n, int32_t 
     int rc = check_common(points, dtype, n, d, eps, min_pts, labels);
     if (rc) return rc;
     if (n == 0) return HCA_OK;
-    cudaStream_t s;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return HCA_ECUDA;
+    // one non-blocking stream per host thread and device, created on first use and kept
+    thread_local cudaStream_t streams[kMaxDevices] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HCA_ECUDA;
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+        streams[dev] = nullptr;
+        return HCA_ECUDA;
+    }
+    cudaStream_t s = streams[dev];
     const size_t in_bytes = (size_t)n * d * (dtype == HCA_F32 ? 4 : 8);
     void *dp = nullptr, *dl = nullptr;
     if (pool_alloc(&dp, in_bytes, s) != cudaSuccess || pool_alloc(&dl, (size_t)n * 4, s) != cudaSuccess) {
         pool_free(dp, s);
         cudaStreamSynchronize(s);
-        cudaStreamDestroy(s);
         return HCA_ENOMEM;
     }
     rc = HCA_OK;
@@ -213,7 +219,6 @@ extern "C" int hca_dbscan(const void *points, int32_t dtype, int64_t n, int32_t 
     pool_free(dp, s);
     pool_free(dl, s);
     cudaStreamSynchronize(s);
-    cudaStreamDestroy(s);
     return rc;
 }
 

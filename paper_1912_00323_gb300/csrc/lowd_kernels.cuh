@@ -732,7 +732,7 @@ __device__ __forceinline__ float rep_dist(int r, const float *lo2, const float *
 }
 
 // Algorithm 2: for every cell with core points and every direction delta, the core point
-// nearest to the ideal position of delta.  The work is split into chunks of at most 256
+// nearest to the ideal position of delta.  The work is split into chunks of at most 128
 // points of one cell (chunk_off[c] = first chunk of cell c), one warp per chunk, so a cell of
 // any size is shared out evenly.  A chunk of at most 32 points (most cells) is staged in
 // shared memory, one point per lane, and then lane r scans its points for direction r: no
@@ -740,10 +740,12 @@ __device__ __forceinline__ float rep_dist(int r, const float *lo2, const float *
 // direction.  A cell of several chunks combines them by 64-bit atomicMin of (distance bits,
 // index) (non-negative float bits order like the floats).  Among equal distances any holder
 // may be kept: the representative only decides which pair is tested first, never a label.
+constexpr uint32_t kRepChunk = 128;  // points per work chunk of the representative pass
+
 template <typename T, int D>
-__global__ void __launch_bounds__(256) k_reps(LowdView<T, D> v) {
+__global__ void __launch_bounds__(256, 3) k_reps(LowdView<T, D> v) {
     constexpr int ndir = RepDirs<D>::value;
-    constexpr uint32_t kChunk = 256;
+    constexpr uint32_t kChunk = kRepChunk;
     __shared__ float2 s_lh[8][32][D];  // per warp: (lo2, hi2) of every dimension of its 32 points
     const uint32_t C = v.ctr->n_cells, NC = v.ctr->n_chunks;
     const int lane = lane_id(), wib = threadIdx.x >> 5;
@@ -873,12 +875,12 @@ __global__ void __launch_bounds__(256) k_reps(LowdView<T, D> v) {
     }
 }
 
-// Chunks of the representative-point pass: ceil(size / 256) for cells with core points.
+// Chunks of the representative-point pass: ceil(size / kRepChunk) for cells with core points.
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_rep_chunks(LowdView<T, D> v, uint32_t *__restrict__ nch) {
     const uint32_t C = v.ctr->n_cells;
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x)
-        nch[c] = v.cell_core[c] ? (v.cell_start[c + 1] - v.cell_start[c] + 255u) / 256u : 0u;
+        nch[c] = v.cell_core[c] ? (v.cell_start[c + 1] - v.cell_start[c] + kRepChunk - 1u) / kRepChunk : 0u;
 }
 
 // chunk_cell[t] = the cell of chunk t (every cell writes its id into its chunk slots).
