@@ -99,6 +99,22 @@ def workload(name, rank):
     return X, eps, min_pts, desc
 
 
+def max_over_ranks(x, dist, device):
+    """The largest value of x over all ranks (x itself without a process group): every rank's
+    step time is reduced this way, so the reported time is the slowest rank's."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(points_per_rank, world_size, ms):
+    """Whole-job throughput of independent replicas: every rank's points over the slowest time."""
+    return points_per_rank * world_size / (ms / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -280,12 +296,8 @@ def run_ours(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    ms = sum(step_ms) / len(step_ms)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = n * ws / (ms / 1e3)
+    ms = max_over_ranks(sum(step_ms) / len(step_ms), dist, dev)
+    value = replica_value(n, ws, ms)
 
     # end to end through the host entry point: pinned host points in, host labels out
     host_pts = torch.from_numpy(X).pin_memory()
@@ -298,11 +310,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         pkg.hca_dbscan(host_pts, eps, min_pts, labels=host_lab)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_s = statistics.median(e2e_t)
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(statistics.median(e2e_t), dist, dev)
     if not np.array_equal(host_lab.numpy(), labels.cpu().numpy()):
         raise RuntimeError("host and device entry points disagree")
 
@@ -372,18 +380,14 @@ def run_ours(args):
             if not torch.equal(plan.labels, labels):
                 raise RuntimeError("plan and call disagree")
         gm = statistics.median(g_ms)
-        graph = {"ms_per_step": gm, "value": n * ws / (gm / 1e3),
+        graph = {"ms_per_step": gm, "value": replica_value(n, ws, gm),
                  "path": "hca_plan_create with the data's extents; hca_plan_launch = one CUDA graph launch",
                  "labels": "identical to the call"}
-    auto = statistics.median(auto_ms)
-    if dist:
-        t = torch.tensor([auto], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        auto = float(t.item())
-    if dist:
-        t = torch.tensor([plain], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        plain = float(t.item())
+    auto = max_over_ranks(statistics.median(auto_ms), dist, dev)
+    plain = max_over_ranks(plain, dist, dev)
+    if graph is not None:
+        graph["ms_per_step"] = max_over_ranks(graph["ms_per_step"], dist, dev)
+        graph["value"] = replica_value(n, ws, graph["ms_per_step"])
 
     if rank != 0:
         if dist:
@@ -424,7 +428,7 @@ def run_ours(args):
         "config": {"workload": args.workload + ": " + desc, "n": n, "d": d, "eps": eps,
                    "min_pts": min_pts, "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-        "e2e": {"value": n * ws / e2e_s, "unit": "points/s", "h2d_bytes_per_step": int(X.nbytes),
+        "e2e": {"value": replica_value(n, ws, 1e3 * e2e_s), "unit": "points/s", "h2d_bytes_per_step": int(X.nbytes),
                 "d2h_bytes_per_step": 4 * n},
         "gpu_launches": int(stats["kernel_launches"]) * args.steps,
         "roofline": roofline,
