@@ -37,7 +37,7 @@ METRIC = "points clustered/sec at 1 GB300 (labels == oracle)"
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_reps launch on the
 # mixed3d workload at n = 2,000,000, from an ncu full capture of that launch; reported for that
 # workload and size only
-REPS_TRAFFIC_MIXED3D_2M = 34.336256e6 + 0.007168e6
+REPS_TRAFFIC_MIXED3D_2M = 35.377920e6 + 0.125184e6
 L2_FLUSH_BYTES = 256 << 20
 
 # Algorithmic bytes per stage, per point (n) and per cell (C) / pencil (P): the data each
