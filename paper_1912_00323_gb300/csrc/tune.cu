@@ -18,9 +18,28 @@ std::mutex g_tune_mu;
 hca_tuning g_tune[kMaxDim + 1];
 bool g_tune_init = false;
 
+// Defaults per d: the coarse-grid split that the autotuner chose on the measured workloads —
+// d <= 8 (the batched blob sets at d = 8: thresholds 16 / 16 / 4, no first links in tensor-core
+// cells) and d > 8 (the 16-D anisotropic clusters: 8 / 4 / 1 with first links everywhere).
+hca_tuning default_tuning(int d) {
+    hca_tuning t = kDefaultTuning;
+    if (d <= 8) {
+        t.tc_min_count = 16;
+        t.tc_min_merge = 16;
+        t.tc_min_labels = 4;
+        t.first_links = 0;
+    } else {
+        t.tc_min_count = 8;
+        t.tc_min_merge = 4;
+        t.tc_min_labels = 1;
+        t.first_links = 1;
+    }
+    return t;
+}
+
 void ensure_init() {  // caller holds g_tune_mu
     if (g_tune_init) return;
-    for (int d = 0; d <= kMaxDim; ++d) g_tune[d] = kDefaultTuning;
+    for (int d = 0; d <= kMaxDim; ++d) g_tune[d] = default_tuning(d);
     g_tune_init = true;
 }
 
@@ -44,7 +63,7 @@ std::vector<hca_tuning> candidates(int d, int32_t dtype) {
     else paths = {2};
     const int mins[4][3] = {{8, 8, 2}, {32, 8, 2}, {8, 4, 1}, {16, 16, 4}};
     for (int path : paths) {
-        hca_tuning t = kDefaultTuning;
+        hca_tuning t = default_tuning(d);
         t.path = path;
         if (path == 1 || dtype != HCA_F32) {
             out.push_back(t);  // nothing else applies
@@ -75,7 +94,7 @@ int tune_with(int d, int32_t dtype, cudaStream_t s, int repeats, Run run, hca_tu
     }
     int rc = HCA_OK;
     double best = DBL_MAX;
-    hca_tuning pick = kDefaultTuning;
+    hca_tuning pick = default_tuning(d);
     for (const hca_tuning &t : candidates(d, dtype)) {
         rc = run(t);
         if (rc) break;
@@ -114,7 +133,7 @@ int tune_with(int d, int32_t dtype, cudaStream_t s, int repeats, Run run, hca_tu
 hca_tuning tuning_for(int d) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     ensure_init();
-    return (d >= 1 && d <= kMaxDim) ? g_tune[d] : kDefaultTuning;
+    return (d >= 1 && d <= kMaxDim) ? g_tune[d] : default_tuning(d);
 }
 
 }  // namespace hca
@@ -129,7 +148,7 @@ extern "C" int hca_tuning_get(int32_t d, hca_tuning *out) {
 
 extern "C" int hca_tuning_set(int32_t d, const hca_tuning *t) {
     if (d < 1 || d > kMaxDim) return HCA_EINVAL;
-    const hca_tuning v = t ? *t : kDefaultTuning;
+    const hca_tuning v = t ? *t : default_tuning(d);
     if (!valid_tuning(d, v)) return HCA_EINVAL;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     ensure_init();

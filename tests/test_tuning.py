@@ -17,16 +17,23 @@ def pkg():
         pkg.hca_tuning_set(d, None)
 
 
-DEFAULT = {"path": 0, "tc_min_count": 8, "tc_min_merge": 8, "tc_min_labels": 2, "tc_handoff": 8,
-           "first_links": 1}
+LOW_D = {"path": 0, "tc_min_count": 16, "tc_min_merge": 16, "tc_min_labels": 4, "tc_handoff": 8,
+         "first_links": 0}
+HIGH_D = {"path": 0, "tc_min_count": 8, "tc_min_merge": 4, "tc_min_labels": 1, "tc_handoff": 8,
+          "first_links": 1}
+
+
+def default(d):
+    return LOW_D if d <= 8 else HIGH_D
 
 
 def test_defaults_and_roundtrip(pkg):
-    for d in (1, 3, 5, 16, 64):
-        assert pkg.hca_tuning_get(d) == DEFAULT
+    for d in (1, 3, 5, 8, 9, 16, 64):
+        assert pkg.hca_tuning_get(d) == default(d)
+    DEFAULT = default(16)
     pkg.hca_tuning_set(16, {"tc_min_count": 40, "tc_handoff": 0, "first_links": 0})
     assert pkg.hca_tuning_get(16) == dict(DEFAULT, tc_min_count=40, tc_handoff=0, first_links=0)
-    assert pkg.hca_tuning_get(15) == DEFAULT            # per dimension
+    assert pkg.hca_tuning_get(15) == default(15)        # per dimension
     pkg.hca_tuning_set(16, None)
     assert pkg.hca_tuning_get(16) == DEFAULT
 
@@ -39,7 +46,7 @@ def test_rejects_out_of_range(pkg, d, field, value):
     with pytest.raises(pkg.HcaError) as e:
         pkg.hca_tuning_set(d, {field: value})
     assert e.value.code == pkg.HCA_EINVAL
-    assert pkg.hca_tuning_get(d) == DEFAULT             # nothing changed
+    assert pkg.hca_tuning_get(d) == default(d)          # nothing changed
 
 
 def test_bad_dimension(pkg):
