@@ -37,7 +37,7 @@ METRIC = "points clustered/sec at 1 GB300 (labels == oracle)"
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_reps launch on the
 # mixed3d workload at n = 2,000,000, from an ncu full capture of that launch; reported for that
 # workload and size only
-REPS_TRAFFIC_MIXED3D_2M = 35.377920e6 + 0.125184e6
+REPS_TRAFFIC_MIXED3D_2M = 44.760832e6 + 1.304576e6
 L2_FLUSH_BYTES = 256 << 20
 
 # Algorithmic bytes per stage, per point (n) and per cell (C) / pencil (P): the data each
@@ -47,9 +47,10 @@ L2_FLUSH_BYTES = 256 << 20
 #   cells: read index (4) + the point (4 d), write the padded point (16 for d = 3) + cell id (4);
 #          per cell write start (4) + key (8)
 #   reps:  see below (the stage is the k_reps kernel alone)
-def stage_bytes(stage, n, d, C, P, passes, key_bytes):
-    pt = 4 * d
-    pad = 16 if d == 3 else pt
+def stage_bytes(stage, n, d, C, P, passes, key_bytes, core_cells=0, esz=4):
+    # esz: bytes per coordinate; sorted points are padded to 4 coordinates at d = 3
+    pt = esz * d
+    pad = 4 * esz if d == 3 else pt
     if stage == "minmax":
         return n * pt
     if stage == "bin":
@@ -61,10 +62,11 @@ def stage_bytes(stage, n, d, C, P, passes, key_bytes):
     if stage == "hash":
         return C * 8 + P * 16
     if stage == "reps":
-        # k_reps: read every point and its core flag, per cell its key and start, write the
-        # 64-bit (distance, index) word of every representative direction
+        # k_reps: read every point, its core flag and its cell id; per cell holding a core
+        # point read its key and write, for every representative direction, the 64-bit
+        # (distance, index) word and the representative's coordinates
         ndir = {1: 2, 2: 8, 3: 26, 4: 8}.get(d, 0)
-        return n * (pad + 1) + C * (12 + 8 * ndir)
+        return n * (pad + 1 + 4) + core_cells * (8 + ndir * (8 + pad))
     return None
 
 
@@ -402,7 +404,8 @@ def run_ours(args):
     dominant = max(med, key=med.get)
     roof_rows = {}
     for k, t in med.items():
-        b = stage_bytes(k, n, d, C, P, stats["sort_passes"], key_bytes)
+        b = stage_bytes(k, n, d, C, P, stats["sort_passes"], key_bytes, stats["n_core_cells"],
+                        X.dtype.itemsize)
         if b is not None and t > 0:
             roof_rows[k] = {"ms": t, "bytes": b, "gbs": b / (t / 1e3) / 1e9}
     # the roofline object describes k_reps (the representative stage is that one launch) when

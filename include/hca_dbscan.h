@@ -115,6 +115,9 @@ typedef struct hca_stats {
        decided by the exact predicate */
     int64_t n_tc_tiles;
     int64_t n_tc_rechecks;
+    /* d <= 4 (hypercube neighbour search): cells holding at least one core point (the cells
+       with representative points, Algorithm 2); 0 on the coarse-grid path */
+    int64_t n_core_cells;
 } hca_stats;
 
 /*
@@ -280,6 +283,8 @@ HCA_API int hca_plan_destroy(hca_plan *plan);
  *                  0..127.
  *   first_links    1: first-link pass in every coarse cell; 0: only in cells whose unions run
  *                  on the CUDA cores.
+ * Defaults: path 0, tc_handoff 8; d <= 8: thresholds 16 / 16 / 4, first_links 0; d > 8:
+ * thresholds 8 / 4 / 1, first_links 1.
  */
 typedef struct hca_tuning {
     int32_t path;

@@ -43,7 +43,8 @@ class HcaStats(ctypes.Structure):
                 ("n_count_chunks", ctypes.c_int64), ("n_rep_tests", ctypes.c_int64),
                 ("n_rep_hits", ctypes.c_int64), ("n_exhaustive_pairs", ctypes.c_int64),
                 ("n_exhaustive_chunks", ctypes.c_int64), ("n_border_chunks", ctypes.c_int64),
-                ("n_tc_tiles", ctypes.c_int64), ("n_tc_rechecks", ctypes.c_int64)]
+                ("n_tc_tiles", ctypes.c_int64), ("n_tc_rechecks", ctypes.c_int64),
+                ("n_core_cells", ctypes.c_int64)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_ if name not in ("stage_ms", "reserved")}

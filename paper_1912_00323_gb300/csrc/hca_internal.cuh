@@ -21,11 +21,9 @@ constexpr uint32_t kErrHashFull = 1u;
 constexpr uint32_t kErrLoop = 2u;
 constexpr uint32_t kErrBox = 8u;   // a point lies outside the extents a plan declared
 
-// Default tuning (include/hca_dbscan.h): dimension-chosen neighbour search; tensor-core tiles
+// Base tuning (include/hca_dbscan.h): dimension-chosen neighbour search; tensor-core tiles
 // from 8 rows (counts, unions) and 2 non-core rows (labels); hand-off at 8 open count rows;
-// first links everywhere.  A 128-row chunk with r rows of a phase costs about the same per 128
-// candidates as r rows on the CUDA cores at r ~ 2 (labels) and r ~ 8 (counts, unions),
-// measured on the 16-D workload and the batched d = 8 sets.
+// first links everywhere.  The defaults per d (tune.cu) adjust the split from it.
 constexpr hca_tuning kDefaultTuning = {0, 8, 8, 2, 8, 1};
 
 // Device counters and status, one struct per call in the workspace.
@@ -38,13 +36,14 @@ struct DevCounters {
     uint32_t n_core;
     uint32_t n_clusters;
     uint32_t n_noise;
-    uint32_t minmax_enc[2 * kMaxD * 2];  // order-preserving encodings of min / max per dim
+    uint32_t n_core_cells;  // cells holding a core point (hypercube path)
+    uint64_t minmax_enc[2 * kMaxD];  // order-preserving encodings of min (first kMaxD) / max per dim
     uint32_t nan_seen;
     uint32_t n_chunks;     // 32-point chunks of the coarse cells (high-dimensional path)
     uint32_t n_tc_chunks[3];  // 128-row chunks of the tensor-core phases: counts, unions, labels
     uint32_t tc_next[3];      // next unclaimed chunk of each tensor-core phase
     uint32_t hd_next[4];      // next unclaimed 32-point chunk: counts, first links, unions, labels
-    uint32_t lowd_next[5];    // next unclaimed batch (representatives: [1], labels: [4])
+    uint32_t lowd_next[5];    // next unclaimed batch (labels: [4])
     unsigned long long work[8];  // work counters (see hca_stats)
     uint32_t digit_counts[8 * 256];  // radix digit counts per pass, filled while binning
 };

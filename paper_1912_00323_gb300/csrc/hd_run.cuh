@@ -480,7 +480,7 @@ int run_hd(const RunArgs &a) {
         lv.hvals = (uint32_t *)(b + o_hv);
         lv.ranges = (uint2 *)(b + o_ranges);
         lv.ctr = ctr;
-        k_ranges<float, 3><<<grid_for(n * (int64_t)st.n_all, 256, sms, 16), 256, 0, s>>>(lv, st);
+        k_ranges<float, 3><<<grid_for((n / kRangeRun + 1) * (int64_t)st.n_all, 256, sms, 16), 256, 0, s>>>(lv, st);
         k_chunk_counts<<<gpts, 256, 0, s>>>((const uint32_t *)(b + o_cstart), ctr, (uint32_t *)(b + o_nch));
         exclusive_scan_u32((uint32_t *)(b + o_nch), (uint32_t *)(b + o_choff), n, &ctr->n_cells,
                            &ctr->n_chunks, part, s, &launches);

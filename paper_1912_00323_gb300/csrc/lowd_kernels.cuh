@@ -39,8 +39,6 @@ struct LowdView {
     uint32_t *parent;
     uint64_t *reps;
     Pt<T, D> *rep_pts;            // coordinates of reps[c * ndir + r]
-    const uint32_t *chunk_off;    // first 256-point chunk of each cell (representative pass)
-    uint32_t *chunk_cell;         // cell of each chunk
     uint32_t *comp_min;
     uint2 *ranges;                // [cell * n_all + k]: neighbour cells [lo, hi) in pencil k
     int32_t *labels;              // output, input order
@@ -229,44 +227,27 @@ __device__ __forceinline__ uint32_t hash_lookup(const uint64_t *hkeys, const uin
     return 0xffffffffu;
 }
 
-// Cell range [lo, hi) of the neighbours of cell `a` (coordinates ac) in stencil pencil k.
-// half: for the zero offset only cells after `a` along the last coordinate.
-template <typename T, int D>
-__device__ __forceinline__ bool pencil_range(const LowdView<T, D> &v, const Stencil &st, int k,
-                                             const int *ac, bool half, uint32_t &lo, uint32_t &hi,
-                                             const GridParams &g, uint32_t set) {
-    uint64_t pkey = v.gtab ? (uint64_t)set << (g.key_bits - g.prefix_shift) : 0ull;
+// First position in [a, e) of a pencil's cells (keys ascending) whose key is not below kt
+// (Upper: above kt).  A few linear steps first, since the bounds of consecutive cells of a
+// pencil move little, then a binary search over the rest.
+template <bool Upper>
+__device__ __forceinline__ uint32_t key_bound_from(const uint64_t *__restrict__ ck, uint32_t a, uint32_t e,
+                                                   uint64_t kt) {
 #pragma unroll
-    for (int i = 0; i < D - 1; ++i) {
-        int c = ac[i] + (int)st.off[k][i];
-        if (c < 0 || c >= (int)g.ncell[i]) return false;
-        pkey |= (uint64_t)c << (g.shift[i] - g.prefix_shift);
+    for (int step = 0; step < 4; ++step) {
+        if (a >= e) return a;
+        const uint64_t x = __ldg(ck + a);
+        if (Upper ? (x > kt) : (x >= kt)) return a;
+        ++a;
     }
-    const uint32_t p = hash_lookup(v.hkeys, v.hvals, v.ctr->hash_mask, pkey);
-    if (p == 0xffffffffu) return false;
-    uint32_t ps = v.pencil_start[p], pe = v.pencil_start[p + 1];
-    const int r = st.reach[k];
-    int llo = ac[D - 1] - r, lhi = ac[D - 1] + r;
-    if (half && k == 0) llo = ac[D - 1] + 1;
-    if (llo < 0) llo = 0;
-    if (lhi > (int)g.ncell[D - 1] - 1) lhi = (int)g.ncell[D - 1] - 1;
-    if (llo > lhi) return false;
-    const uint64_t base = pkey << g.prefix_shift;  // set id and all coordinates but the last
-    const uint64_t klo = base | (uint64_t)llo, khi = base | (uint64_t)lhi;
-    // lower bound of klo, then upper bound of khi, inside the pencil
-    uint32_t a = ps, b = pe;
+    uint32_t b = e;
     while (a < b) {
-        uint32_t m = (a + b) >> 1;
-        if (__ldg(v.cell_key + m) < klo) a = m + 1; else b = m;
+        const uint32_t m = (a + b) >> 1;
+        const uint64_t x = __ldg(ck + m);
+        if (Upper ? (x <= kt) : (x < kt)) a = m + 1;
+        else b = m;
     }
-    lo = a;
-    b = pe;
-    while (a < b) {
-        uint32_t m = (a + b) >> 1;
-        if (__ldg(v.cell_key + m) <= khi) a = m + 1; else b = m;
-    }
-    hi = a;
-    return lo < hi;
+    return a;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -450,7 +431,7 @@ __global__ void __launch_bounds__(256) k_minmax(const T *__restrict__ in, int64_
             a = smn[w][i] < a ? smn[w][i] : a;
             b = smx[w][i] > b ? smx[w][i] : b;
         }
-        uint64_t *mm = reinterpret_cast<uint64_t *>(ctr->minmax_enc);
+        uint64_t *mm = ctr->minmax_enc;
         atomicMin((unsigned long long *)&mm[i], (unsigned long long)enc_double((double)a));
         atomicMax((unsigned long long *)&mm[kMaxD + i], (unsigned long long)enc_double((double)b));
     }
@@ -580,26 +561,66 @@ static __global__ void __launch_bounds__(256) k_pencils(const uint64_t *__restri
 }
 
 // Neighbour cells of every cell, once: for cell c and stencil pencil k the range of cells
-// [lo, hi) of that pencil within reach (hash lookup of the pencil, then two binary searches
-// along its last coordinate).  One thread per (cell, pencil).
+// [lo, hi) of that pencil within reach along the last coordinate.  One thread per run of
+// kRangeRun consecutive cells and stencil pencil k.  Consecutive cells mostly share their
+// pencil (all coordinates but the last), so the thread looks the neighbour pencil up in the
+// hash table once per pencil of its run; along a pencil the last coordinate increases, so
+// both ends of the neighbour range only move forward and are found from the previous cell's.
+constexpr uint32_t kRangeRun = 16;
+
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_ranges(LowdView<T, D> v, Stencil st_in) {
     __shared__ Stencil st;
     load_stencil<T, D>(st, st_in);
     const uint32_t C = v.ctr->n_cells;
     const int na = st.n_all;
-    const uint64_t total = (uint64_t)C * na;
+    const uint64_t total = (uint64_t)((C + kRangeRun - 1) / kRangeRun) * na;
+    const uint64_t last_mask = (1ull << v.g.bits[D - 1]) - 1ull;
     for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t c = (uint32_t)(idx / na);
-        const int k = (int)(idx - (uint64_t)c * na);
-        int ac[D];
-        const uint64_t key = v.cell_key[c];
-        unpack_key<D>(key, v.g, ac);
-        const uint32_t set = set_of_key(v, key);
-        uint32_t lo = 0, hi = 0;
-        if (!pencil_range<T, D>(v, st, k, ac, false, lo, hi, params_of(v, set), set)) lo = hi = 0;
-        v.ranges[idx] = make_uint2(lo, hi);
+        const uint32_t c0 = (uint32_t)(idx / na) * kRangeRun;
+        const int k = (int)(idx % na);
+        const uint32_t c1 = min(c0 + kRangeRun, C);
+        const int reach = st.reach[k];
+        uint64_t pcur = ~0ull, base = 0;
+        uint32_t qe = 0, lo = 0, hi = 0;
+        int nlast = 0;
+        bool ok = false;
+        for (uint32_t c = c0; c < c1; ++c) {
+            const uint64_t key = v.cell_key[c];
+            const uint64_t pref = key >> v.g.prefix_shift;  // set id and all coordinates but the last
+            if (pref != pcur) {
+                // the neighbour pencil of this cell's pencil at offset k
+                pcur = pref;
+                int ac[D];
+                unpack_key<D>(key, v.g, ac);
+                const uint32_t set = set_of_key(v, key);
+                const GridParams &g = params_of(v, set);
+                uint64_t pkey = v.gtab ? (uint64_t)set << (g.key_bits - g.prefix_shift) : 0ull;
+                ok = true;
+#pragma unroll
+                for (int i = 0; i < D - 1; ++i) {
+                    const int cc = ac[i] + (int)st.off[k][i];
+                    if (cc < 0 || cc >= (int)g.ncell[i]) ok = false;
+                    pkey |= (uint64_t)(cc & ((1 << g.bits[i]) - 1)) << (g.shift[i] - g.prefix_shift);
+                }
+                const uint32_t q = ok ? hash_lookup(v.hkeys, v.hvals, v.ctr->hash_mask, pkey) : 0xffffffffu;
+                ok = q != 0xffffffffu;
+                lo = hi = ok ? v.pencil_start[q] : 0u;
+                qe = ok ? v.pencil_start[q + 1] : 0u;
+                base = pkey << g.prefix_shift;
+                nlast = (int)g.ncell[D - 1];
+            }
+            uint2 out = make_uint2(0u, 0u);
+            if (ok) {
+                const int a = (int)(key & last_mask);
+                const int llo = max(a - reach, 0), lhi = min(a + reach, nlast - 1);
+                lo = key_bound_from<false>(v.cell_key, lo, qe, base | (uint64_t)llo);
+                hi = key_bound_from<true>(v.cell_key, max(hi, lo), qe, base | (uint64_t)lhi);
+                if (lo < hi) out = make_uint2(lo, hi);
+            }
+            v.ranges[(uint64_t)c * na + k] = out;
+        }
     }
 }
 
@@ -615,7 +636,7 @@ template <typename T, int D>
 __global__ void __launch_bounds__(256) k_core(LowdView<T, D> v, int n_all) {
     const uint32_t C = v.ctr->n_cells;
     const int lane = lane_id();
-    uint32_t dense_cells = 0, chunks = 0;
+    uint32_t dense_cells = 0, core_cells = 0, chunks = 0;
     for (uint32_t A = global_warp(); A < C; A += total_warps()) {
         const GridParams &G = params_of(v, set_of_key(v, v.cell_key[A]));
         const uint32_t min_pts = G.min_pts;
@@ -629,6 +650,7 @@ __global__ void __launch_bounds__(256) k_core(LowdView<T, D> v, int n_all) {
             for (int r = lane; r < RepDirs<D>::value; r += 32) v.reps[(uint64_t)A * RepDirs<D>::value + r] = ~0ull;
             if (lane == 0) v.cell_core[A] = 1;
             ++dense_cells;
+            ++core_cells;
             continue;
         }
         bool any_core = false;
@@ -702,8 +724,10 @@ __global__ void __launch_bounds__(256) k_core(LowdView<T, D> v, int n_all) {
         if (any_core)
             for (int r = lane; r < RepDirs<D>::value; r += 32) v.reps[(uint64_t)A * RepDirs<D>::value + r] = ~0ull;
         if (lane == 0) v.cell_core[A] = any_core ? 1 : 0;
+        core_cells += any_core ? 1u : 0u;
     }
     if (lane == 0 && dense_cells) atomicAdd(&v.ctr->n_dense, dense_cells);
+    if (lane == 0 && core_cells) atomicAdd(&v.ctr->n_core_cells, core_cells);
     add_counter(&v.ctr->work[0], lane == 0 ? chunks : 0u);
 }
 
@@ -732,34 +756,104 @@ __device__ __forceinline__ float rep_dist(int r, const float *lo2, const float *
 }
 
 // Algorithm 2: for every cell with core points and every direction delta, the core point
-// nearest to the ideal position of delta.  The work is split into chunks of at most 128
-// points of one cell (chunk_off[c] = first chunk of cell c), one warp per chunk, so a cell of
-// any size is shared out evenly.  A chunk of at most 32 points (most cells) is staged in
-// shared memory, one point per lane, and then lane r scans its points for direction r: no
-// reduction.  A larger chunk keeps per-lane minima over its points and reduces once per
-// direction.  A cell of several chunks combines them by 64-bit atomicMin of (distance bits,
-// index) (non-negative float bits order like the floats).  Among equal distances any holder
-// may be kept: the representative only decides which pair is tested first, never a label.
-constexpr uint32_t kRepChunk = 128;  // points per work chunk of the representative pass
+// nearest to the ideal position of delta, and that point's coordinates (rep_pts).
+// The points are in cell order, so the pass walks them in windows of kRepWin consecutive
+// points, one warp per window: every load of a window is issued at once (point, core flag,
+// cell id, then the cell key), which keeps the pass a stream over the sorted points.  Lane r
+// of a group of `width` lanes takes direction r and scans the group's core points in order,
+// keeping the nearest per run of one cell (ties: the first in cell order).  A cell that lies
+// wholly inside the scanned range gets its representatives and their coordinates by plain
+// stores; a cell that crosses a range boundary combines its pieces by 64-bit atomicMin of
+// (distance bits, sorted index) (non-negative float bits order like the floats) and gets its
+// coordinates from k_rep_fix.  The representative only decides which pair a merge tests
+// first, never a label.
+constexpr uint32_t kRepWin = 128;     // points per warp window
+constexpr int kRepWarps = 4;          // warps per block
+
+template <int NDIR>
+struct RepWidth {  // lanes per direction group: the power of two >= NDIR
+    static constexpr int value = NDIR <= 2 ? 2 : NDIR <= 4 ? 4 : NDIR <= 8 ? 8 : NDIR <= 16 ? 16 : 32;
+};
+
+template <int D>
+struct RepGeom {
+    static constexpr int ndir = RepDirs<D>::value;
+    static constexpr int width = RepWidth<ndir>::value;
+    static constexpr int groups = 32 / width;
+    static constexpr uint32_t sub = kRepWin / groups;  // points scanned by one group
+};
+
+// Bits of the 32-point slice `it` of a window that fall in group g's range [g sub, (g+1) sub).
+template <int D>
+__device__ __forceinline__ unsigned rep_group_bits(int it, int g) {
+    constexpr int sub = (int)RepGeom<D>::sub;
+    const int lo = max(g * sub - 32 * it, 0), hi = min((g + 1) * sub - 32 * it, 32);
+    if (hi <= lo) return 0u;
+    const unsigned upto = hi == 32 ? 0xffffffffu : ((1u << hi) - 1u);
+    return upto & ~((1u << lo) - 1u);
+}
 
 template <typename T, int D>
-__global__ void __launch_bounds__(256, 3) k_reps(LowdView<T, D> v) {
-    constexpr int ndir = RepDirs<D>::value;
-    constexpr uint32_t kChunk = kRepChunk;
-    __shared__ float2 s_lh[8][32][D];  // per warp: (lo2, hi2) of every dimension of its 32 points
-    const uint32_t C = v.ctr->n_cells, NC = v.ctr->n_chunks;
+__global__ void __launch_bounds__(32 * kRepWarps) k_reps(LowdView<T, D> v, int64_t n) {
+    using Geo = RepGeom<D>;
+    constexpr int ndir = Geo::ndir;
+    constexpr int kPer = (int)(kRepWin / 32);
+    __shared__ float2 s_lh[kRepWarps][kRepWin][D];    // (lo2, hi2) of every dimension
+    __shared__ Pt<T, D> s_pt[kRepWarps][kRepWin];
+    __shared__ uint32_t s_cell[kRepWarps][kRepWin + 2];  // cell ids of points w0 - 1 .. w0 + kRepWin
     const int lane = lane_id(), wib = threadIdx.x >> 5;
-    (void)C;
-    // this lane's direction in the transposed scan: weights of lo2 / hi2 per dimension
+    const int64_t w0 = ((int64_t)blockIdx.x * kRepWarps + wib) * kRepWin;
+    if (w0 >= n) return;
+    // ---- loads: cell ids, core flags and points of the window, then the cells' keys ----
+    uint32_t cid[kPer];
+    uint8_t cf[kPer];
+    Pt<T, D> pp[kPer];
+#pragma unroll
+    for (int it = 0; it < kPer; ++it) {
+        const int64_t j = w0 + lane + 32 * it;
+        const bool in = j < n;
+        cid[it] = in ? v.cell_of[j] : 0xffffffffu;
+        cf[it] = in ? v.core[j] : (uint8_t)0;
+        pp[it] = in ? v.pts[j] : zero_pt<T, D>();
+    }
+    if (lane == 0) s_cell[wib][0] = w0 > 0 ? v.cell_of[w0 - 1] : 0xffffffffu;
+    if (lane == 1) s_cell[wib][kRepWin + 1] = w0 + kRepWin < n ? v.cell_of[w0 + kRepWin] : 0xffffffffu;
+    uint64_t key[kPer];
+#pragma unroll
+    for (int it = 0; it < kPer; ++it) key[it] = cf[it] ? v.cell_key[cid[it]] : 0ull;
+    unsigned cmask[kPer];
+#pragma unroll
+    for (int it = 0; it < kPer; ++it) {
+        const int p = lane + 32 * it;
+        s_cell[wib][p + 1] = cid[it];
+        cmask[it] = __ballot_sync(0xffffffffu, cf[it] != 0);
+        if (cf[it]) {
+            const GridParams &G = params_of(v, set_of_key(v, key[it]));
+            int ac[D];
+            unpack_key<D>(key[it], G, ac);
+            float u[D];
+            band_coords<T, D>(pp[it], G, u);
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const float x = u[k] - (float)ac[k];
+                s_lh[wib][p][k] = make_float2(x * x, (1.f - x) * (1.f - x));
+            }
+            s_pt[wib][p] = pp[it];
+        }
+    }
+    __syncwarp();
+    // ---- scan: lane r of group g takes direction r over the group's points ----
+    const int g = lane / Geo::width, r = lane % Geo::width;
+    const bool active = r < ndir;
     float wlo[D], whi[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) {
         wlo[k] = 0.f;
         whi[k] = 0.f;
     }
-    if (lane < ndir) {
+    if (active) {
         if (D <= 3) {
-            int code = lane < (ndir / 2) ? lane : lane + 1;
+            int code = r < (ndir / 2) ? r : r + 1;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 const int sgn = code % 3 - 1;
@@ -770,138 +864,74 @@ __global__ void __launch_bounds__(256, 3) k_reps(LowdView<T, D> v) {
         } else {
 #pragma unroll
             for (int k = 0; k < D; ++k)
-                if (k == (lane >> 1)) {
-                    if (lane & 1) whi[k] = 1.f;
+                if (k == (r >> 1)) {
+                    if (r & 1) whi[k] = 1.f;
                     else wlo[k] = 1.f;
                 }
         }
     }
-    LOWD_FOR_EACH(v, t, NC, 1) {
-        const uint32_t A = v.chunk_cell[t];
-        const GridParams &G = params_of(v, set_of_key(v, v.cell_key[A]));
-        const uint32_t s = v.cell_start[A], e = v.cell_start[A + 1];
-        const uint32_t j0 = s + kChunk * (t - v.chunk_off[A]);
-        const uint32_t j1 = min(j0 + kChunk, e);
-        int ac[D];
-        unpack_key<D>(v.cell_key[A], v.g, ac);
-        const bool single = e - s <= kChunk;
-        if (j1 - j0 <= 32) {
-            const uint32_t j = j0 + lane;
-            const bool ok = j < j1 && v.core[j];
-            if (ok) {
-                float u[D];
-                band_coords<T, D>(v.pts[j], G, u);
-#pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    const float x = u[k] - (float)ac[k];
-                    s_lh[wib][lane][k] = make_float2(x * x, (1.f - x) * (1.f - x));
-                }
-            }
-            unsigned m = __ballot_sync(0xffffffffu, ok);
-            __syncwarp();
-            if (lane < ndir && m) {
-                float best = FLT_MAX;
-                uint32_t bi = 0xffffffffu;
-                while (m) {
-                    const int k = __ffs(m) - 1;
-                    m &= m - 1;
-                    float dd = 0.f;
-#pragma unroll
-                    for (int i = 0; i < D; ++i) {
-                        const float2 lh = s_lh[wib][k][i];
-                        dd = __fmaf_rn(wlo[i], lh.x, dd);
-                        dd = __fmaf_rn(whi[i], lh.y, dd);
-                    }
-                    if (dd < best) {
-                        best = dd;
-                        bi = j0 + (uint32_t)k;
-                    }
-                }
-                const uint64_t val = ((uint64_t)__float_as_uint(best) << 32) | bi;
-                if (single) v.reps[(uint64_t)A * ndir + lane] = val;
-                else atomicMin((unsigned long long *)&v.reps[(uint64_t)A * ndir + lane], (unsigned long long)val);
-            }
-            __syncwarp();
-            continue;
+    // cells of the points just before and just after the group's range: a run of either
+    // cell continues outside the range
+    const uint32_t cprev = s_cell[wib][g * Geo::sub], cnext = s_cell[wib][(g + 1) * Geo::sub + 1];
+    uint32_t cur = 0xffffffffu;
+    float best = FLT_MAX;
+    int bp = 0;
+    auto flush = [&]() {
+        if (!active) return;
+        const uint64_t slot = (uint64_t)cur * ndir + r;
+        const uint64_t val = ((uint64_t)__float_as_uint(best) << 32) | (uint32_t)(w0 + bp);
+        if (cur == cprev || cur == cnext) {
+            atomicMin((unsigned long long *)&v.reps[slot], (unsigned long long)val);
+        } else {
+            v.reps[slot] = val;
+            v.rep_pts[slot] = s_pt[wib][bp];
         }
-        float best[ndir];
-        uint32_t bidx[ndir];
+    };
 #pragma unroll
-        for (int r = 0; r < ndir; ++r) { best[r] = FLT_MAX; bidx[r] = 0xffffffffu; }
-        // every load of this lane's points (at most kChunk / 32) is issued before any is used
-        constexpr int kPer = (int)(kChunk / 32);
-        Pt<T, D> pp[kPer];
-        bool pc[kPer];
-#pragma unroll
-        for (int it = 0; it < kPer; ++it) {
-            const uint32_t j = j0 + lane + 32u * it;
-            const bool ok = j < j1;
-            pc[it] = ok && v.core[j];
-            pp[it] = ok ? v.pts[j] : zero_pt<T, D>();
-        }
-#pragma unroll
-        for (int it = 0; it < kPer; ++it) {
-            if (!pc[it]) continue;
-            const uint32_t j = j0 + lane + 32u * it;
-            float u[D], lo2[D], hi2[D];
-            band_coords<T, D>(pp[it], G, u);
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                const float x = u[k] - (float)ac[k];
-                lo2[k] = x * x;
-                hi2[k] = (1.f - x) * (1.f - x);
+    for (int it = 0; it < kPer; ++it) {
+        unsigned mm = cmask[it] & rep_group_bits<D>(it, g);
+        while (mm) {
+            const int p = 32 * it + __ffs(mm) - 1;
+            mm &= mm - 1;
+            const uint32_t c = s_cell[wib][p + 1];
+            if (c != cur) {
+                if (cur != 0xffffffffu) flush();
+                cur = c;
+                best = FLT_MAX;
             }
+            float dd = 0.f;
 #pragma unroll
-            for (int r = 0; r < ndir; ++r) {
-                const float dd = rep_dist<D>(r, lo2, hi2);
-                if (dd < best[r]) { best[r] = dd; bidx[r] = j; }
+            for (int i = 0; i < D; ++i) {
+                const float2 lh = s_lh[wib][p][i];
+                dd = __fmaf_rn(wlo[i], lh.x, dd);
+                dd = __fmaf_rn(whi[i], lh.y, dd);
             }
-        }
-#pragma unroll
-        for (int r = 0; r < ndir; ++r) {
-            // warp minimum of the distance, then the lowest lane holding it supplies the index
-            float m = best[r];
-#pragma unroll
-            for (int o = 16; o; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
-            const unsigned holders = __ballot_sync(0xffffffffu, best[r] == m && bidx[r] != 0xffffffffu);
-            if (!holders) continue;
-            const uint32_t idx = __shfl_sync(0xffffffffu, bidx[r], __ffs(holders) - 1);
-            if (lane == 0) {
-                const uint64_t val = ((uint64_t)__float_as_uint(m) << 32) | idx;
-                if (single) v.reps[(uint64_t)A * ndir + r] = val;
-                else atomicMin((unsigned long long *)&v.reps[(uint64_t)A * ndir + r], (unsigned long long)val);
+            if (dd < best) {
+                best = dd;
+                bp = p;
             }
         }
     }
+    if (cur != 0xffffffffu) flush();
 }
 
-// Chunks of the representative-point pass: ceil(size / kRepChunk) for cells with core points.
+// Coordinates of the representatives of the cells that cross a scan-range boundary of
+// k_reps (their pieces were combined by atomicMin): one thread per (boundary, direction).
+// A cell that crosses several boundaries is written several times with the same values.
 template <typename T, int D>
-__global__ void __launch_bounds__(256) k_rep_chunks(LowdView<T, D> v, uint32_t *__restrict__ nch) {
-    const uint32_t C = v.ctr->n_cells;
-    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x)
-        nch[c] = v.cell_core[c] ? (v.cell_start[c + 1] - v.cell_start[c] + kRepChunk - 1u) / kRepChunk : 0u;
-}
-
-// chunk_cell[t] = the cell of chunk t (every cell writes its id into its chunk slots).
-template <typename T, int D>
-__global__ void __launch_bounds__(256) k_chunk_cells(LowdView<T, D> v, const uint32_t *__restrict__ nch,
-                                                    uint32_t *__restrict__ chunk_cell) {
-    const uint32_t C = v.ctr->n_cells;
-    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x)
-        for (uint32_t i = 0; i < nch[c]; ++i) chunk_cell[v.chunk_off[c] + i] = c;
-}
-
-// Coordinates of every representative point, so that a merge test reads them directly.
-template <typename T, int D>
-__global__ void __launch_bounds__(256) k_rep_pts(LowdView<T, D> v) {
-    constexpr int ndir = RepDirs<D>::value;
-    const uint64_t total = (uint64_t)v.ctr->n_cells * ndir;
-    for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t c = (uint32_t)(idx / ndir);
-        if (!v.cell_core[c]) continue;
-        v.rep_pts[idx] = v.pts[(uint32_t)v.reps[idx]];
+__global__ void __launch_bounds__(256) k_rep_fix(LowdView<T, D> v, int64_t n) {
+    using Geo = RepGeom<D>;
+    constexpr int ndir = Geo::ndir;
+    const int64_t nb = (n + Geo::sub - 1) / Geo::sub;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nb * ndir;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = (idx / ndir) * Geo::sub;
+        const int r = (int)(idx % ndir);
+        if (j == 0 || j >= n) continue;
+        const uint32_t c = v.cell_of[j];
+        if (c != v.cell_of[j - 1] || !v.cell_core[c]) continue;
+        const uint64_t slot = (uint64_t)c * ndir + r;
+        v.rep_pts[slot] = v.pts[(uint32_t)v.reps[slot]];
     }
 }
 
@@ -1278,7 +1308,7 @@ __global__ void __launch_bounds__(256) k_box_check(BoxArgs single, const double 
     if (!boxes) {
         if (blockIdx.x != 0 || threadIdx.x >= D) return;
         const int i = threadIdx.x;
-        const uint64_t *enc = reinterpret_cast<const uint64_t *>(ctr->minmax_enc);
+        const uint64_t *enc = ctr->minmax_enc;
         if (dec_double_dev(enc[i]) < single.mn[i] || dec_double_dev(enc[kMaxD + i]) > single.mx[i])
             atomicOr(&ctr->status, kErrBox);
         return;

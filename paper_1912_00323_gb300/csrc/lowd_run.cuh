@@ -442,8 +442,8 @@ int run_lowd(const RunArgs &a) {
             rc = build_grids([&](int set, int i) { return dec_double(hmm[(size_t)set * kMaxD + i]); },
                              [&](int set, int i) { return dec_double(hmm[(size_t)kMaxD * nsets + (size_t)set * kMaxD + i]); });
         else
-            rc = build_grids([&](int, int i) { return dec_double(reinterpret_cast<const uint64_t *>(h->minmax_enc)[i]); },
-                             [&](int, int i) { return dec_double(reinterpret_cast<const uint64_t *>(h->minmax_enc)[kMaxD + i]); });
+            rc = build_grids([&](int, int i) { return dec_double(h->minmax_enc[i]); },
+                             [&](int, int i) { return dec_double(h->minmax_enc[kMaxD + i]); });
         if (rc) goto out;
         if (batched) cudaMemcpyAsync(d_gtab, gsets.data(), sizeof(GridParams) * nsets, cudaMemcpyHostToDevice, s);
         // neighbour ranges (one (lo, hi) pair per cell and stencil pencil) and the coordinates
@@ -541,29 +541,20 @@ int run_lowd(const RunArgs &a) {
     v.core_out = a.d_core;
     v.ctr = ctr;
     // ---- neighbour cells of every cell (stencil pencils -> cell ranges) ----
-    k_ranges<T, D><<<grid_for(n * (int64_t)st.n_all, 256, sms, 16), 256, 0, s>>>(v, st);
+    k_ranges<T, D><<<grid_for((n / kRangeRun + 1) * (int64_t)st.n_all, 256, sms, 16), 256, 0, s>>>(v, st);
     ++launches;
     mark(5);
     // ---- Definition 2: dense cells and exact counts ----
     k_core<T, D><<<gwarp, 256, 0, s>>>(v, st.n_all);
     ++launches;
-    // ---- Algorithm 2: representative points (the stage times k_reps alone; its chunk table
-    // is counted with the core stage and the gather of the representatives' coordinates with
-    // the merge stage) ----
-    {
-        uint32_t *nch = (uint32_t *)(b + o_pflags), *choff = (uint32_t *)(b + o_pexcl);  // reused
-        k_rep_chunks<T, D><<<gpts, 256, 0, s>>>(v, nch);
-        exclusive_scan_u32(nch, choff, n, &ctr->n_cells, &ctr->n_chunks, (uint32_t *)(b + o_part), s, &launches);
-        v.chunk_off = choff;
-        v.chunk_cell = (uint32_t *)(b + o_excl);  // reused: free after the cell pass
-        k_chunk_cells<T, D><<<gpts, 256, 0, s>>>(v, nch, v.chunk_cell);
-        ++launches;
-        mark(6);
-        k_reps<T, D><<<grid_for(n / 256 + 1 + n / 8, 8, sms, 16), 256, 0, s>>>(v);
-        mark(7);
-        k_rep_pts<T, D><<<grid_for(n * (int64_t)ndir, 256, sms, 8), 256, 0, s>>>(v);
-        launches += 3;
-    }
+    // ---- Algorithm 2: representative points and their coordinates (the stage times k_reps
+    // alone; the coordinates of boundary-crossing cells are counted with the merge stage) ----
+    mark(6);
+    k_reps<T, D><<<(unsigned)((n + (int64_t)kRepWin * kRepWarps - 1) / ((int64_t)kRepWin * kRepWarps)),
+                   32 * kRepWarps, 0, s>>>(v, n);
+    mark(7);
+    k_rep_fix<T, D><<<grid_for((n / RepGeom<D>::sub + 1) * ndir, 256, sms, 8), 256, 0, s>>>(v, n);
+    launches += 2;
     // ---- Algorithm 3: first links, pointer jumping, then one merge pass over every pair ----
     k_hook<T, D><<<gwarp, 256, 0, s>>>(v, st.n_all, st.n_half);
     for (int r = 0; r < 5; ++r) k_jump<T, D><<<gpts, 256, 0, s>>>(v);
@@ -593,6 +584,7 @@ int run_lowd(const RunArgs &a) {
         st_out->n_cells = h->n_cells;
         st_out->n_pencils = h->n_pencils;
         st_out->n_dense_cells = h->n_dense;
+        st_out->n_core_cells = h->n_core_cells;
         st_out->n_core_points = h->n_core;
         st_out->n_clusters = h->n_clusters;
         st_out->n_noise = h->n_noise;

@@ -151,6 +151,7 @@ extern "C" int hca_plan_wait(hca_plan *plan, void *stream, hca_stats *stats) {
         stats->n_cells = h->n_cells;
         stats->n_pencils = h->n_pencils;
         stats->n_dense_cells = h->n_dense;
+        stats->n_core_cells = h->n_core_cells;
         stats->n_core_points = h->n_core;
         stats->n_clusters = h->n_clusters;
         stats->n_noise = h->n_noise;

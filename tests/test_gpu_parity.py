@@ -106,6 +106,9 @@ def test_mixed3d_full(env):
     assert st["n_core_points"] == int(want[1].sum())
     assert st["n_noise"] == int((want[0] < 0).sum())
     assert st["n_clusters"] == len(np.unique(want[0][want[1] == 1]))
+    # cells with a core point: every dense cell, and at most every cell
+    assert st["n_dense_cells"] <= st["n_core_cells"] <= st["n_cells"]
+    assert st["n_core_cells"] > st["n_dense_cells"]
 
 
 def test_mixed3d_full_repeated(env):
