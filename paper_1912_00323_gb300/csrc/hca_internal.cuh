@@ -37,6 +37,7 @@ struct DevCounters {
     uint32_t n_clusters;
     uint32_t n_noise;
     uint32_t n_core_cells;  // cells holding a core point (hypercube path)
+    uint32_t n_list[3];     // hypercube path: cells to count, cells with core points, cells to label
     uint64_t minmax_enc[2 * kMaxD];  // order-preserving encodings of min (first kMaxD) / max per dim
     uint32_t nan_seen;
     uint32_t n_chunks;     // 32-point chunks of the coarse cells (high-dimensional path)

@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(256) k_compress_hd(HdView<T, DP> v) {
         v.parent[j] = r;
         roots += (r == (uint32_t)j);
     }
-    for (int o = 16; o; o >>= 1) roots += __shfl_xor_sync(0xffffffffu, roots, o);
+    roots = __reduce_add_sync(0xffffffffu, roots);
     if (lane_id() == 0 && roots) atomicAdd(&v.ctr->n_clusters, roots);
 }
 
@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(256) k_comp_min_hd(HdView<T, DP> v) {
         ncore += (lane == 0) ? __popc(vm) : 0u;
         const uint32_t r0 = __shfl_sync(0xffffffffu, r, __ffs(vm) - 1);
         if (__all_sync(0xffffffffu, !valid || r == r0)) {
-            for (int o = 16; o; o >>= 1) val = min(val, __shfl_xor_sync(0xffffffffu, val, o));
+            val = __reduce_min_sync(0xffffffffu, val);
             if (lane == 0) atomicMin(&v.comp_min[r0], val);
         } else if (valid) {
             atomicMin(&v.comp_min[r], val);
@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_labels_hd(HdView<T, DP> v) {
                                 const bool need = qc && lq < bj;
                                 if (!__any_sync(0xffffffffu, need)) continue;
                                 uint32_t cand = (need && hd_within<DP>(rows + jj * DP, qv, G)) ? lq : kNoLabel;
-                                for (int o = 16; o; o >>= 1) cand = min(cand, __shfl_xor_sync(0xffffffffu, cand, o));
+                                cand = __reduce_min_sync(0xffffffffu, cand);
                                 if (lane == jj && cand < best) best = cand;
                             }
                         }
@@ -546,7 +546,7 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_labels_hd(HdView<T, DP> v) {
             }
         }
     }
-    for (int o = 16; o; o >>= 1) noise += __shfl_xor_sync(0xffffffffu, noise, o);
+    noise = __reduce_add_sync(0xffffffffu, noise);
     if (lane == 0 && noise) atomicAdd(&v.ctr->n_noise, noise);
     add_counter(&v.ctr->work[5], lane == 0 ? chunks : 0u);
 }

@@ -41,6 +41,9 @@ struct LowdView {
     Pt<T, D> *rep_pts;            // coordinates of reps[c * ndir + r]
     uint32_t *comp_min;
     uint2 *ranges;                // [cell * n_all + k]: neighbour cells [lo, hi) in pencil k
+    uint32_t *list_count;         // cells whose points k_core decides (ctr->n_list[0])
+    uint32_t *list_core;          // cells holding a core point (ctr->n_list[1])
+    uint32_t *list_label;         // cells holding a non-core point that may have a core neighbour (ctr->n_list[2])
     int32_t *labels;              // output, input order
     uint8_t *core_out;            // optional output, input order
     DevCounters *ctr;
@@ -374,7 +377,7 @@ __device__ __forceinline__ void load_stencil(Stencil &st, const Stencil &st_in) 
 }
 
 __device__ __forceinline__ void add_counter(unsigned long long *ctr, uint32_t v) {
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    v = __reduce_add_sync(0xffffffffu, v);
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(ctr, (unsigned long long)v);
 }
 
@@ -624,36 +627,123 @@ __global__ void __launch_bounds__(256) k_ranges(LowdView<T, D> v, Stencil st_in)
     }
 }
 
+// Append val to a work list when pred holds (warp-aggregated; every lane of the warp calls).
+__device__ __forceinline__ void warp_push(uint32_t *list, uint32_t *count, bool pred, uint32_t val) {
+    const unsigned m = __ballot_sync(0xffffffffu, pred);
+    if (!m) return;
+    const int leader = __ffs(m) - 1, lane = lane_id();
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = val;
+}
+
+// A warp's pending entries of a work list, one per lane, appended 32 at a time (one atomic per
+// 32 entries instead of one per entry).  Every call is warp-uniform.
+struct WarpList {
+    uint32_t pending = 0, val = 0;  // lane i holds entry i while i < pending
+    __device__ __forceinline__ void add(uint32_t *list, uint32_t *count, uint32_t x) {
+        if (lane_id() == (int)pending) val = x;
+        if (++pending == 32u) flush(list, count);
+    }
+    __device__ __forceinline__ void flush(uint32_t *list, uint32_t *count) {
+        if (!pending) return;
+        uint32_t base = 0;
+        if (lane_id() == 0) base = atomicAdd(count, pending);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (lane_id() < (int)pending) list[base + lane_id()] = val;
+        pending = 0;
+    }
+};
+
+// Cell triage before Definition 2, one thread per cell.  Initialises the union-find and
+// cluster-id slots.  A cell of at least MINPTS points (core as a whole) and a cell whose
+// stencil neighbourhood holds at least MINPTS points go on the list k_core counts.  In any
+// other cell no point can reach MINPTS (every point within eps of it lies in the stencil
+// cells), so all its points are non-core here; if no other cell lies within reach they are
+// noise and get label -1 at once, else the cell goes on the label list.
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_triage(LowdView<T, D> v, int n_all) {
+    const uint32_t C = v.ctr->n_cells;
+    uint32_t noise = 0;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < C; base += stride) {
+        const uint32_t A = base + lane_id();
+        bool to_count = false, to_label = false;
+        if (A < C) {
+            const uint32_t s = v.cell_start[A], e = v.cell_start[A + 1], m = e - s;
+            const uint64_t key = v.cell_key[A];
+            const uint32_t set = set_of_key(v, key);
+            const uint32_t min_pts = params_of(v, set).min_pts;
+            v.parent[A] = A;
+            v.comp_min[A] = kNoLabel;
+            if (m >= min_pts) {
+                to_count = true;
+            } else {
+                uint32_t reach_pts = 0, reach_cells = 0;
+#pragma unroll 8
+                for (int k = 0; k < n_all; ++k) {
+                    const uint2 rg = v.ranges[(uint64_t)A * n_all + k];
+                    if (rg.y > rg.x) {
+                        reach_cells += rg.y - rg.x;
+                        reach_pts += v.cell_start[rg.y] - v.cell_start[rg.x];
+                    }
+                }
+                if (reach_pts >= min_pts) {
+                    to_count = true;
+                } else {
+                    v.cell_core[A] = 0;
+                    for (uint32_t i = s; i < e; ++i) v.core[i] = 0;
+                    if (reach_cells <= 1) {  // only the cell itself
+                        for (uint32_t i = s; i < e; ++i) {
+                            const uint32_t o = v.perm[i];
+                            v.labels[o] = -1;
+                            if (v.core_out) v.core_out[o] = 0;
+                        }
+                        noise += m;
+                    } else {
+                        to_label = true;
+                    }
+                }
+            }
+        }
+        warp_push(v.list_count, &v.ctr->n_list[0], to_count, A);
+        warp_push(v.list_label, &v.ctr->n_list[2], to_label, A);
+    }
+    noise = __reduce_add_sync(0xffffffffu, noise);
+    if (lane_id() == 0 && noise) atomicAdd(&v.ctr->n_noise, noise);
+}
+
 // Definition 2 with the hypercube shortcut: a cell holding >= MINPTS points is core as a
 // whole (its diagonal is at most eps); every point of another cell (fewer than MINPTS points)
 // is counted exactly over its own cell and the neighbour cells, stopping once it reaches
-// MINPTS.  One warp per cell.  The neighbour cells are walked 32 at a time, one per lane; for
-// each open point of the cell every lane classifies its cell's box against the point: a box
-// wholly within eps adds the cell's size (warp sum), one wholly beyond eps is dropped, and the
-// remaining cells are compared point by point with a warp ballot.  Also initialises the
-// per-cell union-find, representative and cluster-id slots.
+// MINPTS.  One warp per cell of the triage's count list.  The neighbour cells are walked 32 at
+// a time, one per lane; for each open point of the cell every lane classifies its cell's box
+// against the point: a box wholly within eps adds the cell's size (warp sum), one wholly
+// beyond eps is dropped, and the remaining cells are compared point by point with a warp
+// ballot.  Also initialises the representative slots of cells with core points and fills the
+// lists of cells with core points (merging) and with non-core points (labels).
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_core(LowdView<T, D> v, int n_all) {
-    const uint32_t C = v.ctr->n_cells;
     const int lane = lane_id();
     uint32_t dense_cells = 0, core_cells = 0, chunks = 0;
-    for (uint32_t A = global_warp(); A < C; A += total_warps()) {
+    WarpList lcore, llabel;
+    const uint32_t NL = v.ctr->n_list[0];
+    for (uint32_t w = global_warp(); w < NL; w += total_warps()) {
+        const uint32_t A = v.list_count[w];
         const GridParams &G = params_of(v, set_of_key(v, v.cell_key[A]));
         const uint32_t min_pts = G.min_pts;
         const uint32_t s = v.cell_start[A], e = v.cell_start[A + 1], m = e - s;
-        if (lane == 0) {
-            v.parent[A] = A;
-            v.comp_min[A] = kNoLabel;
-        }
         if (m >= min_pts) {
             for (uint32_t i = s + lane; i < e; i += 32) v.core[i] = 1;
             for (int r = lane; r < RepDirs<D>::value; r += 32) v.reps[(uint64_t)A * RepDirs<D>::value + r] = ~0ull;
             if (lane == 0) v.cell_core[A] = 1;
+            lcore.add(v.list_core, &v.ctr->n_list[1], A);
             ++dense_cells;
             ++core_cells;
             continue;
         }
-        bool any_core = false;
+        bool any_core = false, any_noncore = false;
         for (uint32_t base = s; base < e; base += 32) {
             const uint32_t i = base + lane;
             const bool have = i < e;
@@ -683,8 +773,7 @@ __global__ void __launch_bounds__(256) k_core(LowdView<T, D> v, int n_all) {
                         for (int k2 = 0; k2 < D; ++k2) tj[k2] = __shfl_sync(0xffffffffu, ta[k2], jj);
                         const int cls = okb ? box_class<D>(tj, cb, G) : 0;
                         uint32_t full = cls == 2 ? be - bs : 0u;
-#pragma unroll
-                        for (int o = 16; o; o >>= 1) full += __shfl_xor_sync(0xffffffffu, full, o);
+                        full = __reduce_add_sync(0xffffffffu, full);
                         uint32_t cj = __shfl_sync(0xffffffffu, cnt, jj) + full;
                         unsigned partial = __ballot_sync(0xffffffffu, cls == 1);
                         if (partial && cj < min_pts) {
@@ -720,12 +809,17 @@ __global__ void __launch_bounds__(256) k_core(LowdView<T, D> v, int n_all) {
             const bool is_core = have && cnt >= min_pts;
             if (have) v.core[i] = is_core ? 1 : 0;
             any_core |= __any_sync(0xffffffffu, is_core);
+            any_noncore |= __any_sync(0xffffffffu, have && !is_core);
         }
         if (any_core)
             for (int r = lane; r < RepDirs<D>::value; r += 32) v.reps[(uint64_t)A * RepDirs<D>::value + r] = ~0ull;
         if (lane == 0) v.cell_core[A] = any_core ? 1 : 0;
+        if (any_core) lcore.add(v.list_core, &v.ctr->n_list[1], A);
+        if (any_noncore) llabel.add(v.list_label, &v.ctr->n_list[2], A);
         core_cells += any_core ? 1u : 0u;
     }
+    lcore.flush(v.list_core, &v.ctr->n_list[1]);
+    llabel.flush(v.list_label, &v.ctr->n_list[2]);
     if (lane == 0 && dense_cells) atomicAdd(&v.ctr->n_dense, dense_cells);
     if (lane == 0 && core_cells) atomicAdd(&v.ctr->n_core_cells, core_cells);
     add_counter(&v.ctr->work[0], lane == 0 ? chunks : 0u);
@@ -989,10 +1083,10 @@ __device__ bool warp_core_pair(const LowdView<T, D> &v, uint32_t A, uint32_t B, 
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_hook(LowdView<T, D> v, int n_all, int n_half) {
     constexpr int ndir = RepDirs<D>::value;
-    const uint32_t C = v.ctr->n_cells;
     const int lane = lane_id();
-    for (uint32_t A = global_warp(); A < C; A += total_warps()) {
-        if (!v.cell_core[A]) continue;
+    const uint32_t NL = v.ctr->n_list[1];
+    for (uint32_t w = global_warp(); w < NL; w += total_warps()) {
+        const uint32_t A = v.list_core[w];
         int ac[D];
         const uint64_t akey = v.cell_key[A];
         unpack_key<D>(akey, v.g, ac);
@@ -1049,11 +1143,11 @@ __global__ void __launch_bounds__(256) k_jump(LowdView<T, D> v) {
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_merge(LowdView<T, D> v, int n_all, int n_half, int pass) {
     constexpr int ndir = RepDirs<D>::value;
-    const uint32_t C = v.ctr->n_cells;
     const int lane = lane_id();
     uint32_t rep_tests = 0, rep_hits = 0, exhaustive = 0, chunks = 0;
-    for (uint32_t A = global_warp(); A < C; A += total_warps()) {
-        if (!v.cell_core[A]) continue;
+    const uint32_t NL = v.ctr->n_list[1];
+    for (uint32_t w = global_warp(); w < NL; w += total_warps()) {
+        const uint32_t A = v.list_core[w];
         int ac[D];
         const uint64_t akey = v.cell_key[A];
         unpack_key<D>(akey, v.g, ac);
@@ -1126,7 +1220,7 @@ __global__ void __launch_bounds__(256) k_compress(LowdView<T, D> v, int count_ro
         v.parent[c] = r;
         roots += (r == c);
     }
-    for (int o = 16; o; o >>= 1) roots += __shfl_xor_sync(0xffffffffu, roots, o);
+    roots = __reduce_add_sync(0xffffffffu, roots);
     if (count_roots && lane_id() == 0 && roots) atomicAdd(&v.ctr->n_clusters, roots);
 }
 
@@ -1148,7 +1242,7 @@ __global__ void __launch_bounds__(256) k_comp_min(LowdView<T, D> v) {
         ncore += (lane == 0) ? __popc(vm) : 0u;
         const uint32_t r0 = __shfl_sync(0xffffffffu, r, __ffs(vm) - 1);
         if (__all_sync(0xffffffffu, !valid || r == r0)) {
-            for (int o = 16; o; o >>= 1) val = min(val, __shfl_xor_sync(0xffffffffu, val, o));
+            val = __reduce_min_sync(0xffffffffu, val);
             if (lane == 0) atomicMin(&v.comp_min[r0], val);
         } else if (valid) {
             atomicMin(&v.comp_min[r], val);
@@ -1180,10 +1274,11 @@ __global__ void __launch_bounds__(256) k_label_core(LowdView<T, D> v) {
 // dropped, and the others are compared point by point.  Writes labels in input order.
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_labels(LowdView<T, D> v, int n_all) {
-    const uint32_t C = v.ctr->n_cells;
     const int lane = lane_id();
     uint32_t noise = 0, chunks = 0;
-    LOWD_FOR_EACH(v, A, C, 4) {
+    const uint32_t NL = v.ctr->n_list[2];
+    LOWD_FOR_EACH(v, X, NL, 4) {
+        const uint32_t A = v.list_label[X];
         const uint32_t s = v.cell_start[A], e = v.cell_start[A + 1];
         const uint64_t akey = v.cell_key[A];
         const uint32_t aset = set_of_key(v, akey);
@@ -1228,8 +1323,7 @@ __global__ void __launch_bounds__(256) k_labels(LowdView<T, D> v, int n_all) {
                             for (int k2 = 0; k2 < D; ++k2) tj[k2] = __shfl_sync(0xffffffffu, ta[k2], jj);
                             const int cls = cand ? box_class<D>(tj, cb, G) : 0;
                             uint32_t m2 = cls == 2 ? clB : kNoLabel;
-#pragma unroll
-                            for (int o = 16; o; o >>= 1) m2 = min(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+                            m2 = __reduce_min_sync(0xffffffffu, m2);
                             bj = min(bj, m2);
                             unsigned partial = __ballot_sync(0xffffffffu, cls == 1 && clB < bj);
                             if (partial) {
@@ -1275,7 +1369,7 @@ __global__ void __launch_bounds__(256) k_labels(LowdView<T, D> v, int n_all) {
             }
         }
     }
-    for (int o = 16; o; o >>= 1) noise += __shfl_xor_sync(0xffffffffu, noise, o);
+    noise = __reduce_add_sync(0xffffffffu, noise);
     if (lane == 0 && noise) atomicAdd(&v.ctr->n_noise, noise);
     add_counter(&v.ctr->work[5], lane == 0 ? chunks : 0u);
 }

@@ -536,6 +536,9 @@ int run_lowd(const RunArgs &a) {
     v.reps = (uint64_t *)(b + o_reps);
     v.comp_min = (uint32_t *)(b + o_cmin);
     v.ranges = (uint2 *)ws_ranges;
+    v.list_count = (uint32_t *)(b + o_excl);   // the scan scratch of the cell and pencil passes is free now
+    v.list_core = (uint32_t *)(b + o_pflags);
+    v.list_label = (uint32_t *)(b + o_pexcl);
     v.rep_pts = (Pt<T, D> *)((char *)ws_ranges + align_up(sizeof(uint2) * (size_t)n * st.n_all));
     v.labels = a.d_labels;
     v.core_out = a.d_core;
@@ -544,9 +547,10 @@ int run_lowd(const RunArgs &a) {
     k_ranges<T, D><<<grid_for((n / kRangeRun + 1) * (int64_t)st.n_all, 256, sms, 16), 256, 0, s>>>(v, st);
     ++launches;
     mark(5);
-    // ---- Definition 2: dense cells and exact counts ----
+    // ---- Definition 2: triage of the cells, then dense cells and exact counts ----
+    k_triage<T, D><<<gpts, 256, 0, s>>>(v, st.n_all);
     k_core<T, D><<<gwarp, 256, 0, s>>>(v, st.n_all);
-    ++launches;
+    launches += 2;
     // ---- Algorithm 2: representative points and their coordinates (the stage times k_reps
     // alone; the coordinates of boundary-crossing cells are counted with the merge stage) ----
     mark(6);

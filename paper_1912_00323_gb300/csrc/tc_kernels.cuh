@@ -402,8 +402,7 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
             } else if (MODE == kLabels) {
                 S.cpay[tid] = pre_pay;
                 uint32_t gm = pre_pay;
-#pragma unroll
-                for (int o = 16; o; o >>= 1) gm = min(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+                gm = __reduce_min_sync(0xffffffffu, gm);
                 if ((tid & 31) == 0) S.gsum[warp] = gm;
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -567,7 +566,7 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
     add_counter(&v.ctr->work[7], n_re);
     if (MODE == kMerge) add_counter(&v.ctr->work[2], tid == 0 ? n_skip : 0u);
     if (MODE == kLabels) {
-        for (int o = 16; o; o >>= 1) n_noise += __shfl_xor_sync(0xffffffffu, n_noise, o);
+        n_noise = __reduce_add_sync(0xffffffffu, n_noise);
         if ((tid & 31) == 0 && n_noise) atomicAdd(&v.ctr->n_noise, n_noise);
     }
 }
