@@ -80,6 +80,7 @@ struct Stencil {
     int n_half;
     int8_t off[kMaxPencils][kMaxD - 1 > 0 ? kMaxD - 1 : 1];
     int8_t reach[kMaxPencils];   // max |delta_last| that can hold a point within eps
+    uint16_t near[kMaxPencils];  // all pencils, nearest offsets first (counting order)
 };
 
 template <typename T, int D>

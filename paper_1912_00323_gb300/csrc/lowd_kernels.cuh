@@ -569,7 +569,7 @@ static __global__ void __launch_bounds__(256) k_pencils(const uint64_t *__restri
 // pencil (all coordinates but the last), so the thread looks the neighbour pencil up in the
 // hash table once per pencil of its run; along a pencil the last coordinate increases, so
 // both ends of the neighbour range only move forward and are found from the previous cell's.
-constexpr uint32_t kRangeRun = 16;
+constexpr uint32_t kRangeRun = 4;
 
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_ranges(LowdView<T, D> v, Stencil st_in) {
@@ -724,7 +724,10 @@ __global__ void __launch_bounds__(256) k_triage(LowdView<T, D> v, int n_all) {
 // ballot.  Also initialises the representative slots of cells with core points and fills the
 // lists of cells with core points (merging) and with non-core points (labels).
 template <typename T, int D>
-__global__ void __launch_bounds__(256) k_core(LowdView<T, D> v, int n_all) {
+__global__ void __launch_bounds__(256) k_core(LowdView<T, D> v, Stencil st_in) {
+    __shared__ Stencil st;
+    load_stencil<T, D>(st, st_in);
+    const int n_all = st.n_all;
     const int lane = lane_id();
     uint32_t dense_cells = 0, core_cells = 0, chunks = 0;
     WarpList lcore, llabel;
@@ -753,8 +756,8 @@ __global__ void __launch_bounds__(256) k_core(LowdView<T, D> v, int n_all) {
             uint32_t cnt = m;  // the own cell: every point within eps
             unsigned open = __ballot_sync(0xffffffffu, have && cnt < min_pts);
             for (int g0 = 0; g0 < n_all && open; g0 += 32) {
-                const int k = g0 + lane;
-                const uint2 rg = k < n_all ? v.ranges[(uint64_t)A * n_all + k] : make_uint2(0u, 0u);
+                const int k = g0 + lane;  // pencils nearest first: most points settle early
+                const uint2 rg = k < n_all ? v.ranges[(uint64_t)A * n_all + st.near[k]] : make_uint2(0u, 0u);
                 const LaneRanges lr = lane_ranges(rg.x, rg.y);
                 for (uint32_t f0 = 0; f0 < lr.total && open; f0 += 32) {
                     const uint32_t f = f0 + lane;
@@ -1101,10 +1104,11 @@ __global__ void __launch_bounds__(256) k_hook(LowdView<T, D> v, int n_all, int n
             for (uint32_t f0 = 0; f0 < lr.total && !linked; f0 += 32) {
                 const uint32_t f = f0 + lane;
                 const uint32_t B = flat_cell(lr, f < lr.total ? f : 0u);
+                const uint64_t bkey = f < lr.total ? v.cell_key[B] : 0ull;  // loaded with the core flag
                 bool hit = f < lr.total && v.cell_core[B];
                 if (hit) {
                     int bc[D], delta[D];
-                    unpack_key<D>(v.cell_key[B], v.g, bc);
+                    unpack_key<D>(bkey, v.g, bc);
 #pragma unroll
                     for (int i = 0; i < D; ++i) delta[i] = bc[i] - ac[i];
                     const int ra = rep_dir_of<D>(delta);
@@ -1160,10 +1164,11 @@ __global__ void __launch_bounds__(256) k_merge(LowdView<T, D> v, int n_all, int 
             for (uint32_t f0 = 0; f0 < lr.total; f0 += 32) {
                 const uint32_t f = f0 + lane;
                 const uint32_t B = flat_cell(lr, f < lr.total ? f : 0u);
+                const uint64_t bkey = f < lr.total ? v.cell_key[B] : 0ull;  // loaded with the core flag
                 bool pending = f < lr.total && v.cell_core[B];
                 int bc[D], delta[D];
                 if (pending) {
-                    unpack_key<D>(v.cell_key[B], v.g, bc);
+                    unpack_key<D>(bkey, v.g, bc);
                     int cheb = 0;
 #pragma unroll
                     for (int i = 0; i < D; ++i) {

@@ -5,6 +5,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "lowd_kernels.cuh"
@@ -167,6 +168,21 @@ inline int make_stencil_union(int D, const std::vector<double> &eps, const std::
         if (cls == 1) st.n_half = k;
     }
     st.n_all = k;
+    // counting order: by the gap of the offset (the squared distance, in cells, between the
+    // cell and the nearest cell of the pencil), then by the sum of |offsets|
+    std::vector<int> order(k);
+    for (int j = 0; j < k; ++j) order[j] = j;
+    auto near_key = [&](int j) {
+        int gap = 0, l1 = 0;
+        for (int i = 0; i < D - 1; ++i) {
+            const int a = st.off[j][i] < 0 ? -st.off[j][i] : st.off[j][i];
+            gap += (a > 1 ? a - 1 : 0) * (a > 1 ? a - 1 : 0);
+            l1 += a;
+        }
+        return gap * 1024 + l1;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return near_key(x) < near_key(y); });
+    for (int j = 0; j < k; ++j) st.near[j] = (uint16_t)order[j];
     return HCA_OK;
 }
 
@@ -549,7 +565,7 @@ int run_lowd(const RunArgs &a) {
     mark(5);
     // ---- Definition 2: triage of the cells, then dense cells and exact counts ----
     k_triage<T, D><<<gpts, 256, 0, s>>>(v, st.n_all);
-    k_core<T, D><<<gwarp, 256, 0, s>>>(v, st.n_all);
+    k_core<T, D><<<gwarp, 256, 0, s>>>(v, st);
     launches += 2;
     // ---- Algorithm 2: representative points and their coordinates (the stage times k_reps
     // alone; the coordinates of boundary-crossing cells are counted with the merge stage) ----
