@@ -1230,44 +1230,42 @@ __global__ void __launch_bounds__(256) k_compress(LowdView<T, D> v, int count_ro
 }
 
 // Canonical cluster id (Algorithm 4 numbers clusters in traversal order; the fixed rule
-// here is the smallest input index among the cluster's core points).
+// here is the smallest input index among the cluster's core points).  The radix sort is
+// stable and starts from input order, so inside a cell the points keep their input order and
+// the first core point of a cell holds the cell's smallest core index: one atomicMin per cell
+// with core points.
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_comp_min(LowdView<T, D> v) {
+    const uint32_t NL = v.ctr->n_list[1];
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < NL; w += gridDim.x * blockDim.x) {
+        const uint32_t A = v.list_core[w];
+        const uint32_t e = v.cell_start[A + 1];
+        uint32_t i = v.cell_start[A];
+        while (i < e && !v.core[i]) ++i;
+        if (i < e) atomicMin(&v.comp_min[v.parent[A]], v.perm[i]);
+    }
+}
+
+// Cluster ids of core points, point-parallel (a cell can hold tens of thousands of points);
+// also counts the core points.
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_label_core(LowdView<T, D> v) {
     const int64_t n = v.g.n;
     const int lane = lane_id();
     uint32_t ncore = 0;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
-         base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = base + lane;
-        const bool valid = j < n && v.core[j];
-        const uint32_t r = valid ? v.parent[v.cell_of[j]] : 0xffffffffu;
-        uint32_t val = valid ? v.perm[j] : kNoLabel;
-        const unsigned vm = __ballot_sync(0xffffffffu, valid);
-        if (!vm) continue;
-        ncore += (lane == 0) ? __popc(vm) : 0u;
-        const uint32_t r0 = __shfl_sync(0xffffffffu, r, __ffs(vm) - 1);
-        if (__all_sync(0xffffffffu, !valid || r == r0)) {
-            val = __reduce_min_sync(0xffffffffu, val);
-            if (lane == 0) atomicMin(&v.comp_min[r0], val);
-        } else if (valid) {
-            atomicMin(&v.comp_min[r], val);
-        }
-    }
-    if (lane == 0 && ncore) atomicAdd(&v.ctr->n_core, ncore);
-}
-
-// Cluster ids of core points, point-parallel (a cell can hold tens of thousands of points).
-template <typename T, int D>
-__global__ void __launch_bounds__(256) k_label_core(LowdView<T, D> v) {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < v.g.n;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        if (!v.core[j]) continue;
+    for (int64_t jb = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); jb < n;
+         jb += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = jb + lane;
+        const bool isc = j < n && v.core[j];
+        ncore += __popc(__ballot_sync(0xffffffffu, isc));
+        if (!isc) continue;
         const uint32_t o = v.perm[j];
         const uint32_t c = v.cell_of[j];
         const uint32_t base = v.gtab ? (uint32_t)v.set_off[set_of_key(v, v.cell_key[c])] : 0u;
         v.labels[o] = (int32_t)(v.comp_min[v.parent[c]] - base);
         if (v.core_out) v.core_out[o] = 1;
     }
+    if (lane == 0 && ncore) atomicAdd(&v.ctr->n_core, ncore);
 }
 
 // Algorithm 4 and Definition 5 with the canonical rule: core points take their cluster id;
@@ -1278,7 +1276,7 @@ __global__ void __launch_bounds__(256) k_label_core(LowdView<T, D> v) {
 // wholly within eps settles that point at once (warp minimum), one wholly beyond eps is
 // dropped, and the others are compared point by point.  Writes labels in input order.
 template <typename T, int D>
-__global__ void __launch_bounds__(256) k_labels(LowdView<T, D> v, int n_all) {
+__global__ void __launch_bounds__(256, 4) k_labels(LowdView<T, D> v, int n_all) {
     const int lane = lane_id();
     uint32_t noise = 0, chunks = 0;
     const uint32_t NL = v.ctr->n_list[2];

@@ -577,8 +577,8 @@ int run_lowd(const RunArgs &a) {
     launches += 2;
     // ---- Algorithm 3: first links, pointer jumping, then one merge pass over every pair ----
     k_hook<T, D><<<gwarp, 256, 0, s>>>(v, st.n_all, st.n_half);
-    for (int r = 0; r < 5; ++r) k_jump<T, D><<<gpts, 256, 0, s>>>(v);
-    launches += 6;
+    for (int r = 0; r < 3; ++r) k_jump<T, D><<<gpts, 256, 0, s>>>(v);
+    launches += 4;
     k_merge<T, D><<<gwarp, 256, 0, s>>>(v, st.n_all, st.n_half, 2);
     k_compress<T, D><<<gpts, 256, 0, s>>>(v, 1);
     launches += 2;
