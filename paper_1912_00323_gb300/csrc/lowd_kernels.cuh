@@ -786,6 +786,13 @@ __global__ void __launch_bounds__(256) k_core(LowdView<T, D> v, Stencil st_in) {
                                 partial &= partial - 1;
                                 const uint32_t ps = __shfl_sync(0xffffffffu, bs, t);
                                 const uint32_t pe = __shfl_sync(0xffffffffu, be, t);
+                                if (pe - ps <= 32) {  // most cells: one chunk
+                                    const uint32_t q = ps + lane;
+                                    const bool hit = q < pe && within_eps<D>(aj, v.pts[q], G);
+                                    cj += __popc(__ballot_sync(0xffffffffu, hit));
+                                    ++chunks;
+                                    continue;
+                                }
                                 for (uint32_t qb = ps; qb < pe && cj < min_pts; qb += 128) {
                                     // four chunks of candidates in flight
                                     Pt<T, D> q4[4];
@@ -1338,6 +1345,13 @@ __global__ void __launch_bounds__(256, 4) k_labels(LowdView<T, D> v, int n_all) 
                                     if (cl2 >= bj) continue;
                                     const uint32_t ps = __shfl_sync(0xffffffffu, bs, t);
                                     const uint32_t pe = __shfl_sync(0xffffffffu, be, t);
+                                    if (pe - ps <= 32) {  // most cells: one chunk
+                                        const uint32_t q = ps + lane;
+                                        const bool hit = q < pe && v.core[q] && within_eps<D>(aj, v.pts[q], G);
+                                        ++chunks;
+                                        if (__any_sync(0xffffffffu, hit)) bj = cl2;
+                                        continue;
+                                    }
                                     for (uint32_t qb = ps; qb < pe; qb += 128) {
                                         Pt<T, D> q4[4];
                                         bool c4[4];
