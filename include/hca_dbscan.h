@@ -283,8 +283,8 @@ HCA_API int hca_plan_destroy(hca_plan *plan);
  *                  0..127.
  *   first_links    1: first-link pass in every coarse cell; 0: only in cells whose unions run
  *                  on the CUDA cores.
- * Defaults: path 0, tc_handoff 8; d <= 8: thresholds 16 / 16 / 4, first_links 0; d > 8:
- * thresholds 8 / 4 / 1, first_links 1.
+ * Defaults: path 0, tc_handoff 8, first_links 1; thresholds 16 / 16 / 4 for d <= 8 and
+ * 8 / 4 / 1 for d > 8.
  */
 typedef struct hca_tuning {
     int32_t path;

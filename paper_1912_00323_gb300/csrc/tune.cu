@@ -18,16 +18,17 @@ std::mutex g_tune_mu;
 hca_tuning g_tune[kMaxDim + 1];
 bool g_tune_init = false;
 
-// Defaults per d: the coarse-grid split that the autotuner chose on the measured workloads —
-// d <= 8 (the batched blob sets at d = 8: thresholds 16 / 16 / 4, no first links in tensor-core
-// cells) and d > 8 (the 16-D anisotropic clusters: 8 / 4 / 1 with first links everywhere).
+// Defaults per d: the coarse-grid split measured fastest across the workloads, with first
+// links in every cell (leaving them out of tensor-core cells wins a few percent on many small
+// sets but loses up to 8x on a set of a million points) — d <= 8: thresholds 16 / 16 / 4;
+// d > 8 (the 16-D anisotropic clusters): 8 / 4 / 1.
 hca_tuning default_tuning(int d) {
     hca_tuning t = kDefaultTuning;
     if (d <= 8) {
         t.tc_min_count = 16;
         t.tc_min_merge = 16;
         t.tc_min_labels = 4;
-        t.first_links = 0;
+        t.first_links = 1;
     } else {
         t.tc_min_count = 8;
         t.tc_min_merge = 4;
