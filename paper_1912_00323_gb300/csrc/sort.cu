@@ -3,7 +3,7 @@
 // A first kernel counts the digits of every pass over all keys (the counts do not depend on
 // the order, so one read of the keys serves all passes); a caller that produced the keys may
 // pass these counts in instead.  Each pass kernel then takes a tile
-// of 2048 keys, ranks every key stably among the keys of its tile with the same digit (warp
+// of 4096 keys, ranks every key stably among the keys of its tile with the same digit (warp
 // match + per-warp digit counters + an exclusive scan across warps), learns how many keys of
 // each digit the earlier tiles hold by decoupled look-back, and scatters the tile through
 // shared memory in digit order so that the global stores of each digit run are coalesced.
@@ -25,7 +25,7 @@ namespace {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortItems = 8;   // per lane: a warp covers 256 consecutive keys
+constexpr int kSortItems = 16;  // per lane: a warp covers 512 consecutive keys
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kRadix = 256;
 constexpr int kMaxPasses = 8;
