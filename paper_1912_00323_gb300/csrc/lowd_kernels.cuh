@@ -835,30 +835,6 @@ __global__ void __launch_bounds__(256) k_core(LowdView<T, D> v, Stencil st_in) {
     add_counter(&v.ctr->work[0], lane == 0 ? chunks : 0u);
 }
 
-// Squared distance, in band units, from a point at cell-local position u (u_i in [0, 1)) to
-// the ideal position of direction r (the face / edge / corner of the cube in that direction,
-// Sec. 2): the sum over the dimensions the direction constrains of (1 - u_i)^2 or u_i^2.
-template <int D>
-__device__ __forceinline__ float rep_dist(int r, const float *lo2, const float *hi2) {
-    constexpr int ndir = RepDirs<D>::value;
-    float dist = 0.f;
-    if (D <= 3) {
-        int code = r < (ndir / 2) ? r : r + 1;
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-            const int sgn = code % 3 - 1;
-            code /= 3;
-            dist += sgn > 0 ? hi2[k] : (sgn < 0 ? lo2[k] : 0.f);
-        }
-    } else {
-        const int ax = r >> 1;
-#pragma unroll
-        for (int k = 0; k < D; ++k)
-            if (k == ax) dist = (r & 1) ? hi2[k] : lo2[k];
-    }
-    return dist;
-}
-
 // Algorithm 2: for every cell with core points and every direction delta, the core point
 // nearest to the ideal position of delta, and that point's coordinates (rep_pts).
 // The points are in cell order, so the pass walks them in windows of kRepWin consecutive
@@ -946,7 +922,10 @@ __global__ void __launch_bounds__(32 * kRepWarps) k_reps(LowdView<T, D> v, int64
         }
     }
     __syncwarp();
-    // ---- scan: lane r of group g takes direction r over the group's points ----
+    // ---- scan: lane r of group g takes direction r over the group's points.  The squared
+    // distance of a point at cell-local position x to the ideal position of direction delta
+    // (the face / edge / corner of the cube, Sec. 2) sums (1 - x_i)^2 over the dimensions with
+    // delta_i = +1 and x_i^2 over those with delta_i = -1: weights whi / wlo of the lane ----
     const int g = lane / Geo::width, r = lane % Geo::width;
     const bool active = r < ndir;
     float wlo[D], whi[D];
