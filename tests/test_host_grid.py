@@ -1,0 +1,109 @@
+"""Host logic of the hypercube grid (Algorithm 1): make_grid chooses the cell side so that a
+cell holds only points within eps of each other, which is what lets a cell of at least MINPTS
+points be core as a whole (Sec. 2).  A host-only program compiled against csrc/lowd_run.cuh
+dumps the grids built for 96 seeded random cases (d = 1..4, float and double input, eps over
+six decades, extents up to 10^5 eps); the checks below hold them against exact rational
+arithmetic:
+
+* the side inequality  d ((1 + 2 tau) side)^2 <= (eps (1 - 2^-20))^2,  side = 1 / inv_side;
+* the binning error bound: the band coordinate the device computes (float input: two FP32
+  roundings, fl32(fl32(x - o) * inv); double: the same in FP64) lies within tau of the exact
+  (x - o) * inv for random points and the extremes of every extent, and the last cell index
+  is inside the grid;
+* the FP32 filter thresholds bracket fl64(eps^2) by at least the relative guard band 2^-16.
+
+Needs nvcc (host code only, no GPU)."""
+import math
+import os
+import shutil
+import subprocess
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _nvcc():
+    exe = shutil.which("nvcc")
+    if exe:
+        return exe
+    cand = "/usr/local/cuda/bin/nvcc"
+    return cand if os.path.exists(cand) else None
+
+
+def _f32(text):
+    """A float printed with 9 significant digits, read back as that float (round trip)."""
+    return float(np.float32(float(text)))
+
+
+@pytest.fixture(scope="module")
+def grids(tmp_path_factory):
+    nvcc = _nvcc()
+    if nvcc is None:
+        pytest.skip("nvcc not available")
+    exe = tmp_path_factory.mktemp("grid") / "grid_dump"
+    subprocess.run([nvcc, "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a",
+                    "-I", os.path.join(ROOT, "include"), "-I", os.path.join(ROOT, "paper_1912_00323_gb300", "csrc"),
+                    os.path.join(ROOT, "tests", "host", "grid_dump.cu"), "-o", str(exe)],
+                   check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines()
+    cases = []
+    for line in out:
+        head, tail = line.split("|")
+        h, t = head.split(), tail.split()
+        D, f32, eps = int(h[1]), h[2] == "1", float(h[3])
+        ext = [float(x) for x in h[4:4 + 2 * D]]
+        rc, bin64 = int(t[0]), t[1] == "1"
+        cases.append({"D": D, "f32": f32, "eps": eps, "mn": ext[0::2], "mx": ext[1::2], "rc": rc,
+                      "bin64": bin64, "inv": float(t[2]), "inv_f": _f32(t[3]), "tau": float(t[4]),
+                      "ncell": [int(x) for x in t[5:5 + D]], "key_bits": int(t[5 + D]),
+                      "lo32": _f32(t[6 + D]), "hi32": _f32(t[7 + D])})
+    assert len(cases) == 96
+    assert all(c["rc"] == 0 for c in cases)
+    return cases
+
+
+def test_cell_diagonal_stays_within_eps(grids):
+    shrink = 1 - Fraction(1, 2 ** 20)
+    for c in grids:
+        side = 1 / Fraction(c["inv"])
+        w = side * (1 + 2 * Fraction(c["tau"]))
+        assert c["D"] * w * w <= (Fraction(c["eps"]) * shrink) ** 2, c
+
+
+def test_band_coordinates_within_tau(grids):
+    rng = np.random.default_rng(1912)
+    for c in grids:
+        tau = Fraction(c["tau"])
+        inv = Fraction(c["inv"])
+        for i in range(c["D"]):
+            lo, hi = c["mn"][i], c["mx"][i]
+            xs = np.concatenate([[lo, hi], lo + (hi - lo) * rng.random(300)])
+            if c["f32"]:
+                xs = np.clip(xs.astype(np.float32), np.float32(lo), np.float32(hi))
+            if c["f32"] and not c["bin64"]:
+                assert c["inv"] == c["inv_f"]  # FP32 binning uses the float factor exactly
+                o = np.float32(lo)
+                t = (xs - o).astype(np.float32) * np.float32(c["inv_f"])
+                t = t.astype(np.float32)
+            else:
+                o = np.float64(lo)
+                t = (xs.astype(np.float64) - o) * np.float64(c["inv"])
+            for x, tv in zip(xs.tolist(), t.tolist()):
+                exact = (Fraction(x) - Fraction(float(o))) * inv
+                assert abs(Fraction(tv) - exact) <= tau, (c, x)
+            assert math.floor(max(t.tolist())) <= c["ncell"][i] - 1
+        assert c["key_bits"] == sum(max(1, math.ceil(math.log2(n))) for n in c["ncell"])
+        assert c["key_bits"] <= 63
+
+
+def test_fp32_filter_thresholds_bracket_eps2(grids):
+    for c in grids:
+        eps2 = Fraction(c["eps"] * c["eps"])  # fl64(eps * eps), the exact predicate's threshold
+        if c["f32"]:
+            assert Fraction(c["lo32"]) <= eps2 * (1 - Fraction(1, 2 ** 16))
+            assert Fraction(c["hi32"]) >= eps2 * (1 + Fraction(1, 2 ** 16))
+        else:
+            assert c["lo32"] == -1.0 and c["hi32"] == math.inf
