@@ -12,6 +12,11 @@ arithmetic:
   is inside the grid;
 * the FP32 filter thresholds bracket fl64(eps^2) by at least the relative guard band 2^-16.
 
+For the coarse grid of the d >= 5 path (make_coarse_grid, 64 seeded cases): a side of at least
+eps (1 + 2^-50) beyond the binning error, so two points within eps (whose coordinates differ
+by at most eps (1 + 2^-50)) always fall in the same or adjacent coarse cells; checked exactly
+and on sampled pairs at up to that distance per coordinate.
+
 Needs nvcc (host code only, no GPU)."""
 import math
 import os
@@ -107,3 +112,55 @@ def test_fp32_filter_thresholds_bracket_eps2(grids):
             assert Fraction(c["hi32"]) >= eps2 * (1 + Fraction(1, 2 ** 16))
         else:
             assert c["lo32"] == -1.0 and c["hi32"] == math.inf
+
+
+@pytest.fixture(scope="module")
+def coarse(tmp_path_factory):
+    nvcc = _nvcc()
+    if nvcc is None:
+        pytest.skip("nvcc not available")
+    exe = tmp_path_factory.mktemp("coarse") / "coarse_grid_dump"
+    subprocess.run([nvcc, "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a",
+                    "-I", os.path.join(ROOT, "include"), "-I", os.path.join(ROOT, "paper_1912_00323_gb300", "csrc"),
+                    os.path.join(ROOT, "tests", "host", "coarse_grid_dump.cu"), "-o", str(exe)],
+                   check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines()
+    cases = []
+    for line in out:
+        head, tail = line.split("|")
+        h, t = head.split(), tail.split()
+        ext = [float(x) for x in h[3:9]]
+        cases.append({"f32": h[1] == "1", "eps": float(h[2]), "mn": ext[0::2], "mx": ext[1::2],
+                      "rc": int(t[0]), "inv": float(t[1]), "tau": float(t[2]), "ncell": [int(x) for x in t[3:6]]})
+    assert len(cases) == 64 and all(c["rc"] == 0 for c in cases)
+    return cases
+
+
+def test_coarse_side_covers_eps(coarse):
+    for c in coarse:
+        side = 1 / Fraction(c["inv"])
+        reach = Fraction(c["eps"]) * (1 + Fraction(1, 2 ** 50))
+        assert Fraction(c["tau"]) <= Fraction(1, 2 ** 14)
+        # the band coordinates of two points at most `reach` apart differ by < 1 - 2 tau
+        assert reach / side < 1 - 2 * Fraction(c["tau"]), c
+
+
+def test_points_within_eps_land_in_adjacent_coarse_cells(coarse):
+    rng = np.random.default_rng(5)
+    for c in coarse:
+        mn, mx = np.array(c["mn"]), np.array(c["mx"])
+        reach = c["eps"] * (1 + 2.0 ** -50)
+        p = mn + (mx - mn) * rng.random((400, 3))
+        step = reach * rng.choice([-1.0, 1.0], size=(400, 3)) * np.where(rng.random((400, 3)) < 0.2, 1.0,
+                                                                          rng.random((400, 3)))
+        q = np.clip(p + step, mn, mx)
+        if c["f32"]:
+            p, q = p.astype(np.float32).astype(np.float64), q.astype(np.float32).astype(np.float64)
+        keep = np.all(np.abs(q - p) <= reach, axis=1)
+        inv = np.float64(c["inv"])
+        top = np.array(c["ncell"]) - 1
+
+        def cells(x):
+            return np.minimum(np.floor((x - mn) * inv), top)
+        assert keep.sum() > 100
+        assert np.all(np.abs(cells(p[keep]) - cells(q[keep])) <= 1), c
