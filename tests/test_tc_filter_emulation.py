@@ -1,4 +1,5 @@
-"""The tensor-core filter's thresholds against the exact predicate, emulated on the CPU.
+"""The FP32 filters of the GPU path against the exact predicate, emulated on the CPU: the
+tensor-core filter of the coarse-grid path and the scalar FP32 pair test with its guard band.
 
 The coarse-grid path (d >= 5, float input) classifies pairs from D = x.y - colA, accumulated by
 the tensor cores from TF32 hi/lo splits of the centred rows x and candidates y (three products
@@ -121,3 +122,35 @@ def test_filter_decides_pairs_away_from_eps():
         bb = (a + near * scale).astype(F32)
         acc, rej = _classify(a, bb, c, eps * eps, False, False)
         assert np.all(acc if want_acc else rej)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 8, 16, 64])
+def test_fp32_pair_filter_outside_the_guard_band(d):
+    """The CUDA-core pair test for float input: the FP32 sum of squared differences (fused
+    multiply-add, dimension order) decides a pair when it lies below fl32(eps^2 (1 - 2^-16))
+    (rounded down) or above fl32(eps^2 (1 + 2^-16)) (rounded up); inside that band the FP64
+    sum decides.  Outside the band the FP32 decision must equal the exact predicate."""
+    rng = np.random.default_rng(50 + d)
+    eps = 1.5 * np.sqrt(d / 2.0)
+    eps2 = eps * eps
+    lo32 = F32(eps2 * (1 - 2.0 ** -16))
+    if float(lo32) > eps2 * (1 - 2.0 ** -16):
+        lo32 = np.nextafter(lo32, F32(0))
+    hi32 = F32(eps2 * (1 + 2.0 ** -16))
+    if float(hi32) < eps2 * (1 + 2.0 ** -16):
+        hi32 = np.nextafter(hi32, F32(np.inf))
+    n = 50000
+    a = rng.uniform(-1000, 1000, (n, d))
+    u = rng.normal(size=(n, d))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    delta = rng.choice([-1.0, 1.0], n) * 2.0 ** rng.uniform(-24, -10, n)
+    b = a + u * (eps * (1 + delta))[:, None]
+    a, b = a.astype(F32), b.astype(F32)
+    s = np.zeros(n, F32)
+    for i in range(d):
+        t = (a[:, i] - b[:, i]).astype(F32)
+        s = _fma32(t, t, s)
+    exact = _exact_within(a, b, eps2)
+    assert not np.any((s < lo32) & ~exact)
+    assert not np.any((s > hi32) & exact)
+    assert np.mean((s >= lo32) & (s <= hi32)) < 0.9  # most pairs are decided in FP32
