@@ -1,7 +1,7 @@
 // Host-only dump of the hypercube grids that make_grid builds (no GPU needed) for seeded random
 // extents, eps, d = 1..4 and float / double input; tests/test_host_grid.py checks them.
 //   grid D f32 eps mn_0 mx_0 .. mn_{D-1} mx_{D-1} | rc bin_fp64 inv_side inv_side_f tau ncell_0 ..
-//        key_bits lo32 hi32
+//        key_bits lo32 hi32 box_ok tau_box box_full box_none
 #include <math.h>
 #include <stdio.h>
 
@@ -35,7 +35,8 @@ int main() {
         for (int i = 0; i < D; ++i) printf(" %.17g %.17g", mn[i], mx[i]);
         printf(" | %d %d %.17g %.9g %.17g", rc, g.bin_fp64, g.inv_side, (double)g.inv_side_f, tau);
         for (int i = 0; i < D; ++i) printf(" %u", g.ncell[i]);
-        printf(" %d %.9g %.9g\n", g.key_bits, (double)g.lo32, (double)g.hi32);
+        printf(" %d %.9g %.9g %d %.9g %.9g %.9g\n", g.key_bits, (double)g.lo32, (double)g.hi32, g.box_ok,
+               (double)g.tau_box, (double)g.box_full, (double)g.box_none);
     }
     return 0;
 }

@@ -12,6 +12,9 @@ arithmetic:
   is inside the grid;
 * the FP32 filter thresholds bracket fl64(eps^2) by at least the relative guard band 2^-16.
 
+The cell-box test (box_class) on the same grids: a neighbour cell classified wholly within eps
+of a point (or wholly beyond) holds only points that the exact predicate puts within (beyond).
+
 For the coarse grid of the d >= 5 path (make_coarse_grid, 64 seeded cases): a side of at least
 eps (1 + 2^-50) beyond the binning error, so two points within eps (whose coordinates differ
 by at most eps (1 + 2^-50)) always fall in the same or adjacent coarse cells; checked exactly
@@ -64,7 +67,8 @@ def grids(tmp_path_factory):
         cases.append({"D": D, "f32": f32, "eps": eps, "mn": ext[0::2], "mx": ext[1::2], "rc": rc,
                       "bin64": bin64, "inv": float(t[2]), "inv_f": _f32(t[3]), "tau": float(t[4]),
                       "ncell": [int(x) for x in t[5:5 + D]], "key_bits": int(t[5 + D]),
-                      "lo32": _f32(t[6 + D]), "hi32": _f32(t[7 + D])})
+                      "lo32": _f32(t[6 + D]), "hi32": _f32(t[7 + D]), "box_ok": t[8 + D] == "1",
+                      "tau_box": _f32(t[9 + D]), "box_full": _f32(t[10 + D]), "box_none": _f32(t[11 + D])})
     assert len(cases) == 96
     assert all(c["rc"] == 0 for c in cases)
     return cases
@@ -164,3 +168,78 @@ def test_points_within_eps_land_in_adjacent_coarse_cells(coarse):
             return np.minimum(np.floor((x - mn) * inv), top)
         assert keep.sum() > 100
         assert np.all(np.abs(cells(p[keep]) - cells(q[keep])) <= 1), c
+
+
+def _band32(x, c, i):
+    """The band coordinate as the device's box tests see it (FP32)."""
+    if c["f32"] and not c["bin64"]:
+        return ((x.astype(np.float32) - np.float32(c["mn"][i])).astype(np.float32)
+                * np.float32(c["inv_f"])).astype(np.float32)
+    return ((x.astype(np.float64) - np.float64(c["mn"][i])) * np.float64(c["inv"])).astype(np.float32)
+
+
+def _cell(x, c, i):
+    """The device's cell index of coordinate i (binning in FP32 or FP64, clamped)."""
+    if c["f32"] and not c["bin64"]:
+        t = _band32(x, c, i).astype(np.float64)
+    else:
+        t = (x.astype(np.float64) - np.float64(c["mn"][i])) * np.float64(c["inv"])
+    return np.minimum(np.floor(t), c["ncell"][i] - 1).astype(np.int64)
+
+
+def _box_class(tp, cb, c):
+    """0: the cell is wholly beyond eps of the point, 2: wholly within, 1: undecided."""
+    f = np.float32
+    mn = np.zeros(len(tp), f)
+    mx = np.zeros(len(tp), f)
+    for i in range(tp.shape[1]):
+        lo = (cb[:, i].astype(f) - f(c["tau_box"])).astype(f)
+        hi = ((cb[:, i].astype(f) + f(1.0)).astype(f) + f(c["tau_box"])).astype(f)
+        t = tp[:, i]
+        gap = np.maximum(np.maximum((lo - t).astype(f), (t - hi).astype(f)), f(0))
+        far = np.maximum(np.abs((t - lo).astype(f)), np.abs((t - hi).astype(f)))
+        mn = (gap.astype(np.float64) * gap + mn).astype(f)
+        mx = (far.astype(np.float64) * far + mx).astype(f)
+    return np.where(mn > f(c["box_none"]), 0, np.where(mx < f(c["box_full"]), 2, 1))
+
+
+def test_cell_box_classes_agree_with_exact_predicate(grids):
+    """The cell-box test (a neighbour cell wholly within eps of a point counts whole, one wholly
+    beyond is dropped): for random points and neighbour cells, every point binned into the cell
+    obeys the class the box test gives."""
+    rng = np.random.default_rng(11)
+    dtype_of = {True: np.float32, False: np.float64}
+    n_full = n_none = 0
+    for c in grids:
+        if not c["box_ok"]:
+            continue
+        D, dt = c["D"], dtype_of[c["f32"]]
+        mn, mx = np.array(c["mn"]), np.array(c["mx"])
+        P = 200
+        p = (mn + (mx - mn) * rng.random((P, D))).astype(dt)
+        tp = np.stack([_band32(p[:, i], c, i) for i in range(D)], axis=1)
+        cp = np.stack([_cell(p[:, i], c, i) for i in range(D)], axis=1)
+        cb = cp + rng.integers(-2, 3, (P, D))
+        inside = np.all((cb >= 0) & (cb <= np.array(c["ncell"]) - 1), axis=1)
+        cls = _box_class(tp, cb, c)
+        for k in np.nonzero(inside & (cls != 1))[0]:
+            M = 64
+            frac = rng.random((M, D))
+            frac[:8] = np.where(rng.random((8, D)) < 0.5, 0.0, 1.0 - 1e-9)  # cell faces
+            q = (mn + (cb[k] + frac) / c["inv"]).astype(dt)
+            qc = np.stack([_cell(q[:, i], c, i) for i in range(D)], axis=1)
+            q = q[np.all(qc == cb[k], axis=1)]
+            if len(q) == 0:
+                continue
+            s = np.zeros(len(q))
+            for i in range(D):
+                t = p[k, i].astype(np.float64) - q[:, i].astype(np.float64)
+                s = s + t * t
+            within = s <= c["eps"] * c["eps"]
+            if cls[k] == 2:
+                assert np.all(within), (c, k)
+                n_full += 1
+            else:
+                assert not np.any(within), (c, k)
+                n_none += 1
+    assert n_full > 50 and n_none > 50  # both decisions are exercised
