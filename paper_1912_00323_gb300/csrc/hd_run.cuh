@@ -253,6 +253,7 @@ int run_hd(const RunArgs &a) {
     unsigned long long *mm = (unsigned long long *)(b + o_mm);
     DevCounters *h = a.h_ext ? a.h_ext : host_counters();
     int rc = HCA_OK;
+    bool tc_phases = false;  // the tensor-core split ran every phase
 
     cudaEvent_t ev[HCA_NUM_STAGES + 1] = {};
     const bool timing = (a.flags & HCA_FLAG_TIMING) && a.stats && !a.deferred;
@@ -519,30 +520,31 @@ int run_hd(const RunArgs &a) {
                                         (uint32_t)a.tune.tc_min_labels},
                                        (uint32_t)a.tune.first_links, (uint32_t)a.tune.tc_handoff},
                               mark, launches);
-            goto done_phases;
+            tc_phases = true;
         }
     }
-    // ---- Definition 2: exact counts over the neighbouring coarse cells ----
-    cudaMemsetAsync(hv.cell_core, 0, (size_t)n, s);
-    k_count_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
-    ++launches;
-    mark(6);
-    // (no representative points in this path: every pair of core points is a candidate)
-    mark(7);
-    // ---- Definitions 3-5: first links, pointer jumping, then the remaining unions ----
-    k_uf_init_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
-    k_hook_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
-    for (int r = 0; r < 6; ++r) k_jump_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
-    k_merge_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
-    k_compress_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
-    launches += 10;
-    mark(8);
-    // ---- Algorithm 4: canonical ids, border and noise points ----
-    k_comp_min_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
-    k_labels_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
-    launches += 2;
-    mark(9);
-done_phases:
+    if (!tc_phases) {
+        // ---- Definition 2: exact counts over the neighbouring coarse cells ----
+        cudaMemsetAsync(hv.cell_core, 0, (size_t)n, s);
+        k_count_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
+        ++launches;
+        mark(6);
+        // (no representative points in this path: every pair of core points is a candidate)
+        mark(7);
+        // ---- Definitions 3-5: first links, pointer jumping, then the remaining unions ----
+        k_uf_init_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
+        k_hook_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
+        for (int r = 0; r < 6; ++r) k_jump_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
+        k_merge_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
+        k_compress_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
+        launches += 10;
+        mark(8);
+        // ---- Algorithm 4: canonical ids, border and noise points ----
+        k_comp_min_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
+        k_labels_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
+        launches += 2;
+        mark(9);
+    }
     if (cudaGetLastError() != cudaSuccess) { rc = HCA_ECUDA; goto out; }
     if (cudaMemcpyAsync(h, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s) != cudaSuccess) {
         rc = HCA_ECUDA;
