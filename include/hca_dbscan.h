@@ -223,12 +223,16 @@ HCA_API int hca_radix_sort_pairs(void *d_keys, uint32_t *d_vals, int64_t n, int3
  * The paper has no counterpart: this entry point serves callers that cannot allocate device
  * memory while they run (a fixed memory budget set at start-up, a framework whose allocator
  * owns all device memory, code that must not risk the synchronisation cudaMalloc / cudaFree
- * can cause).  Same arguments, result and stream semantics as hca_radix_sort_pairs.
+ * can cause).  Same arguments and result as hca_radix_sort_pairs.
  *   n  at most HCA_SORT_NOALLOC_MAX_PAIRS (2^18); larger n returns HCA_ETOOLARGE.
- * Scratch: a fixed array of about 3.3 MiB inside the library (a __device__ variable), held on
- * every GPU that loads the library until the process exits.  The first call on a device looks
- * up that array's device address (cudaGetSymbolAddress) and caches it; make that first call
- * before any stream capture.  Calls no cudaMalloc, cudaFree or other allocating routine.
+ * Scratch: a fixed array of about 3.2 MiB inside the library (a __device__ variable: the
+ * alternate keys and values of 2^18 pairs plus the sort's look-back words), held on every GPU
+ * that loads the library until the process exits.  The first call in a CUDA context of a
+ * device looks up that array's device address (cudaGetSymbolAddress) and caches it for that
+ * context; make that first call before any stream capture.  A cudaDeviceReset ends the
+ * context, and the next call looks the address up again.  Calls no cudaMalloc, cudaFree or
+ * other allocating routine.  Synchronous: the call reads the sort's status word back and
+ * returns after the sort is complete on `stream`.
  * Every call uses the same array: calls whose work overlaps on the GPU (other streams, other
  * threads, without ordering between them) race and give wrong results; order them.  A call
  * leaves its scratch contents behind; none of them is read by the next call.

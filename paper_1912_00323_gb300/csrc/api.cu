@@ -232,22 +232,20 @@ extern "C" int hca_radix_sort_pairs(void *d_keys, uint32_t *d_vals, int64_t n, i
     if (n <= 1) return HCA_OK;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t hist = sort_hist_size(n);
-    const int64_t scan_max = n > (int64_t)hist ? n : (int64_t)hist;
-    const size_t bytes = (size_t)n * key_bytes + (size_t)n * 4 + 4 * hist + 4 * scan_partials_size(scan_max) + 1024;
+    const size_t bytes = (size_t)n * key_bytes + (size_t)n * 4 + 4 * hist + 512;
     void *ws = nullptr;
     if (pool_alloc(&ws, bytes, s) != cudaSuccess) return HCA_ENOMEM;
     char *b = (char *)ws;
     void *kalt = b;
     uint32_t *valt = (uint32_t *)(b + (((size_t)n * key_bytes + 255) & ~(size_t)255));
     uint32_t *h = (uint32_t *)((char *)valt + (((size_t)n * 4 + 255) & ~(size_t)255));
-    uint32_t *part = h + ((hist + 63) & ~(size_t)63);
     bool flipped;
     if (key_bytes == 4)
         flipped = radix_sort_pairs<uint32_t>((uint32_t *)d_keys, d_vals, (uint32_t *)kalt, valt, n,
-                                             begin_bit, end_bit, h, part, s, nullptr);
+                                             begin_bit, end_bit, h, nullptr, s, nullptr);
     else
         flipped = radix_sort_pairs<uint64_t>((uint64_t *)d_keys, d_vals, (uint64_t *)kalt, valt, n,
-                                             begin_bit, end_bit, h, part, s, nullptr);
+                                             begin_bit, end_bit, h, nullptr, s, nullptr);
     int rc = HCA_OK;
     if (flipped) {
         if (cudaMemcpyAsync(d_keys, kalt, (size_t)n * key_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||

@@ -110,12 +110,27 @@ size_t scan_partials_size(int64_t m_max);
 void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t m_max, const uint32_t *m_dev,
                         uint32_t *total, uint32_t *partials, cudaStream_t s, int *launches);
 
+// Geometry of the onesweep radix sort (sort.cu): keys per tile, digits per pass, and the
+// most passes a call can make.  The scratch of a sort of n pairs is sort_hist_elems(n)
+// uint32: two words per tile and digit for the look-back, the digit counts of every pass,
+// one ticket per pass and a status word.
+constexpr int kSortTileKeys = 4096;
+constexpr int kSortRadix = 256;
+constexpr int kSortMaxPasses = 8;
+constexpr int64_t sort_tiles_for(int64_t n) {
+    return n <= kSortTileKeys ? 1 : (n + kSortTileKeys - 1) / kSortTileKeys;
+}
+constexpr size_t sort_hist_elems(int64_t n) {
+    return (size_t)(2 * sort_tiles_for(n) * kSortRadix + kSortMaxPasses * kSortRadix + kSortMaxPasses + 2);
+}
+
 // LSD radix sort of (key, value) pairs by bits [begin_bit, end_bit), 8 bits per pass.
 // Ping-pongs between (keys, vals) and (keys_alt, vals_alt); returns true when the sorted
 // result ends up in the alternate buffers.  hist: sort_hist_size(n) uint32 of scratch
 // (8-byte aligned; cleared by the sort itself).  A bounded look-back wait that ran out sets
 // bit 2 of *err_out (device word; NULL: the status word inside hist, sort_status_word).
-size_t sort_hist_size(int64_t n);
+// `partials` is not used by the sort (callers may pass NULL).
+inline size_t sort_hist_size(int64_t n) { return sort_hist_elems(n); }
 uint32_t *sort_status_word(uint32_t *hist, int64_t n);
 // digit_counts (optional, device): counts of every 8-bit digit of every pass, [pass][256],
 // already computed by the caller.

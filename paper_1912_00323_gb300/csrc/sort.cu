@@ -27,8 +27,9 @@ constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 16;  // per lane: a warp covers 512 consecutive keys
 constexpr int kSortTile = kSortThreads * kSortItems;
-constexpr int kRadix = 256;
-constexpr int kMaxPasses = 8;
+constexpr int kRadix = kSortRadix;
+constexpr int kMaxPasses = kSortMaxPasses;
+static_assert(kSortTile == kSortTileKeys, "tile size shared with the scratch sizing");
 constexpr uint32_t kSpinLimit = 1u << 24;
 constexpr uint64_t kStateAgg = 1, kStatePrefix = 2;
 
@@ -178,18 +179,9 @@ constexpr size_t pass_smem() {
     return sizeof(uint32_t) * (kSortWarps * kRadix + 2 * kRadix + 4) + (sizeof(K) + sizeof(uint32_t)) * kSortTile;
 }
 
-int64_t sort_tiles(int64_t n) {
-    const int64_t nb = (n + kSortTile - 1) / kSortTile;
-    return nb < 1 ? 1 : nb;
-}
+int64_t sort_tiles(int64_t n) { return sort_tiles_for(n); }
 
 }  // namespace
-
-size_t sort_hist_size(int64_t n) {
-    // look-back words (two 32-bit halves per tile and digit), digit counts of every pass,
-    // pass tickets and a status word
-    return (size_t)(2 * sort_tiles(n) * kRadix + kMaxPasses * kRadix + kMaxPasses + 2);
-}
 
 uint32_t *sort_status_word(uint32_t *hist, int64_t n) {
     return hist + 2 * sort_tiles(n) * kRadix + kMaxPasses * kRadix + kMaxPasses;

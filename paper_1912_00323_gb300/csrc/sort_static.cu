@@ -7,9 +7,13 @@
 // entry point takes the caller's keys and values and uses only the array below.
 //
 // The array is a file-scope __device__ variable: every GPU on which the library is loaded
-// holds its HCA_SORT_NOALLOC_MAX_PAIRS * 12 bytes (plus look-back space, about 3.3 MiB in all)
-// until the process exits.  In host code its name is only a stand-in: the device address is
-// looked up once per device with cudaGetSymbolAddress, by the first call on that device.
+// holds it until the process exits.  Its size follows the sort's own geometry: the
+// alternate keys and values of HCA_SORT_NOALLOC_MAX_PAIRS pairs (12 bytes each, 3 MiB) and
+// the look-back words, digit counts, tickets and status word of that many pairs (about
+// 136 KiB with 4096-key tiles).  In host code its name is only a stand-in: its device address
+// is looked up with cudaGetSymbolAddress, with the device current, the first time a call
+// runs in a CUDA context of that device (normally once per device; again after
+// cudaDeviceReset, which destroys the context the cached address belongs to).
 #include <mutex>
 
 #include "hca_internal.cuh"
@@ -19,32 +23,65 @@ namespace {
 
 constexpr int64_t kMaxPairs = HCA_SORT_NOALLOC_MAX_PAIRS;
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-// sort scratch words for kMaxPairs: look-back words (2 per 2048-key tile and digit), digit
-// counts of up to 8 passes, tickets and a status word
-constexpr size_t kHistElems = 2 * ((kMaxPairs + 2047) / 2048) * 256 + 8 * 256 + 10;
-constexpr size_t kPartElems = ((kMaxPairs > (int64_t)kHistElems ? kMaxPairs : (int64_t)kHistElems) + 2047) / 2048 + 2;
+constexpr size_t kHistElems = sort_hist_elems(kMaxPairs);
 constexpr size_t kOffVals = align256(sizeof(uint64_t) * kMaxPairs);
 constexpr size_t kOffHist = kOffVals + align256(sizeof(uint32_t) * kMaxPairs);
-constexpr size_t kOffPart = kOffHist + align256(sizeof(uint32_t) * kHistElems);
-constexpr size_t kScratchBytes = kOffPart + align256(sizeof(uint32_t) * kPartElems);
+constexpr size_t kScratchBytes = kOffHist + align256(sizeof(uint32_t) * kHistElems);
 
 __device__ __align__(256) unsigned char g_sort_scratch[kScratchBytes];
 
+// The unique id of the calling thread's current CUDA context (0 when none is current or the
+// driver does not provide the query).  Driver entry points are found through the runtime, so
+// the library does not link the driver library itself.
+typedef int (*ctx_get_current_t)(void **);
+typedef int (*ctx_get_id_t)(void *, unsigned long long *);
+
+unsigned long long current_context_id() {
+    static ctx_get_current_t get_current = nullptr;
+    static ctx_get_id_t get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = (ctx_get_current_t)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (ctx_get_id_t)f;
+    });
+    if (!get_current || !get_id) return 0;
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void *g_scratch_addr[kMaxDevices] = {};
+struct ScratchSlot {
+    unsigned long long ctx_id;
+    void *addr;
+};
+ScratchSlot g_slot[kMaxDevices] = {};
 
-// Device address of g_sort_scratch on the current device (looked up once per device).
+// Device address of g_sort_scratch in the current context of the current device.  The
+// look-up runs once per context; a context whose id cannot be read is looked up every call.
 int scratch_address(void **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HCA_ECUDA;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[dev]) {
+    unsigned long long id = current_context_id();
+    ScratchSlot &slot = g_slot[dev];
+    if (id == 0 || slot.ctx_id != id || !slot.addr) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_sort_scratch) != cudaSuccess || !p) return HCA_ECUDA;
-        g_scratch_addr[dev] = p;
+        if (id == 0) id = current_context_id();  // the look-up may have created the context
+        slot.ctx_id = id;
+        slot.addr = p;
     }
-    *out = g_scratch_addr[dev];
+    *out = slot.addr;
     return HCA_OK;
 }
 
@@ -63,10 +100,7 @@ extern "C" int hca_radix_sort_pairs_noalloc(void *d_keys, uint32_t *d_vals, int6
     if (n > 0 && (!d_keys || !d_vals)) return HCA_EINVAL;
     if (((uintptr_t)d_keys) % key_bytes || ((uintptr_t)d_vals) % 4) return HCA_EINVAL;
     if (n <= 1) return HCA_OK;
-    const size_t hist_need = sort_hist_size(n);
-    if (hist_need > kHistElems ||
-        scan_partials_size(n > (int64_t)hist_need ? n : (int64_t)hist_need) > kPartElems)
-        return HCA_ETOOLARGE;
+    if (sort_hist_size(n) > kHistElems) return HCA_ETOOLARGE;
     void *base = nullptr;
     int rc = scratch_address(&base);
     if (rc) return rc;
@@ -74,23 +108,23 @@ extern "C" int hca_radix_sort_pairs_noalloc(void *d_keys, uint32_t *d_vals, int6
     char *b = (char *)base;
     uint32_t *valt = (uint32_t *)(b + kOffVals);
     uint32_t *hist = (uint32_t *)(b + kOffHist);
-    uint32_t *part = (uint32_t *)(b + kOffPart);
     // The sort clears its counters, tickets and look-back words itself at the start of every
     // call; every other scratch word is written before it is read, so nothing left by an
     // earlier call is used.
     bool flipped;
     if (key_bytes == 4)
         flipped = radix_sort_pairs<uint32_t>((uint32_t *)d_keys, d_vals, (uint32_t *)b, valt, n,
-                                             begin_bit, end_bit, hist, part, s, nullptr);
+                                             begin_bit, end_bit, hist, nullptr, s, nullptr);
     else
         flipped = radix_sort_pairs<uint64_t>((uint64_t *)d_keys, d_vals, (uint64_t *)b, valt, n,
-                                             begin_bit, end_bit, hist, part, s, nullptr);
+                                             begin_bit, end_bit, hist, nullptr, s, nullptr);
     rc = HCA_OK;
     if (flipped) {
         if (cudaMemcpyAsync(d_keys, b, (size_t)n * key_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
             cudaMemcpyAsync(d_vals, valt, (size_t)n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             rc = HCA_ECUDA;
     }
+    // the look-back status word is read back, so every call waits for its sort on `stream`
     uint32_t status = 0;
     if (cudaMemcpyAsync(&status, sort_status_word(hist, n), sizeof(status), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         rc = HCA_ECUDA;

@@ -54,6 +54,29 @@ def test_noalloc_sort_matches_allocating_sort_twice(env, kbytes, bits):
         assert torch.equal(v1, v2), f"values differ on call {call}"
 
 
+@pytest.mark.parametrize("kbytes,bits", [(4, (0, 32)), (8, (3, 50))])
+def test_noalloc_sort_matches_numpy_stable_argsort(env, kbytes, bits):
+    """Independent of the allocating sort: numpy's stable argsort of the keys masked to bits
+    [begin, end) fixes the permutation, so keys and values must match it exactly."""
+    torch, pkg, noalloc = env
+    stream = torch.cuda.current_stream().cuda_stream
+    n = 200_003
+    k, v = _inputs(torch, n, kbytes, 7 + kbytes)
+    kh = k.cpu().numpy().view(np.uint32 if kbytes == 4 else np.uint64)
+    vh = v.cpu().numpy().view(np.uint32)
+    lo, hi = bits
+    mask = (1 << (hi - lo)) - 1
+    digit = (kh.astype(np.uint64) >> np.uint64(lo)) & np.uint64(mask)
+    order = np.argsort(digit, kind="stable")
+    rc = noalloc(k.data_ptr(), v.data_ptr(), n, kbytes, lo, hi, stream)
+    assert rc == 0, pkg.hca_strerror(rc)
+    torch.cuda.synchronize()
+    got_k = k.cpu().numpy().view(kh.dtype)
+    got_v = v.cpu().numpy().view(np.uint32)
+    assert np.array_equal(got_k, kh[order])
+    assert np.array_equal(got_v, vh[order])
+
+
 def test_noalloc_sort_rejects_more_than_its_scratch(env):
     torch, pkg, noalloc = env
     k = torch.zeros(MAX_PAIRS + 1, dtype=torch.int32, device="cuda")
