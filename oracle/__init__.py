@@ -7,7 +7,9 @@ does.  Everything here computes in IEEE double precision.
 
 Functions (numpy in, numpy out):
   bruteforce(X, eps, min_pts, threads)  DBSCAN from Definitions 1-5 of the supplement, O(n^2)
-  grid(X, eps, min_pts)                 HCA-DBSCAN with DBSCAN semantics (Sec. 2, Alg. 1-4)
+  grid(X, eps, min_pts, threads)        HCA-DBSCAN with DBSCAN semantics (Sec. 2, Alg. 1-4);
+                                        threads > 1 shares the counts, merging and border
+                                        points among host threads (same result)
   literal(X, eps)                       Alg. 2-4 as printed (representative points only)
   stencil_count(d, rule, side, eps)     neighbour hypercube counts (Sec. 2)
   rep_dirs(d)                           the 3^d - 1 representative directions (Sec. 2)
@@ -46,6 +48,8 @@ def _bind(lib):
                                           ctypes.c_int32, ctypes.c_int32, i32p, u8p]
     lib.hca_oracle_grid.argtypes = [dp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
                                     ctypes.c_int32, i32p, u8p]
+    lib.hca_oracle_grid_mt.argtypes = [dp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
+                                       ctypes.c_int32, ctypes.c_int32, i32p, u8p]
     lib.hca_oracle_literal.argtypes = [dp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, i32p]
     lib.hca_oracle_stencil_count.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                              ctypes.c_double]
@@ -53,7 +57,7 @@ def _bind(lib):
     lib.hca_oracle_rep_dirs.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int8)]
     lib.hca_oracle_rep_dirs.restype = ctypes.c_int64
     lib.hca_oracle_grid_cells.argtypes = [dp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, i64p]
-    for f in (lib.hca_oracle_bruteforce, lib.hca_oracle_grid, lib.hca_oracle_literal,
+    for f in (lib.hca_oracle_bruteforce, lib.hca_oracle_grid, lib.hca_oracle_grid_mt, lib.hca_oracle_literal,
               lib.hca_oracle_grid_cells):
         f.restype = ctypes.c_int
     return lib
@@ -117,14 +121,20 @@ def bruteforce(X, eps: float, min_pts: int, threads: int = 0, lib=None):
     return labels, core
 
 
-def grid(X, eps: float, min_pts: int, lib=None):
+def grid(X, eps: float, min_pts: int, threads: int = 1, lib=None):
+    """threads: host threads (0 = every core); 1 runs hca_oracle_grid itself."""
     lib = lib or _load()
     X = _prep(X)
     n, d = X.shape
     labels = np.empty(n, np.int32)
     core = np.empty(n, np.uint8)
-    rc = lib.hca_oracle_grid(_ptr(X, ctypes.c_double), n, d, float(eps), int(min_pts),
-                             _ptr(labels, ctypes.c_int32), _ptr(core, ctypes.c_uint8))
+    threads = threads or os.cpu_count() or 1
+    if threads == 1:
+        rc = lib.hca_oracle_grid(_ptr(X, ctypes.c_double), n, d, float(eps), int(min_pts),
+                                 _ptr(labels, ctypes.c_int32), _ptr(core, ctypes.c_uint8))
+    else:
+        rc = lib.hca_oracle_grid_mt(_ptr(X, ctypes.c_double), n, d, float(eps), int(min_pts),
+                                    int(threads), _ptr(labels, ctypes.c_int32), _ptr(core, ctypes.c_uint8))
     _check(rc, "hca_oracle_grid")
     return labels, core
 
@@ -172,8 +182,8 @@ class _Bound:
     def bruteforce(self, X, eps, min_pts, threads=0):
         return bruteforce(X, eps, min_pts, threads, lib=self._lib)
 
-    def grid(self, X, eps, min_pts):
-        return grid(X, eps, min_pts, lib=self._lib)
+    def grid(self, X, eps, min_pts, threads=1):
+        return grid(X, eps, min_pts, threads, lib=self._lib)
 
     def literal(self, X, eps):
         return literal(X, eps, lib=self._lib)

@@ -30,6 +30,7 @@
  *                           side eps/sqrt(d)), Algorithm 2 (representative points),
  *                           Algorithm 3 / 4 (merging neighbouring hypercubes), with MINPTS
  *                           handled by dense hypercubes and exact counts.
+ *   hca_oracle_grid_mt      the same on several host threads (same result).
  *   hca_oracle_literal      Algorithms 2-4 as printed: representative points only, strict
  *                           "<", no MINPTS.  An ablation, not an authority.
  *   hca_oracle_stencil_count  number of neighbour hypercubes under three rules (Sec. 2).
@@ -38,6 +39,7 @@
  */
 #include <math.h>
 #include <pthread.h>
+#include <stdatomic.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -496,6 +498,244 @@ static int64_t dir_index(const int64_t *delta, int d)
 
 #define STENCIL_MAX_D 4
 
+/* Everything the threads of one hca_oracle_grid call share.  Each phase hands out its items
+ * (cells or points) in chunks from the counter `next`; a thread writes only the slots of the
+ * items it took (core flags in the count phase, labels in the border phase), so the threads
+ * never write the same memory. */
+typedef struct {
+    const double *X;
+    int64_t n;
+    int d;
+    double eps2;
+    int min_pts;
+    const grid_t *g;
+    int use_stencil;
+    const int64_t *offs;        /* stencil offsets, noff rows of d (d <= 4) */
+    int64_t noff;
+    const int64_t *xorder;      /* points sorted by x_0, ties by index (d > 4) */
+    const int64_t *pos;         /* position of each point in xorder */
+    double win;                 /* window of the leading-dimension sweep */
+    uint8_t *core;              /* count phase output */
+    const uint8_t *cell_core;   /* cells holding a core point */
+    const int64_t *rep;         /* representative points, ndir per cell (stencil path) */
+    int64_t ndir;
+    const int64_t *cell_label;  /* border phase: canonical id of each cell's cluster, or INT64_MAX */
+    int32_t *labels;            /* border phase output */
+    int64_t items, chunk;       /* the current phase's items and chunk size */
+    _Atomic int64_t next;       /* next unclaimed item of the current phase */
+} grid_ctx;
+
+typedef struct {
+    grid_ctx *c;
+    int rc;
+    int64_t *edges;             /* merge phase: cell pairs joined by this thread's union-find */
+    int64_t nedge, cap;
+} grid_job;
+
+static int claim(grid_ctx *c, int64_t *lo, int64_t *hi)
+{
+    int64_t a = atomic_fetch_add(&c->next, c->chunk);
+    if (a >= c->items) return 0;
+    *lo = a;
+    *hi = a + c->chunk < c->items ? a + c->chunk : c->items;
+    return 1;
+}
+
+/* Run fn on `threads` threads (the calling thread included) over c->items items. */
+static void run_phase(void *(*fn)(void *), grid_ctx *c, grid_job *jobs, int threads, int64_t items,
+                      int64_t chunk)
+{
+    c->items = items;
+    c->chunk = chunk < 1 ? 1 : chunk;
+    atomic_store(&c->next, 0);
+    pthread_t tid[256];
+    int started[256];
+    for (int t = 1; t < threads; ++t) started[t] = pthread_create(&tid[t], NULL, fn, &jobs[t]) == 0;
+    fn(&jobs[0]);
+    for (int t = 1; t < threads; ++t) {
+        if (started[t]) pthread_join(tid[t], NULL);
+        else fn(&jobs[t]); /* the counter is shared, so a thread that failed to start just runs late */
+    }
+}
+
+/* MINPTS (Definition 2): a cube with at least MINPTS points is dense, and every point in it
+ * is core; a point of another cube is counted exactly over its own cube (all within eps, the
+ * diagonal is at most eps) and the neighbour cubes.  The count stops once it reaches MINPTS:
+ * core(p) needs only |N_eps(p)| >= MINPTS. */
+static void *grid_count_worker(void *arg)
+{
+    grid_job *j = (grid_job *)arg;
+    grid_ctx *c = j->c;
+    const grid_t *g = c->g;
+    const int d = c->d;
+    const double *X = c->X;
+    int64_t coord[STENCIL_MAX_D];
+    int64_t lo, hi;
+    while (claim(c, &lo, &hi)) {
+        for (int64_t cell = lo; cell < hi; ++cell) {
+            int64_t f = g->cell_first[cell], l = g->cell_first[cell + 1];
+            int dense = (l - f) >= c->min_pts;
+            for (int64_t k = f; k < l; ++k) {
+                int64_t p = g->order[k];
+                if (dense) { c->core[p] = 1; continue; }
+                int64_t cnt = l - f; /* own cube: every point within eps (diagonal <= eps) */
+                if (c->use_stencil) {
+                    const int64_t *cp = g->cc + p * d;
+                    for (int64_t o = 0; o < c->noff && cnt < c->min_pts; ++o) {
+                        for (int i = 0; i < d; ++i) coord[i] = cp[i] + c->offs[o * d + i];
+                        int64_t nb = grid_lookup(g, coord);
+                        if (nb < 0) continue;
+                        for (int64_t kk = g->cell_first[nb]; kk < g->cell_first[nb + 1]; ++kk)
+                            cnt += le_eps(X + p * d, X + g->order[kk] * d, d, c->eps2);
+                    }
+                } else {
+                    int64_t pos = c->pos[p];
+                    for (int dir = -1; dir <= 1 && cnt < c->min_pts; dir += 2) {
+                        for (int64_t k2 = pos + dir; k2 >= 0 && k2 < c->n && cnt < c->min_pts; k2 += dir) {
+                            int64_t q = c->xorder[k2];
+                            if (fabs(X[q * d] - X[p * d]) > c->win) break;
+                            if (g->cell_of[q] == cell) continue; /* counted above */
+                            cnt += le_eps(X + p * d, X + q * d, d, c->eps2);
+                        }
+                    }
+                }
+                c->core[p] = cnt >= c->min_pts;
+            }
+        }
+    }
+    return NULL;
+}
+
+static int push_edge(grid_job *j, int64_t a, int64_t b)
+{
+    if (j->nedge == j->cap) {
+        int64_t cap = j->cap ? 2 * j->cap : 1024;
+        int64_t *e = (int64_t *)realloc(j->edges, sizeof(int64_t) * 2 * cap);
+        if (!e) return ORACLE_ENOMEM;
+        j->edges = e;
+        j->cap = cap;
+    }
+    j->edges[2 * j->nedge] = a;
+    j->edges[2 * j->nedge + 1] = b;
+    ++j->nedge;
+    return 0;
+}
+
+/* Algorithm 3 over the items this thread takes: two neighbouring cubes that both hold core
+ * points are joined iff some core point of one lies within eps of some core point of the
+ * other.  Each thread keeps its own union-find over the cubes and records every pair it
+ * joins; a pair whose cubes its union-find already connects adds nothing to the components
+ * and is skipped.  The recorded pairs of all threads span the same components as all pairs,
+ * and are joined into one union-find afterwards. */
+static void *grid_merge_worker(void *arg)
+{
+    grid_job *j = (grid_job *)arg;
+    grid_ctx *c = j->c;
+    const grid_t *g = c->g;
+    const int d = c->d;
+    const double *X = c->X;
+    int64_t *parent = (int64_t *)malloc(sizeof(int64_t) * g->ncell);
+    if (!parent) { j->rc = ORACLE_ENOMEM; return NULL; }
+    for (int64_t cell = 0; cell < g->ncell; ++cell) parent[cell] = cell;
+    int64_t coord[STENCIL_MAX_D];
+    int64_t lo, hi;
+    while (claim(c, &lo, &hi) && j->rc == 0) {
+        if (c->use_stencil) {
+            for (int64_t a = lo; a < hi; ++a) {
+                if (!c->cell_core[a]) continue;
+                const int64_t *ca = grid_cell_coord(g, a);
+                for (int64_t o = 0; o < c->noff; ++o) {
+                    for (int i = 0; i < d; ++i) coord[i] = ca[i] + c->offs[o * d + i];
+                    int64_t b = grid_lookup(g, coord);
+                    if (b <= a || !c->cell_core[b]) continue; /* each unordered pair once */
+                    if (uf_find(parent, a) == uf_find(parent, b)) continue;
+                    int64_t di = dir_index(c->offs + o * d, d);
+                    int64_t ra = c->rep[a * c->ndir + di], rb = c->rep[b * c->ndir + (c->ndir - 1 - di)];
+                    int found = le_eps(X + ra * d, X + rb * d, d, c->eps2);
+                    for (int64_t i = g->cell_first[a]; i < g->cell_first[a + 1] && !found; ++i) {
+                        int64_t p = g->order[i];
+                        if (!c->core[p]) continue;
+                        for (int64_t k = g->cell_first[b]; k < g->cell_first[b + 1] && !found; ++k) {
+                            int64_t q = g->order[k];
+                            if (c->core[q] && le_eps(X + p * d, X + q * d, d, c->eps2)) found = 1;
+                        }
+                    }
+                    if (found) {
+                        uf_union(parent, a, b);
+                        if (push_edge(j, a, b)) { j->rc = ORACLE_ENOMEM; break; }
+                    }
+                }
+            }
+        } else {
+            /* leading-dimension sweep: every pair within the window is met from the point
+             * that comes first in xorder, so scanning forward sees each pair once */
+            for (int64_t p = lo; p < hi; ++p) {
+                if (!c->core[p]) continue;
+                int64_t cp = g->cell_of[p];
+                for (int64_t k2 = c->pos[p] + 1; k2 < c->n; ++k2) {
+                    int64_t q = c->xorder[k2];
+                    if (fabs(X[q * d] - X[p * d]) > c->win) break;
+                    if (!c->core[q] || g->cell_of[q] == cp) continue;
+                    if (uf_find(parent, cp) == uf_find(parent, g->cell_of[q])) continue;
+                    if (le_eps(X + p * d, X + q * d, d, c->eps2)) {
+                        uf_union(parent, cp, g->cell_of[q]);
+                        if (push_edge(j, cp, g->cell_of[q])) { j->rc = ORACLE_ENOMEM; break; }
+                    }
+                }
+            }
+        }
+    }
+    free(parent);
+    return NULL;
+}
+
+/* Algorithm 4, non-core points: the smallest id among the clusters of the core points
+ * within eps (own cube first: all of its points are within eps), else noise. */
+static void *grid_border_worker(void *arg)
+{
+    grid_job *j = (grid_job *)arg;
+    grid_ctx *c = j->c;
+    const grid_t *g = c->g;
+    const int d = c->d;
+    const double *X = c->X;
+    int64_t coord[STENCIL_MAX_D];
+    int64_t lo, hi;
+    while (claim(c, &lo, &hi)) {
+        for (int64_t p = lo; p < hi; ++p) {
+            if (c->core[p]) continue;
+            int64_t own = g->cell_of[p];
+            int64_t best = c->cell_label[own];
+            if (c->use_stencil) {
+                const int64_t *cp = g->cc + p * d;
+                for (int64_t o = 0; o < c->noff; ++o) {
+                    for (int i = 0; i < d; ++i) coord[i] = cp[i] + c->offs[o * d + i];
+                    int64_t nb = grid_lookup(g, coord);
+                    if (nb < 0 || !c->cell_core[nb]) continue;
+                    int64_t lab = c->cell_label[nb];
+                    if (lab >= best) continue;
+                    for (int64_t kk = g->cell_first[nb]; kk < g->cell_first[nb + 1]; ++kk) {
+                        int64_t q = g->order[kk];
+                        if (c->core[q] && le_eps(X + p * d, X + q * d, d, c->eps2)) { best = lab; break; }
+                    }
+                }
+            } else {
+                int64_t pos = c->pos[p];
+                for (int dir = -1; dir <= 1; dir += 2) {
+                    for (int64_t k2 = pos + dir; k2 >= 0 && k2 < c->n; k2 += dir) {
+                        int64_t q = c->xorder[k2];
+                        if (fabs(X[q * d] - X[p * d]) > c->win) break;
+                        if (!c->core[q]) continue;
+                        int64_t lab = c->cell_label[g->cell_of[q]];
+                        if (lab < best && le_eps(X + p * d, X + q * d, d, c->eps2)) best = lab;
+                    }
+                }
+            }
+            c->labels[p] = best == INT64_MAX ? -1 : (int32_t)best;
+        }
+    }
+    return NULL;
+}
+
 /*
  * Steps, in the paper's order:
  *  Alg. 1   hypercubes of side eps/sqrt(d) (shrunk, see oracle_side) from the shifted
@@ -516,12 +756,17 @@ static int64_t dir_index(const int64_t *delta, int d)
  * for d > 4, or when a band index would exceed 1e7 (where the rounding bound of the band
  * computation no longer holds), the neighbours of a point are found with the leading-
  * dimension pre-sort of Sec. 2: points sorted by coordinate 0, window |x_0 - y_0| <= eps.
+ * `threads` host threads share the counts, the merging and the border points; the result
+ * does not depend on their number (the representative points and the joining of the
+ * threads' merged pairs run on one thread).
  */
-int hca_oracle_grid(const double *X, int64_t n, int32_t d, double eps, int32_t min_pts,
-                    int32_t *labels, uint8_t *core_out)
+int hca_oracle_grid_mt(const double *X, int64_t n, int32_t d, double eps, int32_t min_pts,
+                       int32_t threads, int32_t *labels, uint8_t *core_out)
 {
     int rc = check_args(X, n, d, eps, min_pts, labels);
     if (rc) return rc;
+    if (threads < 1) threads = 1;
+    if (threads > 256) threads = 256;
     if (n == 0) return 0;
     const double eps2 = eps * eps;
     const double side = oracle_side(eps, d);
@@ -537,13 +782,15 @@ int hca_oracle_grid(const double *X, int64_t n, int32_t d, double eps, int32_t m
     uint8_t *cell_core = (uint8_t *)calloc(g.ncell, 1);
     int64_t *parent = (int64_t *)malloc(sizeof(int64_t) * g.ncell);
     int64_t *comp_min = (int64_t *)malloc(sizeof(int64_t) * g.ncell);
+    int64_t *cell_label = (int64_t *)malloc(sizeof(int64_t) * g.ncell);
+    grid_job *jobs = (grid_job *)calloc(threads, sizeof(grid_job));
+    grid_ctx *ctx = (grid_ctx *)calloc(1, sizeof(grid_ctx));
     int64_t *offs = NULL, noff = 0;
     int64_t *xorder = NULL, *tmp = NULL;
-    int64_t *coord = (int64_t *)malloc(sizeof(int64_t) * d);
     int8_t *dirs = NULL;
     int64_t *rep = NULL;
     rc = ORACLE_ENOMEM;
-    if (!core || !cell_core || !parent || !comp_min || !coord) goto done;
+    if (!core || !cell_core || !parent || !comp_min || !cell_label || !jobs || !ctx) goto done;
 
     if (use_stencil) {
         noff = enum_offsets(d, 2, side, eps, NULL);
@@ -556,7 +803,6 @@ int hca_oracle_grid(const double *X, int64_t n, int32_t d, double eps, int32_t m
         tmp = (int64_t *)malloc(sizeof(int64_t) * n);
         int64_t *key = (int64_t *)malloc(sizeof(int64_t) * n);
         if (!xorder || !tmp || !key) { free(key); goto done; }
-        /* rank points by x_0 through an int64 rank of the double order */
         for (int64_t p = 0; p < n; ++p) xorder[p] = p;
         /* simple merge sort on x_0 with an explicit comparator */
         {
@@ -579,39 +825,15 @@ int hca_oracle_grid(const double *X, int64_t n, int32_t d, double eps, int32_t m
         free(tmp);
         tmp = key; /* tmp now holds the position of each point in xorder */
     }
-    const double win = eps * (1.0 + 1e-9);
+
+    ctx->X = X; ctx->n = n; ctx->d = d; ctx->eps2 = eps2; ctx->min_pts = min_pts;
+    ctx->g = &g; ctx->use_stencil = use_stencil; ctx->offs = offs; ctx->noff = noff;
+    ctx->xorder = xorder; ctx->pos = tmp; ctx->win = eps * (1.0 + 1e-9);
+    ctx->core = core; ctx->cell_core = cell_core; ctx->cell_label = cell_label; ctx->labels = labels;
+    for (int t = 0; t < threads; ++t) jobs[t].c = ctx;
 
     /* ---- MINPTS: dense cubes, then exact counts for the other cubes' points ---- */
-    for (int64_t cell = 0; cell < g.ncell; ++cell) {
-        int64_t f = g.cell_first[cell], l = g.cell_first[cell + 1];
-        int dense = (l - f) >= min_pts;
-        for (int64_t k = f; k < l; ++k) {
-            int64_t p = g.order[k];
-            if (dense) { core[p] = 1; continue; }
-            int64_t cnt = l - f; /* own cube: every point within eps (diagonal <= eps) */
-            if (use_stencil) {
-                const int64_t *c = g.cc + p * d;
-                for (int64_t o = 0; o < noff && cnt < min_pts; ++o) {
-                    for (int i = 0; i < d; ++i) coord[i] = c[i] + offs[o * d + i];
-                    int64_t nb = grid_lookup(&g, coord);
-                    if (nb < 0) continue;
-                    for (int64_t kk = g.cell_first[nb]; kk < g.cell_first[nb + 1]; ++kk)
-                        cnt += le_eps(X + p * d, X + g.order[kk] * d, d, eps2);
-                }
-            } else {
-                int64_t pos = tmp[p];
-                for (int dir = -1; dir <= 1; dir += 2) {
-                    for (int64_t k2 = pos + dir; k2 >= 0 && k2 < n; k2 += dir) {
-                        int64_t q = xorder[k2];
-                        if (fabs(X[q * d] - X[p * d]) > win) break;
-                        if (g.cell_of[q] == cell) continue; /* counted above */
-                        cnt += le_eps(X + p * d, X + q * d, d, eps2);
-                    }
-                }
-            }
-            core[p] = cnt >= min_pts;
-        }
-    }
+    run_phase(grid_count_worker, ctx, jobs, threads, g.ncell, 64);
     for (int64_t p = 0; p < n; ++p)
         if (core[p]) cell_core[g.cell_of[p]] = 1;
 
@@ -625,52 +847,16 @@ int hca_oracle_grid(const double *X, int64_t n, int32_t d, double eps, int32_t m
         rep = compute_reps(&g, X, core, dirs, ndir);
         if (!rep) goto done;
     }
+    ctx->rep = rep;
+    ctx->ndir = ndir;
 
     /* ---- Alg. 3: merge neighbouring cubes that hold core points ---- */
+    run_phase(grid_merge_worker, ctx, jobs, threads, use_stencil ? g.ncell : n, use_stencil ? 64 : 256);
     for (int64_t cell = 0; cell < g.ncell; ++cell) parent[cell] = cell;
-    if (use_stencil) {
-        for (int64_t a = 0; a < g.ncell; ++a) {
-            if (!cell_core[a]) continue;
-            const int64_t *ca = grid_cell_coord(&g, a);
-            for (int64_t o = 0; o < noff; ++o) {
-                for (int i = 0; i < d; ++i) coord[i] = ca[i] + offs[o * d + i];
-                int64_t b = grid_lookup(&g, coord);
-                if (b <= a || !cell_core[b]) continue; /* each unordered pair once */
-                if (uf_find(parent, a) == uf_find(parent, b)) continue;
-                int64_t di = dir_index(offs + o * d, d);
-                int64_t ra = rep[a * ndir + di], rb = rep[b * ndir + (ndir - 1 - di)];
-                if (le_eps(X + ra * d, X + rb * d, d, eps2)) { uf_union(parent, a, b); continue; }
-                int found = 0;
-                for (int64_t i = g.cell_first[a]; i < g.cell_first[a + 1] && !found; ++i) {
-                    int64_t p = g.order[i];
-                    if (!core[p]) continue;
-                    for (int64_t j = g.cell_first[b]; j < g.cell_first[b + 1] && !found; ++j) {
-                        int64_t q = g.order[j];
-                        if (core[q] && le_eps(X + p * d, X + q * d, d, eps2)) found = 1;
-                    }
-                }
-                if (found) uf_union(parent, a, b);
-            }
-        }
-    } else {
-        for (int64_t p = 0; p < n; ++p) {
-            if (!core[p]) continue;
-            int64_t pos = tmp[p];
-            for (int64_t k2 = pos + 1; k2 < n; ++k2) {
-                int64_t q = xorder[k2];
-                if (fabs(X[q * d] - X[p * d]) > win) break;
-                if (!core[q] || g.cell_of[q] == g.cell_of[p]) continue;
-                if (uf_find(parent, g.cell_of[p]) == uf_find(parent, g.cell_of[q])) continue;
-                if (le_eps(X + p * d, X + q * d, d, eps2)) uf_union(parent, g.cell_of[p], g.cell_of[q]);
-            }
-            for (int64_t k2 = pos - 1; k2 >= 0; --k2) {
-                int64_t q = xorder[k2];
-                if (fabs(X[q * d] - X[p * d]) > win) break;
-                if (!core[q] || g.cell_of[q] == g.cell_of[p]) continue;
-                if (uf_find(parent, g.cell_of[p]) == uf_find(parent, g.cell_of[q])) continue;
-                if (le_eps(X + p * d, X + q * d, d, eps2)) uf_union(parent, g.cell_of[p], g.cell_of[q]);
-            }
-        }
+    for (int t = 0; t < threads; ++t) {
+        if (jobs[t].rc) goto done;
+        for (int64_t e = 0; e < jobs[t].nedge; ++e)
+            uf_union(parent, jobs[t].edges[2 * e], jobs[t].edges[2 * e + 1]);
     }
 
     /* ---- Alg. 4: canonical cluster ids, then border and noise points ---- */
@@ -680,46 +866,27 @@ int hca_oracle_grid(const double *X, int64_t n, int32_t d, double eps, int32_t m
         int64_t r = uf_find(parent, g.cell_of[p]);
         if (p < comp_min[r]) comp_min[r] = p;
     }
+    for (int64_t cell = 0; cell < g.ncell; ++cell)
+        cell_label[cell] = cell_core[cell] ? comp_min[uf_find(parent, cell)] : INT64_MAX;
     for (int64_t p = 0; p < n; ++p)
-        labels[p] = core[p] ? (int32_t)comp_min[uf_find(parent, g.cell_of[p])] : -1;
-    for (int64_t p = 0; p < n; ++p) {
-        if (core[p]) continue;
-        int64_t own = g.cell_of[p];
-        int64_t best = cell_core[own] ? comp_min[uf_find(parent, own)] : INT64_MAX;
-        if (use_stencil) {
-            const int64_t *c = g.cc + p * d;
-            for (int64_t o = 0; o < noff; ++o) {
-                for (int i = 0; i < d; ++i) coord[i] = c[i] + offs[o * d + i];
-                int64_t nb = grid_lookup(&g, coord);
-                if (nb < 0 || !cell_core[nb]) continue;
-                int64_t lab = comp_min[uf_find(parent, nb)];
-                if (lab >= best) continue;
-                for (int64_t kk = g.cell_first[nb]; kk < g.cell_first[nb + 1]; ++kk) {
-                    int64_t q = g.order[kk];
-                    if (core[q] && le_eps(X + p * d, X + q * d, d, eps2)) { best = lab; break; }
-                }
-            }
-        } else {
-            int64_t pos = tmp[p];
-            for (int dir = -1; dir <= 1; dir += 2) {
-                for (int64_t k2 = pos + dir; k2 >= 0 && k2 < n; k2 += dir) {
-                    int64_t q = xorder[k2];
-                    if (fabs(X[q * d] - X[p * d]) > win) break;
-                    if (!core[q]) continue;
-                    int64_t lab = comp_min[uf_find(parent, g.cell_of[q])];
-                    if (lab < best && le_eps(X + p * d, X + q * d, d, eps2)) best = lab;
-                }
-            }
-        }
-        labels[p] = best == INT64_MAX ? -1 : (int32_t)best;
-    }
+        labels[p] = core[p] ? (int32_t)cell_label[g.cell_of[p]] : -1;
+    run_phase(grid_border_worker, ctx, jobs, threads, n, 256);
     if (core_out) memcpy(core_out, core, n);
     rc = 0;
 done:
-    free(core); free(cell_core); free(parent); free(comp_min); free(offs);
-    free(xorder); free(tmp); free(coord); free(dirs); free(rep);
+    if (jobs)
+        for (int t = 0; t < threads; ++t) free(jobs[t].edges);
+    free(core); free(cell_core); free(parent); free(comp_min); free(cell_label); free(jobs); free(ctx);
+    free(offs); free(xorder); free(tmp); free(dirs); free(rep);
     grid_free(&g);
     return rc;
+}
+
+/* hca_oracle_grid_mt on the calling thread alone. */
+int hca_oracle_grid(const double *X, int64_t n, int32_t d, double eps, int32_t min_pts,
+                    int32_t *labels, uint8_t *core_out)
+{
+    return hca_oracle_grid_mt(X, n, d, eps, min_pts, 1, labels, core_out);
 }
 
 /* ------------------------------------------------------------------------------------- */

@@ -15,9 +15,10 @@ CASES = [(d, seed, mp) for d in (1, 2, 3, 4, 5, 6) for seed in (0, 1) for mp in 
 def test_grid_equals_bruteforce_on_lattice_ties(oracle_mod, d, seed, min_pts):
     X, eps, _ = workloads.lattice(600, d, seed=100 * d + seed, spread=2.0 + d, box=8.0 + 4 * d)
     a = oracle_mod.bruteforce(X, eps, min_pts)
-    b = oracle_mod.grid(X, eps, min_pts)
-    np.testing.assert_array_equal(b[1], a[1])
-    np.testing.assert_array_equal(b[0], a[0])
+    for threads in (1, 4):
+        b = oracle_mod.grid(X, eps, min_pts, threads=threads)
+        np.testing.assert_array_equal(b[1], a[1])
+        np.testing.assert_array_equal(b[0], a[0])
 
 
 @pytest.mark.parametrize("name,n", [("blobs2d", 3000), ("mixed3d", 6000), ("aniso16d", 3000)])
@@ -26,8 +27,24 @@ def test_grid_equals_bruteforce_on_workload_recipes(oracle_mod, name, n):
     if name == "aniso16d":
         X, eps, min_pts = workloads.aniso16d(n=n, n_clusters=5)
     a = oracle_mod.bruteforce(X.astype(np.float64), eps, min_pts)
-    b = oracle_mod.grid(X.astype(np.float64), eps, min_pts)
     assert a[1].any() and (a[0] < 0).any()       # not degenerate: core and noise present
+    for threads in (1, 3, 8):
+        b = oracle_mod.grid(X.astype(np.float64), eps, min_pts, threads=threads)
+        np.testing.assert_array_equal(b[1], a[1])
+        np.testing.assert_array_equal(b[0], a[0])
+
+
+@pytest.mark.parametrize("name,n", [("mixed3d", 40_000), ("aniso16d", 20_000)])
+def test_threaded_grid_equals_one_thread(oracle_mod, name, n):
+    """Larger than the brute-force cases: the threaded counts, merging and border points
+    give the one-thread result (each thread's merges are joined into one union-find)."""
+    X, eps, min_pts = workloads.WORKLOADS[name](n=n)
+    if name == "aniso16d":
+        X, eps, min_pts = workloads.aniso16d(n=n, n_clusters=10)
+    X = X.astype(np.float64)
+    a = oracle_mod.grid(X, eps, min_pts, threads=1)
+    b = oracle_mod.grid(X, eps, min_pts, threads=6)
+    assert len(np.unique(a[0][a[0] >= 0])) > 2
     np.testing.assert_array_equal(b[1], a[1])
     np.testing.assert_array_equal(b[0], a[0])
 

@@ -30,23 +30,29 @@ MUTANTS = {
     "wide_cube": ("return eps / sqrt((double)d) * (1.0 - 1.0 / 1048576.0);",
                   "return eps * (1.0 - 1.0 / 1048576.0);"),
     # grid: a border point ignores the core points of its own hypercube
-    "border_own_cube": ("int64_t best = cell_core[own] ? comp_min[uf_find(parent, own)] : INT64_MAX;",
-                        "int64_t best = INT64_MAX;"),
+    "border_own_cube": ("int64_t best = c->cell_label[own];", "int64_t best = INT64_MAX;"),
+    # grid, threaded merging: the pairs joined by the calling thread are not carried over
+    "lost_thread_merges": ("for (int t = 0; t < threads; ++t) {\n        if (jobs[t].rc) goto done;",
+                           "for (int t = 1; t < threads; ++t) {\n        if (jobs[t].rc) goto done;"),
+    # grid, counts: the early stop one short of MINPTS
+    "count_stops_early": ("c->core[p] = cnt >= c->min_pts;", "c->core[p] = cnt >= c->min_pts - 1;"),
 }
 
 
 def _pins_hold(o):
+    grid3 = lambda X, eps, mp: o.grid(X, eps, mp, threads=3)   # noqa: E731
     for path in all_cases():
         X, eps, min_pts, exp = load(path)
-        for f in (o.bruteforce, o.grid):
+        for f in (o.bruteforce, o.grid, grid3):
             lab, core = f(X, eps, min_pts)
             if not (np.array_equal(lab, exp["labels"]) and np.array_equal(core, exp["core"])):
                 return False
-    for d, seed in ((2, 5), (3, 6), (1, 7)):
+    for d, seed in ((2, 5), (3, 6), (1, 7), (5, 8)):
         X, eps, mp = workloads.lattice(300, d, seed=seed, spread=2.0 + d, box=6.0 + 3 * d)
-        a, b = o.bruteforce(X, eps, mp), o.grid(X, eps, mp)
-        if not (np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])):
-            return False
+        a = o.bruteforce(X, eps, mp)
+        for b in (o.grid(X, eps, mp), grid3(X, eps, mp)):
+            if not (np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])):
+                return False
     skl = pytest.importorskip("sklearn.cluster")
     r = np.random.Generator(np.random.PCG64(3))
     X = np.concatenate([r.normal(r.uniform(0, 10, 2), 0.7, size=(150, 2)) for _ in range(3)]
