@@ -30,8 +30,10 @@
  *   - every entry point returns HCA_OK (0) or a negative HCA_E* code; on a negative code the
  *     output buffers hold no result (they may have been partly written); n = 0 succeeds
  *     without touching any buffer.
- * Limits: 1 <= d <= 4, n < 2^31, 0 < eps finite, min_pts >= 1, and the grid of cells
- * (extent / (eps / sqrt(d)) per dimension) must fit 64-bit cell keys (HCA_ERANGE otherwise).
+ * Limits: 1 <= d <= 64, n < 2^31, 0 < eps finite, min_pts >= 1.  For d <= 4 the grid of
+ * hypercubes (extent / (eps / sqrt(d)) cells per dimension) must fit 64-bit cell keys; for
+ * d >= 5 the coarse grid (extent / eps cells in each of three dimensions) must fit them
+ * (HCA_ERANGE otherwise).
  */
 #ifndef HCA_DBSCAN_H
 #define HCA_DBSCAN_H
@@ -58,7 +60,8 @@ extern "C" {
 #define HCA_ENOMEM (-2)    /* device workspace could not be allocated */
 #define HCA_ECUDA (-3)     /* a CUDA runtime call failed */
 #define HCA_ERANGE (-4)    /* coordinate extent too large for the cell grid at this eps */
-#define HCA_ENOTIMPL (-5)  /* supported by the interface, not by this build (e.g. d > 4) */
+#define HCA_ENOTIMPL (-5)  /* supported by the interface, not by this build (a batched call whose
+                              sets need more than 512 neighbour pencils in their union) */
 #define HCA_EDEVICE (-6)   /* a kernel's own consistency check tripped (bounded loop limit,
                               full hash table); the outputs hold no result */
 #define HCA_ETOOLARGE (-7) /* n above the fixed scratch of hca_radix_sort_pairs_noalloc */
@@ -118,6 +121,12 @@ typedef struct hca_stats {
     /* d <= 4 (hypercube neighbour search): cells holding at least one core point (the cells
        with representative points, Algorithm 2); 0 on the coarse-grid path */
     int64_t n_core_cells;
+    /* d >= 5, float input: point pairs (valid row x valid candidate) of the tensor-core tiles
+       computed, and with HCA_FLAG_TIMING the CUDA-event time of the tensor-core kernel of the
+       counts, unions and labels (one launch each) */
+    int64_t n_tc_pairs;
+    float tc_ms[3];
+    int32_t reserved2;
 } hca_stats;
 
 /*
@@ -151,22 +160,32 @@ HCA_API int hca_dbscan_device_ex(const void *d_points, int32_t dtype, int64_t n,
                          hca_stats *stats, int32_t flags);
 
 /*
- * hca_dbscan_batched -- cluster many independent point sets in one call.
- *   d_points  device, the sets' points concatenated: set s is rows [offsets[s], offsets[s+1])
- *             of a row-major (offsets[n_sets] x d) array of `dtype`.
- *   offsets   host, n_sets + 1 non-decreasing int64, offsets[0] = 0; empty sets are allowed.
+ * hca_dbscan_batched -- cluster many independent point sets, each with its own dimension,
+ * eps and MINPTS, in one call (the paper clusters one set per run; this batching has no
+ * counterpart there).
+ *   d_points   device, the sets' points concatenated: set s is a row-major n_s x d_per_set[s]
+ *              block (n_s = offsets[s+1] - offsets[s]) that starts right after the block of
+ *              set s - 1, i.e. at element sum_{t<s} n_t * d_per_set[t].
+ *   offsets    host, n_sets + 1 non-decreasing int64 point offsets, offsets[0] = 0; empty sets
+ *              are allowed.
+ *   d_per_set  host, n_sets dimensions (1..64).
  *   eps, min_pts  host, n_sets values: each set's own parameters (Definitions 1-2).
- *   d_labels  device, offsets[n_sets] int32: each set's labels, with cluster ids that are
- *             indices WITHIN the set (the same values a separate call on that set returns).
- *   d_core    device, optional core flags; stats host, optional (totals over the sets).
- * All sets go through one pipeline: the set id sits above the cell key (the hypercube key for
- * d <= 4, the coarse-grid key for d >= 5), so one sort, one pencil hash and one launch of each
- * kernel serve every set, and cells never mix sets.  Returns after the labels are complete on
- * `stream`.  One d per call: group sets of different d into separate calls.
+ *   d_labels   device, offsets[n_sets] int32: set s's labels at [offsets[s], offsets[s+1]),
+ *              with cluster ids that are indices WITHIN the set (the values a separate call on
+ *              that set returns).
+ *   d_core     device, optional core flags (laid out as d_labels); stats host, optional
+ *              (totals over the sets; stage times summed over the d groups).
+ * The sets of one d go through one pipeline: the set id sits above the cell key (the
+ * hypercube key for d <= 4, the coarse-grid key for d >= 5), so one sort, one pencil hash and
+ * one launch of each kernel serve every set of that d, and cells never mix sets.  The d groups
+ * run one after another on `stream`, each with the tuning of its d; a group whose sets are
+ * not consecutive is gathered into library workspace first and its labels scattered back.
+ * Returns after the labels are complete on `stream`.
  */
 HCA_API int hca_dbscan_batched(const void *d_points, int32_t dtype, int32_t n_sets, const int64_t *offsets,
-                               int32_t d, const double *eps, const int32_t *min_pts, int32_t *d_labels,
-                               uint8_t *d_core, void *stream, hca_stats *stats, int32_t flags);
+                               const int32_t *d_per_set, const double *eps, const int32_t *min_pts,
+                               int32_t *d_labels, uint8_t *d_core, void *stream, hca_stats *stats,
+                               int32_t flags);
 
 /*
  * Request server: asynchronous clustering jobs with continuous batching (the serving form of
@@ -225,7 +244,7 @@ HCA_API int hca_radix_sort_pairs(void *d_keys, uint32_t *d_vals, int64_t n, int3
  * owns all device memory, code that must not risk the synchronisation cudaMalloc / cudaFree
  * can cause).  Same arguments and result as hca_radix_sort_pairs.
  *   n  at most HCA_SORT_NOALLOC_MAX_PAIRS (2^18); larger n returns HCA_ETOOLARGE.
- * Scratch: a fixed array of about 3.2 MiB inside the library (a __device__ variable: the
+ * Scratch: a fixed array of about 3.1 MiB inside the library (a __device__ variable: the
  * alternate keys and values of 2^18 pairs plus the sort's look-back words), held on every GPU
  * that loads the library until the process exits.  The first call in a CUDA context of a
  * device looks up that array's device address (cudaGetSymbolAddress) and caches it for that
@@ -249,10 +268,14 @@ HCA_API int hca_radix_sort_pairs_noalloc(void *d_keys, uint32_t *d_vals, int64_t
  * so a launch never waits for the host: the whole call is one graph launch.
  *   d_points, d_labels, d_core  device buffers bound to the plan (as in hca_dbscan_device_ex;
  *              d_core nullable); the caller may rewrite d_points between launches.
- *   box_min, box_max  host, d values (batched: n_sets x d, set-major): every coordinate of
- *              every launch's points must lie in [box_min, box_max]; a launch whose points do
- *              not makes hca_plan_wait return HCA_ERANGE (its labels are then undefined).  A
- *              larger box gives the same labels (the grid origin does not change a label).
+ *   box_min, box_max  host, d values (batched: d_per_set[s] values per set, set after set):
+ *              every coordinate of every launch's points must lie in [box_min, box_max]; a
+ *              launch whose points do not makes hca_plan_wait return HCA_ERANGE (its labels
+ *              are then undefined).  A larger box gives the same labels (the grid origin does
+ *              not change a label).
+ * A batched plan takes the sets of hca_dbscan_batched (one d per set).  Its d groups are
+ * captured as parallel branches of the one graph (gathering and scattering included), so they
+ * overlap on the device, and hca_plan_launch is one graph launch for all of them.
  * hca_plan_create[_batched] synchronises (it sizes and allocates the workspace and captures
  * the graph; no kernel runs).  hca_plan_launch enqueues one clustering on `stream` and returns.
  * hca_plan_wait synchronises `stream` and returns the launch's code: HCA_OK, HCA_ERANGE (a
@@ -265,7 +288,7 @@ HCA_API int hca_plan_create(hca_plan **out, const void *d_points, int32_t dtype,
                             double eps, int32_t min_pts, const double *box_min, const double *box_max,
                             int32_t *d_labels, uint8_t *d_core);
 HCA_API int hca_plan_create_batched(hca_plan **out, const void *d_points, int32_t dtype, int32_t n_sets,
-                                    const int64_t *offsets, int32_t d, const double *eps,
+                                    const int64_t *offsets, const int32_t *d_per_set, const double *eps,
                                     const int32_t *min_pts, const double *box_min,
                                     const double *box_max, int32_t *d_labels, uint8_t *d_core);
 HCA_API int hca_plan_launch(hca_plan *plan, void *stream);
@@ -317,9 +340,13 @@ HCA_API int hca_tuning_set(int32_t d, const hca_tuning *t);
 HCA_API int hca_autotune(const void *d_points, int32_t dtype, int64_t n, int32_t d, double eps,
                          int32_t min_pts, void *stream, int32_t repeats, hca_tuning *out,
                          double *best_ms);
-/* hca_autotune for the sets of a batched call (arguments as hca_dbscan_batched). */
+/* hca_autotune for the sets of a batched call (arguments as hca_dbscan_batched): every d
+ * present is tuned on its own sets and keeps its fastest candidate.
+ *   out      host, nullable: 64 entries; entry d - 1 receives the tuning kept for each d
+ *            present (the other entries are not written).
+ *   best_ms  host, nullable: the sum over the d groups of their best times. */
 HCA_API int hca_autotune_batched(const void *d_points, int32_t dtype, int32_t n_sets,
-                                 const int64_t *offsets, int32_t d, const double *eps,
+                                 const int64_t *offsets, const int32_t *d_per_set, const double *eps,
                                  const int32_t *min_pts, void *stream, int32_t repeats,
                                  hca_tuning *out, double *best_ms);
 

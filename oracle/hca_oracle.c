@@ -58,6 +58,9 @@ static int le_eps(const double *p, const double *q, int d, double eps2)
     for (int i = 0; i < d; ++i) {
         double t = p[i] - q[i];
         s = s + t * t;
+        /* every term is >= 0 and rounding is monotone, so the partial sum never decreases:
+           once above eps^2 the full sum is too */
+        if (s > eps2) return 0;
     }
     return s <= eps2;
 }
@@ -515,6 +518,10 @@ typedef struct {
     const int64_t *xorder;      /* points sorted by x_0, ties by index (d > 4) */
     const int64_t *pos;         /* position of each point in xorder */
     double win;                 /* window of the leading-dimension sweep */
+    const double *x0s;          /* x_0 of the point at each position of xorder */
+    const double *x1s;          /* x_1 of the point at each position of xorder (NULL if d = 1) */
+    const int64_t *cell_s;      /* cube of the point at each position of xorder */
+    uint8_t *core_s;            /* core flag of the point at each position (after the counts) */
     uint8_t *core;              /* count phase output */
     const uint8_t *cell_core;   /* cells holding a core point */
     const int64_t *rep;         /* representative points, ndir per cell (stencil path) */
@@ -592,10 +599,10 @@ static void *grid_count_worker(void *arg)
                     int64_t pos = c->pos[p];
                     for (int dir = -1; dir <= 1 && cnt < c->min_pts; dir += 2) {
                         for (int64_t k2 = pos + dir; k2 >= 0 && k2 < c->n && cnt < c->min_pts; k2 += dir) {
-                            int64_t q = c->xorder[k2];
-                            if (fabs(X[q * d] - X[p * d]) > c->win) break;
-                            if (g->cell_of[q] == cell) continue; /* counted above */
-                            cnt += le_eps(X + p * d, X + q * d, d, c->eps2);
+                            if (fabs(c->x0s[k2] - X[p * d]) > c->win) break;
+                            if (c->cell_s[k2] == cell) continue; /* counted above */
+                            if (c->x1s && fabs(c->x1s[k2] - X[p * d + 1]) > c->win) continue;
+                            cnt += le_eps(X + p * d, X + c->xorder[k2] * d, d, c->eps2);
                         }
                     }
                 }
@@ -673,13 +680,14 @@ static void *grid_merge_worker(void *arg)
                 if (!c->core[p]) continue;
                 int64_t cp = g->cell_of[p];
                 for (int64_t k2 = c->pos[p] + 1; k2 < c->n; ++k2) {
-                    int64_t q = c->xorder[k2];
-                    if (fabs(X[q * d] - X[p * d]) > c->win) break;
-                    if (!c->core[q] || g->cell_of[q] == cp) continue;
-                    if (uf_find(parent, cp) == uf_find(parent, g->cell_of[q])) continue;
-                    if (le_eps(X + p * d, X + q * d, d, c->eps2)) {
-                        uf_union(parent, cp, g->cell_of[q]);
-                        if (push_edge(j, cp, g->cell_of[q])) { j->rc = ORACLE_ENOMEM; break; }
+                    if (fabs(c->x0s[k2] - X[p * d]) > c->win) break;
+                    int64_t cq = c->cell_s[k2];
+                    if (!c->core_s[k2] || cq == cp) continue;
+                    if (c->x1s && fabs(c->x1s[k2] - X[p * d + 1]) > c->win) continue;
+                    if (uf_find(parent, cp) == uf_find(parent, cq)) continue;
+                    if (le_eps(X + p * d, X + c->xorder[k2] * d, d, c->eps2)) {
+                        uf_union(parent, cp, cq);
+                        if (push_edge(j, cp, cq)) { j->rc = ORACLE_ENOMEM; break; }
                     }
                 }
             }
@@ -722,11 +730,11 @@ static void *grid_border_worker(void *arg)
                 int64_t pos = c->pos[p];
                 for (int dir = -1; dir <= 1; dir += 2) {
                     for (int64_t k2 = pos + dir; k2 >= 0 && k2 < c->n; k2 += dir) {
-                        int64_t q = c->xorder[k2];
-                        if (fabs(X[q * d] - X[p * d]) > c->win) break;
-                        if (!c->core[q]) continue;
-                        int64_t lab = c->cell_label[g->cell_of[q]];
-                        if (lab < best && le_eps(X + p * d, X + q * d, d, c->eps2)) best = lab;
+                        if (fabs(c->x0s[k2] - X[p * d]) > c->win) break;
+                        if (!c->core_s[k2]) continue;
+                        if (c->x1s && fabs(c->x1s[k2] - X[p * d + 1]) > c->win) continue;
+                        int64_t lab = c->cell_label[c->cell_s[k2]];
+                        if (lab < best && le_eps(X + p * d, X + c->xorder[k2] * d, d, c->eps2)) best = lab;
                     }
                 }
             }
@@ -786,7 +794,9 @@ int hca_oracle_grid_mt(const double *X, int64_t n, int32_t d, double eps, int32_
     grid_job *jobs = (grid_job *)calloc(threads, sizeof(grid_job));
     grid_ctx *ctx = (grid_ctx *)calloc(1, sizeof(grid_ctx));
     int64_t *offs = NULL, noff = 0;
-    int64_t *xorder = NULL, *tmp = NULL;
+    int64_t *xorder = NULL, *tmp = NULL, *cell_s = NULL;
+    double *x0s = NULL, *x1s = NULL;
+    uint8_t *core_s = NULL;
     int8_t *dirs = NULL;
     int64_t *rep = NULL;
     rc = ORACLE_ENOMEM;
@@ -824,11 +834,25 @@ int hca_oracle_grid_mt(const double *X, int64_t n, int32_t d, double eps, int32_
         for (int64_t k = 0; k < n; ++k) key[xorder[k]] = k; /* position of each point */
         free(tmp);
         tmp = key; /* tmp now holds the position of each point in xorder */
+        /* the sweep reads x_0, x_1, the cube and the core flag of the points in xorder order;
+           a pair with |x_0 - y_0| or |x_1 - y_1| above eps (1 + 1e-9) is farther than eps
+           (its first or second term alone exceeds eps^2), so those comparisons are skipped */
+        x0s = (double *)malloc(sizeof(double) * n);
+        x1s = d >= 2 ? (double *)malloc(sizeof(double) * n) : NULL;
+        cell_s = (int64_t *)malloc(sizeof(int64_t) * n);
+        core_s = (uint8_t *)malloc(n);
+        if (!x0s || (d >= 2 && !x1s) || !cell_s || !core_s) goto done;
+        for (int64_t k = 0; k < n; ++k) {
+            x0s[k] = X[xorder[k] * d];
+            if (x1s) x1s[k] = X[xorder[k] * d + 1];
+            cell_s[k] = g.cell_of[xorder[k]];
+        }
     }
 
     ctx->X = X; ctx->n = n; ctx->d = d; ctx->eps2 = eps2; ctx->min_pts = min_pts;
     ctx->g = &g; ctx->use_stencil = use_stencil; ctx->offs = offs; ctx->noff = noff;
     ctx->xorder = xorder; ctx->pos = tmp; ctx->win = eps * (1.0 + 1e-9);
+    ctx->x0s = x0s; ctx->x1s = x1s; ctx->cell_s = cell_s; ctx->core_s = core_s;
     ctx->core = core; ctx->cell_core = cell_core; ctx->cell_label = cell_label; ctx->labels = labels;
     for (int t = 0; t < threads; ++t) jobs[t].c = ctx;
 
@@ -836,6 +860,8 @@ int hca_oracle_grid_mt(const double *X, int64_t n, int32_t d, double eps, int32_
     run_phase(grid_count_worker, ctx, jobs, threads, g.ncell, 64);
     for (int64_t p = 0; p < n; ++p)
         if (core[p]) cell_core[g.cell_of[p]] = 1;
+    if (core_s)
+        for (int64_t k = 0; k < n; ++k) core_s[k] = core[xorder[k]];
 
     /* ---- Alg. 2: representative points over core points (stencil path) ---- */
     int64_t ndir = 0;
@@ -877,7 +903,7 @@ done:
     if (jobs)
         for (int t = 0; t < threads; ++t) free(jobs[t].edges);
     free(core); free(cell_core); free(parent); free(comp_min); free(cell_label); free(jobs); free(ctx);
-    free(offs); free(xorder); free(tmp); free(dirs); free(rep);
+    free(offs); free(xorder); free(tmp); free(dirs); free(rep); free(x0s); free(x1s); free(cell_s); free(core_s);
     grid_free(&g);
     return rc;
 }

@@ -7,7 +7,8 @@ CPU fallback: if the library is missing or cannot be loaded, every call raises.
 Names follow include/hca_dbscan.h:
   hca_dbscan(points, eps, min_pts)               host numpy array in, int32 labels out
   hca_dbscan_device(points, eps, min_pts, ...)   CUDA torch tensor in, CUDA labels out
-  hca_dbscan_batched(points, offsets, eps, min_pts)  many sets, one call
+  hca_dbscan_batched(points, offsets, eps, min_pts, dims)  many sets (each its own d), one call
+  pack_sets(sets)                                 concatenate sets of any d for the batched calls
   hca_radix_sort_pairs(keys, vals, begin, end)   in-place device sort (the Sec. 2 pre-sort)
   hca_strerror(code), hca_version()
 """
@@ -44,11 +45,14 @@ class HcaStats(ctypes.Structure):
                 ("n_rep_hits", ctypes.c_int64), ("n_exhaustive_pairs", ctypes.c_int64),
                 ("n_exhaustive_chunks", ctypes.c_int64), ("n_border_chunks", ctypes.c_int64),
                 ("n_tc_tiles", ctypes.c_int64), ("n_tc_rechecks", ctypes.c_int64),
-                ("n_core_cells", ctypes.c_int64)]
+                ("n_core_cells", ctypes.c_int64), ("n_tc_pairs", ctypes.c_int64),
+                ("tc_ms", ctypes.c_float * 3), ("reserved2", ctypes.c_int32)]
 
     def as_dict(self):
-        d = {name: getattr(self, name) for name, _ in self._fields_ if name not in ("stage_ms", "reserved")}
+        skip = ("stage_ms", "reserved", "tc_ms", "reserved2")
+        d = {name: getattr(self, name) for name, _ in self._fields_ if name not in skip}
         d["stage_ms"] = {s: float(self.stage_ms[i]) for i, s in enumerate(STAGES)}
+        d["tc_ms"] = {s: float(self.tc_ms[i]) for i, s in enumerate(("counts", "unions", "labels"))}
         return d
 
 
@@ -91,7 +95,7 @@ def load():
     lib.hca_dbscan_device_ex.argtypes = [vp, i32, i64, i32, dbl, i32, vp, vp, vp,
                                          ctypes.POINTER(HcaStats), i32]
     lib.hca_radix_sort_pairs.argtypes = [vp, vp, i64, i32, i32, i32, vp]
-    lib.hca_dbscan_batched.argtypes = [vp, i32, i32, vp, i32, vp, vp, vp, vp, vp,
+    lib.hca_dbscan_batched.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp,
                                        ctypes.POINTER(HcaStats), i32]
     lib.hca_dbscan_batched.restype = ctypes.c_int
     lib.hca_server_create.argtypes = [ctypes.POINTER(vp), i32, i64, i32]
@@ -106,12 +110,12 @@ def load():
     lib.hca_tuning_set.argtypes = [i32, ctypes.POINTER(HcaTuning)]
     lib.hca_autotune.argtypes = [vp, i32, i64, i32, dbl, i32, vp, i32, ctypes.POINTER(HcaTuning),
                                  ctypes.POINTER(ctypes.c_double)]
-    lib.hca_autotune_batched.argtypes = [vp, i32, i32, vp, i32, vp, vp, vp, i32, ctypes.POINTER(HcaTuning),
+    lib.hca_autotune_batched.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, i32, ctypes.POINTER(HcaTuning),
                                          ctypes.POINTER(ctypes.c_double)]
     for f in ("hca_tuning_get", "hca_tuning_set", "hca_autotune", "hca_autotune_batched"):
         getattr(lib, f).restype = ctypes.c_int
     lib.hca_plan_create.argtypes = [ctypes.POINTER(vp), vp, i32, i64, i32, dbl, i32, vp, vp, vp, vp]
-    lib.hca_plan_create_batched.argtypes = [ctypes.POINTER(vp), vp, i32, i32, vp, i32, vp, vp, vp, vp, vp, vp]
+    lib.hca_plan_create_batched.argtypes = [ctypes.POINTER(vp), vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.hca_plan_launch.argtypes = [vp, vp]
     lib.hca_plan_wait.argtypes = [vp, vp, ctypes.POINTER(HcaStats)]
     lib.hca_plan_destroy.argtypes = [vp]
@@ -209,30 +213,64 @@ def hca_dbscan_device(points, eps: float, min_pts: int, labels=None, core=None, 
     return labels
 
 
-def hca_dbscan_batched(points, offsets, eps, min_pts, labels=None, core=None, stream=None,
+def _set_args(points, offsets, eps, min_pts, dims):
+    """Host arrays of a batched call: int64 offsets, int32 dims, float64 eps, int32 min_pts,
+    checked against the length of the flat point buffer."""
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    e = np.ascontiguousarray(np.asarray(eps, dtype=np.float64))
+    m = np.ascontiguousarray(np.asarray(min_pts, dtype=np.int32))
+    if off.ndim != 1 or len(off) != len(e) + 1 or len(e) != len(m):
+        raise ValueError("offsets must have n_sets + 1 entries; eps and min_pts n_sets")
+    if dims is None:
+        if points.dim() != 2:
+            raise ValueError("dims is required when points is not an (N, d) tensor")
+        dims = [points.shape[1]] * len(e)
+    dd = np.ascontiguousarray(np.asarray(dims, dtype=np.int32))
+    if dd.shape != e.shape:
+        raise ValueError("dims must have n_sets entries")
+    if int(np.sum(np.diff(off) * dd.astype(np.int64))) != points.numel():
+        raise ValueError("the sets' n_s * d_s must add up to the number of point values")
+    return off, dd, e, m
+
+
+def pack_sets(sets, device="cuda"):
+    """Concatenate point sets of any dimension for the batched calls: `sets` is a sequence of
+    (n_s, d_s) arrays or tensors of one float dtype.  Returns (flat CUDA tensor, offsets, dims)."""
+    import torch
+    parts, offs, dims = [], [0], []
+    for x in sets:
+        t = x if hasattr(x, "data_ptr") else torch.from_numpy(np.ascontiguousarray(x))
+        if t.dim() == 1:
+            t = t[:, None]
+        parts.append(t.reshape(-1))
+        offs.append(offs[-1] + t.shape[0])
+        dims.append(t.shape[1])
+    flat = torch.cat(parts).to(device) if parts else torch.empty(0, device=device)
+    return flat.contiguous(), np.asarray(offs, np.int64), np.asarray(dims, np.int32)
+
+
+def hca_dbscan_batched(points, offsets, eps, min_pts, dims=None, labels=None, core=None, stream=None,
                        stats: bool = False, timing: bool = False, fp64_only: bool = False,
                        tensor_cores: bool = True):
-    """Cluster the sets points[offsets[s]:offsets[s+1]] (a CUDA tensor (N, d)), each with its
-    own eps[s] and min_pts[s] (host sequences).  Labels are per set (ids are indices within the
-    set).  Returns the label tensor, or (labels, stats_dict) when stats or timing is requested."""
+    """Cluster many sets in one call, each with its own dimension dims[s], eps[s] and
+    min_pts[s] (host sequences).  `points` is a CUDA tensor holding the sets' row-major blocks
+    one after another (an (N, d) tensor when every set has d = points.shape[1] and dims is
+    None; any flat layout from pack_sets otherwise).  Labels are per set (ids are indices within
+    the set), laid out by offsets.  Returns the label tensor, or (labels, stats_dict) when stats
+    or timing is requested."""
     import torch
     lib = load()
     if not points.is_cuda:
         raise ValueError("hca_dbscan_batched takes a CUDA tensor")
     pts = points.contiguous()
-    n = pts.shape[0]
-    d = pts.shape[1] if pts.dim() == 2 else 1
-    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
-    e = np.ascontiguousarray(np.asarray(eps, dtype=np.float64))
-    m = np.ascontiguousarray(np.asarray(min_pts, dtype=np.int32))
-    if off.ndim != 1 or len(off) != len(e) + 1 or len(e) != len(m) or off[-1] != n:
-        raise ValueError("offsets must have n_sets + 1 entries ending at len(points); eps, min_pts n_sets")
+    off, dd, e, m = _set_args(pts, offsets, eps, min_pts, dims)
+    n = int(off[-1])
     if labels is None:
         labels = torch.empty(n, dtype=torch.int32, device=pts.device)
     flags = ((HCA_FLAG_TIMING if timing else 0) | (HCA_FLAG_FP64_ONLY if fp64_only else 0)
              | (0 if tensor_cores else HCA_FLAG_NO_TENSOR_CORES))
     st = HcaStats()
-    rc = lib.hca_dbscan_batched(pts.data_ptr(), _dtype_code(pts.dtype), len(e), off.ctypes.data, d,
+    rc = lib.hca_dbscan_batched(pts.data_ptr(), _dtype_code(pts.dtype), len(e), off.ctypes.data, dd.ctypes.data,
                                 e.ctypes.data, m.ctypes.data, labels.data_ptr(),
                                 core.data_ptr() if core is not None else None, _stream_ptr(stream),
                                 ctypes.byref(st), flags)
@@ -295,38 +333,39 @@ def hca_autotune(points, eps: float, min_pts: int, stream=None, repeats: int = 2
     return t.as_dict(), ms.value
 
 
-def hca_autotune_batched(points, offsets, eps, min_pts, stream=None, repeats: int = 2):
-    """hca_autotune for the sets of a batched call; returns (tuning dict, best ms)."""
+def hca_autotune_batched(points, offsets, eps, min_pts, dims=None, stream=None, repeats: int = 2):
+    """hca_autotune for the sets of a batched call (arguments as hca_dbscan_batched): every d
+    present is tuned on its own sets.  Returns ({d: tuning dict}, sum of the best ms)."""
     lib = load()
     pts = points.contiguous()
-    d = pts.shape[1] if pts.dim() == 2 else 1
-    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
-    e = np.ascontiguousarray(np.asarray(eps, dtype=np.float64))
-    m = np.ascontiguousarray(np.asarray(min_pts, dtype=np.int32))
-    if off.ndim != 1 or len(off) != len(e) + 1 or len(e) != len(m) or off[-1] != pts.shape[0]:
-        raise ValueError("offsets must have n_sets + 1 entries ending at len(points); eps, min_pts n_sets")
-    t, ms = HcaTuning(), ctypes.c_double()
-    rc = lib.hca_autotune_batched(pts.data_ptr(), _dtype_code(pts.dtype), len(e), off.ctypes.data, d,
+    off, dd, e, m = _set_args(pts, offsets, eps, min_pts, dims)
+    table = (HcaTuning * 64)()
+    ms = ctypes.c_double()
+    rc = lib.hca_autotune_batched(pts.data_ptr(), _dtype_code(pts.dtype), len(e), off.ctypes.data, dd.ctypes.data,
                                   e.ctypes.data, m.ctypes.data, _stream_ptr(stream), int(repeats),
-                                  ctypes.byref(t), ctypes.byref(ms))
+                                  table, ctypes.byref(ms))
     if rc != HCA_OK:
         raise HcaError(rc, "hca_autotune_batched")
-    return t.as_dict(), ms.value
+    present = sorted({int(x) for x, a, b in zip(dd, off[:-1], off[1:]) if b > a})
+    return {d: table[d - 1].as_dict() for d in present}, ms.value
 
 
 class Plan:
     """One clustering call captured as a CUDA graph (hca_plan_*), with the tuning of d at creation.
     Bound to the CUDA tensors `points` (n, d) and `labels` (n,) (and `core`, optional); the
     points may be rewritten between launches as long as they stay inside the declared box
-    (box_min, box_max: d values, or n_sets x d for a batched plan)."""
+    (box_min, box_max: d values; for a batched plan, d_s values per set, set after set).  A
+    batched plan (offsets given) takes the sets of hca_dbscan_batched, each with its own d
+    (dims), and runs them all in one graph launch."""
 
-    def __init__(self, points, eps, min_pts, box_min, box_max, labels=None, core=None, offsets=None):
+    def __init__(self, points, eps, min_pts, box_min, box_max, labels=None, core=None, offsets=None,
+                 dims=None):
         import torch
         lib = load()
         if not points.is_cuda or not points.is_contiguous():
             raise ValueError("Plan takes a contiguous CUDA tensor")
         self.points = points
-        n = points.shape[0]
+        n = points.shape[0] if offsets is None else int(np.asarray(offsets)[-1])
         d = points.shape[1] if points.dim() == 2 else 1
         self.labels = labels if labels is not None else torch.empty(n, dtype=torch.int32, device=points.device)
         self.core = core
@@ -339,15 +378,11 @@ class Plan:
                                      float(eps), int(min_pts), self._bmn.ctypes.data, self._bmx.ctypes.data,
                                      self.labels.data_ptr(), cp)
         else:
-            self._off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
-            self._eps = np.ascontiguousarray(np.asarray(eps, dtype=np.float64))
-            self._mp = np.ascontiguousarray(np.asarray(min_pts, dtype=np.int32))
-            if len(self._off) != len(self._eps) + 1 or self._off[-1] != n:
-                raise ValueError("offsets must have n_sets + 1 entries ending at len(points)")
+            self._off, self._dims, self._eps, self._mp = _set_args(points, offsets, eps, min_pts, dims)
             rc = lib.hca_plan_create_batched(ctypes.byref(h), points.data_ptr(), _dtype_code(points.dtype),
-                                             len(self._eps), self._off.ctypes.data, d, self._eps.ctypes.data,
-                                             self._mp.ctypes.data, self._bmn.ctypes.data, self._bmx.ctypes.data,
-                                             self.labels.data_ptr(), cp)
+                                             len(self._eps), self._off.ctypes.data, self._dims.ctypes.data,
+                                             self._eps.ctypes.data, self._mp.ctypes.data, self._bmn.ctypes.data,
+                                             self._bmx.ctypes.data, self.labels.data_ptr(), cp)
         if rc != HCA_OK:
             raise HcaError(rc, "hca_plan_create")
         self._h = h

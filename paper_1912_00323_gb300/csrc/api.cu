@@ -177,10 +177,10 @@ extern "C" int hca_dbscan_device_ex(const void *d_points, int32_t dtype, int64_t
 }
 
 extern "C" int hca_dbscan_batched(const void *d_points, int32_t dtype, int32_t n_sets, const int64_t *offsets,
-                                  int32_t d, const double *eps, const int32_t *min_pts, int32_t *d_labels,
-                                  uint8_t *d_core, void *stream, hca_stats *stats, int32_t flags) {
-    return batched_tuned(d_points, dtype, n_sets, offsets, d, eps, min_pts, d_labels, d_core, stream, stats,
-                         flags, tuning_for(d));
+                                  const int32_t *d_per_set, const double *eps, const int32_t *min_pts,
+                                  int32_t *d_labels, uint8_t *d_core, void *stream, hca_stats *stats, int32_t flags) {
+    return batched_mixed(d_points, dtype, n_sets, offsets, d_per_set, eps, min_pts, d_labels, d_core, stream,
+                         stats, flags, nullptr);
 }
 
 extern "C" int hca_dbscan_device(const void *d_points, int32_t dtype, int64_t n, int32_t d, double eps,

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/hca_dbscan.h"
 
 namespace hca {
@@ -46,6 +48,7 @@ struct DevCounters {
     uint32_t hd_next[4];      // next unclaimed 32-point chunk: counts, first links, unions, labels
     uint32_t lowd_next[5];    // next unclaimed batch (labels: [4])
     unsigned long long work[8];  // work counters (see hca_stats)
+    unsigned long long tc_pairs;  // point pairs of the tensor-core tiles computed
     uint32_t digit_counts[8 * 256];  // radix digit counts per pass, filled while binning
 };
 
@@ -114,7 +117,7 @@ void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t m_max, const 
 // most passes a call can make.  The scratch of a sort of n pairs is sort_hist_elems(n)
 // uint32: two words per tile and digit for the look-back, the digit counts of every pass,
 // one ticket per pass and a status word.
-constexpr int kSortTileKeys = 4096;
+constexpr int kSortTileKeys = 13312;
 constexpr int kSortRadix = 256;
 constexpr int kSortMaxPasses = 8;
 constexpr int64_t sort_tiles_for(int64_t n) {
@@ -190,6 +193,44 @@ int device_ex_tuned(const void *d_points, int32_t dtype, int64_t n, int32_t d, d
 int batched_tuned(const void *d_points, int32_t dtype, int32_t n_sets, const int64_t *offsets, int32_t d,
                   const double *eps, const int32_t *min_pts, int32_t *d_labels, uint8_t *d_core, void *stream,
                   hca_stats *stats, int32_t flags, const hca_tuning &tune);
+// multi.cu: batched calls with one d per set.  The sets are grouped by d (increasing d); a
+// group whose sets are consecutive in the caller's buffers runs in place, any other group is
+// gathered into a compact copy (points, labels, core flags, segment table) and scattered back.
+struct SetGroup {
+    int d = 0;
+    std::vector<int32_t> sets;            // the call's set indices, increasing
+    std::vector<int64_t> off;             // group-local point offsets (sets + 1)
+    std::vector<double> eps;
+    std::vector<int32_t> min_pts;
+    std::vector<double> box_mn, box_mx;   // declared boxes of the sets, d values each (plans)
+    std::vector<int64_t> far_pts;         // element offset of each set in the caller's points
+    std::vector<int64_t> far_lab;         // point offset of each set in the caller's labels
+    int64_t n = 0;                        // points of the group
+    bool gather = false;                  // sets not consecutive: run on a compact copy
+    int64_t first_point = 0;              // in place: first set's point offset
+    size_t first_elem = 0;                // in place: first set's element offset
+};
+struct GroupBuffers {
+    void *points;
+    int32_t *labels;
+    uint8_t *core;
+    int64_t *table;
+};
+int group_sets(int32_t n_sets, const int64_t *offsets, const int32_t *d_per_set, const double *eps,
+               const int32_t *min_pts, const double *box_mn, const double *box_mx, std::vector<SetGroup> &out);
+size_t group_gather_bytes(const SetGroup &g, int32_t dtype, bool with_core);
+void group_gather_layout(const SetGroup &g, int32_t dtype, bool with_core, void *buf, GroupBuffers &gb);
+void group_table(const SetGroup &g, std::vector<int64_t> &t);
+void group_gather(const SetGroup &g, int32_t dtype, const void *d_points, const GroupBuffers &gb, cudaStream_t s);
+void group_scatter(const SetGroup &g, const GroupBuffers &gb, int32_t *d_labels, uint8_t *d_core, cudaStream_t s);
+void add_stats(hca_stats &acc, const hca_stats &x);
+int run_group(const SetGroup &g, const void *d_points, int32_t dtype, int32_t *d_labels, uint8_t *d_core,
+              cudaStream_t s, hca_stats *stats, int32_t flags, const hca_tuning &tune);
+// tune_by_d: nullable, 64 tunings indexed by d - 1 (NULL: the table of tune.cu)
+int batched_mixed(const void *d_points, int32_t dtype, int32_t n_sets, const int64_t *offsets,
+                  const int32_t *d_per_set, const double *eps, const int32_t *min_pts, int32_t *d_labels,
+                  uint8_t *d_core, void *stream, hca_stats *stats, int32_t flags, const hca_tuning *tune_by_d);
+
 template <typename T, int D>
 int run_lowd(const RunArgs &a);
 template <typename T, int DP>

@@ -140,7 +140,9 @@ inline uint32_t *part_of(char *b, size_t o) { return (uint32_t *)(b + o); }
 template <int DP, typename Mark>
 void run_tc_phases(HdView<float, DP> &hv, cudaStream_t s, char *b, int64_t n, int grid_tc, size_t tc_smem,
                    int gpts, int gcell, size_t smem, uint32_t *part, const TcOffsets &o, int nsets,
-                   DevCounters *ctr, const TcTuning &tune, Mark &mark, int &launches) {
+                   DevCounters *ctr, const TcTuning &tune, Mark &mark, int &launches, cudaEvent_t *tev) {
+    // tev (nullable): six events recorded around the three tensor-core launches
+    auto tmark = [&](int i) { if (tev) cudaEventRecord(tev[i], s); };
     uint32_t *nch = (uint32_t *)(b + o.nch), *nch2 = (uint32_t *)(b + o.nch2);
     uint32_t *ch0 = (uint32_t *)(b + o.ch0), *ch1 = (uint32_t *)(b + o.ch1), *ch2 = (uint32_t *)(b + o.ch2);
     uint32_t *flags = (uint32_t *)(b + o.flags), *cx = (uint32_t *)(b + o.cx);
@@ -156,7 +158,9 @@ void run_tc_phases(HdView<float, DP> &hv, cudaStream_t s, char *b, int64_t n, in
     cudaMemsetAsync(hv.cell_core, 0, (size_t)n, s);
     tc::k_tc_chunks_count<<<gpts, 256, 0, s>>>(hv.cell_start, ctr, tune.min[0], nch);
     exclusive_scan_u32(nch, ch0, n, &ctr->n_cells, &ctr->n_tc_chunks[tc::kCount], part, s, &launches);
+    tmark(0);
     tc::k_tc_hd<DP, tc::kCount><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch0, cx, clist, nclist, clab});
+    tmark(1);
     k_count_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
     launches += 3;
     mark(6);
@@ -173,7 +177,9 @@ void run_tc_phases(HdView<float, DP> &hv, cudaStream_t s, char *b, int64_t n, in
     k_uf_init_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
     k_hook_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
     for (int r = 0; r < 6; ++r) k_jump_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
+    tmark(2);
     tc::k_tc_hd<DP, tc::kMerge><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch1, cx, clist, nclist, clab});
+    tmark(3);
     k_merge_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
     k_compress_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
     launches += 11;
@@ -181,7 +187,9 @@ void run_tc_phases(HdView<float, DP> &hv, cudaStream_t s, char *b, int64_t n, in
     // ---- Algorithm 4: canonical ids, core labels, border and noise points ----
     k_comp_min_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
     tc::k_tc_core_labels<DP><<<gpts, 256, 0, s>>>(hv, tc::Tables{ch2, cx, clist, nclist, clab}, nsets, clab);
+    tmark(4);
     tc::k_tc_hd<DP, tc::kLabels><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch2, cx, clist, nclist, clab});
+    tmark(5);
     k_labels_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
     launches += 4;
     mark(9);
@@ -256,9 +264,12 @@ int run_hd(const RunArgs &a) {
     bool tc_phases = false;  // the tensor-core split ran every phase
 
     cudaEvent_t ev[HCA_NUM_STAGES + 1] = {};
+    cudaEvent_t tev[6] = {};
     const bool timing = (a.flags & HCA_FLAG_TIMING) && a.stats && !a.deferred;
-    if (timing)
+    if (timing) {
         for (int i = 0; i <= HCA_NUM_STAGES; ++i) cudaEventCreate(&ev[i]);
+        for (int i = 0; i < 6; ++i) cudaEventCreate(&tev[i]);
+    }
     auto mark = [&](int i) { if (timing) cudaEventRecord(ev[i], s); };
 
     GridParams g;
@@ -519,7 +530,7 @@ int run_hd(const RunArgs &a) {
                               TcTuning{{(uint32_t)a.tune.tc_min_count, (uint32_t)a.tune.tc_min_merge,
                                         (uint32_t)a.tune.tc_min_labels},
                                        (uint32_t)a.tune.first_links, (uint32_t)a.tune.tc_handoff},
-                              mark, launches);
+                              mark, launches, timing ? tev : nullptr);
             tc_phases = true;
         }
     }
@@ -574,16 +585,25 @@ int run_hd(const RunArgs &a) {
         so->n_border_chunks = (int64_t)h->work[5];
         so->n_tc_tiles = (int64_t)h->work[6];
         so->n_tc_rechecks = (int64_t)h->work[7];
+        so->n_tc_pairs = (int64_t)h->tc_pairs;
         for (int i = 0; i < HCA_NUM_STAGES; ++i) {
             float ms = 0.f;
             if (timing) cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
             so->stage_ms[i] = ms;
         }
+        for (int i = 0; i < 3; ++i) {
+            float ms = 0.f;
+            if (timing && tc_phases) cudaEventElapsedTime(&ms, tev[2 * i], tev[2 * i + 1]);
+            so->tc_ms[i] = ms;
+        }
     }
 out:
-    if (timing)
+    if (timing) {
         for (int i = 0; i <= HCA_NUM_STAGES; ++i)
             if (ev[i]) cudaEventDestroy(ev[i]);
+        for (int i = 0; i < 6; ++i)
+            if (tev[i]) cudaEventDestroy(tev[i]);
+    }
     if (own_ws) pool_free(ws, s);
     if (rc != HCA_OK && !a.deferred) cudaStreamSynchronize(s);
     return rc;

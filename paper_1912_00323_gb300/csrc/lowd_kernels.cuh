@@ -385,10 +385,43 @@ __device__ __forceinline__ void add_counter(unsigned long long *ctr, uint32_t v)
 // Stage kernels
 // ------------------------------------------------------------------------------------------
 
+// Points per thread step of the streaming kernels (min/max, binning): the fewest consecutive
+// points whose bytes are a multiple of 16, so a thread reads them with 16-byte loads.
+template <typename T, int D>
+struct VecPts {
+    static constexpr int bytes = D * (int)sizeof(T);
+    static constexpr int pts = bytes % 16 == 0 ? 1 : (bytes % 8 == 0 ? 2 : 4);
+    static constexpr int vec = pts * bytes / 16;  // 16-byte loads per step
+};
+
+// Coordinates of points [j0, j0 + P) (P = VecPts::pts) into x[P * D]: 16-byte loads when the
+// whole group is in range and `vec_ok` (the input is 16-byte aligned), else element loads;
+// points past n read as zero.
+template <typename T, int D>
+__device__ __forceinline__ void load_pts(const T *__restrict__ in, int64_t j0, int64_t n, bool vec_ok,
+                                         T (&x)[VecPts<T, D>::pts * D]) {
+    constexpr int P = VecPts<T, D>::pts, V = VecPts<T, D>::vec;
+    if (vec_ok && j0 + P <= n) {
+        const float4 *src = reinterpret_cast<const float4 *>(in + j0 * D);
+        union {
+            float4 v[V];
+            T e[P * D];
+        } u;
+#pragma unroll
+        for (int k = 0; k < V; ++k) u.v[k] = __ldg(src + k);
+#pragma unroll
+        for (int k = 0; k < P * D; ++k) x[k] = u.e[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < P * D; ++k) x[k] = j0 + k / D < n ? in[j0 * D + k] : T(0);
+    }
+}
+
 // Origin shift (Sec. 2): per-dimension min and max in the input's own precision, plus a NaN
-// check.
+// check.  Each thread step reads VecPts::pts consecutive points with 16-byte loads.
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_minmax(const T *__restrict__ in, int64_t n, DevCounters *ctr) {
+    constexpr int P = VecPts<T, D>::pts;
     T mn[D], mx[D];
 #pragma unroll
     for (int i = 0; i < D; ++i) {
@@ -396,14 +429,21 @@ __global__ void __launch_bounds__(256) k_minmax(const T *__restrict__ in, int64_
         mx[i] = -mn[i];
     }
     bool nan = false;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
-         j += (int64_t)gridDim.x * blockDim.x) {
+    const bool vec_ok = ((uintptr_t)in & 15u) == 0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c * P < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        T x[P * D];
+        load_pts<T, D>(in, c * P, n, vec_ok, x);
 #pragma unroll
-        for (int i = 0; i < D; ++i) {
-            const T x = in[j * D + i];
-            nan |= (x != x);
-            mn[i] = x < mn[i] ? x : mn[i];
-            mx[i] = x > mx[i] ? x : mx[i];
+        for (int t = 0; t < P; ++t) {
+            if (c * P + t >= n) continue;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const T v = x[t * D + i];
+                nan |= (v != v);
+                mn[i] = v < mn[i] ? v : mn[i];
+                mx[i] = v > mx[i] ? v : mx[i];
+            }
         }
     }
 #pragma unroll
@@ -442,36 +482,68 @@ __global__ void __launch_bounds__(256) k_minmax(const T *__restrict__ in, int64_
 }
 
 // Algorithm 1: band index of every coordinate, c_i = floor((x_i - o_i) / side), packed into a
-// key whose order is lexicographic in (c_0, ..., c_{d-1}).
+// key whose order is lexicographic in (c_0, ..., c_{d-1}).  Each thread step bins
+// VecPts::pts consecutive points read with 16-byte loads and stores their keys and indices
+// together.
 template <typename T, int D, typename K>
 __global__ void __launch_bounds__(256) k_bin(const T *__restrict__ in, GridParams g,
                                             K *__restrict__ keys, uint32_t *__restrict__ idx,
                                             uint32_t *__restrict__ digit_counts) {
+    constexpr int P = VecPts<T, D>::pts;
     // digit counts of every radix pass, for the sort that follows
     __shared__ uint32_t h[8][256];
     const int passes = (g.key_bits + 7) / 8;
     for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < g.n;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t key = 0;
+    const bool vec_ok = ((uintptr_t)in & 15u) == 0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c * P < g.n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j0 = c * P;
+        T x[P * D];
+        load_pts<T, D>(in, j0, g.n, vec_ok, x);
+        K kk[P];
 #pragma unroll
-        for (int i = 0; i < D; ++i) {
-            const T x = in[j * D + i];
-            uint32_t c;
-            if (sizeof(T) == 4 && !g.bin_fp64) {
-                float t = __fmul_rn(__fsub_rn((float)x, g.origin_f[i]), g.inv_side_f);
-                c = (uint32_t)floorf(t);
-            } else {
-                double t = __dmul_rn(__dsub_rn((double)x, g.origin[i]), g.inv_side);
-                c = (uint32_t)floor(t);
+        for (int t = 0; t < P; ++t) {
+            uint64_t key = 0;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                uint32_t cc;
+                if (sizeof(T) == 4 && !g.bin_fp64) {
+                    float u = __fmul_rn(__fsub_rn((float)x[t * D + i], g.origin_f[i]), g.inv_side_f);
+                    cc = (uint32_t)floorf(u);
+                } else {
+                    double u = __dmul_rn(__dsub_rn((double)x[t * D + i], g.origin[i]), g.inv_side);
+                    cc = (uint32_t)floor(u);
+                }
+                if (cc > g.ncell[i] - 1) cc = g.ncell[i] - 1;
+                key |= (uint64_t)cc << g.shift[i];
             }
-            if (c > g.ncell[i] - 1) c = g.ncell[i] - 1;
-            key |= (uint64_t)c << g.shift[i];
+            kk[t] = (K)key;
+            if (j0 + t < g.n)
+                for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(uint32_t)(key >> (8 * p)) & 0xffu], 1u);
         }
-        keys[j] = (K)key;
-        idx[j] = (uint32_t)j;
-        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(uint32_t)(key >> (8 * p)) & 0xffu], 1u);
+        if (j0 + P <= g.n && sizeof(K) * P == 16) {
+            // P keys (16 bytes) and P indices at once
+            if (sizeof(K) == 4) {
+                *reinterpret_cast<uint4 *>(keys + j0) =
+                    make_uint4((uint32_t)kk[0], (uint32_t)kk[P > 1 ? 1 : 0], (uint32_t)kk[P > 2 ? 2 : 0],
+                               (uint32_t)kk[P > 3 ? 3 : 0]);
+                *reinterpret_cast<uint4 *>(idx + j0) =
+                    make_uint4((uint32_t)j0, (uint32_t)j0 + 1u, (uint32_t)j0 + 2u, (uint32_t)j0 + 3u);
+            } else {
+                *reinterpret_cast<ulonglong2 *>(keys + j0) =
+                    make_ulonglong2((unsigned long long)kk[0], (unsigned long long)kk[P > 1 ? 1 : 0]);
+                *reinterpret_cast<uint2 *>(idx + j0) = make_uint2((uint32_t)j0, (uint32_t)j0 + 1u);
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < P; ++t) {
+                if (j0 + t < g.n) {
+                    keys[j0 + t] = kk[t];
+                    idx[j0 + t] = (uint32_t)(j0 + t);
+                }
+            }
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {

@@ -60,7 +60,7 @@ void run_group(hca_server *sv, std::vector<int64_t> &ids, cudaStream_t s) {
     const size_t esz = dtype == HCA_F32 ? 4 : 8;
     std::vector<int64_t> off(reqs.size() + 1, 0);
     std::vector<double> eps(reqs.size());
-    std::vector<int32_t> mp(reqs.size());
+    std::vector<int32_t> mp(reqs.size()), dims(reqs.size(), d);
     for (size_t i = 0; i < reqs.size(); ++i) {
         off[i + 1] = off[i] + reqs[i].n;
         eps[i] = reqs[i].eps;
@@ -80,7 +80,7 @@ void run_group(hca_server *sv, std::vector<int64_t> &ids, cudaStream_t s) {
             rc = HCA_ECUDA;
     }
     if (rc == HCA_OK && n > 0)
-        rc = hca_dbscan_batched(dp, dtype, (int32_t)reqs.size(), off.data(), d, eps.data(), mp.data(),
+        rc = hca_dbscan_batched(dp, dtype, (int32_t)reqs.size(), off.data(), dims.data(), eps.data(), mp.data(),
                                 (int32_t *)dl, nullptr, (void *)s, nullptr, 0);
     for (size_t i = 0; i < reqs.size() && rc == HCA_OK; ++i) {
         if (reqs[i].n == 0) continue;

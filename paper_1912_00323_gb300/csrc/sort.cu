@@ -2,11 +2,19 @@
 //
 // A first kernel counts the digits of every pass over all keys (the counts do not depend on
 // the order, so one read of the keys serves all passes); a caller that produced the keys may
-// pass these counts in instead.  Each pass kernel then takes a tile
-// of 4096 keys, ranks every key stably among the keys of its tile with the same digit (warp
-// match + per-warp digit counters + an exclusive scan across warps), learns how many keys of
-// each digit the earlier tiles hold by decoupled look-back, and scatters the tile through
-// shared memory in digit order so that the global stores of each digit run are coalesced.
+// pass these counts in instead.  Each pass kernel then takes a tile of 13,312 keys (1024
+// threads x 13), ranks every key stably among the keys of its tile with the same digit (warp
+// match + per-warp digit counters + an exclusive scan across warps), publishes the tile's digit
+// counts, scatters the tile through shared memory in digit order, learns how many keys of each
+// digit the earlier tiles hold by decoupled look-back, and writes the digit runs out with
+// coalesced stores.
+//
+// Tile size.  A tile is one CTA per SM (its shared memory holds the whole tile), so at two
+// million keys the ~150 tiles all run at once.  With every tile running together a published
+// prefix reaches the later tiles only through their own reads, so the look-back reads 64
+// predecessors per round trip (four thread quarters of 16 words per digit): the last tile of
+// two million keys needs three round trips instead of the dozens that a 4096-key tile with a
+// few words per trip needed.
 //
 // Look-back: a tile publishes, per digit, first its own count (state AGG) and then the count of
 // all tiles up to and including itself (state PREFIX).  A tile reads its predecessors'
@@ -15,7 +23,9 @@
 // tiles that are already running; every wait is bounded (kSpinLimit), and a wait that runs
 // out sets the caller's status word instead of hanging.  Each status word packs
 // (epoch, state, count) into 64 bits so flag and value are read and written together; the
-// epoch (pass number + 1) makes words left by an earlier pass invisible.
+// epoch (pass number + 1) makes words left by an earlier pass invisible.  Words are tile-major
+// (the 256 digits of one tile are consecutive), so a warp reads 32 digits of a tile in one
+// coalesced 256-byte access.
 #include "block_scan.cuh"
 #include "hca_internal.cuh"
 
@@ -23,13 +33,17 @@ namespace hca {
 
 namespace {
 
-constexpr int kSortThreads = 256;
+constexpr int kSortThreads = 1024;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortItems = 16;  // per lane: a warp covers 512 consecutive keys
+constexpr int kSortItems = 13;  // per lane: a warp covers 416 consecutive keys
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kRadix = kSortRadix;
 constexpr int kMaxPasses = kSortMaxPasses;
+constexpr int kQuarters = kSortThreads / kRadix;  // threads per digit in the look-back
+constexpr int kLbWords = 16;                      // predecessors per thread per round trip
+constexpr int kHistThreads = 256;
 static_assert(kSortTile == kSortTileKeys, "tile size shared with the scratch sizing");
+static_assert(kQuarters * kRadix == kSortThreads, "whole quarters of digits");
 constexpr uint32_t kSpinLimit = 1u << 24;
 constexpr uint64_t kStateAgg = 1, kStatePrefix = 2;
 
@@ -39,10 +53,10 @@ __device__ __forceinline__ uint64_t os_pack(uint32_t epoch, uint64_t state, uint
 
 // Digit counts of every pass: ghist[p * 256 + digit].
 template <typename K>
-__global__ void __launch_bounds__(kSortThreads) k_os_hist(const K *__restrict__ keys, int64_t n, int begin_bit,
+__global__ void __launch_bounds__(kHistThreads) k_os_hist(const K *__restrict__ keys, int64_t n, int begin_bit,
                                                          int end_bit, uint32_t *__restrict__ ghist) {
     __shared__ uint32_t h[kMaxPasses][kRadix];
-    for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += kSortThreads) (&h[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += kHistThreads) (&h[0][0])[i] = 0;
     __syncthreads();
     const int passes = (end_bit - begin_bit + 7) / 8;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
@@ -58,125 +72,188 @@ __global__ void __launch_bounds__(kSortThreads) k_os_hist(const K *__restrict__ 
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * kRadix; i += kSortThreads) {
+    for (int i = threadIdx.x; i < passes * kRadix; i += kHistThreads) {
         const uint32_t c = (&h[0][0])[i];
         if (c) atomicAdd(&ghist[i], c);
     }
 }
 
-// One pass: rank, look back, scatter.
+// Shared memory of a pass (dynamic, 16-byte aligned).
 template <typename K>
-__global__ void __launch_bounds__(kSortThreads) k_os_pass(
+struct PassSmem {
+    uint32_t whist[kSortWarps][kRadix];   // per-warp digit counts, then per-warp digit offsets
+    uint32_t part[kQuarters][kRadix];     // counts of warps [8q, 8q + 8), per digit
+    uint32_t lstart[kRadix];              // first position of each digit in the tile
+    uint32_t goff[kRadix];                // global position of the tile's first key of each digit
+    uint32_t lb_sum[kQuarters][kRadix];   // look-back: AGG sum of a quarter's window
+    uint32_t lb_used[kQuarters][kRadix];  // predecessors the quarter consumed
+    uint32_t lb_kind[kQuarters][kRadix];  // 0 window read through, 1 met a PREFIX, 2 met an unpublished word
+    int32_t lb_next[kRadix];              // nearest predecessor not yet added, per digit (-1: done)
+    uint32_t tile_id, pad[3];
+    K keys[kSortTile];
+    uint32_t vals[kSortTile];
+};
+
+// One pass: rank within the tile, publish the tile's digit counts, scatter the tile into
+// shared memory in digit order, look back for the counts of the earlier tiles, write out.
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads, 1) k_os_pass(
     const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, K *__restrict__ keys_out,
     uint32_t *__restrict__ vals_out, int64_t n, int shift, int mask_bits,
     const uint32_t *__restrict__ ghist_pass, unsigned long long *status, uint32_t *ticket, uint32_t epoch,
     uint32_t *err) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    uint32_t(*whist)[kRadix] = reinterpret_cast<uint32_t(*)[kRadix]>(sm);  // [warps][digits]
-    uint32_t *lstart = reinterpret_cast<uint32_t *>(sm) + kSortWarps * kRadix;
-    uint32_t *goff = lstart + kRadix;
-    uint32_t *tile_id = goff + kRadix;
-    K *skeys = reinterpret_cast<K *>(tile_id + 4);
-    uint32_t *svals = reinterpret_cast<uint32_t *>(skeys + kSortTile);
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    PassSmem<K> &S = *reinterpret_cast<PassSmem<K> *>(sm_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int dg = threadIdx.x & (kRadix - 1), q = threadIdx.x / kRadix;
     const uint32_t mask = (1u << mask_bits) - 1u;
-    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&whist[0][0])[i] = 0;
-    if (threadIdx.x == 0) tile_id[0] = atomicAdd(ticket, 1u);
+    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&S.whist[0][0])[i] = 0;
+    if (threadIdx.x == 0) S.tile_id = atomicAdd(ticket, 1u);
     __syncthreads();
-    const uint32_t tile = tile_id[0];
+    const uint32_t tile = S.tile_id;
 
     const int64_t tbase = (int64_t)tile * kSortTile;
     const int64_t wbase = tbase + (int64_t)warp * (32 * kSortItems);
     K k[kSortItems];
     uint32_t v[kSortItems];
-    uint32_t rank[kSortItems];
+    uint32_t rank2[(kSortItems + 1) / 2];  // rank within the warp's digit run, two 16-bit ranks per word
+    static_assert(32 * kSortItems < 65536, "16-bit ranks");
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const int64_t i = wbase + r * 32 + lane;
+        k[r] = i < n ? keys_in[i] : K(0);
+    }
+    // ranks within the warp; the values are loaded meanwhile (needed only for the scatter)
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const int64_t i = wbase + r * 32 + lane;
         const bool valid = i < n;
-        k[r] = valid ? keys_in[i] : K(0);
         v[r] = valid ? vals_in[i] : 0u;
-        const uint32_t dg = valid ? ((uint32_t)(k[r] >> shift) & mask) : (uint32_t)kRadix;
-        const unsigned peers = __match_any_sync(0xffffffffu, dg);
-        const uint32_t before = valid ? whist[warp][dg] : 0u;
+        const uint32_t d = valid ? ((uint32_t)(k[r] >> shift) & mask) : (uint32_t)kRadix;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = valid ? S.whist[warp][d] : 0u;
         __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) whist[warp][dg] = before + __popc(peers);
+        if (valid && lane == __ffs(peers) - 1) S.whist[warp][d] = before + __popc(peers);
         __syncwarp();
-        rank[r] = before + __popc(peers & ((1u << lane) - 1u));
+        const uint32_t rk = before + __popc(peers & ((1u << lane) - 1u));
+        if (r & 1) rank2[r >> 1] |= rk << 16;
+        else rank2[r >> 1] = rk;
     }
     __syncthreads();
-    const int dg = threadIdx.x;  // kSortThreads == kRadix: one thread per digit
-    uint32_t count = 0;
+    // per digit: the count of each quarter's eight warps, then per-warp exclusive offsets
+    {
+        uint32_t c = 0;
 #pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) {
-        const uint32_t t = whist[w][dg];
-        whist[w][dg] = count;
-        count += t;
+        for (int w = 0; w < kSortWarps / kQuarters; ++w) c += S.whist[q * (kSortWarps / kQuarters) + w][dg];
+        S.part[q][dg] = c;
     }
-    // decoupled look-back over the earlier tiles, per digit
-    volatile unsigned long long *st = status;
-    uint32_t excl = 0;
-    if (tile == 0) {
-        st[dg] = os_pack(epoch, kStatePrefix, count);
-    } else {
-        st[(uint64_t)tile * kRadix + dg] = os_pack(epoch, kStateAgg, count);
-        // read eight predecessors per round trip, nearest first; stop at the first PREFIX, and
-        // re-read from the first word that is not published yet
-        int64_t j = (int64_t)tile - 1;
-        uint32_t spins = 0;
-        bool done = false;
-        while (!done && j >= 0) {
-            uint64_t w[8];
+    __syncthreads();
+    uint32_t count = 0;  // the tile's count of digit dg
+    {
+        uint32_t base = 0;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) w[u] = (j - u >= 0) ? st[(uint64_t)(j - u) * kRadix + dg] : 0ull;
-            int u = 0;
-            for (; u < 8 && j - u >= 0; ++u) {
-                const uint32_t hi = (uint32_t)(w[u] >> 32);
-                if ((hi >> 2) != epoch || (hi & 3u) == 0u) break;   // not published yet
-                excl += (uint32_t)w[u];
-                if ((hi & 3u) == kStatePrefix) { done = true; break; }
-            }
-            if (done) break;
-            if (u < 8 && j - u >= 0) {                               // wait on tile j - u
-                if (++spins > kSpinLimit) {
-                    atomicOr(err, 2u);
-                    break;
-                }
-            }
-            j -= u;
+        for (int qq = 0; qq < kQuarters; ++qq) {
+            const uint32_t c = S.part[qq][dg];
+            base += qq < q ? c : 0u;
+            count += c;
         }
-        st[(uint64_t)tile * kRadix + dg] = os_pack(epoch, kStatePrefix, excl + count);
+#pragma unroll
+        for (int w = 0; w < kSortWarps / kQuarters; ++w) {
+            uint32_t &h = S.whist[q * (kSortWarps / kQuarters) + w][dg];
+            const uint32_t t = h;
+            h = base;
+            base += t;
+        }
     }
-    // global start of this digit: exclusive scan of the pass's digit counts
-    uint32_t total_unused;
-    const uint32_t gdig = block_exclusive_scan<kSortThreads>(ghist_pass[dg], &total_unused);
-    goff[dg] = gdig + excl;
-    uint32_t tile_count;
-    lstart[dg] = block_exclusive_scan<kSortThreads>(count, &tile_count);
+    // publish this tile's count of the digit at once, so later tiles can read past it
+    volatile unsigned long long *st = status;
+    if (q == 0) st[(uint64_t)tile * kRadix + dg] = os_pack(epoch, tile == 0 ? kStatePrefix : kStateAgg, count);
+    // local and global digit starts (the global one from the pass's digit counts)
+    uint32_t tile_count, total_unused;
+    const uint32_t lst = block_exclusive_scan<kSortThreads>(q == 0 ? count : 0u, &tile_count);
+    const uint32_t gdig = block_exclusive_scan<kSortThreads>(q == 0 ? ghist_pass[dg] : 0u, &total_unused);
+    if (q == 0) {
+        S.lstart[dg] = lst;
+        S.lb_next[dg] = (int32_t)tile - 1;
+    }
     __syncthreads();
+    // the tile in digit order in shared memory (frees the key registers before the look-back)
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const int64_t i = wbase + r * 32 + lane;
         if (i < n) {
             const uint32_t d = (uint32_t)(k[r] >> shift) & mask;
-            const uint32_t lpos = lstart[d] + whist[warp][d] + rank[r];
-            skeys[lpos] = k[r];
-            svals[lpos] = v[r];
+            const uint32_t lpos = S.lstart[d] + S.whist[warp][d] + ((rank2[r >> 1] >> (16 * (r & 1))) & 0xffffu);
+            S.keys[lpos] = k[r];
+            S.vals[lpos] = v[r];
         }
+    }
+    // decoupled look-back over the earlier tiles: per round trip, quarter q of digit dg reads
+    // the 16 predecessors [j - 16 q - 15, j - 16 q] (j = nearest not yet added), adds the AGG
+    // counts from its nearest down to the first PREFIX (included) or unpublished word
+    // (excluded); the quarter-0 thread then joins the quarters in order.  Bounded wait.
+    uint32_t excl = 0, spins = 0;
+    int32_t next = (int32_t)tile - 1;  // quarter 0: nearest predecessor not yet added (-1: done)
+    for (;;) {
+        const int32_t j = S.lb_next[dg];
+        if (j >= 0) {
+            const int32_t hi = j - kLbWords * q;
+            unsigned long long w[kLbWords];
+#pragma unroll
+            for (int u = 0; u < kLbWords; ++u)
+                w[u] = hi - u >= 0 ? st[(uint64_t)(hi - u) * kRadix + dg] : 0ull;
+            uint32_t sum = 0, used = 0, kind = 0;
+#pragma unroll
+            for (int u = 0; u < kLbWords; ++u) {
+                if (kind != 0 || hi - u < 0) continue;
+                const uint32_t h32 = (uint32_t)(w[u] >> 32);
+                if ((h32 >> 2) != epoch || (h32 & 3u) == 0u) {
+                    kind = 2;
+                    continue;
+                }
+                sum += (uint32_t)w[u];
+                ++used;
+                if ((h32 & 3u) == kStatePrefix) kind = 1;
+            }
+            S.lb_sum[q][dg] = sum;
+            S.lb_used[q][dg] = used;
+            S.lb_kind[q][dg] = kind;
+        }
+        __syncthreads();
+        if (q == 0 && j >= 0) {
+            int32_t nj = j;
+            bool done = false, stalled = false;
+#pragma unroll
+            for (int qq = 0; qq < kQuarters; ++qq) {
+                if (done || stalled) continue;
+                excl += S.lb_sum[qq][dg];
+                nj -= (int32_t)S.lb_used[qq][dg];
+                const uint32_t kind = S.lb_kind[qq][dg];
+                if (kind == 1 || nj < 0) done = true;
+                else if (kind == 2) stalled = true;
+            }
+            if (stalled && ++spins > kSpinLimit) {
+                atomicOr(err, 2u);
+                done = true;
+            }
+            next = done ? -1 : nj;
+            S.lb_next[dg] = next;
+        }
+        // every digit done: the quarter-0 threads decide, read after this barrier
+        if (__syncthreads_and(q != 0 || next < 0)) break;
+    }
+    if (q == 0) {
+        if (tile > 0) st[(uint64_t)tile * kRadix + dg] = os_pack(epoch, kStatePrefix, excl + count);
+        S.goff[dg] = gdig + excl;
     }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < tile_count; i += kSortThreads) {
-        const K key = skeys[i];
+        const K key = S.keys[i];
         const uint32_t d = (uint32_t)(key >> shift) & mask;
-        const uint32_t gpos = goff[d] + (i - lstart[d]);
+        const uint32_t gpos = S.goff[d] + (i - S.lstart[d]);
         keys_out[gpos] = key;
-        vals_out[gpos] = svals[i];
+        vals_out[gpos] = S.vals[i];
     }
-}
-
-template <typename K>
-constexpr size_t pass_smem() {
-    return sizeof(uint32_t) * (kSortWarps * kRadix + 2 * kRadix + 4) + (sizeof(K) + sizeof(uint32_t)) * kSortTile;
 }
 
 int64_t sort_tiles(int64_t n) { return sort_tiles_for(n); }
@@ -193,7 +270,6 @@ bool radix_sort_pairs(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt, 
                       cudaStream_t s, int *launches, uint32_t *err_out, const uint32_t *digit_counts) {
     (void)partials;
     if (n <= 1 || end_bit <= begin_bit) return false;
-    static_assert(kSortThreads == kRadix, "one thread per digit in the pass kernel");
     const int nb = (int)sort_tiles(n);
     const int passes = (end_bit - begin_bit + 7) / 8;
     unsigned long long *status = reinterpret_cast<unsigned long long *>(hist);  // 8-byte aligned
@@ -204,20 +280,20 @@ bool radix_sort_pairs(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt, 
     if (digit_counts) {
         ghist = const_cast<uint32_t *>(digit_counts);
     } else {
-        k_os_hist<K><<<nb < 1216 ? nb : 1216, kSortThreads, 0, s>>>(keys, n, begin_bit, end_bit, ghist);
+        const int64_t hb = (n + kHistThreads - 1) / kHistThreads;
+        k_os_hist<K><<<hb < 1216 ? (int)hb : 1216, kHistThreads, 0, s>>>(keys, n, begin_bit, end_bit, ghist);
         if (launches) *launches += 1;
     }
-    if (pass_smem<K>() > 48 * 1024)
-        cudaFuncSetAttribute(k_os_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<K>());
+    const size_t smem = sizeof(PassSmem<K>);
+    cudaFuncSetAttribute(k_os_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     bool flipped = false;
     K *kin = keys, *kout = keys_alt;
     uint32_t *vin = vals, *vout = vals_alt;
     for (int p = 0; p < passes; ++p) {
         const int shift = begin_bit + 8 * p;
         const int bits = (end_bit - shift) < 8 ? (end_bit - shift) : 8;
-        k_os_pass<K><<<nb, kSortThreads, pass_smem<K>(), s>>>(kin, vin, kout, vout, n, shift, bits,
-                                                              ghist + p * kRadix, status, tickets + p,
-                                                              (uint32_t)(p + 1), err);
+        k_os_pass<K><<<nb, kSortThreads, smem, s>>>(kin, vin, kout, vout, n, shift, bits, ghist + p * kRadix,
+                                                    status, tickets + p, (uint32_t)(p + 1), err);
         K *tk = kin; kin = kout; kout = tk;
         uint32_t *tv = vin; vin = vout; vout = tv;
         flipped = !flipped;

@@ -10,7 +10,7 @@
 // holds it until the process exits.  Its size follows the sort's own geometry: the
 // alternate keys and values of HCA_SORT_NOALLOC_MAX_PAIRS pairs (12 bytes each, 3 MiB) and
 // the look-back words, digit counts, tickets and status word of that many pairs (about
-// 136 KiB with 4096-key tiles).  In host code its name is only a stand-in: its device address
+// 48 KiB with the sort's 13,312-key tiles).  In host code its name is only a stand-in: its device address
 // is looked up with cudaGetSymbolAddress, with the device current, the first time a call
 // runs in a CUDA context of that device (normally once per device; again after
 // cudaDeviceReset, which destroys the context the cached address belongs to).

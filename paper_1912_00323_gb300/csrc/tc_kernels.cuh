@@ -289,6 +289,7 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
     uint32_t phase = 0;
     bool failed = false;  // CTA-uniform
     uint32_t n_tiles = 0, n_skip = 0, n_re = 0, n_noise = 0;
+    unsigned long long n_pairs = 0;  // thread 0: valid rows x valid candidates of the tiles computed
 
     for (;;) {
         __syncthreads();  // every thread is done with the shared memory of the previous chunk
@@ -449,6 +450,7 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
             phase ^= 1u;
             asm volatile("tcgen05.fence::after_thread_sync;");
             ++n_tiles;
+            if (tid == 0) n_pairs += (unsigned long long)min((uint32_t)kTile, rend - k0) * nq;
             bool need = have && (MODE != kCount || !done);
             if (__any_sync(0xffffffffu, need)) {
                 for (uint32_t c0 = 0; c0 < nq; c0 += 32) {
@@ -563,6 +565,7 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTile));
     add_counter(&v.ctr->work[6], tid == 0 ? n_tiles : 0u);
+    if (tid == 0 && n_pairs) atomicAdd(&v.ctr->tc_pairs, n_pairs);
     add_counter(&v.ctr->work[7], n_re);
     if (MODE == kMerge) add_counter(&v.ctr->work[2], tid == 0 ? n_skip : 0u);
     if (MODE == kLabels) {

@@ -175,21 +175,33 @@ extern "C" int hca_autotune(const void *d_points, int32_t dtype, int64_t n, int3
 }
 
 extern "C" int hca_autotune_batched(const void *d_points, int32_t dtype, int32_t n_sets, const int64_t *offsets,
-                                    int32_t d, const double *eps, const int32_t *min_pts, void *stream,
-                                    int32_t repeats, hca_tuning *out, double *best_ms) {
-    if (n_sets < 1 || !offsets || offsets[0] != 0) return HCA_EINVAL;
+                                    const int32_t *d_per_set, const double *eps, const int32_t *min_pts,
+                                    void *stream, int32_t repeats, hca_tuning *out, double *best_ms) {
+    std::vector<SetGroup> groups;
+    int rc = group_sets(n_sets, offsets, d_per_set, eps, min_pts, nullptr, nullptr, groups);
+    if (rc) return rc;
     const int64_t n = offsets[n_sets];
-    int rc = check_common(d_points, dtype, n, d, 1.0, 1, d_points);
+    rc = check_common(d_points, dtype, n, 1, 1.0, 1, d_points);
     if (rc) return rc;
     if (n == 0) return HCA_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    void *lab = nullptr;
-    if (pool_alloc(&lab, (size_t)n * 4, s) != cudaSuccess) return HCA_ENOMEM;
-    rc = tune_with(d, dtype, s, repeats, [&](const hca_tuning &t) {
-        return batched_tuned(d_points, dtype, n_sets, offsets, d, eps, min_pts, (int32_t *)lab, nullptr, stream,
-                             nullptr, 0, t);
-    }, out, best_ms);
-    pool_free(lab, s);
-    cudaStreamSynchronize(s);
-    return rc;
+    double total = 0.0;
+    for (const SetGroup &g : groups) {
+        if (g.n == 0) continue;
+        // the labels of the trial runs go to a scratch buffer laid out as the caller's
+        void *lab = nullptr;
+        if (pool_alloc(&lab, (size_t)n * 4, s) != cudaSuccess) return HCA_ENOMEM;
+        hca_tuning pick;
+        double ms = 0.0;
+        rc = tune_with(g.d, dtype, s, repeats, [&](const hca_tuning &t) {
+            return run_group(g, d_points, dtype, (int32_t *)lab, nullptr, s, nullptr, 0, t);
+        }, &pick, &ms);
+        pool_free(lab, s);
+        cudaStreamSynchronize(s);
+        if (rc) return rc;
+        if (out) out[g.d - 1] = pick;
+        total += ms;
+    }
+    if (best_ms) *best_ms = total;
+    return HCA_OK;
 }

@@ -93,3 +93,38 @@ def test_server_argument_checks(pkg):
     assert lib.hca_submit(None, None, None) == pkg.HCA_EINVAL
     assert lib.hca_poll(None, 1) == pkg.HCA_EINVAL
     assert lib.hca_cancel(None, 1) == pkg.HCA_EINVAL
+
+
+def test_batched_call_checks_per_set_dimensions_on_the_host(pkg):
+    """hca_dbscan_batched takes one d per set: a d outside 1..64, a NULL d array, decreasing
+    offsets or a bad eps are refused before any device work."""
+    import ctypes
+    lib = pkg.load()
+    off = (ctypes.c_int64 * 3)(0, 4, 9)
+    eps = (ctypes.c_double * 2)(1.0, 1.0)
+    mp = (ctypes.c_int32 * 2)(3, 3)
+    for dims in ((2, 0), (2, 65)):
+        dd = (ctypes.c_int32 * 2)(*dims)
+        assert lib.hca_dbscan_batched(None, 0, 2, off, dd, eps, mp, None, None, None, None, 0) == pkg.HCA_EINVAL
+    assert lib.hca_dbscan_batched(None, 0, 2, off, None, eps, mp, None, None, None, None, 0) == pkg.HCA_EINVAL
+    dd = (ctypes.c_int32 * 2)(2, 3)
+    bad_eps = (ctypes.c_double * 2)(1.0, float("nan"))
+    assert lib.hca_dbscan_batched(None, 0, 2, off, dd, bad_eps, mp, None, None, None, None, 0) == pkg.HCA_EINVAL
+    dec = (ctypes.c_int64 * 3)(0, 4, 2)
+    assert lib.hca_dbscan_batched(None, 0, 2, dec, dd, eps, mp, None, None, None, None, 0) == pkg.HCA_EINVAL
+
+
+def test_pack_sets_layout():
+    """pack_sets lays the sets' row-major blocks one after another (argument marshalling only)."""
+    torch = pytest.importorskip("torch")
+    import paper_1912_00323_gb300 as p
+    a = np.arange(6, dtype=np.float32).reshape(3, 2)
+    b = np.arange(100, 108, dtype=np.float32).reshape(2, 4)
+    c = np.zeros((0, 3), np.float32)
+    flat, off, dims = p.pack_sets([a, c, b], device="cpu")
+    assert off.tolist() == [0, 3, 3, 5] and dims.tolist() == [2, 3, 4]
+    assert flat.numpy().tolist() == a.ravel().tolist() + b.ravel().tolist()
+    o, dd, e, m = p._set_args(flat, off, [1.0, 1.0, 1.0], [2, 2, 2], dims)
+    assert dd.dtype == np.int32 and o.dtype == np.int64
+    with pytest.raises(ValueError):
+        p._set_args(flat, off, [1.0, 1.0, 1.0], [2, 2, 2], [2, 3, 5])   # 3*2 + 2*5 != 14 values

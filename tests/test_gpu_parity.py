@@ -5,6 +5,7 @@ point sets: hand-derived fixtures, lattice sets with many pairs at exactly eps, 
 full-size copies of the workload recipes, and edge cases."""
 import math
 import os
+import sys
 
 import numpy as np
 import pytest
@@ -218,7 +219,7 @@ def test_error_codes(env):
     assert e.value.code == pkg.HCA_ERANGE
 
 
-@pytest.mark.parametrize("n", [2, 100, 4096, 4097, 1_000_003])
+@pytest.mark.parametrize("n", [2, 100, 4096, 4097, 13312, 13313, 1_000_003, 4_000_037])
 @pytest.mark.parametrize("kbytes,bits", [(4, (0, 32)), (4, (0, 13)), (8, (0, 64)), (8, (5, 41))])
 def test_radix_sort_matches_stable_argsort(env, n, kbytes, bits):
     torch, pkg, _ = env
@@ -262,6 +263,33 @@ def test_aniso16d_reduced(env, n, clusters):
     want = oracle.grid(X.astype(np.float64), eps, min_pts)
     assert want[1].any() and (want[0] < 0).any()
     assert_parity(run_device(env, X, eps, min_pts), want)
+
+
+def _aniso16d_oracle(oracle, X, eps, min_pts):
+    """The oracle's labels and core flags for the full 16-D workload: the stored result of
+    tests/golden/make_aniso16d_full.py when this platform generates the same coordinates
+    (SHA-256 of the array), else the threaded oracle run here on every host core."""
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+    import make_aniso16d_full as golden
+    if os.path.exists(golden.OUT):
+        npz = np.load(golden.OUT)
+        if str(npz["sha256"]) == golden.input_sha256(X):
+            return golden.decode(npz) + ("stored",)
+    lab, core = oracle.grid(X.astype(np.float64), eps, min_pts, threads=0)
+    return lab, core, "computed"
+
+
+def test_aniso16d_full_element_by_element(env):
+    """The 16-D workload at full size (n = 1,000,000 float32 on the 2^-12 lattice, 100
+    anisotropic clusters + 10% noise, eps 4, minPts 20), on the tensor-core tiles: every label
+    and core flag equals the oracle's (Definitions 1-5, canonical ids)."""
+    torch, pkg, oracle = env
+    X, eps, min_pts = workloads.aniso16d()
+    want_lab, want_core, how = _aniso16d_oracle(oracle, X, eps, min_pts)
+    got = run_device(env, X, eps, min_pts, stats=True)
+    assert got[2]["n_tc_tiles"] > 0
+    assert len(np.unique(want_lab[want_lab >= 0])) >= 50, how
+    assert_parity(got, (want_lab, want_core))
 
 
 def test_aniso16d_full_sampled(env):
@@ -362,6 +390,61 @@ def test_batched_recipe_equals_separate_calls(env, dims):
         if s % 20 == 0:
             want = oracle.grid(X.astype(np.float64), eps, mp)
             np.testing.assert_array_equal(single, want[0], err_msg=f"set {s} vs oracle")
+
+
+def _mixed_sets(seed, count, dims=(2, 3, 8)):
+    """Interleaved sets of several dimensions (blobs + noise, own eps and MINPTS), a few empty."""
+    r = np.random.Generator(np.random.PCG64(seed))
+    sets = []
+    for k in range(count):
+        d = int(dims[k % len(dims)])
+        (X, eps, mp), = workloads.batched_sets(n_sets=1, seed=seed * 1000 + k, n_min=50, n_max=9000, dims=(d,))
+        if r.uniform() < 0.08:
+            X = X[:0]
+        sets.append((X, eps, mp))
+    return sets
+
+
+@pytest.mark.parametrize("order", ["interleaved", "grouped"])
+def test_batched_mixed_dimensions_one_call(env, order):
+    """One hca_dbscan_batched call over sets of d = 2, 3 and 8 (each with its own eps and
+    MINPTS): every set's labels and core flags equal the oracle's.  Interleaved sets are
+    gathered per d and scattered back; sets already grouped by d run in place."""
+    torch, pkg, oracle = env
+    sets = _mixed_sets(61, 45)
+    if order == "grouped":
+        sets = sorted(sets, key=lambda s: s[0].shape[1])
+    flat, off, dims = pkg.pack_sets([s[0] for s in sets])
+    core = torch.empty(int(off[-1]), dtype=torch.uint8, device="cuda")
+    lab, st = pkg.hca_dbscan_batched(flat, off, [s[1] for s in sets], [s[2] for s in sets], dims=dims,
+                                     core=core, stats=True)
+    lab, core = lab.cpu().numpy(), core.cpu().numpy()
+    assert st["n_points"] == off[-1]
+    for s, (X, eps, mp) in enumerate(sets):
+        if len(X) == 0:
+            continue
+        want = oracle.grid(X.astype(np.float64), eps, mp)
+        np.testing.assert_array_equal(lab[off[s]:off[s + 1]], want[0], err_msg=f"set {s} (d={X.shape[1]})")
+        np.testing.assert_array_equal(core[off[s]:off[s + 1]], want[1], err_msg=f"set {s} (d={X.shape[1]})")
+
+
+def test_batched_mixed_dimensions_float64_and_repeat(env):
+    """float64 sets of d = 1, 4, 5 interleaved; a second call on the same buffers gives the
+    same result (the gather buffers and tables are rebuilt per call)."""
+    torch, pkg, oracle = env
+    sets = []
+    for k in range(18):
+        d = (1, 4, 5)[k % 3]
+        X, eps, mp = workloads.lattice(300 + 50 * k, d, seed=900 + k, spread=2.0 + d, box=6.0 + 3 * d,
+                                       eps_steps=4, min_pts=3 + k % 4)
+        sets.append((X, eps, mp))
+    flat, off, dims = pkg.pack_sets([s[0] for s in sets])
+    args = (flat, off, [s[1] for s in sets], [s[2] for s in sets])
+    a = pkg.hca_dbscan_batched(*args, dims=dims).cpu().numpy()
+    b = pkg.hca_dbscan_batched(*args, dims=dims).cpu().numpy()
+    np.testing.assert_array_equal(a, b)
+    for s, (X, eps, mp) in enumerate(sets):
+        np.testing.assert_array_equal(a[off[s]:off[s + 1]], oracle.grid(X, eps, mp)[0], err_msg=f"set {s}")
 
 
 def test_batched_rejects_bad_offsets(env):

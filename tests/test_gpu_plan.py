@@ -108,6 +108,35 @@ def test_batched_plan(env, d):
             np.testing.assert_array_equal(lab[off[s]:off[s + 1]], want[0], err_msg=f"set {s}")
 
 
+def test_batched_plan_mixed_dimensions_one_graph(env):
+    """A batched plan over interleaved sets of d = 2, 3 and 8: the d groups are branches of
+    one graph (one launch); every relaunch equals the batched call and the oracle."""
+    torch, pkg, oracle = env
+    sets = []
+    for k in range(27):
+        d = (2, 3, 8)[k % 3]
+        (X, e, m), = workloads.batched_sets(n_sets=1, seed=5000 + k, n_min=100, n_max=5000, dims=(d,))
+        sets.append((X, e, m))
+    flat, off, dims = pkg.pack_sets([s[0] for s in sets])
+    lo = np.concatenate([s[0].min(0) for s in sets])
+    hi = np.concatenate([s[0].max(0) for s in sets])
+    eps = [s[1] for s in sets]
+    mp = [s[2] for s in sets]
+    core = torch.empty(int(off[-1]), dtype=torch.uint8, device="cuda")
+    with pkg.Plan(flat, eps, mp, lo, hi, offsets=off, dims=dims, core=core) as plan:
+        for _ in range(3):
+            plan.labels.fill_(-7)
+            plan.launch()
+            st = plan.wait()
+            lab = plan.labels.cpu().numpy()
+            np.testing.assert_array_equal(
+                lab, pkg.hca_dbscan_batched(flat, off, eps, mp, dims=dims).cpu().numpy())
+        assert st["n_core_points"] == int(core.sum().item())
+        for s in range(len(sets)):
+            want = oracle.grid(sets[s][0].astype(np.float64), eps[s], mp[s])
+            np.testing.assert_array_equal(lab[off[s]:off[s + 1]], want[0], err_msg=f"set {s}")
+
+
 @pytest.mark.parametrize("d", [5, 8, 16])
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
 def test_plan_coarse_grid(env, d, dtype):

@@ -105,7 +105,7 @@ def test_autotune_batched_low_d(env):
     mp = [s[2] for s in sets]
     t = torch.from_numpy(X).cuda()
     tune, ms = pkg.hca_autotune_batched(t, off, eps, mp, repeats=1)
-    assert tune["path"] in (1, 2) and ms > 0
+    assert set(tune) == {3} and tune[3]["path"] in (1, 2) and ms > 0
     for path in (1, 2):
         pkg.hca_tuning_set(3, {"path": path})
         lab = pkg.hca_dbscan_batched(t, off, eps, mp).cpu().numpy()

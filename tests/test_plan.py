@@ -28,7 +28,15 @@ def test_create_refuses_bad_arguments(lib):
     off = (ctypes.c_int64 * 3)(0, 5, 3)                 # decreasing offsets
     eps = (ctypes.c_double * 2)(1.0, 1.0)
     mp = (ctypes.c_int32 * 2)(4, 4)
-    assert L.hca_plan_create_batched(ctypes.byref(h), None, 0, 2, off, 2, eps, mp, box, box, None, None) == E
+    dims = (ctypes.c_int32 * 2)(2, 2)
+    assert L.hca_plan_create_batched(ctypes.byref(h), None, 0, 2, off, dims, eps, mp, box, box, None, None) == E
+    off = (ctypes.c_int64 * 3)(0, 5, 8)
+    bad_dims = (ctypes.c_int32 * 2)(2, 65)              # d above 64
+    assert L.hca_plan_create_batched(ctypes.byref(h), None, 0, 2, off, bad_dims, eps, mp, box, box, None,
+                                     None) == E
+    inverted = (ctypes.c_double * 4)(1, 1, 0, 0)        # box_min above box_max
+    assert L.hca_plan_create_batched(ctypes.byref(h), None, 0, 2, off, dims, eps, mp, inverted, box, None,
+                                     None) == E
     assert L.hca_plan_launch(None, None) == E
     assert L.hca_plan_wait(None, None, None) == E
     assert L.hca_plan_destroy(None) == E

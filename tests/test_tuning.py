@@ -67,4 +67,5 @@ def test_autotune_argument_checks(pkg):
     assert lib.hca_autotune(None, 0, 10, 65, 1.0, 4, None, 2, None, None) == pkg.HCA_EINVAL
     assert lib.hca_autotune(None, 7, 10, 3, 1.0, 4, None, 2, None, None) == pkg.HCA_EINVAL
     off = (ctypes.c_int64 * 2)(1, 5)
-    assert lib.hca_autotune_batched(None, 0, 1, off, 3, None, None, None, 2, None, None) == pkg.HCA_EINVAL
+    dims = (ctypes.c_int32 * 1)(3)
+    assert lib.hca_autotune_batched(None, 0, 1, off, dims, None, None, None, 2, None, None) == pkg.HCA_EINVAL
