@@ -532,8 +532,8 @@ def config_batched(pkg, torch, stream, flush, steps, warmup, n_sets, plain_sampl
             "default_tuning_ms": dms[0], "autotune": {"tuning_per_d": tunings, "seconds": tune_s,
                                                      "best_ms_sum": tune_ms},
             "graph_plan": {"ms_per_step": gm, "value": n_total / (gm / 1e3),
-                           "path": "one batched plan: the d groups are parallel branches of one CUDA graph, "
-                                   "one graph launch per step", "labels": "identical to the batched call"},
+                           "path": "one batched plan: the d groups captured one after another into one CUDA "
+                                   "graph, one graph launch per step", "labels": "identical to the batched call"},
             "cuda_cores_only": {"ms_per_step": cms[0], "value": n_total / (cms[0] / 1e3),
                                 "speedup_of_tuned": cms[0] / med},
             "plain_fp64_per_set": {"sets": len(sample), "points": s_points, "seconds": plain_s,

@@ -127,6 +127,9 @@ typedef struct hca_stats {
     int64_t n_tc_pairs;
     float tc_ms[3];
     int32_t reserved2;
+    /* device workspace this call took from the library's pool (bytes; at most the bound of
+       hca_workspace_bytes) */
+    int64_t workspace_bytes;
 } hca_stats;
 
 /*
@@ -209,9 +212,14 @@ typedef struct hca_request {
 typedef struct hca_server hca_server;
 
 /* Start a server on `device` with `workers` worker threads (1..16) and a device-memory budget
- * (bytes charged per job: points, labels and about 1 KB of workspace per point).  A job larger
- * than the whole budget runs alone.  The caller keeps every job's buffers alive until the
- * job completes. */
+ * (bytes charged per job: its points and labels, the hca_workspace_bytes bound of its
+ * workspace, and 16 bytes per point plus 1 KB of slack for sharing a call).  A job larger than
+ * the whole budget runs alone.  Each worker keeps its staging buffers for the points and labels
+ * on the device from batch to batch, and its clustering workspace comes from the library's
+ * pool, which keeps freed blocks for the next call; every intermediate (sorted grid,
+ * union-find state) stays on the device until the job's labels are copied out.  Within a batch
+ * the (d, dtype) groups with the fewest coordinates run first.  The caller keeps every job's
+ * buffers alive until the job completes. */
 HCA_API int hca_server_create(hca_server **server, int32_t device, int64_t hbm_budget_bytes, int32_t workers);
 /* Stop accepting jobs, cancel queued ones (HCA_ECANCELED), finish running ones, free. */
 HCA_API int hca_server_destroy(hca_server *server);
@@ -274,8 +282,8 @@ HCA_API int hca_radix_sort_pairs_noalloc(void *d_keys, uint32_t *d_vals, int64_t
  *              are then undefined).  A larger box gives the same labels (the grid origin does
  *              not change a label).
  * A batched plan takes the sets of hca_dbscan_batched (one d per set).  Its d groups are
- * captured as parallel branches of the one graph (gathering and scattering included), so they
- * overlap on the device, and hca_plan_launch is one graph launch for all of them.
+ * captured one after another into the one graph (gathering and scattering included), so
+ * hca_plan_launch is one graph launch for all of them.
  * hca_plan_create[_batched] synchronises (it sizes and allocates the workspace and captures
  * the graph; no kernel runs).  hca_plan_launch enqueues one clustering on `stream` and returns.
  * hca_plan_wait synchronises `stream` and returns the launch's code: HCA_OK, HCA_ERANGE (a
@@ -349,6 +357,20 @@ HCA_API int hca_autotune_batched(const void *d_points, int32_t dtype, int32_t n_
                                  const int64_t *offsets, const int32_t *d_per_set, const double *eps,
                                  const int32_t *min_pts, void *stream, int32_t repeats,
                                  hca_tuning *out, double *best_ms);
+
+/*
+ * hca_workspace_bytes -- the device memory one clustering call takes from the library's pool:
+ * an upper bound for hca_dbscan_device / hca_dbscan_device_ex on n points of dimension d, for
+ * any extents, eps and MINPTS, with the tuning of d in effect now and `flags`.  The host entry
+ * point hca_dbscan adds its copies of the points and labels (n (d * element size + 4) bytes).
+ * A batched call takes, per d group, at most this bound for the group's points plus a few
+ * hundred bytes per set (more only through the power-of-two rounding of its hash table, below
+ * 16 bytes per point), and a group whose sets are not consecutive also a compact copy of its
+ * points, labels and core flags.  The paper has no counterpart: the request server admits jobs
+ * by this bound.  Needs no device.
+ *   bytes  host, written on success.
+ */
+HCA_API int hca_workspace_bytes(int64_t n, int32_t d, int32_t dtype, int32_t flags, int64_t *bytes);
 
 /* Static description of a return code; never NULL. */
 HCA_API const char *hca_strerror(int code);

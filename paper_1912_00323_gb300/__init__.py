@@ -31,7 +31,7 @@ STAGES = ("minmax", "bin", "sort", "cells", "hash", "core", "reps", "merge", "la
 ABI_FUNCTIONS = ("hca_dbscan", "hca_dbscan_device", "hca_dbscan_device_ex", "hca_dbscan_batched",
                  "hca_radix_sort_pairs", "hca_tuning_get", "hca_tuning_set", "hca_autotune",
                  "hca_autotune_batched", "hca_plan_create", "hca_plan_create_batched", "hca_plan_launch",
-                 "hca_plan_wait", "hca_plan_destroy", "hca_strerror", "hca_version")
+                 "hca_plan_wait", "hca_plan_destroy", "hca_workspace_bytes", "hca_strerror", "hca_version")
 
 
 class HcaStats(ctypes.Structure):
@@ -46,7 +46,8 @@ class HcaStats(ctypes.Structure):
                 ("n_exhaustive_chunks", ctypes.c_int64), ("n_border_chunks", ctypes.c_int64),
                 ("n_tc_tiles", ctypes.c_int64), ("n_tc_rechecks", ctypes.c_int64),
                 ("n_core_cells", ctypes.c_int64), ("n_tc_pairs", ctypes.c_int64),
-                ("tc_ms", ctypes.c_float * 3), ("reserved2", ctypes.c_int32)]
+                ("tc_ms", ctypes.c_float * 3), ("reserved2", ctypes.c_int32),
+                ("workspace_bytes", ctypes.c_int64)]
 
     def as_dict(self):
         skip = ("stage_ms", "reserved", "tc_ms", "reserved2")
@@ -121,6 +122,8 @@ def load():
     lib.hca_plan_destroy.argtypes = [vp]
     for f in ("hca_plan_create", "hca_plan_create_batched", "hca_plan_launch", "hca_plan_wait", "hca_plan_destroy"):
         getattr(lib, f).restype = ctypes.c_int
+    lib.hca_workspace_bytes.argtypes = [i64, i32, i32, i32, ctypes.POINTER(i64)]
+    lib.hca_workspace_bytes.restype = ctypes.c_int
     lib.hca_strerror.argtypes = [ctypes.c_int]
     lib.hca_strerror.restype = ctypes.c_char_p
     lib.hca_version.restype = i32
@@ -279,6 +282,17 @@ def hca_dbscan_batched(points, offsets, eps, min_pts, dims=None, labels=None, co
     if stats or timing:
         return labels, st.as_dict()
     return labels
+
+
+def hca_workspace_bytes(n: int, d: int, dtype="float32", fp64_only: bool = False, tensor_cores: bool = True) -> int:
+    """Upper bound on the device workspace of one clustering call on n points of dimension d
+    (no device needed)."""
+    flags = (HCA_FLAG_FP64_ONLY if fp64_only else 0) | (0 if tensor_cores else HCA_FLAG_NO_TENSOR_CORES)
+    out = ctypes.c_int64()
+    rc = load().hca_workspace_bytes(int(n), int(d), _dtype_code(dtype), flags, ctypes.byref(out))
+    if rc != HCA_OK:
+        raise HcaError(rc, "hca_workspace_bytes")
+    return int(out.value)
 
 
 def hca_radix_sort_pairs(keys, vals, begin_bit: int = 0, end_bit: int | None = None, stream=None):

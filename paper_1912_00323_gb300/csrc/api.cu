@@ -222,6 +222,31 @@ extern "C" int hca_dbscan(const void *points, int32_t dtype, int64_t n, int32_t 
     return rc;
 }
 
+extern "C" int hca_workspace_bytes(int64_t n, int32_t d, int32_t dtype, int32_t flags, int64_t *bytes) {
+    if (!bytes) return HCA_EINVAL;
+    if (n < 0 || n >= ((int64_t)1 << 31) || d < 1 || d > 64) return HCA_EINVAL;
+    if (dtype != HCA_F32 && dtype != HCA_F64) return HCA_EINVAL;
+    *bytes = 0;
+    if (n == 0) return HCA_OK;
+    RunArgs a;
+    a.d_points = nullptr;
+    a.n = n;
+    a.d = d;
+    a.eps = 1.0;
+    a.min_pts = 1;
+    a.d_labels = nullptr;
+    a.d_core = nullptr;
+    a.stream = nullptr;
+    a.stats = nullptr;
+    a.flags = flags;
+    a.tune = tuning_for(d);
+    size_t b = 0;
+    a.ws_query = &b;
+    const int rc = dispatch(a, dtype);
+    if (rc == HCA_OK) *bytes = (int64_t)b;
+    return rc;
+}
+
 extern "C" int hca_radix_sort_pairs(void *d_keys, uint32_t *d_vals, int64_t n, int32_t key_bytes,
                                     int32_t begin_bit, int32_t end_bit, void *stream) {
     if (n < 0 || n >= ((int64_t)1 << 31)) return HCA_EINVAL;

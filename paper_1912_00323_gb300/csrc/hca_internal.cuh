@@ -45,7 +45,7 @@ struct DevCounters {
     uint32_t n_chunks;     // 32-point chunks of the coarse cells (high-dimensional path)
     uint32_t n_tc_chunks[3];  // 128-row chunks of the tensor-core phases: counts, unions, labels
     uint32_t tc_next[3];      // next unclaimed chunk of each tensor-core phase
-    uint32_t hd_next[4];      // next unclaimed 32-point chunk: counts, first links, unions, labels
+    uint32_t hd_next[5];      // next unclaimed 32-point chunk: counts, first links, unions, labels, root links
     uint32_t lowd_next[5];    // next unclaimed batch (labels: [4])
     unsigned long long work[8];  // work counters (see hca_stats)
     unsigned long long tc_pairs;  // point pairs of the tensor-core tiles computed

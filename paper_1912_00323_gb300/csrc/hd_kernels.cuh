@@ -360,6 +360,61 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_hook_hd(HdView<T, DP> v) {
     add_counter(&v.ctr->work[1], lane == 0 ? chunks : 0u);
 }
 
+// Root links (after the first links and pointer jumping): every core point that is still a
+// root hooks to the tree of the first core point within eps (any neighbouring cell, either
+// side) whose tree's root, read without writing, is smaller than it.  Each link joins two trees
+// of one cluster through an edge of the core graph and points to a smaller index, so the links
+// stay a forest inside the clusters; a cluster that the first links left in many trees ends in
+// few, and the union pass that follows can skip most blocks because their rows and candidates
+// already share one tree.  The union pass still decides every pair, so the clusters do not
+// depend on which links were made.
+template <typename T, int DP>
+__global__ void __launch_bounds__(32 * kHdWarps) k_root_link_hd(HdView<T, DP> v) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *rows = reinterpret_cast<T *>(smem_raw) + (threadIdx.x >> 5) * 32 * DP;
+    const int lane = lane_id();
+    HD_FOR_EACH_CHUNK(v, A, base, e, 4) {
+        const uint32_t p = base + lane;
+        unsigned open = __ballot_sync(0xffffffffu, p < e && v.core[p] && __ldcg(v.parent + p) == p);
+        if (!open) continue;
+        const GridParams &G = params_of(v, set_of_key(v, v.cell_key[A]));
+        const uint32_t top = base + 31u - (uint32_t)__clz(open);  // largest open row
+        stage_rows<T, DP>(rows, v.pts, base, e);
+        for (int g0 = 0; g0 < v.n_all && open; g0 += 32) {
+            const int k = g0 + lane;
+            const uint2 rg = k < v.n_all ? v.ranges[(uint64_t)A * v.n_all + k] : make_uint2(0u, 0u);
+            for (int kk = 0; kk < 32 && open; ++kk) {
+                const uint32_t lo = __shfl_sync(0xffffffffu, rg.x, kk);
+                const uint32_t hi = __shfl_sync(0xffffffffu, rg.y, kk);
+                if (lo >= hi) continue;
+                const uint32_t q0 = v.cell_start[lo], q1 = v.cell_start[hi];
+                for (uint32_t qb = q0; qb < q1 && open; qb += 32) {
+                    const uint32_t q = qb + lane;
+                    bool qc = q < q1 && v.core[q];
+                    const uint32_t rq = qc ? uf_root_readonly(v.parent, q, v.ctr) : 0xffffffffu;
+                    qc = qc && rq < top;  // only a smaller root can take a row
+                    if (!__any_sync(0xffffffffu, qc)) continue;
+                    T qv[DP];
+                    hd_load<T, DP>(v.pts, q, qc, qv);
+                    unsigned rem = open;
+                    while (rem) {
+                        const int jj = __ffs(rem) - 1;
+                        rem &= rem - 1;
+                        const bool hit = qc && rq < base + (uint32_t)jj && hd_within<DP>(rows + jj * DP, qv, G);
+                        const unsigned hm = __ballot_sync(0xffffffffu, hit);
+                        if (hm) {
+                            const uint32_t r = __shfl_sync(0xffffffffu, rq, __ffs(hm) - 1);
+                            if (lane == jj) v.parent[base + jj] = r;
+                            open &= ~(1u << jj);
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // One round of pointer jumping over core points: parent[p] = parent[parent[p]].
 template <typename T, int DP>
 __global__ void __launch_bounds__(256) k_jump_hd(HdView<T, DP> v) {

@@ -177,12 +177,14 @@ void run_tc_phases(HdView<float, DP> &hv, cudaStream_t s, char *b, int64_t n, in
     k_uf_init_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
     k_hook_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
     for (int r = 0; r < 6; ++r) k_jump_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
+    k_root_link_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
+    for (int r = 0; r < 3; ++r) k_jump_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
     tmark(2);
     tc::k_tc_hd<DP, tc::kMerge><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch1, cx, clist, nclist, clab});
     tmark(3);
     k_merge_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
     k_compress_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
-    launches += 11;
+    launches += 15;
     mark(8);
     // ---- Algorithm 4: canonical ids, core labels, border and noise points ----
     k_comp_min_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
@@ -202,8 +204,11 @@ int run_hd(const RunArgs &a) {
     const int64_t n = a.n;
     const int d = a.d;
     int launches = 0;
-    const int sms = device_sm_count();
-    if (sms <= 0) return HCA_ECUDA;
+    int sms = device_sm_count();
+    if (sms <= 0) {
+        if (!a.ws_query) return HCA_ECUDA;
+        sms = 1;  // sizing only: no device needed
+    }
 
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
@@ -235,7 +240,10 @@ int run_hd(const RunArgs &a) {
     int tc_occ = 0;
     if constexpr (std::is_same<T, float>::value)
         if (!(a.flags & (HCA_FLAG_FP64_ONLY | HCA_FLAG_NO_TENSOR_CORES))) tc_occ = tc_launch_shape<DP>(tc_smem);
-    const size_t tc_n = tc_occ ? (size_t)n : 0;
+    // (a size query counts the tensor-core tables whenever the input and flags allow them)
+    const bool tc_allowed = std::is_same<T, float>::value &&
+                            !(a.flags & (HCA_FLAG_FP64_ONLY | HCA_FLAG_NO_TENSOR_CORES));
+    const size_t tc_n = (tc_occ || (a.ws_query && tc_allowed)) ? (size_t)n : 0;
     const size_t o_tnch = take(4 * tc_n), o_tnch2 = take(4 * tc_n);
     const size_t o_tch0 = take(4 * tc_n), o_tch1 = take(4 * tc_n), o_tch2 = take(4 * tc_n);
     const size_t o_tflags = take(4 * tc_n), o_cx = take(4 * (tc_n + 1));
@@ -245,8 +253,7 @@ int run_hd(const RunArgs &a) {
     const bool boxed = a.box_mn != nullptr;
     const bool own_ws = a.ws_ext == nullptr;
     void *ws = nullptr;
-    if (a.ws_query) {  // plans size their workspace first (declared extents only)
-        if (!boxed) return HCA_EINVAL;
+    if (a.ws_query) {  // the layout depends on n, d, the sets and the flags only
         *a.ws_query = off;
         return HCA_OK;
     }
@@ -259,7 +266,7 @@ int run_hd(const RunArgs &a) {
     char *b = (char *)ws;
     DevCounters *ctr = (DevCounters *)(b + o_ctr);
     unsigned long long *mm = (unsigned long long *)(b + o_mm);
-    DevCounters *h = a.h_ext ? a.h_ext : host_counters();
+    DevCounters *h = a.h_ext ? a.h_ext : (a.ws_query ? nullptr : host_counters());
     int rc = HCA_OK;
     bool tc_phases = false;  // the tensor-core split ran every phase
 
@@ -519,6 +526,7 @@ int run_hd(const RunArgs &a) {
     hv.n_half = st.n_half;
     allow_smem(k_count_hd<T, DP>, smem);
     allow_smem(k_hook_hd<T, DP>, smem);
+    allow_smem(k_root_link_hd<T, DP>, smem);
     allow_smem(k_merge_hd<T, DP>, smem);
     allow_smem(k_labels_hd<T, DP>, smem);
     if constexpr (std::is_same<T, float>::value) {
@@ -546,9 +554,11 @@ int run_hd(const RunArgs &a) {
         k_uf_init_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
         k_hook_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
         for (int r = 0; r < 6; ++r) k_jump_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
+        k_root_link_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
+        for (int r = 0; r < 3; ++r) k_jump_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
         k_merge_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
         k_compress_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
-        launches += 10;
+        launches += 14;
         mark(8);
         // ---- Algorithm 4: canonical ids, border and noise points ----
         k_comp_min_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
@@ -586,6 +596,7 @@ int run_hd(const RunArgs &a) {
         so->n_tc_tiles = (int64_t)h->work[6];
         so->n_tc_rechecks = (int64_t)h->work[7];
         so->n_tc_pairs = (int64_t)h->tc_pairs;
+        so->workspace_bytes = (int64_t)off;
         for (int i = 0; i < HCA_NUM_STAGES; ++i) {
             float ms = 0.f;
             if (timing) cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);

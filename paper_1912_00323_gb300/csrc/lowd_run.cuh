@@ -260,8 +260,11 @@ int run_lowd(const RunArgs &a) {
     const int64_t n = a.n;
     constexpr int ndir = RepDirs<D>::value;
     int launches = 0;
-    const int sms = device_sm_count();
-    if (sms <= 0) return HCA_ECUDA;
+    int sms = device_sm_count();
+    if (sms <= 0) {
+        if (!a.ws_query) return HCA_ECUDA;
+        sms = 1;  // sizing only: no device needed
+    }
 
     // ---- workspace layout (one pool allocation) ----
     size_t off = 0;
@@ -294,7 +297,7 @@ int run_lowd(const RunArgs &a) {
     const bool own_ws = a.ws_ext == nullptr;
     char *b = nullptr;
     DevCounters *ctr = nullptr;
-    DevCounters *h = a.h_ext ? a.h_ext : host_counters();
+    DevCounters *h = a.h_ext ? a.h_ext : (a.ws_query ? nullptr : host_counters());
     int rc = HCA_OK;
     size_t ranges_bytes = 0;
 
@@ -384,7 +387,7 @@ int run_lowd(const RunArgs &a) {
     const size_t stage_setoff = 0, stage_gtab = align_up(sizeof(int64_t) * ((size_t)nsets + 1));
     const size_t stage_box = stage_gtab + align_up(sizeof(GridParams) * (size_t)nsets);
 
-    if (!h) return HCA_ECUDA;
+    if (!h && !a.ws_query) return HCA_ECUDA;
     if (boxed) {
         rc = build_grids([&](int set, int i) { return a.box_mn[(size_t)set * D + i]; },
                          [&](int set, int i) { return a.box_mx[(size_t)set * D + i]; });
@@ -392,7 +395,17 @@ int run_lowd(const RunArgs &a) {
         ranges_bytes = sizeof(uint2) * (size_t)n * st.n_all + sizeof(Pt<T, D>) * (size_t)n * ndir + 256;
     }
     if (a.ws_query) {  // plans size their workspace first (declared extents only)
-        if (!boxed) return HCA_EINVAL;
+        if (!boxed) {
+            // no extents: bound the neighbour ranges with the widest stencil of D, the one of
+            // the largest binning error the grid allows (tau = 2^-8) and a side below any side
+            // make_grid can choose (eps = 1; a smaller side and more error keep more offsets)
+            const double tau_max = ldexp(1.0, -8);
+            const double side = (1.0 - ldexp(1.0, -20)) * (1.0 - ldexp(1.0, -10)) /
+                                (sqrt((double)D) * (1.0 + 2.0 * tau_max));
+            Stencil wide;
+            if (make_stencil(D, 1.0, side, tau_max, wide) != HCA_OK) return HCA_ENOTIMPL;
+            ranges_bytes = sizeof(uint2) * (size_t)n * wide.n_all + sizeof(Pt<T, D>) * (size_t)n * ndir + 256;
+        }
         *a.ws_query = main_bytes + ranges_bytes;
         return HCA_OK;
     }
@@ -464,8 +477,8 @@ int run_lowd(const RunArgs &a) {
         if (batched) cudaMemcpyAsync(d_gtab, gsets.data(), sizeof(GridParams) * nsets, cudaMemcpyHostToDevice, s);
         // neighbour ranges (one (lo, hi) pair per cell and stencil pencil) and the coordinates
         // of the representative points (ndir per cell)
-        if (pool_alloc(&ws_ranges, sizeof(uint2) * (size_t)n * st.n_all + sizeof(Pt<T, D>) * (size_t)n * ndir + 256,
-                       s) != cudaSuccess || !ws_ranges) {
+        ranges_bytes = sizeof(uint2) * (size_t)n * st.n_all + sizeof(Pt<T, D>) * (size_t)n * ndir + 256;
+        if (pool_alloc(&ws_ranges, ranges_bytes, s) != cudaSuccess || !ws_ranges) {
             rc = HCA_ENOMEM;
             goto out;
         }
@@ -605,6 +618,7 @@ int run_lowd(const RunArgs &a) {
         st_out->n_pencils = h->n_pencils;
         st_out->n_dense_cells = h->n_dense;
         st_out->n_core_cells = h->n_core_cells;
+        st_out->workspace_bytes = (int64_t)(main_bytes + ranges_bytes);
         st_out->n_core_points = h->n_core;
         st_out->n_clusters = h->n_clusters;
         st_out->n_noise = h->n_noise;

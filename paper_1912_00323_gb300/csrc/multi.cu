@@ -174,6 +174,7 @@ void add_stats(hca_stats &acc, const hca_stats &x) {
     acc.n_tc_rechecks += x.n_tc_rechecks;
     acc.n_core_cells += x.n_core_cells;
     acc.n_tc_pairs += x.n_tc_pairs;
+    acc.workspace_bytes += x.workspace_bytes;
     for (int i = 0; i < 3; ++i) acc.tc_ms[i] += x.tc_ms[i];
 }
 

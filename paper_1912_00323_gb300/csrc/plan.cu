@@ -5,9 +5,9 @@
 // With the extents declared, the grids, the stencil and the workspace are known before the
 // first launch, so the call never waits for the host and the whole launch sequence is one
 // graph; a kernel in the graph checks every launch's points against the declared boxes.
-// A batched plan with several dimensions holds one part per d group; the parts are captured
-// as parallel branches of the same graph (fork and join through events), so their kernels
-// overlap on the device and one graph launch runs them all.
+// A batched plan with several dimensions holds one part per d group; each part is captured
+// into a graph of its own and the plan's graph chains them as child-graph nodes, so one graph
+// launch runs them all in order.
 #include <stdlib.h>
 #include <string.h>
 
@@ -26,8 +26,6 @@ struct PlanPart {
     hca::GroupBuffers gb = {};
     hca::DevCounters *h = nullptr;   // pinned: the counters of the last launch
     void *stage = nullptr;           // pinned: per-set tables the graph copies to the device
-    cudaStream_t branch = nullptr;   // capture branch of a multi-part plan
-    cudaEvent_t done = nullptr;
 };
 
 }  // namespace
@@ -35,7 +33,6 @@ struct PlanPart {
 struct hca_plan {
     std::vector<PlanPart> parts;
     cudaStream_t cap = nullptr;
-    cudaEvent_t fork = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -53,14 +50,11 @@ void release(hca_plan *p) {
         }
         if (pt.h) cudaFreeHost(pt.h);
         if (pt.stage) cudaFreeHost(pt.stage);
-        if (pt.branch) cudaStreamDestroy(pt.branch);
-        if (pt.done) cudaEventDestroy(pt.done);
     }
     if (p->cap) {
         cudaStreamSynchronize(p->cap);
         cudaStreamDestroy(p->cap);
     }
-    if (p->fork) cudaEventDestroy(p->fork);
     delete p;
 }
 
@@ -122,7 +116,6 @@ int create(hca_plan **out, const void *d_points, int32_t dtype, bool batched, st
         release(p);
         return HCA_EINVAL;
     }
-    const bool multi = p->parts.size() > 1;
     for (PlanPart &pt : p->parts) {
         const size_t sets = pt.g.sets.size();
         if (pt.g.gather) {
@@ -161,56 +154,47 @@ int create(hca_plan **out, const void *d_points, int32_t dtype, bool batched, st
             rc = HCA_ENOMEM;
             break;
         }
-        if (multi && (cudaStreamCreateWithFlags(&pt.branch, cudaStreamNonBlocking) != cudaSuccess ||
-                      cudaEventCreateWithFlags(&pt.done, cudaEventDisableTiming) != cudaSuccess)) {
+    }
+    if (rc == HCA_OK && cudaStreamSynchronize(p->cap) != cudaSuccess) rc = HCA_ECUDA;
+    // each part is captured into a graph of its own; the plan's graph runs them as a chain of
+    // child-graph nodes, so one graph launch runs every part
+    if (rc == HCA_OK && cudaGraphCreate(&p->graph, 0) != cudaSuccess) {
+        p->graph = nullptr;
+        rc = HCA_ECUDA;
+    }
+    cudaGraphNode_t prev = nullptr;
+    for (PlanPart &pt : p->parts) {
+        if (rc) break;
+        cudaStream_t s = p->cap;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
             rc = HCA_ECUDA;
             break;
         }
-    }
-    if (rc == HCA_OK && multi && cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) != cudaSuccess)
-        rc = HCA_ECUDA;
-    if (rc == HCA_OK && cudaStreamSynchronize(p->cap) != cudaSuccess) rc = HCA_ECUDA;
-    if (rc == HCA_OK) {
-        if (cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        if (pt.g.gather) group_gather(pt.g, dtype, d_points, pt.gb, s);
+        const void *pts;
+        int32_t *lab;
+        uint8_t *core;
+        part_buffers(pt, d_points, dtype, d_labels, d_core, &pts, &lab, &core);
+        RunArgs a = part_args(pt, pts, lab, core);
+        a.ws_ext = pt.ws;
+        a.ws_ext_bytes = pt.ws_bytes;
+        a.h_ext = pt.h;
+        a.h_stage = pt.stage;
+        a.deferred = true;
+        a.stream = s;
+        rc = dispatch(a, dtype);
+        if (rc == HCA_OK && pt.g.gather) group_scatter(pt.g, pt.gb, d_labels, d_core, s);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (rc == HCA_OK && (e != cudaSuccess || !g)) rc = HCA_ECUDA;
+        cudaGraphNode_t node = nullptr;
+        if (rc == HCA_OK &&
+            cudaGraphAddChildGraphNode(&node, p->graph, prev ? &prev : nullptr, prev ? 1 : 0, g) != cudaSuccess)
             rc = HCA_ECUDA;
-        } else {
-            if (multi && cudaEventRecord(p->fork, p->cap) != cudaSuccess) rc = HCA_ECUDA;
-            for (PlanPart &pt : p->parts) {
-                if (rc) break;
-                cudaStream_t s = p->cap;
-                if (multi) {
-                    s = pt.branch;
-                    if (cudaStreamWaitEvent(s, p->fork, 0) != cudaSuccess) {
-                        rc = HCA_ECUDA;
-                        break;
-                    }
-                }
-                if (pt.g.gather) group_gather(pt.g, dtype, d_points, pt.gb, s);
-                const void *pts;
-                int32_t *lab;
-                uint8_t *core;
-                part_buffers(pt, d_points, dtype, d_labels, d_core, &pts, &lab, &core);
-                RunArgs a = part_args(pt, pts, lab, core);
-                a.ws_ext = pt.ws;
-                a.ws_ext_bytes = pt.ws_bytes;
-                a.h_ext = pt.h;
-                a.h_stage = pt.stage;
-                a.deferred = true;
-                a.stream = s;
-                rc = dispatch(a, dtype);
-                if (rc) break;
-                if (pt.g.gather) group_scatter(pt.g, pt.gb, d_labels, d_core, s);
-                if (multi && (cudaEventRecord(pt.done, s) != cudaSuccess ||
-                              cudaStreamWaitEvent(p->cap, pt.done, 0) != cudaSuccess))
-                    rc = HCA_ECUDA;
-            }
-            cudaGraph_t g = nullptr;
-            const cudaError_t e = cudaStreamEndCapture(p->cap, &g);
-            p->graph = g;
-            if (rc == HCA_OK && (e != cudaSuccess || !g)) rc = HCA_ECUDA;
-            if (rc == HCA_OK && cudaGraphInstantiate(&p->exec, p->graph, 0) != cudaSuccess) rc = HCA_ECUDA;
-        }
+        if (g) cudaGraphDestroy(g);  // the child node holds its own copy
+        prev = node;
     }
+    if (rc == HCA_OK && cudaGraphInstantiate(&p->exec, p->graph, 0) != cudaSuccess) rc = HCA_ECUDA;
     cudaGetLastError();
     if (rc != HCA_OK) {
         release(p);

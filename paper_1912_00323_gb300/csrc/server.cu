@@ -1,9 +1,10 @@
 // Request server: asynchronous clustering jobs with continuous batching (host runtime).
 //
 // Jobs are queued by hca_submit.  Worker threads (each with its own CUDA stream) repeatedly
-// take every queued job that fits the device-memory budget, group them by (d, dtype), stage
-// each group's points into one device buffer, cluster the group with one hca_dbscan_batched
-// call, copy each job's labels to its destination, and complete the jobs.  Jobs that arrive
+// take every queued job that fits the device-memory budget (each charged its points, labels
+// and the hca_workspace_bytes bound of its workspace), group them by (d, dtype), stage each
+// group's points into the worker's resident device buffer, cluster the group with one
+// hca_dbscan_batched call, copy each job's labels to its destination, and complete the jobs.  Jobs that arrive
 // while a batch is on the GPU join the next batch of a free worker, and the workers keep as many
 // batches in flight.  All waits on the host are condition-variable waits with deadlines.
 #include <algorithm>
@@ -41,15 +42,39 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-// Device memory a job is charged for: points, labels and the clustering workspace
-// (about 1 KB per point covers the hypercube path's arrays at d <= 4 and the coarse-grid
-// path at d <= 16; larger d add their rows).
+// Device memory a job is charged for: its points and labels in the worker's staging buffers
+// and the bound of hca_workspace_bytes on the clustering workspace, plus 16 bytes per point
+// for the power-of-two rounding of the hash table when jobs share a call and 1 KB for the
+// per-set tables.
 int64_t job_bytes(const hca_request &r) {
     const int64_t esz = r.dtype == HCA_F32 ? 4 : 8;
-    return r.n * (r.d * esz + 4) + r.n * (1024 + 2 * r.d * esz);
+    int64_t ws = 0;
+    if (hca_workspace_bytes(r.n, r.d, r.dtype, 0, &ws) != HCA_OK) ws = r.n * 2048;
+    return r.n * (r.d * esz + 4) + ws + 16 * r.n + 1024;
 }
 
-void run_group(hca_server *sv, std::vector<int64_t> &ids, cudaStream_t s) {
+// Device buffers a worker keeps from batch to batch: the staged points and the labels of
+// its current group, grown (never shrunk) as larger groups arrive.
+struct Staging {
+    void *dp = nullptr;
+    size_t dp_cap = 0;
+    void *dl = nullptr;
+    size_t dl_cap = 0;
+};
+
+bool ensure(void **p, size_t *cap, size_t bytes, cudaStream_t s) {
+    if (bytes <= *cap) return true;
+    size_t want = *cap + *cap / 2;
+    if (want < bytes) want = bytes;
+    if (*p) hca::pool_free(*p, s);
+    *p = nullptr;
+    *cap = 0;
+    if (hca::pool_alloc(p, want, s) != cudaSuccess || !*p) return false;
+    *cap = want;
+    return true;
+}
+
+void run_group(hca_server *sv, std::vector<int64_t> &ids, cudaStream_t s, Staging &stg) {
     // ids share d and dtype; copy their jobs' requests (the map is not touched while running)
     std::vector<hca_request> reqs;
     {
@@ -68,10 +93,10 @@ void run_group(hca_server *sv, std::vector<int64_t> &ids, cudaStream_t s) {
     }
     const int64_t n = off.back();
     int rc = HCA_OK;
-    void *dp = nullptr, *dl = nullptr;
-    if (n > 0 && (hca::pool_alloc(&dp, (size_t)n * d * esz, s) != cudaSuccess ||
-                  hca::pool_alloc(&dl, (size_t)n * 4, s) != cudaSuccess))
+    if (n > 0 && (!ensure(&stg.dp, &stg.dp_cap, (size_t)n * d * esz, s) ||
+                  !ensure(&stg.dl, &stg.dl_cap, (size_t)n * 4, s)))
         rc = HCA_ENOMEM;
+    void *dp = stg.dp, *dl = stg.dl;
     for (size_t i = 0; i < reqs.size() && rc == HCA_OK; ++i) {
         if (reqs[i].n == 0) continue;
         const cudaMemcpyKind kind = reqs[i].on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -89,9 +114,6 @@ void run_group(hca_server *sv, std::vector<int64_t> &ids, cudaStream_t s) {
             rc = HCA_ECUDA;
     }
     if (cudaStreamSynchronize(s) != cudaSuccess && rc == HCA_OK) rc = HCA_ECUDA;
-    hca::pool_free(dp, s);
-    hca::pool_free(dl, s);
-    cudaStreamSynchronize(s);
     const auto now = Clock::now();
     {
         std::lock_guard<std::mutex> lk(sv->mu);
@@ -110,6 +132,7 @@ void worker_main(hca_server *sv) {
     cudaSetDevice(sv->device);
     cudaStream_t s;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return;
+    Staging stg;
     for (;;) {
         std::vector<int64_t> batch;
         {
@@ -134,19 +157,28 @@ void worker_main(hca_server *sv) {
                 continue;
             }
         }
-        // one batched call per (d, dtype) group
+        // one batched call per (d, dtype) group, the groups with the fewest point coordinates
+        // first (their jobs complete soonest)
         std::map<std::pair<int32_t, int32_t>, std::vector<int64_t>> groups;
+        std::map<std::pair<int32_t, int32_t>, int64_t> work;
         {
             std::lock_guard<std::mutex> lk(sv->mu);
             for (int64_t id : batch) {
                 const hca_request &r = sv->jobs[id].req;
                 groups[{r.d, r.dtype}].push_back(id);
+                work[{r.d, r.dtype}] += r.n * r.d;
             }
         }
-        for (auto &kv : groups) run_group(sv, kv.second, s);
+        std::vector<std::pair<int64_t, std::pair<int32_t, int32_t>>> order;
+        for (auto &kv : work) order.push_back({kv.second, kv.first});
+        std::sort(order.begin(), order.end());
+        for (auto &o : order) run_group(sv, groups[o.second], s, stg);
         sv->cv_done.notify_all();
         sv->cv_work.notify_all();
     }
+    if (stg.dp) hca::pool_free(stg.dp, s);
+    if (stg.dl) hca::pool_free(stg.dl, s);
+    cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
 }
 

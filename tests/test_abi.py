@@ -128,3 +128,22 @@ def test_pack_sets_layout():
     assert dd.dtype == np.int32 and o.dtype == np.int64
     with pytest.raises(ValueError):
         p._set_args(flat, off, [1.0, 1.0, 1.0], [2, 2, 2], [2, 3, 5])   # 3*2 + 2*5 != 14 values
+
+
+def test_workspace_bound_on_the_host(pkg):
+    """hca_workspace_bytes needs no device: positive for n > 0, zero for n = 0, non-decreasing
+    in n, and arguments checked."""
+    lib = pkg.load()
+    for d in (1, 2, 3, 4, 5, 16, 64):
+        prev = 0
+        for n in (1, 1000, 100_000, 2_000_000):
+            b = pkg.hca_workspace_bytes(n, d)
+            assert b > 0 and b >= prev
+            prev = b
+        assert pkg.hca_workspace_bytes(0, d) == 0
+    import ctypes
+    out = ctypes.c_int64()
+    assert lib.hca_workspace_bytes(10, 0, 0, 0, ctypes.byref(out)) == pkg.HCA_EINVAL
+    assert lib.hca_workspace_bytes(10, 3, 9, 0, ctypes.byref(out)) == pkg.HCA_EINVAL
+    assert lib.hca_workspace_bytes(-1, 3, 0, 0, ctypes.byref(out)) == pkg.HCA_EINVAL
+    assert lib.hca_workspace_bytes(10, 3, 0, 0, None) == pkg.HCA_EINVAL

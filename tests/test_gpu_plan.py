@@ -109,7 +109,7 @@ def test_batched_plan(env, d):
 
 
 def test_batched_plan_mixed_dimensions_one_graph(env):
-    """A batched plan over interleaved sets of d = 2, 3 and 8: the d groups are branches of
+    """A batched plan over interleaved sets of d = 2, 3 and 8: the d groups are captured into
     one graph (one launch); every relaunch equals the batched call and the oracle."""
     torch, pkg, oracle = env
     sets = []

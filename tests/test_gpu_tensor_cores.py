@@ -40,24 +40,30 @@ def check(got, want):
 
 
 @pytest.mark.parametrize("d", [5, 8, 12, 16, 24, 32, 40, 64])
-@pytest.mark.parametrize("min_pts", [1, 5, 30])
-def test_lattice_ties_on_tensor_cores(env, d, min_pts):
+def test_lattice_ties_on_tensor_cores(env, d):
     """Lattice sets (many pairs at exactly eps, coarse cells with several hundred points, so
-    several 128-row chunks per cell and ragged last tiles): the tensor-core path is used, some
-    pairs fall in its guard band, and the labels equal the oracle's."""
-    _, _, oracle = env
+    several 128-row chunks per cell and ragged last tiles), MINPTS 1, 5 and 30, with the default
+    split and with every cell on the tensor cores: the tensor-core path is used, some pairs fall
+    in its guard band (the first links, root links and pointer jumping can leave every union tile
+    skipped, so the band is met in the labels phase), and the labels equal the oracle's."""
+    _, pkg, oracle = env
     X, eps, _ = workloads.lattice(3000, d, seed=900 + d, step=0.25,
                                   eps_steps=int(round(math.sqrt(2 * d) * 1.8)), spread=2.0,
                                   box=2.0 * d, n_blobs=3)
-    want = oracle.grid(X, eps, min_pts)
-    got = run(env, X.astype(np.float32), eps, min_pts)
-    assert got[2]["n_tc_tiles"] > 0
-    if min_pts < 30:
-        # with MINPTS = 30 the first links and pointer jumping can leave every union tile
-        # skipped and the labels phase can settle each border row before a band pair; the
-        # smaller MINPTS values exercise the band on every d
-        assert got[2]["n_tc_rechecks"] > 0
-    check(got, want)
+    rechecks = 0
+    for tiles_from in (None, 1):   # the default split, then every cell on the tensor cores
+        if tiles_from:
+            pkg.hca_tuning_set(d, {"tc_min_count": 1, "tc_min_merge": 1, "tc_min_labels": 1})
+        try:
+            for min_pts in (1, 5, 30):
+                want = oracle.grid(X, eps, min_pts)
+                got = run(env, X.astype(np.float32), eps, min_pts)
+                assert got[2]["n_tc_tiles"] > 0
+                rechecks += got[2]["n_tc_rechecks"]
+                check(got, want)
+        finally:
+            pkg.hca_tuning_set(d, None)
+    assert rechecks > 0
 
 
 @pytest.mark.parametrize("n", [1, 2, 127, 128, 129, 255, 257, 1000])
