@@ -45,7 +45,7 @@ struct DevCounters {
     uint32_t n_chunks;     // 32-point chunks of the coarse cells (high-dimensional path)
     uint32_t n_tc_chunks[3];  // 128-row chunks of the tensor-core phases: counts, unions, labels
     uint32_t tc_next[3];      // next unclaimed chunk of each tensor-core phase
-    uint32_t hd_next[5];      // next unclaimed 32-point chunk: counts, first links, unions, labels, root links
+    uint32_t hd_next[4];      // next unclaimed 32-point chunk: counts, first links, unions, labels
     uint32_t lowd_next[5];    // next unclaimed batch (labels: [4])
     unsigned long long work[8];  // work counters (see hca_stats)
     unsigned long long tc_pairs;  // point pairs of the tensor-core tiles computed
@@ -151,16 +151,16 @@ int device_sm_count();
 
 // Host orchestration of one clustering call, instantiated per (T, D) in lowd_*.cu.
 struct RunArgs {
-    const void *d_points;
-    int64_t n;
-    int d;
-    double eps;
-    int min_pts;
-    int32_t *d_labels;
-    uint8_t *d_core;
-    cudaStream_t stream;
-    hca_stats *stats;
-    int flags;
+    const void *d_points = nullptr;
+    int64_t n = 0;
+    int d = 0;
+    double eps = 0.0;
+    int min_pts = 0;
+    int32_t *d_labels = nullptr;
+    uint8_t *d_core = nullptr;
+    cudaStream_t stream = nullptr;
+    hca_stats *stats = nullptr;
+    int flags = 0;
     // batched calls (n_sets > 0): sets of consecutive points, each with its own eps and MINPTS
     int nsets = 0;
     const int64_t *h_off = nullptr;      // host, nsets + 1 point offsets

@@ -50,6 +50,11 @@ struct HdView {
     // rows the tensor-core count handed over: count so far and candidate-stream position
     uint32_t *tc_cnt;
     uint32_t *tc_pos;
+    // per coarse cell, the smallest and largest coordinate of its points in every dimension
+    // (DP values each): a point farther than eps from a cell's box is farther than eps from
+    // every point of the cell
+    T *box_lo;
+    T *box_hi;
 };
 
 constexpr int kHdWarps = 4;   // warps per block in the point kernels of this path
@@ -86,6 +91,84 @@ __device__ __forceinline__ bool hd_within(const double *a, const double (&q)[DP]
         e = __dadd_rn(e, __dmul_rn(t, t));
     }
     return e <= g.eps2;
+}
+
+// True when the point a (DP coordinates) is provably farther than eps from every point of the
+// box [lo, hi]: the squared distance to the box, sum_i max(lo_i - a_i, a_i - hi_i, 0)^2, is a
+// lower bound of the squared distance to any point inside.  float: summed in FP32 (each term
+// and the sum within (DP + 2) 2^-24 of exact) against hi32 = eps^2 (1 + 2^-16) rounded up, so a
+// box it calls far is farther than eps in exact arithmetic and in the FP64 predicate (when the
+// FP32 filter is off, hi32 is infinite and no box is called far); double: summed in FP64
+// against eps^2 (1 + 2^-40).
+template <int DP>
+__device__ __forceinline__ bool box_far(const float *a, const float *lo, const float *hi, const GridParams &g) {
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < DP; i += 4) {
+        const float4 av = *reinterpret_cast<const float4 *>(a + i);
+        const float4 l = __ldg(reinterpret_cast<const float4 *>(lo + i));
+        const float4 h = __ldg(reinterpret_cast<const float4 *>(hi + i));
+        float t = fmaxf(fmaxf(__fsub_rn(l.x, av.x), __fsub_rn(av.x, h.x)), 0.f); s = __fmaf_rn(t, t, s);
+        t = fmaxf(fmaxf(__fsub_rn(l.y, av.y), __fsub_rn(av.y, h.y)), 0.f);       s = __fmaf_rn(t, t, s);
+        t = fmaxf(fmaxf(__fsub_rn(l.z, av.z), __fsub_rn(av.z, h.z)), 0.f);       s = __fmaf_rn(t, t, s);
+        t = fmaxf(fmaxf(__fsub_rn(l.w, av.w), __fsub_rn(av.w, h.w)), 0.f);       s = __fmaf_rn(t, t, s);
+    }
+    return s > g.hi32;
+}
+template <int DP>
+__device__ __forceinline__ bool box_far(const double *a, const double *lo, const double *hi, const GridParams &g) {
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < DP; ++i) {
+        const double t = fmax(fmax(__dsub_rn(__ldg(lo + i), a[i]), __dsub_rn(a[i], __ldg(hi + i))), 0.0);
+        s = __fma_rn(t, t, s);
+    }
+    return s > g.eps2 * (1.0 + 0x1p-40);
+}
+
+// Box of every coarse cell (one warp per cell, eight dimensions at a time).
+template <typename T, int DP>
+__global__ void __launch_bounds__(256) k_cell_box_hd(HdView<T, DP> v) {
+    const int lane = lane_id();
+    const uint32_t C = v.ctr->n_cells;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < C; c += warps) {
+        const uint32_t s0 = v.cell_start[c], s1 = v.cell_start[c + 1];
+#pragma unroll
+        for (int g0 = 0; g0 < DP; g0 += 8) {
+            T mn[8], mx[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                mn[i] = sizeof(T) == 4 ? (T)FLT_MAX : (T)DBL_MAX;
+                mx[i] = -mn[i];
+            }
+            for (uint32_t j = s0 + lane; j < s1; j += 32) {
+                const T *r = v.pts + (uint64_t)j * DP + g0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const T x = r[i];
+                    mn[i] = x < mn[i] ? x : mn[i];
+                    mx[i] = x > mx[i] ? x : mx[i];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                for (int o = 16; o; o >>= 1) {
+                    const T a = __shfl_xor_sync(0xffffffffu, mn[i], o), b = __shfl_xor_sync(0xffffffffu, mx[i], o);
+                    mn[i] = a < mn[i] ? a : mn[i];
+                    mx[i] = b > mx[i] ? b : mx[i];
+                }
+            }
+            if (lane < 8) {
+                T a = mn[0], b = mx[0];
+#pragma unroll
+                for (int i = 1; i < 8; ++i)
+                    if (lane == i) { a = mn[i]; b = mx[i]; }
+                v.box_lo[(uint64_t)c * DP + g0 + lane] = a;
+                v.box_hi[(uint64_t)c * DP + g0 + lane] = b;
+            }
+        }
+    }
 }
 
 template <typename T, int DP>
@@ -260,34 +343,39 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_count_hd(HdView<T, DP> v) {
         for (int g0 = 0; g0 < v.n_all && open; g0 += 32) {
             const int k = g0 + lane;
             const uint2 rg = k < v.n_all ? v.ranges[(uint64_t)A * v.n_all + k] : make_uint2(0u, 0u);
-            // the cells of one pencil range are consecutive, so their points are one span
+            // the cells of a pencil range, one at a time: a cell whose box is farther than eps
+            // from every open row adds nothing to their counts and is passed over
             for (int kk = 0; kk < 32 && open; ++kk) {
                 const uint32_t lo = __shfl_sync(0xffffffffu, rg.x, kk);
                 const uint32_t hi = __shfl_sync(0xffffffffu, rg.y, kk);
-                if (lo >= hi) continue;
-                uint32_t q0 = v.cell_start[lo];
-                const uint32_t q1 = v.cell_start[hi];
-                if (skip) {
-                    if (skip >= q1 - q0) {
-                        skip -= q1 - q0;
-                        continue;
+                for (uint32_t B = lo; B < hi && open; ++B) {
+                    uint32_t q0 = v.cell_start[B];
+                    const uint32_t q1 = v.cell_start[B + 1];
+                    if (skip) {  // positions count every point of the stream (the tensor-core order)
+                        if (skip >= q1 - q0) {
+                            skip -= q1 - q0;
+                            continue;
+                        }
+                        q0 += skip;
+                        skip = 0;
                     }
-                    q0 += skip;
-                    skip = 0;
-                }
-                for (uint32_t qb = q0; qb < q1 && open; qb += 32) {
-                    const uint32_t q = qb + lane;
-                    T qv[DP];
-                    hd_load<T, DP>(v.pts, q, q < q1, qv);
-                    ++chunks;
-                    unsigned rem = open;
-                    while (rem) {
-                        const int jj = __ffs(rem) - 1;
-                        rem &= rem - 1;
-                        const unsigned hits = __ballot_sync(0xffffffffu, q < q1 && hd_within<DP>(rows + jj * DP, qv, G));
-                        if (lane == jj) cnt += __popc(hits);
+                    const unsigned near = open & __ballot_sync(0xffffffffu,
+                        !box_far<DP>(rows + lane * DP, v.box_lo + (uint64_t)B * DP, v.box_hi + (uint64_t)B * DP, G));
+                    if (!near) continue;
+                    for (uint32_t qb = q0; qb < q1 && open; qb += 32) {
+                        const uint32_t q = qb + lane;
+                        T qv[DP];
+                        hd_load<T, DP>(v.pts, q, q < q1, qv);
+                        ++chunks;
+                        unsigned rem = open & near;
+                        while (rem) {
+                            const int jj = __ffs(rem) - 1;
+                            rem &= rem - 1;
+                            const unsigned hits = __ballot_sync(0xffffffffu, q < q1 && hd_within<DP>(rows + jj * DP, qv, G));
+                            if (lane == jj) cnt += __popc(hits);
+                        }
+                        open &= __ballot_sync(0xffffffffu, have && cnt < min_pts);
                     }
-                    open &= __ballot_sync(0xffffffffu, have && cnt < min_pts);
                 }
             }
         }
@@ -358,61 +446,6 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_hook_hd(HdView<T, DP> v) {
         __syncwarp();
     }
     add_counter(&v.ctr->work[1], lane == 0 ? chunks : 0u);
-}
-
-// Root links (after the first links and pointer jumping): every core point that is still a
-// root hooks to the tree of the first core point within eps (any neighbouring cell, either
-// side) whose tree's root, read without writing, is smaller than it.  Each link joins two trees
-// of one cluster through an edge of the core graph and points to a smaller index, so the links
-// stay a forest inside the clusters; a cluster that the first links left in many trees ends in
-// few, and the union pass that follows can skip most blocks because their rows and candidates
-// already share one tree.  The union pass still decides every pair, so the clusters do not
-// depend on which links were made.
-template <typename T, int DP>
-__global__ void __launch_bounds__(32 * kHdWarps) k_root_link_hd(HdView<T, DP> v) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *rows = reinterpret_cast<T *>(smem_raw) + (threadIdx.x >> 5) * 32 * DP;
-    const int lane = lane_id();
-    HD_FOR_EACH_CHUNK(v, A, base, e, 4) {
-        const uint32_t p = base + lane;
-        unsigned open = __ballot_sync(0xffffffffu, p < e && v.core[p] && __ldcg(v.parent + p) == p);
-        if (!open) continue;
-        const GridParams &G = params_of(v, set_of_key(v, v.cell_key[A]));
-        const uint32_t top = base + 31u - (uint32_t)__clz(open);  // largest open row
-        stage_rows<T, DP>(rows, v.pts, base, e);
-        for (int g0 = 0; g0 < v.n_all && open; g0 += 32) {
-            const int k = g0 + lane;
-            const uint2 rg = k < v.n_all ? v.ranges[(uint64_t)A * v.n_all + k] : make_uint2(0u, 0u);
-            for (int kk = 0; kk < 32 && open; ++kk) {
-                const uint32_t lo = __shfl_sync(0xffffffffu, rg.x, kk);
-                const uint32_t hi = __shfl_sync(0xffffffffu, rg.y, kk);
-                if (lo >= hi) continue;
-                const uint32_t q0 = v.cell_start[lo], q1 = v.cell_start[hi];
-                for (uint32_t qb = q0; qb < q1 && open; qb += 32) {
-                    const uint32_t q = qb + lane;
-                    bool qc = q < q1 && v.core[q];
-                    const uint32_t rq = qc ? uf_root_readonly(v.parent, q, v.ctr) : 0xffffffffu;
-                    qc = qc && rq < top;  // only a smaller root can take a row
-                    if (!__any_sync(0xffffffffu, qc)) continue;
-                    T qv[DP];
-                    hd_load<T, DP>(v.pts, q, qc, qv);
-                    unsigned rem = open;
-                    while (rem) {
-                        const int jj = __ffs(rem) - 1;
-                        rem &= rem - 1;
-                        const bool hit = qc && rq < base + (uint32_t)jj && hd_within<DP>(rows + jj * DP, qv, G);
-                        const unsigned hm = __ballot_sync(0xffffffffu, hit);
-                        if (hm) {
-                            const uint32_t r = __shfl_sync(0xffffffffu, rq, __ffs(hm) - 1);
-                            if (lane == jj) v.parent[base + jj] = r;
-                            open &= ~(1u << jj);
-                        }
-                    }
-                }
-            }
-        }
-        __syncwarp();
-    }
 }
 
 // One round of pointer jumping over core points: parent[p] = parent[parent[p]].
@@ -566,26 +599,32 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_labels_hd(HdView<T, DP> v) {
                     for (int kk = 0; kk < 32; ++kk) {
                         const uint32_t lo = __shfl_sync(0xffffffffu, rg.x, kk);
                         const uint32_t hi = __shfl_sync(0xffffffffu, rg.y, kk);
-                        if (lo >= hi) continue;
-                        const uint32_t q0 = v.cell_start[lo], q1 = v.cell_start[hi];
-                        for (uint32_t qb = q0; qb < q1; qb += 32) {
-                            const uint32_t q = qb + lane;
-                            const bool qc = q < q1 && v.core[q];
-                            if (!__any_sync(0xffffffffu, qc)) continue;
-                            const uint32_t lq = qc ? v.comp_min[v.parent[q]] : kNoLabel;
-                            T qv[DP];
-                            hd_load<T, DP>(v.pts, q, qc, qv);
-                            ++chunks;
-                            unsigned rem = smask;
-                            while (rem) {
-                                const int jj = __ffs(rem) - 1;
-                                rem &= rem - 1;
-                                const uint32_t bj = __shfl_sync(0xffffffffu, best, jj);
-                                const bool need = qc && lq < bj;
-                                if (!__any_sync(0xffffffffu, need)) continue;
-                                uint32_t cand = (need && hd_within<DP>(rows + jj * DP, qv, G)) ? lq : kNoLabel;
-                                cand = __reduce_min_sync(0xffffffffu, cand);
-                                if (lane == jj && cand < best) best = cand;
+                        for (uint32_t B = lo; B < hi; ++B) {
+                            // a cell whose box is farther than eps from every row is passed over
+                            const unsigned near = smask & __ballot_sync(0xffffffffu,
+                                !box_far<DP>(rows + lane * DP, v.box_lo + (uint64_t)B * DP,
+                                             v.box_hi + (uint64_t)B * DP, G));
+                            if (!near) continue;
+                            const uint32_t q0 = v.cell_start[B], q1 = v.cell_start[B + 1];
+                            for (uint32_t qb = q0; qb < q1; qb += 32) {
+                                const uint32_t q = qb + lane;
+                                const bool qc = q < q1 && v.core[q];
+                                if (!__any_sync(0xffffffffu, qc)) continue;
+                                const uint32_t lq = qc ? v.comp_min[v.parent[q]] : kNoLabel;
+                                T qv[DP];
+                                hd_load<T, DP>(v.pts, q, qc, qv);
+                                ++chunks;
+                                unsigned rem = near;
+                                while (rem) {
+                                    const int jj = __ffs(rem) - 1;
+                                    rem &= rem - 1;
+                                    const uint32_t bj = __shfl_sync(0xffffffffu, best, jj);
+                                    const bool need = qc && lq < bj;
+                                    if (!__any_sync(0xffffffffu, need)) continue;
+                                    uint32_t cand = (need && hd_within<DP>(rows + jj * DP, qv, G)) ? lq : kNoLabel;
+                                    cand = __reduce_min_sync(0xffffffffu, cand);
+                                    if (lane == jj && cand < best) best = cand;
+                                }
                             }
                         }
                     }

@@ -177,14 +177,12 @@ void run_tc_phases(HdView<float, DP> &hv, cudaStream_t s, char *b, int64_t n, in
     k_uf_init_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
     k_hook_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
     for (int r = 0; r < 6; ++r) k_jump_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
-    k_root_link_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
-    for (int r = 0; r < 3; ++r) k_jump_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
     tmark(2);
     tc::k_tc_hd<DP, tc::kMerge><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch1, cx, clist, nclist, clab});
     tmark(3);
     k_merge_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
     k_compress_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
-    launches += 15;
+    launches += 11;
     mark(8);
     // ---- Algorithm 4: canonical ids, core labels, border and noise points ----
     k_comp_min_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
@@ -230,6 +228,7 @@ int run_hd(const RunArgs &a) {
     const size_t o_parent = take(4 * n), o_cmin = take(4 * n);
     const size_t o_ranges = take(sizeof(uint2) * 9 * (size_t)n);
     const size_t o_nch = take(4 * n), o_choff = take(4 * n);
+    const size_t o_blo = take(sizeof(T) * DP * (size_t)n), o_bhi = take(sizeof(T) * DP * (size_t)n);
     const bool batched = a.nsets > 0;
     const int nsets = batched ? a.nsets : 1;
     const size_t o_smm = take(sizeof(unsigned long long) * 2 * 64 * (size_t)nsets);
@@ -524,9 +523,13 @@ int run_hd(const RunArgs &a) {
     hv.ctr = ctr;
     hv.n_all = st.n_all;
     hv.n_half = st.n_half;
+    hv.box_lo = (T *)(b + o_blo);
+    hv.box_hi = (T *)(b + o_bhi);
+    // the box of every coarse cell in all d dimensions (point-to-box distance bounds)
+    k_cell_box_hd<T, DP><<<grid_for(n, 8, sms, 16), 256, 0, s>>>(hv);
+    ++launches;
     allow_smem(k_count_hd<T, DP>, smem);
     allow_smem(k_hook_hd<T, DP>, smem);
-    allow_smem(k_root_link_hd<T, DP>, smem);
     allow_smem(k_merge_hd<T, DP>, smem);
     allow_smem(k_labels_hd<T, DP>, smem);
     if constexpr (std::is_same<T, float>::value) {
@@ -554,11 +557,9 @@ int run_hd(const RunArgs &a) {
         k_uf_init_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
         k_hook_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
         for (int r = 0; r < 6; ++r) k_jump_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
-        k_root_link_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
-        for (int r = 0; r < 3; ++r) k_jump_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
         k_merge_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
         k_compress_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
-        launches += 14;
+        launches += 10;
         mark(8);
         // ---- Algorithm 4: canonical ids, border and noise points ----
         k_comp_min_hd<T, DP><<<gpts, 256, 0, s>>>(hv);

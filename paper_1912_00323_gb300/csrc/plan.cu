@@ -60,6 +60,7 @@ void release(hca_plan *p) {
 
 hca::RunArgs part_args(const PlanPart &pt, const void *pts, int32_t *lab, uint8_t *core) {
     hca::RunArgs a;
+    a.flags = 0;  // plans run the default path (FP32 filter, tensor-core tiles where they apply)
     a.d_points = pts;
     a.n = pt.g.n;
     a.d = pt.g.d;

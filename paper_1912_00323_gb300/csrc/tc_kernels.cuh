@@ -143,8 +143,11 @@ struct Smem {
     uint32_t cidx[kTile];      // per candidate: list index
     uint32_t gsum[4];          // per 32 candidates: unions: bit mask of the candidates whose tree node
                                // differs from ref; labels: the smallest cluster id
-    uint32_t rq0[kMaxRng];     // first list index of each neighbour range
-    uint32_t rpre[kMaxRng + 1];  // stream offset of each range; [kMaxRng] = stream length
+    uint32_t rq0[kMaxRng];     // first list index of each span (a neighbour range, or a kept cell)
+    uint32_t rpre[kMaxRng + 1];  // stream offset of each span; [kMaxRng] = stream length
+    uint32_t bcell[kMaxRng];   // unions, labels: the neighbour cells, range by range
+    uint32_t bnear[kMaxRng];   // 1: some row lies within eps of the cell's box
+    uint32_t nbc, bover;       // number of those cells; 1 if they did not fit (no pruning)
     uint64_t mbar;
     uint32_t taddr, ref, next, pad;
 };
@@ -196,6 +199,23 @@ __device__ __forceinline__ void stage_extra(float *hi_op, float *lo_op, int row,
     *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(hi_op) + o1) = z;
     *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(lo_op) + o0) = z;
     *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(lo_op) + o1) = z;
+}
+
+// box_far for a row held in registers (four coordinates per float4).
+template <int DP>
+__device__ __forceinline__ bool box_far_reg(const float4 (&a)[DP / 4], const float *lo, const float *hi,
+                                            const GridParams &g) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < DP / 4; ++k) {
+        const float4 l = __ldg(reinterpret_cast<const float4 *>(lo) + k);
+        const float4 h = __ldg(reinterpret_cast<const float4 *>(hi) + k);
+        float t = fmaxf(fmaxf(__fsub_rn(l.x, a[k].x), __fsub_rn(a[k].x, h.x)), 0.f); s = __fmaf_rn(t, t, s);
+        t = fmaxf(fmaxf(__fsub_rn(l.y, a[k].y), __fsub_rn(a[k].y, h.y)), 0.f);       s = __fmaf_rn(t, t, s);
+        t = fmaxf(fmaxf(__fsub_rn(l.z, a[k].z), __fsub_rn(a[k].z, h.z)), 0.f);       s = __fmaf_rn(t, t, s);
+        t = fmaxf(fmaxf(__fsub_rn(l.w, a[k].w), __fsub_rn(a[k].w, h.w)), 0.f);       s = __fmaf_rn(t, t, s);
+    }
+    return s > g.hi32;
 }
 
 // The exact predicate on two points of the sorted rows: FP32 filter with the guard band of
@@ -326,8 +346,74 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
                 for (int k = 0; k < DP / 4; ++k) *reinterpret_cast<float4 *>(S.cen + 4 * k) = q[k];
             }
         }
+        // unions and labels: the neighbour cells, then only those whose box lies within eps of
+        // some row of the chunk (every thread tests its own row; a cell that no row reaches holds
+        // no candidate of this chunk); the stream is one span per kept cell.  Counts keep the
+        // whole ranges: the CUDA-core count resumes a handed-over row at a stream position.
+        int nspan = n_rng;
+        bool by_cell = false;
+        if (MODE != kCount) {
+            if (warp == 0) {
+                uint32_t lo = 0, cnt = 0;
+                if (tid < n_rng) {
+                    uint2 rg = v.ranges[(uint64_t)A * v.n_all + tid];
+                    if (MODE == kMerge && tid == 0) rg.x = A;  // own pencil: this cell and the ones after it
+                    if (rg.x < rg.y) {
+                        lo = rg.x;
+                        cnt = rg.y - rg.x;
+                    }
+                }
+                uint32_t incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (tid >= o) incl += y;
+                }
+                const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                for (uint32_t j = 0; j < cnt; ++j)
+                    if (incl - cnt + j < (uint32_t)kMaxRng) S.bcell[incl - cnt + j] = lo + j;
+                S.bnear[tid] = 0u;
+                if (tid == 0) {
+                    S.nbc = total < (uint32_t)kMaxRng ? total : (uint32_t)kMaxRng;
+                    S.bover = total > (uint32_t)kMaxRng ? 1u : 0u;
+                }
+            }
+            __syncthreads();
+            by_cell = S.bover == 0u;
+            if (by_cell) {
+                const uint32_t nbc = S.nbc;
+                if (have)
+                    for (uint32_t i = 0; i < nbc; ++i) {
+                        const uint64_t c = S.bcell[i];
+                        if (!box_far_reg<DP>(q, v.box_lo + c * DP, v.box_hi + c * DP, G)) S.bnear[i] = 1u;
+                    }
+                __syncthreads();
+                if (warp == 0) {
+                    uint32_t q0 = 0, len = 0;
+                    if (tid < (int)nbc && S.bnear[tid]) {
+                        const uint32_t c = S.bcell[tid];
+                        q0 = tt.cx[v.cell_start[c]];
+                        const uint32_t q1 = tt.cx[v.cell_start[c + 1]];
+                        if (MODE == kMerge && c == A) q0 = max(q0, k0);  // earlier rows pair from their side
+                        len = q1 > q0 ? q1 - q0 : 0u;
+                    }
+                    uint32_t incl = len;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (tid >= o) incl += y;
+                    }
+                    if (tid < (int)nbc) {
+                        S.rq0[tid] = q0;
+                        S.rpre[tid] = incl - len;
+                    }
+                    if (tid == 31) S.rpre[kMaxRng] = incl;  // stream length
+                }
+                nspan = (int)nbc;
+            }
+        }
         // the candidate stream: one range per warp-0 lane, then a prefix over the ranges
-        if (warp == 0) {
+        if (warp == 0 && !by_cell) {
             uint32_t q0 = 0, len = 0;
             if (tid < n_rng) {
                 uint2 rg = v.ranges[(uint64_t)A * v.n_all + tid];
@@ -373,7 +459,7 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
         auto prefetch = [&](uint32_t ub) {
             const uint32_t u = ub + (uint32_t)tid;
             pre_in = u < L;
-            pre_k = pre_in ? stream_index(S.rpre, S.rq0, n_rng, u) : 0u;
+            pre_k = pre_in ? stream_index(S.rpre, S.rq0, nspan, u) : 0u;
             const uint32_t qp = pre_in ? (MODE == kCount ? pre_k : __ldg(tt.core_list + pre_k)) : 0u;
             const float4 *src = reinterpret_cast<const float4 *>(v.pts + (uint64_t)qp * DP);
 #pragma unroll
@@ -383,6 +469,28 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
         };
         if (L > 0) prefetch(0);
         for (uint32_t ub = 0; ub < L; ub += kTile) {
+            const bool cin = pre_in;
+            const uint32_t nq = min((uint32_t)kTile, L - ub);
+            uint32_t rq = 0xffffffffu, ref = 0xffffffffu;
+            if (MODE == kMerge) {
+                // tree nodes one step further towards the roots; a block whose rows and
+                // candidates all share one node is skipped before anything is staged
+                if (cin) rq = __ldcg(v.parent + pre_pay);
+                if (have) {
+                    rp = __ldcg(v.parent + rp);
+                    S.ref = rp;  // any row's tree node; all rows write before the barrier
+                }
+                __syncthreads();
+                ref = S.ref;
+                if (__syncthreads_and((!have || rp == ref) && (!cin || rq == ref))) {
+                    ++n_skip;
+                    if (ub + kTile < L) prefetch(ub + kTile);
+                    continue;
+                }
+                S.cpay[tid] = rq;
+                const unsigned dm = __ballot_sync(0xffffffffu, cin && rq != ref);
+                if ((tid & 31) == 0) S.gsum[warp] = dm;  // read after the barrier of the MMA wait
+            }
             // stage the prefetched block
             {
                 const float nb = stage_split<DP, KP>(S.b_hi, S.b_lo, tid, q, S.cen, pre_in);
@@ -391,16 +499,7 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
                 stage_extra<DP, KP>(S.b_hi, S.b_lo, tid, make_float4(-chi, -__fsub_rn(colA, chi), 0.f, 0.f));
                 S.cidx[tid] = pre_k;
             }
-            const bool cin = pre_in;
-            uint32_t rq = 0xffffffffu;
-            if (MODE == kMerge) {
-                if (cin) rq = __ldcg(v.parent + pre_pay);  // one more step towards the root
-                S.cpay[tid] = rq;
-                if (have) {
-                    rp = __ldcg(v.parent + rp);
-                    S.ref = rp;  // any row's tree node; all rows write before the barrier
-                }
-            } else if (MODE == kLabels) {
+            if (MODE == kLabels) {
                 S.cpay[tid] = pre_pay;
                 uint32_t gm = pre_pay;
                 gm = __reduce_min_sync(0xffffffffu, gm);
@@ -408,24 +507,8 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;");
-            bool skip = false;
-            uint32_t ref = 0xffffffffu;
-            if (MODE == kMerge) {
-                __syncthreads();
-                ref = S.ref;
-                const unsigned dm = __ballot_sync(0xffffffffu, cin && rq != ref);
-                if ((tid & 31) == 0) S.gsum[warp] = dm;  // read after the barrier of the MMA wait
-                skip = __syncthreads_and((!have || rp == ref) && (!cin || rq == ref)) != 0;
-            } else {
-                __syncthreads();
-            }
+            __syncthreads();
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t nq = min((uint32_t)kTile, L - ub);
-            if (skip) {
-                ++n_skip;
-                if (ub + kTile < L) prefetch(ub + kTile);
-                continue;
-            }
             if (tid == 0) {
                 const uint32_t ah = smem_u32(S.a_hi), al = smem_u32(S.a_lo);
                 const uint32_t bh = smem_u32(S.b_hi), bl = smem_u32(S.b_lo);
