@@ -50,7 +50,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one radix sort pass
 # (k_os_pass) on the mixed3d workload at n = 2,000,000, from an ncu capture of that kernel;
 # None until a capture of the current kernel exists
-SORT_PASS_TRAFFIC_MIXED3D_2M = None
+SORT_PASS_TRAFFIC_MIXED3D_2M = 16_100_000  # dram read + write per k_os_pass launch (ncu, mean of 4)
 
 # Nominal dense tensor-core rates of a GB300 (TFLOP/s): the TF32 peak of the tile kernel is the
 # measured bf16 GEMM rate scaled by their ratio
@@ -548,8 +548,14 @@ def config_batched(pkg, torch, stream, flush, steps, warmup, n_sets, plain_sampl
 def serving_pool(torch, count, seed):
     """Job data for the serving run, drawn on the GPU (torch's Philox generator) and kept in
     pinned host memory: n log-uniform [1e3, 2e6], d uniform in 2..16, eps = 1.5 sqrt(d/2) on the
-    2^-12 lattice, MINPTS uniform in 4..20, 5 Gaussian blobs (sigma 2 eps / sqrt(d), centres
-    U[10,90]^d) + 10% uniform noise in [0,100]^d, float32 coordinates on the 2^-12 lattice."""
+    2^-12 lattice, MINPTS uniform in 4..20, 5 Gaussian blobs (centres U[10,90]^d) + 10% uniform
+    noise in [0,100]^d, float32 coordinates on the 2^-12 lattice.
+
+    Blob sigma: the batched sets' 2 eps / sqrt(d), capped where a blob of m = 0.18 n points
+    would leave a typical point fewer than K = 40 neighbours.  A point of an isotropic Gaussian
+    typically lies where the density is m (2 pi sigma^2)^(-d/2) e^(-d/2); times the volume V_d
+    eps^d of the eps-ball that is K for sigma = eps (m V_d / K)^(1/d) e^(-1/2) / sqrt(2 pi).
+    Without the cap almost no point of a d >= 12 set is core (the sets are noise)."""
     r = np.random.Generator(np.random.PCG64(seed))
     g = torch.Generator(device="cuda")
     g.manual_seed(seed)
@@ -561,7 +567,10 @@ def serving_pool(torch, count, seed):
         mp = int(r.integers(4, 21))
         n_noise = n // 10
         sizes = [(n - n_noise) // 5 + (1 if k < (n - n_noise) % 5 else 0) for k in range(5)]
-        sigma = 2.0 * eps / math.sqrt(d)
+        m_blob = (n - n_noise) / 5.0
+        v_d = math.pi ** (d / 2.0) / math.gamma(d / 2.0 + 1.0)
+        sigma = min(2.0 * eps / math.sqrt(d),
+                    eps * (m_blob * v_d / 40.0) ** (1.0 / d) * math.exp(-0.5) / math.sqrt(2.0 * math.pi))
         parts = []
         for m in sizes:
             c = torch.rand(d, generator=g, device="cuda", dtype=torch.float64) * 80.0 + 10.0
@@ -574,17 +583,29 @@ def serving_pool(torch, count, seed):
 
 
 def config_serving(pkg, torch, seconds, warmup_s, rate, workers, pool_size, seed=1912_00323 + 4,
-                   plain_jobs=200):
+                   plain_jobs=200, plain_seconds=30.0):
     """Poisson arrivals (rate per second) of jobs drawn from a pool of generated sets, submitted
     to the request server with host buffers: the jobs arriving in the first warmup_s seconds are
     left out of the statistics, p50 / p99 submit-to-labels latency and points/s over the window.
     Beside it, the plain sequential per-request path: the first plain_jobs jobs of the same
-    arrival list, each copied in, clustered with every distance in FP64 and no tensor cores, and
-    copied out alone; their latencies follow from the measured service times in arrival order
-    (one request at a time, first come first served)."""
+    arrival list (fewer once their service times pass plain_seconds), each copied in, clustered
+    with every distance in FP64 and no tensor cores, and copied out alone; their latencies
+    follow from the measured service times in arrival order (one request at a time, first come
+    first served)."""
     t0 = time.perf_counter()
     pool = serving_pool(torch, pool_size, seed)
     gen_s = time.perf_counter() - t0
+    # realised data: core and noise fractions of the pool's sets (one tuned call per set)
+    core_d, noise_d, pts_d = {}, {}, {}
+    for X, eps, mp in pool:
+        _, st = pkg.hca_dbscan_device(X.to("cuda"), eps, mp, stats=True)
+        dd = int(X.shape[1])
+        core_d[dd] = core_d.get(dd, 0) + st["n_core_points"]
+        noise_d[dd] = noise_d.get(dd, 0) + st["n_noise"]
+        pts_d[dd] = pts_d.get(dd, 0) + int(X.shape[0])
+    realised = {"core_fraction": sum(core_d.values()) / sum(pts_d.values()),
+                "noise_fraction": sum(noise_d.values()) / sum(pts_d.values()),
+                "core_fraction_by_d": {dd: round(core_d[dd] / pts_d[dd], 3) for dd in sorted(pts_d)}}
     r = np.random.Generator(np.random.PCG64(seed + 1))
     total = warmup_s + seconds
     arrivals = np.cumsum(r.exponential(1.0 / rate, size=int(rate * total * 1.3) + 16))
@@ -624,6 +645,9 @@ def config_serving(pkg, torch, seconds, warmup_s, rate, workers, pool_size, seed
     m = min(plain_jobs, len(arrivals))
     service = []
     for i in range(m):
+        if sum(service) > plain_seconds:
+            m = i
+            break
         X, eps, mp = pool[picks[i]]
         lab = torch.empty(len(X), dtype=torch.int32).pin_memory()
         torch.cuda.synchronize()
@@ -641,7 +665,7 @@ def config_serving(pkg, torch, seconds, warmup_s, rate, workers, pool_size, seed
     return {"workload": f"serving: Poisson arrivals at {rate:g}/s, {warmup_s:g} s warm-up + {seconds:g} s window; "
                         "n log-uniform [1e3, 2e6], d uniform 2..16, blobs + 10% noise, eps = 1.5 sqrt(d/2), "
                         f"minPts U{{4..20}}; jobs drawn from {len(pool)} generated sets, host buffers",
-            "pool_generation_s": gen_s, "workers": workers, "requests": int(keep.sum()),
+            "pool_generation_s": gen_s, "pool_data": realised, "workers": workers, "requests": int(keep.sum()),
             "p50_ms": float(np.percentile(lat[keep], 50)), "p99_ms": float(np.percentile(lat[keep], 99)),
             "value": served, "unit": "points/s", "offered_points_per_s": offered,
             "keeps_up": bool(window_end - total < 1.0), "wall_s": wall,
