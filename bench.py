@@ -99,6 +99,8 @@ def parse_args(argv=None):
     ap.add_argument("--seconds", type=float, default=60.0, help="serving: arrival window after the warm-up")
     ap.add_argument("--warmup-seconds", type=float, default=5.0, help="serving: arrivals before the window")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrivals per second")
+    ap.add_argument("--exact-rate", action="store_true",
+                    help="serving: keep --rate even above the measured capacity (the queue then grows)")
     ap.add_argument("--workers", type=int, default=4, help="serving: server worker threads (streams)")
     ap.add_argument("--pool", type=int, default=256, help="serving: distinct generated job sets")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -583,10 +585,18 @@ def serving_pool(torch, count, seed):
 
 
 def config_serving(pkg, torch, seconds, warmup_s, rate, workers, pool_size, seed=1912_00323 + 4,
-                   plain_jobs=200, plain_seconds=30.0):
-    """Poisson arrivals (rate per second) of jobs drawn from a pool of generated sets, submitted
-    to the request server with host buffers: the jobs arriving in the first warmup_s seconds are
-    left out of the statistics, p50 / p99 submit-to-labels latency and points/s over the window.
+                   plain_jobs=200, plain_seconds=30.0, burst_jobs=128, exact_rate=False):
+    """Poisson arrivals of jobs drawn from a pool of generated sets, submitted to the request
+    server with host buffers: the jobs arriving in the first warmup_s seconds are left out of
+    the statistics, p50 / p99 submit-to-labels latency and points/s over the window.
+
+    Before the window: every pool set is clustered once alone on the tuned path (device
+    resident; its realised core fraction and its service time), and a burst of burst_jobs
+    arrivals is submitted to the server at once, whose drain time gives the server's capacity
+    in points/s, and in jobs/s of the arrival mix (that rate / the pool's mean job size).  The
+    window runs at `rate` jobs/s, or at 0.8 of that capacity when `rate` is above it (unless
+    exact_rate), and the line says which.
+
     Beside it, the plain sequential per-request path: the first plain_jobs jobs of the same
     arrival list (fewer once their service times pass plain_seconds), each copied in, clustered
     with every distance in FP64 and no tensor cores, and copied out alone; their latencies
@@ -595,26 +605,57 @@ def config_serving(pkg, torch, seconds, warmup_s, rate, workers, pool_size, seed
     t0 = time.perf_counter()
     pool = serving_pool(torch, pool_size, seed)
     gen_s = time.perf_counter() - t0
-    # realised data: core and noise fractions of the pool's sets (one tuned call per set)
+    # realised data and the tuned per-request service time of every pool set
     core_d, noise_d, pts_d = {}, {}, {}
+    service_tuned = []
     for X, eps, mp in pool:
-        _, st = pkg.hca_dbscan_device(X.to("cuda"), eps, mp, stats=True)
+        xd = X.to("cuda")
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        _, st = pkg.hca_dbscan_device(xd, eps, mp, stats=True)
+        torch.cuda.synchronize()
+        service_tuned.append(time.perf_counter() - t1)
         dd = int(X.shape[1])
         core_d[dd] = core_d.get(dd, 0) + st["n_core_points"]
         noise_d[dd] = noise_d.get(dd, 0) + st["n_noise"]
         pts_d[dd] = pts_d.get(dd, 0) + int(X.shape[0])
+        del xd
+    pool_pts = np.array([len(X) for X, _, _ in pool], dtype=np.float64)
     realised = {"core_fraction": sum(core_d.values()) / sum(pts_d.values()),
                 "noise_fraction": sum(noise_d.values()) / sum(pts_d.values()),
                 "core_fraction_by_d": {dd: round(core_d[dd] / pts_d[dd], 3) for dd in sorted(pts_d)}}
+    by_d = {}
+    for (X, _, _), t in zip(pool, service_tuned):
+        by_d[int(X.shape[1])] = by_d.get(int(X.shape[1]), 0.0) + t
+    tuned_seq = {"mean_service_ms": 1e3 * float(np.mean(service_tuned)),
+                 "service_share_by_d": {dd: round(by_d[dd] / sum(service_tuned), 3) for dd in sorted(by_d)},
+                 "capacity_points_per_s": float(pool_pts.sum() / sum(service_tuned)),
+                 "capacity_jobs_per_s": len(pool) / sum(service_tuned),
+                 "path": "every pool set alone, device resident, hca_dbscan_device on the tuned path"}
     r = np.random.Generator(np.random.PCG64(seed + 1))
-    total = warmup_s + seconds
-    arrivals = np.cumsum(r.exponential(1.0 / rate, size=int(rate * total * 1.3) + 16))
-    arrivals = arrivals[arrivals < total]
-    picks = r.integers(0, len(pool), size=len(arrivals))
-    lat = np.zeros(len(arrivals))
-    done_t = np.zeros(len(arrivals))
+    lat = done_t = None
     with pkg.Server(hbm_budget_bytes=96 << 30, workers=workers) as sv:
         sv.wait(sv.submit(*pool[0]))          # warm-up of the server's streams and pools
+        # capacity: a burst submitted at once, drained by the server
+        bpicks = r.integers(0, len(pool), size=burst_jobs)
+        t1 = time.perf_counter()
+        btk = [sv.submit(*pool[k]) for k in bpicks]
+        for tk in btk:
+            sv.wait(tk)
+        burst_s = time.perf_counter() - t1
+        cap_pts = float(pool_pts[bpicks].sum()) / burst_s
+        # jobs per second at that point rate for the arrival mix (uniform over the pool)
+        max_rate = cap_pts / float(pool_pts.mean())
+        capacity = {"jobs": int(burst_jobs), "seconds": burst_s, "points_per_s": cap_pts,
+                    "jobs_per_s_of_the_mix": max_rate,
+                    "path": "a burst of jobs submitted at once; the time until the last one completes"}
+        rate_used = rate if (exact_rate or rate <= 0.8 * max_rate) else 0.8 * max_rate
+        total = warmup_s + seconds
+        arrivals = np.cumsum(r.exponential(1.0 / rate_used, size=int(rate_used * total * 1.3) + 16))
+        arrivals = arrivals[arrivals < total]
+        picks = r.integers(0, len(pool), size=len(arrivals))
+        lat = np.zeros(len(arrivals))
+        done_t = np.zeros(len(arrivals))
         tickets = []
         start = time.perf_counter()
 
@@ -662,9 +703,13 @@ def config_serving(pkg, torch, seconds, warmup_s, rate, workers, pool_size, seed
         finish = max(finish, arrivals[i]) + service[i]
         plain_lat.append(1e3 * (finish - arrivals[i]))
     plain_pts = float(pts[:m].sum())
-    return {"workload": f"serving: Poisson arrivals at {rate:g}/s, {warmup_s:g} s warm-up + {seconds:g} s window; "
-                        "n log-uniform [1e3, 2e6], d uniform 2..16, blobs + 10% noise, eps = 1.5 sqrt(d/2), "
+    return {"workload": f"serving: Poisson arrivals at {rate_used:.4g}/s, {warmup_s:g} s warm-up + {seconds:g} s "
+                        "window; n log-uniform [1e3, 2e6], d uniform 2..16, blobs + 10% noise, eps = 1.5 sqrt(d/2), "
                         f"minPts U{{4..20}}; jobs drawn from {len(pool)} generated sets, host buffers",
+            "requested_rate_per_s": rate, "rate_per_s": rate_used,
+            "saturated_at_requested_rate": bool(rate > max_rate),
+            "max_sustainable_rate_per_s": max_rate, "capacity": capacity,
+            "tuned_sequential": tuned_seq,
             "pool_generation_s": gen_s, "pool_data": realised, "workers": workers, "requests": int(keep.sum()),
             "p50_ms": float(np.percentile(lat[keep], 50)), "p99_ms": float(np.percentile(lat[keep], 99)),
             "value": served, "unit": "points/s", "offered_points_per_s": offered,
@@ -814,7 +859,8 @@ def run_ours(args):
             "c3_aniso16d": config_c3(pkg, torch, stream, flush, max(3, min(args.steps, 10)), args.warmup,
                                      bf16_burst, peak_kind),
             "batched": config_batched(pkg, torch, stream, flush, max(2, min(args.steps, 4)), 1, args.sets),
-            "serving": config_serving(pkg, torch, 10.0, 2.0, args.rate, args.workers, 64, plain_jobs=150),
+            "serving": config_serving(pkg, torch, 10.0, 2.0, args.rate, args.workers, 64, plain_jobs=150,
+                                      plain_seconds=15.0, burst_jobs=64),
         }
 
     if rank != 0:
@@ -900,7 +946,8 @@ def run_serving(args):
     from paper_1912_00323_gb300 import build as pkg_build
     pkg_build.build()
     pkg.load()
-    r = config_serving(pkg, torch, args.seconds, args.warmup_seconds, args.rate, args.workers, args.pool)
+    r = config_serving(pkg, torch, args.seconds, args.warmup_seconds, args.rate, args.workers, args.pool,
+                       exact_rate=args.exact_rate)
     line = {"metric": "serving: p50/p99 submit-to-labels latency and points/s", "n_gpus": 1,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic", **r}
     print(json.dumps(line), flush=True)

@@ -16,6 +16,8 @@
 // the coarse cells, core[j], parent[j] and comp_min[j] over points.
 #pragma once
 
+#include <type_traits>
+
 #include "lowd_kernels.cuh"
 
 namespace hca {
@@ -124,51 +126,6 @@ __device__ __forceinline__ bool box_far(const double *a, const double *lo, const
         s = __fma_rn(t, t, s);
     }
     return s > g.eps2 * (1.0 + 0x1p-40);
-}
-
-// Box of every coarse cell (one warp per cell, eight dimensions at a time).
-template <typename T, int DP>
-__global__ void __launch_bounds__(256) k_cell_box_hd(HdView<T, DP> v) {
-    const int lane = lane_id();
-    const uint32_t C = v.ctr->n_cells;
-    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < C; c += warps) {
-        const uint32_t s0 = v.cell_start[c], s1 = v.cell_start[c + 1];
-#pragma unroll
-        for (int g0 = 0; g0 < DP; g0 += 8) {
-            T mn[8], mx[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                mn[i] = sizeof(T) == 4 ? (T)FLT_MAX : (T)DBL_MAX;
-                mx[i] = -mn[i];
-            }
-            for (uint32_t j = s0 + lane; j < s1; j += 32) {
-                const T *r = v.pts + (uint64_t)j * DP + g0;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const T x = r[i];
-                    mn[i] = x < mn[i] ? x : mn[i];
-                    mx[i] = x > mx[i] ? x : mx[i];
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                for (int o = 16; o; o >>= 1) {
-                    const T a = __shfl_xor_sync(0xffffffffu, mn[i], o), b = __shfl_xor_sync(0xffffffffu, mx[i], o);
-                    mn[i] = a < mn[i] ? a : mn[i];
-                    mx[i] = b > mx[i] ? b : mx[i];
-                }
-            }
-            if (lane < 8) {
-                T a = mn[0], b = mx[0];
-#pragma unroll
-                for (int i = 1; i < 8; ++i)
-                    if (lane == i) { a = mn[i]; b = mx[i]; }
-                v.box_lo[(uint64_t)c * DP + g0 + lane] = a;
-                v.box_hi[(uint64_t)c * DP + g0 + lane] = b;
-            }
-        }
-    }
 }
 
 template <typename T, int DP>
@@ -307,6 +264,125 @@ __device__ __forceinline__ uint32_t chunk_cell(const uint32_t *chunk_off, uint32
     return lo;
 }
 
+// Box of every coarse cell in three launches: clear, accumulate over 32-point chunks (one
+// warp per chunk, so a large cell is spread over many warps), decode.  Coordinates are
+// accumulated as order-preserving unsigned integers (sign bit flipped for x >= 0, every bit
+// for x < 0), so min / max of the codes is min / max of the values and the warps of one cell
+// combine with atomicMin / atomicMax.
+template <typename T>
+struct BoxCode {
+    typedef typename std::conditional<sizeof(T) == 4, uint32_t, unsigned long long>::type U;
+    static __device__ __forceinline__ U enc(T x) {
+        if (sizeof(T) == 4) {
+            const uint32_t u = __float_as_uint((float)x);
+            return (U)(u ^ ((uint32_t)((int32_t)u >> 31) | 0x80000000u));
+        } else {
+            const unsigned long long u = (unsigned long long)__double_as_longlong((double)x);
+            return (U)(u ^ ((unsigned long long)((long long)u >> 63) | 0x8000000000000000ull));
+        }
+    }
+    static __device__ __forceinline__ T dec(U c) {
+        if (sizeof(T) == 4) {
+            const uint32_t u = (uint32_t)c;
+            return (T)__uint_as_float(u ^ ((u >> 31) ? 0x80000000u : 0xffffffffu));
+        } else {
+            const unsigned long long u = (unsigned long long)c;
+            return (T)__longlong_as_double((long long)(u ^ ((u >> 63) ? 0x8000000000000000ull : ~0ull)));
+        }
+    }
+    static __device__ __forceinline__ U warp_min(U v) {
+        if (sizeof(T) == 4) return (U)__reduce_min_sync(0xffffffffu, (uint32_t)v);
+        for (int o = 16; o; o >>= 1) {
+            const U t = __shfl_xor_sync(0xffffffffu, v, o);
+            v = t < v ? t : v;
+        }
+        return v;
+    }
+    static __device__ __forceinline__ U warp_max(U v) {
+        if (sizeof(T) == 4) return (U)__reduce_max_sync(0xffffffffu, (uint32_t)v);
+        for (int o = 16; o; o >>= 1) {
+            const U t = __shfl_xor_sync(0xffffffffu, v, o);
+            v = t > v ? t : v;
+        }
+        return v;
+    }
+};
+
+template <typename T, int DP>
+__global__ void __launch_bounds__(256) k_cell_box_clear(HdView<T, DP> v) {
+    typedef typename BoxCode<T>::U U;
+    const uint64_t m = (uint64_t)v.ctr->n_cells * DP;
+    U *lo = reinterpret_cast<U *>(v.box_lo), *hi = reinterpret_cast<U *>(v.box_hi);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+        lo[i] = ~(U)0;
+        hi[i] = (U)0;
+    }
+}
+
+template <typename T, int DP>
+__global__ void __launch_bounds__(256) k_cell_box_hd(HdView<T, DP> v) {
+    typedef BoxCode<T> BC;
+    typedef typename BC::U U;
+    constexpr int E = DP > 32 ? DP / 32 : 1;  // dimensions per lane in the atomics
+    const int lane = lane_id();
+    const uint32_t C = v.ctr->n_cells, NC = v.ctr->n_chunks;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    U *lo = reinterpret_cast<U *>(v.box_lo), *hi = reinterpret_cast<U *>(v.box_hi);
+    for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < NC; t += warps) {
+        const uint32_t A = chunk_cell(v.chunk_off, C, t);
+        const uint32_t e = v.cell_start[A + 1], base = v.cell_start[A] + 32u * (t - v.chunk_off[A]);
+        const uint32_t p = base + lane;
+        const bool valid = p < e;
+        U mn[E], mx[E];
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            mn[k] = ~(U)0;
+            mx[k] = (U)0;
+        }
+#pragma unroll
+        for (int g0 = 0; g0 < DP; g0 += 4) {
+            T x[4];
+            if (sizeof(T) == 4) {
+                const float4 f = valid ? __ldg(reinterpret_cast<const float4 *>(v.pts + (uint64_t)p * DP + g0))
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                x[0] = (T)f.x; x[1] = (T)f.y; x[2] = (T)f.z; x[3] = (T)f.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) x[i] = valid ? __ldg(v.pts + (uint64_t)p * DP + g0 + i) : (T)0;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const U c = BC::enc(x[i]);
+                const U a = BC::warp_min(valid ? c : ~(U)0);
+                const U b = BC::warp_max(valid ? c : (U)0);
+                if (lane == ((g0 + i) & 31)) {
+                    mn[(g0 + i) >> 5] = a;
+                    mx[(g0 + i) >> 5] = b;
+                }
+            }
+        }
+        if (lane < DP) {
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                atomicMin(lo + (uint64_t)A * DP + lane + 32 * k, mn[k]);
+                atomicMax(hi + (uint64_t)A * DP + lane + 32 * k, mx[k]);
+            }
+        }
+    }
+}
+
+template <typename T, int DP>
+__global__ void __launch_bounds__(256) k_cell_box_decode(HdView<T, DP> v) {
+    typedef BoxCode<T> BC;
+    typedef typename BC::U U;
+    const uint64_t m = (uint64_t)v.ctr->n_cells * DP;
+    U *lo = reinterpret_cast<U *>(v.box_lo), *hi = reinterpret_cast<U *>(v.box_hi);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+        v.box_lo[i] = BC::dec(lo[i]);
+        v.box_hi[i] = BC::dec(hi[i]);
+    }
+}
+
 #define HD_FOR_EACH_CHUNK(v, A, base, e, slot)                                                \
     const uint32_t C_ = (v).ctr->n_cells, NC_ = (v).ctr->n_chunks;                           \
     for (uint32_t t_ = next_chunk(&(v).ctr->hd_next[slot]); t_ < NC_;                        \
@@ -399,7 +475,11 @@ __global__ void __launch_bounds__(256) k_uf_init_hd(HdView<T, DP> v) {
 // First links of the core graph (Definitions 3-5): every core point p hooks to the first core
 // point q < p within eps that the scan meets (p keeps itself when there is none).  Each link
 // is an edge of the graph and points to a smaller index, so the links form a forest whose
-// trees lie inside clusters; the union pass that follows joins the trees.
+// trees lie inside clusters; the union pass that follows joins the trees.  The links only
+// shorten that pass (it tests every pair itself), so a chunk stops looking after
+// kHookBlocks candidate blocks: a point with no lower neighbour (the first point of every
+// cluster) would otherwise make its warp read the whole lower half of its neighbourhood.
+constexpr uint32_t kHookBlocks = 16;
 template <typename T, int DP>
 __global__ void __launch_bounds__(32 * kHdWarps) k_hook_hd(HdView<T, DP> v) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -413,6 +493,7 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_hook_hd(HdView<T, DP> v) {
         if (!open) continue;
         const GridParams &G = params_of(v, set_of_key(v, v.cell_key[A]));
         stage_rows<T, DP>(rows, v.pts, base, e);
+        uint32_t chunks_here = 0;
         for (int g0 = 0; g0 < v.n_all && open; g0 += 32) {
             const int k = g0 + lane;
             const uint2 rg = k < v.n_all ? v.ranges[(uint64_t)A * v.n_all + k] : make_uint2(0u, 0u);
@@ -426,6 +507,10 @@ __global__ void __launch_bounds__(32 * kHdWarps) k_hook_hd(HdView<T, DP> v) {
                     const uint32_t q = qb + lane;
                     const bool qc = q < q1 && v.core[q];
                     if (!__any_sync(0xffffffffu, qc)) continue;
+                    if (++chunks_here > kHookBlocks) {
+                        open = 0;
+                        break;
+                    }
                     T qv[DP];
                     hd_load<T, DP>(v.pts, q, qc, qv);
                     ++chunks;

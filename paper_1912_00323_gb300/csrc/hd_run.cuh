@@ -159,7 +159,7 @@ void run_tc_phases(HdView<float, DP> &hv, cudaStream_t s, char *b, int64_t n, in
     tc::k_tc_chunks_count<<<gpts, 256, 0, s>>>(hv.cell_start, ctr, tune.min[0], nch);
     exclusive_scan_u32(nch, ch0, n, &ctr->n_cells, &ctr->n_tc_chunks[tc::kCount], part, s, &launches);
     tmark(0);
-    tc::k_tc_hd<DP, tc::kCount><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch0, cx, clist, nclist, clab});
+    tc::k_tc_hd<DP, tc::kCount><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch0, cx, clist, nclist, clab, nullptr});
     tmark(1);
     k_count_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
     launches += 3;
@@ -177,18 +177,20 @@ void run_tc_phases(HdView<float, DP> &hv, cudaStream_t s, char *b, int64_t n, in
     k_uf_init_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
     k_hook_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
     for (int r = 0; r < 6; ++r) k_jump_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
+    // (nch is free once the chunk tables are scanned)
+    tc::k_tc_cell_root<DP><<<gpts, 256, 0, s>>>(hv, nch);
     tmark(2);
-    tc::k_tc_hd<DP, tc::kMerge><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch1, cx, clist, nclist, clab});
+    tc::k_tc_hd<DP, tc::kMerge><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch1, cx, clist, nclist, clab, nch});
     tmark(3);
     k_merge_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
     k_compress_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
-    launches += 11;
+    launches += 12;
     mark(8);
     // ---- Algorithm 4: canonical ids, core labels, border and noise points ----
     k_comp_min_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
-    tc::k_tc_core_labels<DP><<<gpts, 256, 0, s>>>(hv, tc::Tables{ch2, cx, clist, nclist, clab}, nsets, clab);
+    tc::k_tc_core_labels<DP><<<gpts, 256, 0, s>>>(hv, tc::Tables{ch2, cx, clist, nclist, clab, nullptr}, nsets, clab);
     tmark(4);
-    tc::k_tc_hd<DP, tc::kLabels><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch2, cx, clist, nclist, clab});
+    tc::k_tc_hd<DP, tc::kLabels><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch2, cx, clist, nclist, clab, nullptr});
     tmark(5);
     k_labels_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
     launches += 4;
@@ -526,8 +528,10 @@ int run_hd(const RunArgs &a) {
     hv.box_lo = (T *)(b + o_blo);
     hv.box_hi = (T *)(b + o_bhi);
     // the box of every coarse cell in all d dimensions (point-to-box distance bounds)
-    k_cell_box_hd<T, DP><<<grid_for(n, 8, sms, 16), 256, 0, s>>>(hv);
-    ++launches;
+    k_cell_box_clear<T, DP><<<grid_for((int64_t)n * DP, 256, sms, 8), 256, 0, s>>>(hv);
+    k_cell_box_hd<T, DP><<<grid_for(n / 32 + 1, 8, sms, 16), 256, 0, s>>>(hv);
+    k_cell_box_decode<T, DP><<<grid_for((int64_t)n * DP, 256, sms, 8), 256, 0, s>>>(hv);
+    launches += 3;
     allow_smem(k_count_hd<T, DP>, smem);
     allow_smem(k_hook_hd<T, DP>, smem);
     allow_smem(k_merge_hd<T, DP>, smem);

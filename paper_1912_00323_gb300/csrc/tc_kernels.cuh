@@ -63,6 +63,8 @@ struct Tables {
     const uint32_t *core_list;  // core points, ascending
     const uint32_t *nc_list;    // non-core points, ascending
     const uint32_t *core_lab;   // cluster id of every core point, by core-list index (labels phase)
+    const uint32_t *cell_root;  // unions: the one root of a cell's core points (~0 if they differ or
+                                // there are none), taken before the phase; nullptr: unused
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -390,7 +392,14 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
                 __syncthreads();
                 if (warp == 0) {
                     uint32_t q0 = 0, len = 0;
-                    if (tid < (int)nbc && S.bnear[tid]) {
+                    bool keep = tid < (int)nbc && S.bnear[tid];
+                    if (MODE == kMerge && keep && tt.cell_root) {
+                        // two cells whose core points were already all in one tree have no pair
+                        // left to join (trees only grow)
+                        const uint32_t ra = tt.cell_root[A];
+                        keep = ra == 0xffffffffu || tt.cell_root[S.bcell[tid]] != ra;
+                    }
+                    if (keep) {
                         const uint32_t c = S.bcell[tid];
                         q0 = tt.cx[v.cell_start[c]];
                         const uint32_t q1 = tt.cx[v.cell_start[c + 1]];
@@ -659,6 +668,27 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
 
 __device__ __forceinline__ uint32_t tc_chunks(uint32_t rows, uint32_t min_rows) {
     return rows >= min_rows ? (rows + (uint32_t)kTile - 1u) / (uint32_t)kTile : 0u;
+}
+
+// The one root of every coarse cell's core points (~0 when they differ or there are none), one
+// warp per cell, with read-only finds (nothing hooks meanwhile).
+template <int DP>
+__global__ void __launch_bounds__(256) k_tc_cell_root(HdView<float, DP> v, uint32_t *__restrict__ cell_root) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t C = v.ctr->n_cells;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < C; c += warps) {
+        uint32_t mn = 0xffffffffu, mx = 0u;
+        for (uint32_t j = v.cell_start[c] + lane; j < v.cell_start[c + 1]; j += 32) {
+            if (!v.core[j]) continue;
+            const uint32_t r = uf_root_readonly(v.parent, j, v.ctr);
+            mn = min(mn, r);
+            mx = max(mx, r);
+        }
+        mn = __reduce_min_sync(0xffffffffu, mn);
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if (lane == 0) cell_root[c] = (mn != 0xffffffffu && mn == mx) ? mn : 0xffffffffu;
+    }
 }
 
 // 128-row chunks of the counts for every coarse cell with at least min_rows points.
