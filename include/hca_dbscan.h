@@ -318,8 +318,11 @@ HCA_API int hca_plan_destroy(hca_plan *plan);
  *                  0..127.
  *   first_links    1: first-link pass in every coarse cell; 0: only in cells whose unions run
  *                  on the CUDA cores.
- * Defaults: path 0, tc_handoff 8, first_links 1; thresholds 16 / 16 / 4 for d <= 8 and
- * 8 / 4 / 1 for d > 8.
+ *   cta_warps      coarse grid: warps per CTA of the CUDA-core chunk kernels (counts, first
+ *                  links, unions, labels; one 32-point chunk per warp, its rows staged in the
+ *                  CTA's shared memory): 2, 4 or 8.
+ * Defaults: path 0, tc_handoff 8, first_links 1, cta_warps 4; thresholds 16 / 16 / 4 for
+ * d <= 8 and 8 / 4 / 1 for d > 8.
  */
 typedef struct hca_tuning {
     int32_t path;
@@ -328,6 +331,7 @@ typedef struct hca_tuning {
     int32_t tc_min_labels;
     int32_t tc_handoff;
     int32_t first_links;
+    int32_t cta_warps;
 } hca_tuning;
 
 /* The tuning used for dimension d (1..64); HCA_EINVAL for a bad d or NULL out. */
@@ -341,7 +345,8 @@ HCA_API int hca_tuning_set(int32_t d, const hca_tuning *t);
  * (same arguments as hca_dbscan_device; the points are only read) and keep the fastest as the
  * tuning of d.  Each candidate runs once untimed and then `repeats` times (1..16) timed with CUDA
  * events on `stream`, keeping its minimum.  Candidates: both neighbour searches for d = 3, 4;
- * for the coarse grid with float input, first links on / off and several row thresholds.
+ * for the coarse grid with float input, first links on / off and several row thresholds; then,
+ * on the coarse grid, 2 and 8 warps per CTA (cta_warps) with the rest of the fastest of those.
  *   out       host, nullable: the tuning kept.   best_ms  host, nullable: its time.
  * Synchronous.  Returns HCA_OK, or the first error of a candidate run (nothing is changed).
  */

@@ -60,7 +60,8 @@ class HcaStats(ctypes.Structure):
 class HcaTuning(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("tc_min_count", ctypes.c_int32),
                 ("tc_min_merge", ctypes.c_int32), ("tc_min_labels", ctypes.c_int32),
-                ("tc_handoff", ctypes.c_int32), ("first_links", ctypes.c_int32)]
+                ("tc_handoff", ctypes.c_int32), ("first_links", ctypes.c_int32),
+                ("cta_warps", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: int(getattr(self, name)) for name, _ in self._fields_}

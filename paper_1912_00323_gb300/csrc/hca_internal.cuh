@@ -26,7 +26,7 @@ constexpr uint32_t kErrBox = 8u;   // a point lies outside the extents a plan de
 // Base tuning (include/hca_dbscan.h): dimension-chosen neighbour search; tensor-core tiles
 // from 8 rows (counts, unions) and 2 non-core rows (labels); hand-off at 8 open count rows;
 // first links everywhere.  The defaults per d (tune.cu) adjust the split from it.
-constexpr hca_tuning kDefaultTuning = {0, 8, 8, 2, 8, 1};
+constexpr hca_tuning kDefaultTuning = {0, 8, 8, 2, 8, 1, 4};
 
 // Device counters and status, one struct per call in the workspace.
 struct DevCounters {
@@ -112,6 +112,19 @@ struct Workspace {
 size_t scan_partials_size(int64_t m_max);
 void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t m_max, const uint32_t *m_dev,
                         uint32_t *total, uint32_t *partials, cudaStream_t s, int *launches);
+
+// Elements per tile of the scan (the tile sums in `partials` are per this many elements).
+constexpr int kScanTileElems = 2048;
+
+// Run-length cells from first-of-cell flags (1 on the first point of every cell, points in
+// cell order).  The kernel that wrote the flags also wrote the sum of every kScanTileElems-flag
+// tile into partials[tile] (tiles = ceil(n / kScanTileElems)).  Scans those sums (the total,
+// the cell count, into *n_cells), then per point replaces the flag by the point's cell id and
+// writes the first point and the key of every cell, and cell_start[n_cells] = n.
+// partials: scan_partials_size(n) uint32.  Two launches.
+template <typename K>
+void cells_from_flags(const K *keys, uint32_t *flags_cell_of, int64_t n, uint32_t *partials, uint32_t *n_cells,
+                      uint32_t *cell_start, uint64_t *cell_key, cudaStream_t s, int *launches);
 
 // Geometry of the onesweep radix sort (sort.cu): keys per tile, digits per pass, and the
 // most passes a call can make.  The scratch of a sort of n pairs is sort_hist_elems(n)

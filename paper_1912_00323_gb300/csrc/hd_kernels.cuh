@@ -59,7 +59,8 @@ struct HdView {
     T *box_hi;
 };
 
-constexpr int kHdWarps = 4;   // warps per block in the point kernels of this path
+constexpr int kHdWarps = 4;     // warps per block in the point kernels of this path (default)
+constexpr int kHdMaxWarps = 8;  // most warps per block a tuning may choose
 
 // dist(a, q) <= eps with a in shared memory and q in registers (same exact predicate and FP32
 // guard band as the hypercube path; summation in dimension order).
@@ -210,19 +211,45 @@ __global__ void __launch_bounds__(256) k_bin_proj(const T *__restrict__ in, int 
     }
 }
 
-// Gather full rows into cell order (zero padded to DP) and flag the first point of each cell.
+// Gather the points into cell order, padded to DP coordinates, and flag the first point of
+// every coarse cell; one block per tile of kScanTileElems rows, DP / 4 threads per row (four
+// coordinates each, one vector store), the tile's flag count to tile_sums[block].
 template <typename T, int DP, typename K>
 __global__ void __launch_bounds__(256) k_gather_hd(const T *__restrict__ in, int d, const K *__restrict__ keys,
                                                   const uint32_t *__restrict__ idx, int64_t n,
-                                                  T *__restrict__ pts, uint32_t *__restrict__ flags) {
-    // one warp per point row: lanes copy coordinates
-    const int lane = threadIdx.x & 31;
-    for (int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; j < n;
-         j += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        const uint32_t o = idx[j];
-        for (int i = lane; i < DP; i += 32) pts[j * DP + i] = i < d ? in[(int64_t)o * d + i] : T(0);
-        if (lane == 0) flags[j] = (j == 0 || keys[j] != keys[j - 1]) ? 1u : 0u;
+                                                  T *__restrict__ pts, uint32_t *__restrict__ flags,
+                                                  uint32_t *__restrict__ tile_sums) {
+    constexpr int G = DP / 4;          // threads per row
+    constexpr int R = 256 / G;         // rows per step of the block
+    const int g = threadIdx.x % G, r0 = threadIdx.x / G;
+    const int64_t base = (int64_t)blockIdx.x * kScanTileElems;
+    uint32_t cnt = 0;
+#pragma unroll 4
+    for (int k = 0; k < kScanTileElems / R; ++k) {
+        const int64_t j = base + (int64_t)k * R + r0;
+        if (j < n) {
+            const uint32_t o = idx[j];
+            const T *src = in + (int64_t)o * d;
+            T x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = 4 * g + u < d ? src[4 * g + u] : T(0);
+            T *dst = pts + j * DP + 4 * g;
+            if (sizeof(T) == 4) {
+                *reinterpret_cast<float4 *>(dst) = make_float4((float)x[0], (float)x[1], (float)x[2], (float)x[3]);
+            } else {
+                reinterpret_cast<double2 *>(dst)[0] = make_double2((double)x[0], (double)x[1]);
+                reinterpret_cast<double2 *>(dst)[1] = make_double2((double)x[2], (double)x[3]);
+            }
+            if (g == 0) {
+                const uint32_t f = (j == 0 || keys[j] != keys[j - 1]) ? 1u : 0u;
+                flags[j] = f;
+                cnt += f;
+            }
+        }
     }
+    uint32_t total;
+    block_exclusive_scan<256>(cnt, &total);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
 }
 
 template <typename T, int DP>
@@ -397,7 +424,7 @@ __global__ void __launch_bounds__(256) k_cell_box_decode(HdView<T, DP> v) {
 // points are staged in shared memory, candidates stream through the lanes, and each open
 // point is compared with a warp ballot.
 template <typename T, int DP>
-__global__ void __launch_bounds__(32 * kHdWarps) k_count_hd(HdView<T, DP> v) {
+__global__ void __launch_bounds__(32 * kHdMaxWarps) k_count_hd(HdView<T, DP> v) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *rows = reinterpret_cast<T *>(smem_raw) + (threadIdx.x >> 5) * 32 * DP;
     const int lane = lane_id();
@@ -481,7 +508,7 @@ __global__ void __launch_bounds__(256) k_uf_init_hd(HdView<T, DP> v) {
 // cluster) would otherwise make its warp read the whole lower half of its neighbourhood.
 constexpr uint32_t kHookBlocks = 16;
 template <typename T, int DP>
-__global__ void __launch_bounds__(32 * kHdWarps) k_hook_hd(HdView<T, DP> v) {
+__global__ void __launch_bounds__(32 * kHdMaxWarps) k_hook_hd(HdView<T, DP> v) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *rows = reinterpret_cast<T *>(smem_raw) + (threadIdx.x >> 5) * 32 * DP;
     const int lane = lane_id();
@@ -549,7 +576,7 @@ __global__ void __launch_bounds__(256) k_jump_hd(HdView<T, DP> v) {
 // (lock-free union-find, root = smallest index).  A 32 x 32 tile whose core points all share
 // one root is skipped without loading coordinates.
 template <typename T, int DP>
-__global__ void __launch_bounds__(32 * kHdWarps) k_merge_hd(HdView<T, DP> v) {
+__global__ void __launch_bounds__(32 * kHdMaxWarps) k_merge_hd(HdView<T, DP> v) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *rows = reinterpret_cast<T *>(smem_raw) + (threadIdx.x >> 5) * 32 * DP;
     const int lane = lane_id();
@@ -657,7 +684,7 @@ __global__ void __launch_bounds__(256) k_comp_min_hd(HdView<T, DP> v) {
 // Algorithm 4 / Definition 5 with the canonical rule, over points: core points take their
 // cluster id, a non-core point the smallest id among its core neighbours, else -1.
 template <typename T, int DP>
-__global__ void __launch_bounds__(32 * kHdWarps) k_labels_hd(HdView<T, DP> v) {
+__global__ void __launch_bounds__(32 * kHdMaxWarps) k_labels_hd(HdView<T, DP> v) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *rows = reinterpret_cast<T *>(smem_raw) + (threadIdx.x >> 5) * 32 * DP;
     const int lane = lane_id();

@@ -139,7 +139,7 @@ inline uint32_t *part_of(char *b, size_t o) { return (uint32_t *)(b + o); }
 // first links + pointer jumping + unions (Definitions 3-5) and labels (Algorithm 4).
 template <int DP, typename Mark>
 void run_tc_phases(HdView<float, DP> &hv, cudaStream_t s, char *b, int64_t n, int grid_tc, size_t tc_smem,
-                   int gpts, int gcell, size_t smem, uint32_t *part, const TcOffsets &o, int nsets,
+                   int gpts, int gcell, int hd_block, size_t smem, uint32_t *part, const TcOffsets &o, int nsets,
                    DevCounters *ctr, const TcTuning &tune, Mark &mark, int &launches, cudaEvent_t *tev) {
     // tev (nullable): six events recorded around the three tensor-core launches
     auto tmark = [&](int i) { if (tev) cudaEventRecord(tev[i], s); };
@@ -161,7 +161,7 @@ void run_tc_phases(HdView<float, DP> &hv, cudaStream_t s, char *b, int64_t n, in
     tmark(0);
     tc::k_tc_hd<DP, tc::kCount><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch0, cx, clist, nclist, clab, nullptr});
     tmark(1);
-    k_count_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
+    k_count_hd<float, DP><<<gcell, hd_block, smem, s>>>(hv);
     launches += 3;
     mark(6);
     // core numbering, core and non-core lists, chunk tables of the unions and the labels
@@ -175,14 +175,14 @@ void run_tc_phases(HdView<float, DP> &hv, cudaStream_t s, char *b, int64_t n, in
     mark(7);
     // ---- Definitions 3-5: first links, pointer jumping, then the remaining unions ----
     k_uf_init_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
-    k_hook_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
+    k_hook_hd<float, DP><<<gcell, hd_block, smem, s>>>(hv);
     for (int r = 0; r < 6; ++r) k_jump_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
     // (nch is free once the chunk tables are scanned)
     tc::k_tc_cell_root<DP><<<gpts, 256, 0, s>>>(hv, nch);
     tmark(2);
     tc::k_tc_hd<DP, tc::kMerge><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch1, cx, clist, nclist, clab, nch});
     tmark(3);
-    k_merge_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
+    k_merge_hd<float, DP><<<gcell, hd_block, smem, s>>>(hv);
     k_compress_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
     launches += 12;
     mark(8);
@@ -192,7 +192,7 @@ void run_tc_phases(HdView<float, DP> &hv, cudaStream_t s, char *b, int64_t n, in
     tmark(4);
     tc::k_tc_hd<DP, tc::kLabels><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch2, cx, clist, nclist, clab, nullptr});
     tmark(5);
-    k_labels_hd<float, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
+    k_labels_hd<float, DP><<<gcell, hd_block, smem, s>>>(hv);
     launches += 4;
     mark(9);
 }
@@ -285,8 +285,11 @@ int run_hd(const RunArgs &a) {
     double tau = 0.0;
     int3 sel = make_int3(0, 1, 2);
     const int gpts = grid_for(n, 256, sms, 8);
-    const int gcell = grid_for((n + 31) / 32 + 1, kHdWarps, sms, 16);
-    const size_t smem = (size_t)kHdWarps * 32 * DP * sizeof(T);
+    // CUDA-core chunk kernels: one 32-point chunk per warp, tuning.cta_warps warps per CTA
+    const int hd_warps = (a.tune.cta_warps == 2 || a.tune.cta_warps == 8) ? a.tune.cta_warps : kHdWarps;
+    const int hd_block = 32 * hd_warps;
+    const int gcell = grid_for((n + 31) / 32 + 1, hd_warps, sms, 64 / hd_warps);
+    const size_t smem = (size_t)hd_warps * 32 * DP * sizeof(T);
     bool flipped = false;
     std::vector<unsigned long long> hmm(128);
     HdView<T, DP> hv;
@@ -439,6 +442,7 @@ int run_hd(const RunArgs &a) {
         uint32_t *ia = (uint32_t *)(b + o_ia), *ib = (uint32_t *)(b + o_ib);
         uint32_t *hist = (uint32_t *)(b + o_hist), *part = (uint32_t *)(b + o_part);
         const bool use32 = sort_bits <= 32;
+        const int gtile = (int)((n + kScanTileElems - 1) / kScanTileElems);  // gather: one block per scan tile
         if (use32) {
             uint32_t *ka = (uint32_t *)(b + o_ka), *kb = (uint32_t *)(b + o_kb);
             if (batched)
@@ -449,9 +453,9 @@ int run_hd(const RunArgs &a) {
             mark(2);
             flipped = radix_sort_pairs<uint32_t>(ka, ia, kb, ib, n, 0, sort_bits, hist, part, s, &launches, &ctr->status);
             mark(3);
-            k_gather_hd<T, DP, uint32_t><<<grid_for(n, 8, sms, 16), 256, 0, s>>>(
+            k_gather_hd<T, DP, uint32_t><<<gtile, 256, 0, s>>>(
                 (const T *)a.d_points, d, flipped ? kb : ka, flipped ? ib : ia, n, (T *)(b + o_pts),
-                (uint32_t *)(b + o_flags));
+                (uint32_t *)(b + o_flags), part);
         } else {
             uint64_t *ka = (uint64_t *)(b + o_ka), *kb = (uint64_t *)(b + o_kb);
             if (batched)
@@ -462,22 +466,20 @@ int run_hd(const RunArgs &a) {
             mark(2);
             flipped = radix_sort_pairs<uint64_t>(ka, ia, kb, ib, n, 0, sort_bits, hist, part, s, &launches, &ctr->status);
             mark(3);
-            k_gather_hd<T, DP, uint64_t><<<grid_for(n, 8, sms, 16), 256, 0, s>>>(
+            k_gather_hd<T, DP, uint64_t><<<gtile, 256, 0, s>>>(
                 (const T *)a.d_points, d, flipped ? kb : ka, flipped ? ib : ia, n, (T *)(b + o_pts),
-                (uint32_t *)(b + o_flags));
+                (uint32_t *)(b + o_flags), part);
         }
         launches += 2;
-        exclusive_scan_u32((uint32_t *)(b + o_flags), (uint32_t *)(b + o_excl), n, nullptr,
-                           &ctr->n_cells, part, s, &launches);
+        // run-length cells: scan of the gather's tile counts, cell ids / starts / keys
         if (use32)
-            k_cells<uint32_t><<<gpts, 256, 0, s>>>((const uint32_t *)(b + (flipped ? o_kb : o_ka)),
-                                                   (uint32_t *)(b + o_flags), (const uint32_t *)(b + o_excl),
-                                                   n, (uint32_t *)(b + o_cstart), (uint64_t *)(b + o_ckey));
+            cells_from_flags<uint32_t>((const uint32_t *)(b + (flipped ? o_kb : o_ka)), (uint32_t *)(b + o_flags), n,
+                                       part, &ctr->n_cells, (uint32_t *)(b + o_cstart), (uint64_t *)(b + o_ckey), s,
+                                       &launches);
         else
-            k_cells<uint64_t><<<gpts, 256, 0, s>>>((const uint64_t *)(b + (flipped ? o_kb : o_ka)),
-                                                   (uint32_t *)(b + o_flags), (const uint32_t *)(b + o_excl),
-                                                   n, (uint32_t *)(b + o_cstart), (uint64_t *)(b + o_ckey));
-        ++launches;
+            cells_from_flags<uint64_t>((const uint64_t *)(b + (flipped ? o_kb : o_ka)), (uint32_t *)(b + o_flags), n,
+                                       part, &ctr->n_cells, (uint32_t *)(b + o_cstart), (uint64_t *)(b + o_ckey), s,
+                                       &launches);
         hv.perm = flipped ? ib : ia;
     }
     mark(4);
@@ -538,7 +540,7 @@ int run_hd(const RunArgs &a) {
     allow_smem(k_labels_hd<T, DP>, smem);
     if constexpr (std::is_same<T, float>::value) {
         if (use_tc && st.n_all <= tc::kMaxRng) {
-            run_tc_phases<DP>(hv, s, b, n, sms * tc_occ, tc_smem, gpts, gcell, smem, part_of(b, o_part),
+            run_tc_phases<DP>(hv, s, b, n, sms * tc_occ, tc_smem, gpts, gcell, hd_block, smem, part_of(b, o_part),
                               TcOffsets{o_tnch, o_tnch2, o_tch0, o_tch1, o_tch2, o_tflags, o_cx, o_clist, o_nclist,
                                         o_clab},
                               batched ? nsets : 0, ctr,
@@ -552,22 +554,22 @@ int run_hd(const RunArgs &a) {
     if (!tc_phases) {
         // ---- Definition 2: exact counts over the neighbouring coarse cells ----
         cudaMemsetAsync(hv.cell_core, 0, (size_t)n, s);
-        k_count_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
+        k_count_hd<T, DP><<<gcell, hd_block, smem, s>>>(hv);
         ++launches;
         mark(6);
         // (no representative points in this path: every pair of core points is a candidate)
         mark(7);
         // ---- Definitions 3-5: first links, pointer jumping, then the remaining unions ----
         k_uf_init_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
-        k_hook_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
+        k_hook_hd<T, DP><<<gcell, hd_block, smem, s>>>(hv);
         for (int r = 0; r < 6; ++r) k_jump_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
-        k_merge_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
+        k_merge_hd<T, DP><<<gcell, hd_block, smem, s>>>(hv);
         k_compress_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
         launches += 10;
         mark(8);
         // ---- Algorithm 4: canonical ids, border and noise points ----
         k_comp_min_hd<T, DP><<<gpts, 256, 0, s>>>(hv);
-        k_labels_hd<T, DP><<<gcell, 32 * kHdWarps, smem, s>>>(hv);
+        k_labels_hd<T, DP><<<gcell, hd_block, smem, s>>>(hv);
         launches += 2;
         mark(9);
     }

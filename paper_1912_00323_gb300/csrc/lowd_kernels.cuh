@@ -16,6 +16,7 @@
 
 #include <float.h>
 
+#include "block_scan.cuh"
 #include "hca_internal.cuh"
 
 namespace hca {
@@ -552,39 +553,33 @@ __global__ void __launch_bounds__(256) k_bin(const T *__restrict__ in, GridParam
     }
 }
 
-// Gather the points into cell order and flag the first point of every cell.
+// Gather the points into cell order and flag the first point of every cell; one block per
+// tile of kScanTileElems points, whose flag count goes to tile_sums[block] for the run-length
+// cells that follow (cells_from_flags).
 template <typename T, int D, typename K>
 __global__ void __launch_bounds__(256) k_gather(const T *__restrict__ in, const K *__restrict__ keys,
                                                const uint32_t *__restrict__ idx, int64_t n,
-                                               Pt<T, D> *__restrict__ pts, uint32_t *__restrict__ flags) {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t o = idx[j];
-        Pt<T, D> p = zero_pt<T, D>();
+                                               Pt<T, D> *__restrict__ pts, uint32_t *__restrict__ flags,
+                                               uint32_t *__restrict__ tile_sums) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTileElems;
+    uint32_t cnt = 0;
 #pragma unroll
-        for (int i = 0; i < D; ++i) p.x[i] = in[(int64_t)o * D + i];
-        pts[j] = p;
-        flags[j] = (j == 0 || keys[j] != keys[j - 1]) ? 1u : 0u;
-    }
-}
-
-// Run-length cells: cell id of every point, first point and key of every cell.
-template <typename K>
-__global__ void __launch_bounds__(256) k_cells(const K *__restrict__ keys, uint32_t *flags_cell_of,
-                                              const uint32_t *__restrict__ excl, int64_t n,
-                                              uint32_t *__restrict__ cell_start,
-                                              uint64_t *__restrict__ cell_key) {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t f = flags_cell_of[j];
-        const uint32_t c = excl[j] + f - 1u;
-        flags_cell_of[j] = c;
-        if (f) {
-            cell_start[c] = (uint32_t)j;
-            cell_key[c] = (uint64_t)keys[j];
+    for (int k = 0; k < kScanTileElems / 256; ++k) {
+        const int64_t j = base + k * 256 + threadIdx.x;
+        if (j < n) {
+            const uint32_t o = idx[j];
+            Pt<T, D> p = zero_pt<T, D>();
+#pragma unroll
+            for (int i = 0; i < D; ++i) p.x[i] = in[(int64_t)o * D + i];
+            pts[j] = p;
+            const uint32_t f = (j == 0 || keys[j] != keys[j - 1]) ? 1u : 0u;
+            flags[j] = f;
+            cnt += f;
         }
-        if (j == n - 1) cell_start[c + 1] = (uint32_t)n;
     }
+    uint32_t total;
+    block_exclusive_scan<256>(cnt, &total);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
 }
 
 // First cell of every pencil (cells sharing all coordinates but the last).

@@ -489,6 +489,7 @@ int run_lowd(const RunArgs &a) {
         uint32_t *ia = (uint32_t *)(b + o_ia), *ib = (uint32_t *)(b + o_ib);
         uint32_t *hist = (uint32_t *)(b + o_hist), *part = (uint32_t *)(b + o_part);
         const bool use32 = sort_bits <= 32;
+        const int gtile = (int)((n + kScanTileElems - 1) / kScanTileElems);  // gather: one block per scan tile
         if (use32) {
             uint32_t *ka = (uint32_t *)(b + o_ka), *kb = (uint32_t *)(b + o_kb);
             if (batched)
@@ -500,9 +501,9 @@ int run_lowd(const RunArgs &a) {
             mark(2);
             flipped = radix_sort_pairs<uint32_t>(ka, ia, kb, ib, n, 0, sort_bits, hist, part, s, &launches, &ctr->status, ctr->digit_counts);
             mark(3);
-            k_gather<T, D, uint32_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, flipped ? kb : ka,
-                                                          flipped ? ib : ia, n, (Pt<T, D> *)(b + o_pts),
-                                                          (uint32_t *)(b + o_flags));
+            k_gather<T, D, uint32_t><<<gtile, 256, 0, s>>>((const T *)a.d_points, flipped ? kb : ka,
+                                                           flipped ? ib : ia, n, (Pt<T, D> *)(b + o_pts),
+                                                           (uint32_t *)(b + o_flags), part);
         } else {
             uint64_t *ka = (uint64_t *)(b + o_ka), *kb = (uint64_t *)(b + o_kb);
             if (batched)
@@ -514,23 +515,20 @@ int run_lowd(const RunArgs &a) {
             mark(2);
             flipped = radix_sort_pairs<uint64_t>(ka, ia, kb, ib, n, 0, sort_bits, hist, part, s, &launches, &ctr->status, ctr->digit_counts);
             mark(3);
-            k_gather<T, D, uint64_t><<<gpts, 256, 0, s>>>((const T *)a.d_points, flipped ? kb : ka,
-                                                          flipped ? ib : ia, n, (Pt<T, D> *)(b + o_pts),
-                                                          (uint32_t *)(b + o_flags));
+            k_gather<T, D, uint64_t><<<gtile, 256, 0, s>>>((const T *)a.d_points, flipped ? kb : ka,
+                                                           flipped ? ib : ia, n, (Pt<T, D> *)(b + o_pts),
+                                                           (uint32_t *)(b + o_flags), part);
         }
         ++launches;
-        exclusive_scan_u32((uint32_t *)(b + o_flags), (uint32_t *)(b + o_excl), n, nullptr,
-                           &ctr->n_cells, part, s, &launches);
-        if (use32) {
-            k_cells<uint32_t><<<gpts, 256, 0, s>>>((const uint32_t *)(b + (flipped ? o_kb : o_ka)),
-                                                   (uint32_t *)(b + o_flags), (const uint32_t *)(b + o_excl),
-                                                   n, (uint32_t *)(b + o_cstart), (uint64_t *)(b + o_ckey));
-        } else {
-            k_cells<uint64_t><<<gpts, 256, 0, s>>>((const uint64_t *)(b + (flipped ? o_kb : o_ka)),
-                                                   (uint32_t *)(b + o_flags), (const uint32_t *)(b + o_excl),
-                                                   n, (uint32_t *)(b + o_cstart), (uint64_t *)(b + o_ckey));
-        }
-        ++launches;
+        // run-length cells: scan of the gather's tile counts, cell ids / starts / keys
+        if (use32)
+            cells_from_flags<uint32_t>((const uint32_t *)(b + (flipped ? o_kb : o_ka)), (uint32_t *)(b + o_flags), n,
+                                       part, &ctr->n_cells, (uint32_t *)(b + o_cstart), (uint64_t *)(b + o_ckey), s,
+                                       &launches);
+        else
+            cells_from_flags<uint64_t>((const uint64_t *)(b + (flipped ? o_kb : o_ka)), (uint32_t *)(b + o_flags), n,
+                                       part, &ctr->n_cells, (uint32_t *)(b + o_cstart), (uint64_t *)(b + o_ckey), s,
+                                       &launches);
         v.perm = flipped ? ib : ia;
     }
     mark(4);

@@ -1,6 +1,6 @@
-// Device-wide exclusive prefix sum of uint32 (reduce, scan of tile sums, scan-and-apply).
-// Used for the run-length encoding of sorted cell keys and pencils, and for the radix
-// sort's digit offsets.
+// Device-wide exclusive prefix sum of uint32 (reduce, scan of tile sums, scan-and-apply), and
+// the run-length cells of sorted cell keys from first-of-cell flags whose tile sums the gather
+// kernels produce (scan of tile sums, scan-and-apply with the cell tables written in place).
 #include "block_scan.cuh"
 #include "hca_internal.cuh"
 
@@ -11,6 +11,7 @@ namespace {
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
+static_assert(kScanTile == kScanTileElems, "tile size shared with the gather kernels");
 
 __device__ __forceinline__ int64_t scan_len(int64_t m_max, const uint32_t *m_dev) {
     if (!m_dev) return m_max;
@@ -88,7 +89,70 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t *in,
     }
 }
 
+// Per tile: exclusive prefix of the flags (tile offset from the scanned tile sums) -> cell id
+// of every point, first point and key of every cell, the end of the last cell.
+template <typename K>
+__global__ void __launch_bounds__(kScanThreads) k_cells_apply(const K *__restrict__ keys, uint32_t *flags_cell_of,
+                                                              int64_t n, const uint32_t *__restrict__ partials,
+                                                              uint32_t *__restrict__ cell_start,
+                                                              uint64_t *__restrict__ cell_key) {
+    __shared__ uint32_t tile[kScanTile];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    if (base >= n) return;
+    uint32_t f[kScanItems];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = base + k * kScanThreads + threadIdx.x;
+        f[k] = i < n ? flags_cell_of[i] : 0u;
+        tile[k * kScanThreads + threadIdx.x] = f[k];
+    }
+    __syncthreads();
+    uint32_t v[kScanItems];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = tile[threadIdx.x * kScanItems + k];
+        sum += v[k];
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_scan<kScanThreads>(sum, &total) + partials[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        tile[threadIdx.x * kScanItems + k] = run;
+        run += v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = base + k * kScanThreads + threadIdx.x;
+        if (i < n) {
+            const uint32_t c = tile[k * kScanThreads + threadIdx.x] + f[k] - 1u;
+            flags_cell_of[i] = c;
+            if (f[k]) {
+                cell_start[c] = (uint32_t)i;
+                cell_key[c] = (uint64_t)keys[i];
+            }
+            if (i == n - 1) cell_start[c + 1] = (uint32_t)n;
+        }
+    }
+}
+
 }  // namespace
+
+template <typename K>
+void cells_from_flags(const K *keys, uint32_t *flags_cell_of, int64_t n, uint32_t *partials, uint32_t *n_cells,
+                      uint32_t *cell_start, uint64_t *cell_key, cudaStream_t s, int *launches) {
+    int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb == 0) nb = 1;
+    k_scan_partials<<<1, 1024, 0, s>>>(partials, nb, n_cells);
+    k_cells_apply<K><<<(unsigned)nb, kScanThreads, 0, s>>>(keys, flags_cell_of, n, partials, cell_start, cell_key);
+    if (launches) *launches += 2;
+}
+
+template void cells_from_flags<uint32_t>(const uint32_t *, uint32_t *, int64_t, uint32_t *, uint32_t *, uint32_t *,
+                                         uint64_t *, cudaStream_t, int *);
+template void cells_from_flags<uint64_t>(const uint64_t *, uint32_t *, int64_t, uint32_t *, uint32_t *, uint32_t *,
+                                         uint64_t *, cudaStream_t, int *);
 
 size_t scan_partials_size(int64_t m_max) {
     return (size_t)((m_max + kScanTile - 1) / kScanTile) + 2;

@@ -51,6 +51,7 @@ bool valid_tuning(int d, const hca_tuning &t) {
     if (t.tc_min_count < 1 || t.tc_min_merge < 1 || t.tc_min_labels < 1) return false;
     if (t.tc_handoff < 0 || t.tc_handoff > 127) return false;
     if (t.first_links != 0 && t.first_links != 1) return false;
+    if (t.cta_warps != 2 && t.cta_warps != 4 && t.cta_warps != 8) return false;
     return true;
 }
 
@@ -83,7 +84,9 @@ std::vector<hca_tuning> candidates(int d, int32_t dtype) {
 }
 
 // Time `run` (one clustering on `s`) under every candidate: one untimed run, then `repeats`
-// timed runs, minimum kept.  Stores the fastest for d.
+// timed runs, minimum kept.  Then, on the coarse grid, the CTA size of the CUDA-core chunk
+// kernels (2 and 8 warps besides the default 4) with the rest of the fastest candidate.
+// Stores the fastest for d.
 template <typename Run>
 int tune_with(int d, int32_t dtype, cudaStream_t s, int repeats, Run run, hca_tuning *out, double *best_ms) {
     if (repeats < 1 || repeats > 16) return HCA_EINVAL;
@@ -96,9 +99,9 @@ int tune_with(int d, int32_t dtype, cudaStream_t s, int repeats, Run run, hca_tu
     int rc = HCA_OK;
     double best = DBL_MAX;
     hca_tuning pick = default_tuning(d);
-    for (const hca_tuning &t : candidates(d, dtype)) {
+    auto trial = [&](const hca_tuning &t) {
         rc = run(t);
-        if (rc) break;
+        if (rc) return;
         double tmin = DBL_MAX;
         for (int r = 0; r < repeats && rc == HCA_OK; ++r) {
             cudaEventRecord(e0, s);
@@ -110,10 +113,22 @@ int tune_with(int d, int32_t dtype, cudaStream_t s, int repeats, Run run, hca_tu
                 rc = HCA_ECUDA;
             if (rc == HCA_OK && ms < tmin) tmin = ms;
         }
-        if (rc) break;
-        if (tmin < best) {
+        if (rc == HCA_OK && tmin < best) {
             best = tmin;
             pick = t;
+        }
+    };
+    for (const hca_tuning &t : candidates(d, dtype)) {
+        trial(t);
+        if (rc) break;
+    }
+    if (rc == HCA_OK && pick.path == 2) {
+        const hca_tuning base = pick;
+        for (int w : {2, 8}) {
+            hca_tuning t = base;
+            t.cta_warps = w;
+            trial(t);
+            if (rc) break;
         }
     }
     cudaEventDestroy(e0);

@@ -72,7 +72,9 @@ def test_coarse_grid_mixed3d_reduced(env):
     {"tc_min_count": 1, "tc_min_merge": 1, "tc_min_labels": 1, "tc_handoff": 0, "first_links": 0},
     {"tc_min_count": 1, "tc_min_merge": 1, "tc_min_labels": 1, "tc_handoff": 127, "first_links": 1},
     {"tc_min_count": 1 << 30, "tc_min_merge": 1 << 30, "tc_min_labels": 1 << 30},
-    {"tc_min_count": 200, "tc_min_merge": 3, "tc_min_labels": 50, "tc_handoff": 30, "first_links": 0}])
+    {"tc_min_count": 200, "tc_min_merge": 3, "tc_min_labels": 50, "tc_handoff": 30, "first_links": 0},
+    {"cta_warps": 2, "first_links": 0},
+    {"cta_warps": 8, "tc_min_count": 1 << 30, "tc_min_merge": 1 << 30, "tc_min_labels": 1 << 30}])
 @pytest.mark.parametrize("d", [8, 16, 40])
 def test_extreme_splits(env, tune, d):
     _, pkg, oracle = env
@@ -82,6 +84,20 @@ def test_extreme_splits(env, tune, d):
     want = oracle.grid(X, eps, 5)
     pkg.hca_tuning_set(d, tune)
     check(run(env, X.astype(np.float32), eps, 5), want)
+
+
+@pytest.mark.parametrize("warps", [2, 8])
+@pytest.mark.parametrize("d", [6, 40])
+def test_cta_warps_double_input(env, warps, d):
+    """Double input keeps every phase on the CUDA-core chunk kernels: each CTA size gives the
+    oracle's labels (d = 40 pads rows to 64 doubles: 128 KiB of rows per 8-warp CTA)."""
+    _, pkg, oracle = env
+    X, eps, _ = workloads.lattice(2500, d, seed=900 + d, step=0.25,
+                                  eps_steps=int(round(math.sqrt(2 * d) * 1.8)), spread=2.0, box=2.0 * d,
+                                  n_blobs=3)
+    want = oracle.grid(X, eps, 5)
+    pkg.hca_tuning_set(d, {"cta_warps": warps})
+    check(run(env, X, eps, 5), want)
 
 
 def test_autotune_keeps_labels(env):

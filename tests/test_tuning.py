@@ -18,9 +18,9 @@ def pkg():
 
 
 LOW_D = {"path": 0, "tc_min_count": 16, "tc_min_merge": 16, "tc_min_labels": 4, "tc_handoff": 8,
-         "first_links": 1}
+         "first_links": 1, "cta_warps": 4}
 HIGH_D = {"path": 0, "tc_min_count": 8, "tc_min_merge": 4, "tc_min_labels": 1, "tc_handoff": 8,
-          "first_links": 1}
+          "first_links": 1, "cta_warps": 4}
 
 
 def default(d):
@@ -31,8 +31,8 @@ def test_defaults_and_roundtrip(pkg):
     for d in (1, 3, 5, 8, 9, 16, 64):
         assert pkg.hca_tuning_get(d) == default(d)
     DEFAULT = default(16)
-    pkg.hca_tuning_set(16, {"tc_min_count": 40, "tc_handoff": 0, "first_links": 0})
-    assert pkg.hca_tuning_get(16) == dict(DEFAULT, tc_min_count=40, tc_handoff=0, first_links=0)
+    pkg.hca_tuning_set(16, {"tc_min_count": 40, "tc_handoff": 0, "first_links": 0, "cta_warps": 8})
+    assert pkg.hca_tuning_get(16) == dict(DEFAULT, tc_min_count=40, tc_handoff=0, first_links=0, cta_warps=8)
     assert pkg.hca_tuning_get(15) == default(15)        # per dimension
     pkg.hca_tuning_set(16, None)
     assert pkg.hca_tuning_get(16) == DEFAULT
@@ -41,7 +41,8 @@ def test_defaults_and_roundtrip(pkg):
 @pytest.mark.parametrize("d,field,value", [
     (5, "path", 1), (2, "path", 2), (3, "path", 3), (3, "path", -1),
     (8, "tc_min_count", 0), (8, "tc_min_merge", 0), (8, "tc_min_labels", 0),
-    (8, "tc_handoff", -1), (8, "tc_handoff", 128), (8, "first_links", 2)])
+    (8, "tc_handoff", -1), (8, "tc_handoff", 128), (8, "first_links", 2),
+    (8, "cta_warps", 0), (8, "cta_warps", 3), (8, "cta_warps", 16)])
 def test_rejects_out_of_range(pkg, d, field, value):
     with pytest.raises(pkg.HcaError) as e:
         pkg.hca_tuning_set(d, {field: value})
