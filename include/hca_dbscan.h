@@ -322,7 +322,7 @@ HCA_API int hca_plan_destroy(hca_plan *plan);
  *                  links, unions, labels; one 32-point chunk per warp, its rows staged in the
  *                  CTA's shared memory): 2, 4 or 8.
  * Defaults: path 0, tc_handoff 8, first_links 1, cta_warps 4; thresholds 16 / 16 / 4 for
- * d <= 8 and 8 / 4 / 1 for d > 8.
+ * d <= 8 and 8 / 1 / 1 for d > 8.
  */
 typedef struct hca_tuning {
     int32_t path;

@@ -21,7 +21,9 @@ bool g_tune_init = false;
 // Defaults per d: the coarse-grid split measured fastest across the workloads, with first
 // links in every cell (leaving them out of tensor-core cells wins a few percent on many small
 // sets but loses up to 8x on a set of a million points) — d <= 8: thresholds 16 / 16 / 4;
-// d > 8 (the 16-D anisotropic clusters): 8 / 4 / 1.
+// d > 8 (the 16-D anisotropic clusters): 8 / 1 / 1 (the unions of every cell with a core
+// point on the tensor cores: a cell of one to three core points next to a cluster streams
+// the cluster's core points, 128 per tile there against 32 per warp step on the CUDA cores).
 hca_tuning default_tuning(int d) {
     hca_tuning t = kDefaultTuning;
     if (d <= 8) {
@@ -31,7 +33,7 @@ hca_tuning default_tuning(int d) {
         t.first_links = 1;
     } else {
         t.tc_min_count = 8;
-        t.tc_min_merge = 4;
+        t.tc_min_merge = 1;
         t.tc_min_labels = 1;
         t.first_links = 1;
     }
@@ -56,14 +58,14 @@ bool valid_tuning(int d, const hca_tuning &t) {
 }
 
 // Candidates for dimension d: the neighbour searches that exist for d, and for the coarse grid
-// with float input the first-link choice and four row-threshold sets (counts, unions, labels).
+// with float input the first-link choice and six row-threshold sets (counts, unions, labels).
 std::vector<hca_tuning> candidates(int d, int32_t dtype) {
     std::vector<hca_tuning> out;
     std::vector<int> paths;
     if (d <= 2) paths = {1};
     else if (d <= 4) paths = {1, 2};
     else paths = {2};
-    const int mins[4][3] = {{8, 8, 2}, {32, 8, 2}, {8, 4, 1}, {16, 16, 4}};
+    const int mins[6][3] = {{8, 8, 2}, {32, 8, 2}, {8, 4, 1}, {16, 16, 4}, {8, 1, 1}, {16, 1, 4}};
     for (int path : paths) {
         hca_tuning t = default_tuning(d);
         t.path = path;
