@@ -317,18 +317,31 @@ def single_config(pkg, torch, X, eps, min_pts, steps, warmup, flush, stream, pla
     pts = torch.from_numpy(X).to("cuda")
     labels = torch.empty(n, dtype=torch.int32, device="cuda")
 
-    def step():
-        return pkg.hca_dbscan_device(pts, eps, min_pts, labels=labels, stream=stream, stats=True, timing=True)[1]
+    def step(timing=False):
+        return pkg.hca_dbscan_device(pts, eps, min_pts, labels=labels, stream=stream, stats=True,
+                                     timing=timing)[1]
 
-    for _ in range(max(warmup, 1)):
+    for _ in range(max(warmup, 2)):
         step()
     torch.cuda.synchronize()
-    ms, stats = time_steps(torch, stream, flush, step, steps)
+    ms, _ = time_steps(torch, stream, flush, step, steps)
     med = statistics.median(ms)
+    # stage times from the library's events (those calls launch directly, without the graph)
+    _, stats = time_steps(torch, stream, flush, lambda: step(True), max(3, min(steps, 10)))
     stage = {k: statistics.median([s["stage_ms"][k] for s in stats]) for k in stats[0]["stage_ms"]}
     tc = {k: statistics.median([s["tc_ms"][k] for s in stats]) for k in stats[0]["tc_ms"]}
     out = {"ms_per_step": med, "value": n / (med / 1e3), "unit": "points/s", "steps": steps,
            "stage_ms": stage, "tc_ms": tc, "stats": stats[-1], "labels": labels}
+    direct_lab = torch.empty_like(labels)
+
+    def direct():
+        pkg.hca_dbscan_device(pts, eps, min_pts, labels=direct_lab, stream=stream, graph_cache=False)
+    direct()
+    dms, _ = time_steps(torch, stream, flush, direct, max(3, min(steps, 20)))
+    if not torch.equal(direct_lab, labels):
+        raise RuntimeError("direct launches and the repeated-call graph disagree")
+    out["direct_launches"] = {"ms_per_step": statistics.median(dms),
+                              "path": "HCA_FLAG_NO_GRAPH_CACHE: each kernel launched by the host in turn"}
 
     plain_lab = torch.empty_like(labels)
 
@@ -336,6 +349,8 @@ def single_config(pkg, torch, X, eps, min_pts, steps, warmup, flush, stream, pla
         pkg.hca_dbscan_device(pts, eps, min_pts, labels=plain_lab, stream=stream, fp64_only=True,
                               tensor_cores=False)
     plain()
+    if plain_steps > 1:
+        plain()  # the second identical call captures its graph: keep that out of the timing
     pms, _ = time_steps(torch, stream, flush, plain, plain_steps)
     if not torch.equal(plain_lab, labels):
         raise RuntimeError("plain FP64 path and tuned path disagree")
@@ -774,14 +789,10 @@ def run_ours(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            _, stats = step(True)
+            _, call_stats = step(False)
             e1.record(stream)
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
-            for k, v in stats["stage_ms"].items():
-                stage_ms.setdefault(k, []).append(v)
-            for k, v in stats["tc_ms"].items():
-                tc_ms.setdefault(k, []).append(v)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
     if dist:
@@ -789,6 +800,28 @@ def run_ours(args):
     torch.cuda.synchronize()
     ms = max_over_ranks(sum(step_ms) / len(step_ms), dist, dev)
     value = replica_value(n, ws, ms)
+
+    # stage times: the same call with the library's stage events (HCA_FLAG_TIMING runs the
+    # launches directly, not the graph of repeated calls)
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.zero_()
+        _, stats = step(True)
+        for k, v in stats["stage_ms"].items():
+            stage_ms.setdefault(k, []).append(v)
+        for k, v in stats["tc_ms"].items():
+            tc_ms.setdefault(k, []).append(v)
+    torch.cuda.synchronize()
+
+    # the call without the graph of repeated calls: every kernel launched by the host in turn
+    direct_lab = torch.empty_like(labels)
+
+    def direct_step():
+        pkg.hca_dbscan_device(pts, eps, min_pts, labels=direct_lab, stream=stream, graph_cache=False)
+    direct_step()
+    direct_ms, _ = time_steps(torch, stream, flush, direct_step, max(3, min(args.steps, 20)))
+    if not torch.equal(direct_lab, labels):
+        raise RuntimeError("direct launches and the repeated-call graph disagree")
+    direct = max_over_ranks(statistics.median(direct_ms), dist, dev)
 
     # end to end through the host entry point: pinned host points in, host labels out
     host_pts = torch.from_numpy(X).pin_memory()
@@ -813,6 +846,7 @@ def run_ours(args):
         pkg.hca_dbscan_device(pts, eps, min_pts, labels=plain_lab, stream=stream, fp64_only=True,
                               tensor_cores=False)
     plain_step()
+    plain_step()  # the second identical call captures its graph: keep that out of the timing
     plain_ms, _ = time_steps(torch, stream, flush, plain_step, max(3, min(args.steps, 20)))
     if not torch.equal(plain_lab, labels):
         raise RuntimeError("plain FP64 path and tuned path disagree")
@@ -827,6 +861,7 @@ def run_ours(args):
 
     def auto_step():
         pkg.hca_dbscan_device(pts, eps, min_pts, labels=auto_lab, stream=stream)
+    auto_step()
     auto_step()
     auto_ms, _ = time_steps(torch, stream, flush, auto_step, max(3, min(args.steps, 20)))
     pkg.hca_tuning_set(d, None)
@@ -893,7 +928,13 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "e2e": {"value": replica_value(n, ws, 1e3 * e2e_s), "unit": "points/s", "h2d_bytes_per_step": int(X.nbytes),
                 "d2h_bytes_per_step": 4 * n},
-        "gpu_launches": int(stats["kernel_launches"]) * args.steps,
+        "gpu_launches": int(call_stats["kernel_launches"]) * args.steps,
+        "path": ("hca_dbscan_device, the default call: the extents measured on the device and read "
+                 "back, then the repeated call's CUDA graph replayed (captured by the library on the "
+                 "second identical call; every kernel runs every step)"),
+        "direct_launches": {"ms_per_step": direct, "value": n * ws / (direct / 1e3),
+                            "path": "the same call with HCA_FLAG_NO_GRAPH_CACHE: each kernel launched "
+                                    "by the host in turn", "labels": "identical"},
         "roofline": roofline,
         "stage_ms": med, "dominant_stage": dominant,
         "stage_gbs": {k: round(v["gbs"], 1) for k, v in roof_rows.items()},

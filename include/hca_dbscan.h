@@ -23,7 +23,8 @@
  *     (HCA_F32) or double (HCA_F64), every coordinate finite;
  *   - labels are int32 in input order; the caller owns every buffer it passes;
  *   - the library owns only its workspace, taken from a library-private stream-ordered
- *     pool of device memory and returned to that pool before each call returns;
+ *     pool of device memory and returned to that pool before each call returns (except the
+ *     graph a thread keeps for repeated calls, see hca_dbscan_device);
  *   - "device" entry points take device pointers and a CUDA stream passed as void*
  *     (a cudaStream_t; NULL = legacy default stream); they return once the result is
  *     complete on that stream;
@@ -77,6 +78,8 @@ extern "C" {
 #define HCA_FLAG_FP64_ONLY 2  /* decide every distance in FP64 (no FP32 filter); same result */
 #define HCA_FLAG_NO_TENSOR_CORES 4  /* d >= 5, float input: compare pairs on the CUDA cores
                                        instead of the tensor-core distance tiles; same result */
+#define HCA_FLAG_NO_GRAPH_CACHE 8   /* run the call's launches directly, without the graph
+                                       kept for repeated calls (hca_dbscan_device) */
 
 /* stages timed with HCA_FLAG_TIMING (index into hca_stats.stage_ms) */
 #define HCA_STAGE_MINMAX 0    /* origin shift: per-dimension min / max (Sec. 2) */
@@ -148,6 +151,20 @@ HCA_API int hca_dbscan(const void *points, int32_t dtype, int64_t n, int32_t d, 
  *   d_labels  device, n int32; written on success.
  *   stream    cudaStream_t as void*; all work is ordered on it.
  * Same result as hca_dbscan.  Returns after the labels are complete on `stream`.
+ *
+ * Repeated calls.  A call measures the points' extents first and builds its grid from them on
+ * the host, so it waits for the GPU once before its main launch sequence, which it then
+ * enqueues kernel by kernel.  When a host thread makes the same call twice in a row (same
+ * device and CUDA context, same buffers, n, d, dtype, eps, min_pts, flags and tuning), the
+ * second call also captures that sequence into a CUDA graph, with its measured extents as
+ * declared extents (as hca_plan_create does), and later identical calls replay the graph:
+ * one graph launch and one synchronisation per call.  The graph recomputes everything from
+ * the points in the buffers at each launch, extents check included; points outside the
+ * captured extents make that call run again without the graph (and the next repeat captures
+ * anew).  The labels are the same either way: the grid origin does not change a label.  The
+ * graph and its workspace stay with the thread until it makes a call with other arguments or
+ * calls hca_graph_cache_release.  Calls with HCA_FLAG_TIMING or HCA_FLAG_NO_GRAPH_CACHE, and
+ * the batched, plan, server and autotuner entry points, never use it.
  */
 HCA_API int hca_dbscan_device(const void *d_points, int32_t dtype, int64_t n, int32_t d, double eps,
                       int32_t min_pts, int32_t *d_labels, void *stream);
@@ -155,7 +172,8 @@ HCA_API int hca_dbscan_device(const void *d_points, int32_t dtype, int64_t n, in
 /*
  * hca_dbscan_device_ex -- hca_dbscan_device with optional extra outputs.
  *   d_core  device, n uint8 (nullable): 1 for core points, 0 otherwise, input order.
- *   stats   host (nullable): counts of the run; stage times when flags has HCA_FLAG_TIMING.
+ *   stats   host (nullable): counts of the run; stage times when flags has HCA_FLAG_TIMING
+ *           (a call replayed from the graph of repeated calls reports the counts, not times).
  *   flags   bitwise OR of HCA_FLAG_*.
  */
 HCA_API int hca_dbscan_device_ex(const void *d_points, int32_t dtype, int64_t n, int32_t d, double eps,
@@ -288,7 +306,7 @@ HCA_API int hca_radix_sort_pairs_noalloc(void *d_keys, uint32_t *d_vals, int64_t
  * the graph; no kernel runs).  hca_plan_launch enqueues one clustering on `stream` and returns.
  * hca_plan_wait synchronises `stream` and returns the launch's code: HCA_OK, HCA_ERANGE (a
  * point outside its box), HCA_EINVAL (a NaN coordinate) or HCA_EDEVICE; `stats` (nullable)
- * receives its counts (n_cells, n_pencils, n_dense_cells, n_core_points, n_clusters, n_noise).
+ * receives its counts (every field but the stage and tensor-core times).
  * Launches of one plan share its workspace: order them (one stream, or wait in between).
  */
 typedef struct hca_plan hca_plan;
@@ -302,6 +320,10 @@ HCA_API int hca_plan_create_batched(hca_plan **out, const void *d_points, int32_
 HCA_API int hca_plan_launch(hca_plan *plan, void *stream);
 HCA_API int hca_plan_wait(hca_plan *plan, void *stream, hca_stats *stats);
 HCA_API int hca_plan_destroy(hca_plan *plan);
+
+/* Free the calling thread's graph of repeated calls and its workspace (hca_dbscan_device), if
+ * it holds one; the thread's next calls start over.  HCA_OK.  The paper has no counterpart. */
+HCA_API int hca_graph_cache_release(void);
 
 /*
  * Tuning of the neighbour search and of the tensor-core tiles, per dimension d (process-wide,

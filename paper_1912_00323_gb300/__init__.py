@@ -25,13 +25,14 @@ LIB_PATH = os.path.join(_HERE, "libhca_dbscan.so")
 HCA_F32, HCA_F64 = 0, 1
 HCA_OK, HCA_EINVAL, HCA_ENOMEM, HCA_ECUDA, HCA_ERANGE, HCA_ENOTIMPL, HCA_EDEVICE = 0, -1, -2, -3, -4, -5, -6
 HCA_ETOOLARGE, HCA_ETIMEDOUT, HCA_ECANCELED, HCA_EBUSY = -7, -8, -9, -10
-HCA_FLAG_TIMING, HCA_FLAG_FP64_ONLY, HCA_FLAG_NO_TENSOR_CORES = 1, 2, 4
+HCA_FLAG_TIMING, HCA_FLAG_FP64_ONLY, HCA_FLAG_NO_TENSOR_CORES, HCA_FLAG_NO_GRAPH_CACHE = 1, 2, 4, 8
 STAGES = ("minmax", "bin", "sort", "cells", "hash", "core", "reps", "merge", "labels")
 
 ABI_FUNCTIONS = ("hca_dbscan", "hca_dbscan_device", "hca_dbscan_device_ex", "hca_dbscan_batched",
                  "hca_radix_sort_pairs", "hca_tuning_get", "hca_tuning_set", "hca_autotune",
                  "hca_autotune_batched", "hca_plan_create", "hca_plan_create_batched", "hca_plan_launch",
-                 "hca_plan_wait", "hca_plan_destroy", "hca_workspace_bytes", "hca_strerror", "hca_version")
+                 "hca_plan_wait", "hca_plan_destroy", "hca_workspace_bytes", "hca_graph_cache_release",
+                 "hca_strerror", "hca_version")
 
 
 class HcaStats(ctypes.Structure):
@@ -124,6 +125,8 @@ def load():
     for f in ("hca_plan_create", "hca_plan_create_batched", "hca_plan_launch", "hca_plan_wait", "hca_plan_destroy"):
         getattr(lib, f).restype = ctypes.c_int
     lib.hca_workspace_bytes.argtypes = [i64, i32, i32, i32, ctypes.POINTER(i64)]
+    lib.hca_graph_cache_release.argtypes = []
+    lib.hca_graph_cache_release.restype = ctypes.c_int
     lib.hca_workspace_bytes.restype = ctypes.c_int
     lib.hca_strerror.argtypes = [ctypes.c_int]
     lib.hca_strerror.restype = ctypes.c_char_p
@@ -189,11 +192,13 @@ def _stream_ptr(stream):
 
 def hca_dbscan_device(points, eps: float, min_pts: int, labels=None, core=None, stream=None,
                       stats: bool = False, timing: bool = False, fp64_only: bool = False,
-                      tensor_cores: bool = True):
+                      tensor_cores: bool = True, graph_cache: bool = True):
     """Cluster a CUDA tensor of shape (n, d).  Returns the int32 label tensor, or
     (labels, stats_dict) when stats or timing is requested.  `core`, if given, is a uint8
     CUDA tensor of length n that receives the core flags.  tensor_cores=False keeps the d >= 5
-    float path on the CUDA cores (same labels)."""
+    float path on the CUDA cores (same labels).  graph_cache=False runs the call's launches
+    directly even when the same call repeats (the library otherwise replays a CUDA graph of
+    it; same labels)."""
     import torch
     lib = load()
     if not points.is_cuda:
@@ -205,7 +210,8 @@ def hca_dbscan_device(points, eps: float, min_pts: int, labels=None, core=None, 
     if labels is None:
         labels = torch.empty(n, dtype=torch.int32, device=pts.device)
     flags = ((HCA_FLAG_TIMING if timing else 0) | (HCA_FLAG_FP64_ONLY if fp64_only else 0)
-             | (0 if tensor_cores else HCA_FLAG_NO_TENSOR_CORES))
+             | (0 if tensor_cores else HCA_FLAG_NO_TENSOR_CORES)
+             | (0 if graph_cache else HCA_FLAG_NO_GRAPH_CACHE))
     st = HcaStats()
     rc = lib.hca_dbscan_device_ex(pts.data_ptr(), code, n, d, float(eps), int(min_pts),
                                   labels.data_ptr(), core.data_ptr() if core is not None else None,
@@ -283,6 +289,13 @@ def hca_dbscan_batched(points, offsets, eps, min_pts, dims=None, labels=None, co
     if stats or timing:
         return labels, st.as_dict()
     return labels
+
+
+def hca_graph_cache_release():
+    """Free the calling thread's graph of repeated hca_dbscan_device calls and its workspace."""
+    rc = load().hca_graph_cache_release()
+    if rc != HCA_OK:
+        raise HcaError(rc, "hca_graph_cache_release")
 
 
 def hca_workspace_bytes(n: int, d: int, dtype="float32", fp64_only: bool = False, tensor_cores: bool = True) -> int:

@@ -1,7 +1,10 @@
 // C ABI entry points (include/hca_dbscan.h): argument checks, the library's device memory
 // pool, and dispatch to the per-(type, dimension) pipelines.
 #include <math.h>
+#include <string.h>
+
 #include <mutex>
+#include <vector>
 
 #include "hca_internal.cuh"
 
@@ -102,7 +105,7 @@ int dispatch(const RunArgs &a, int32_t dtype) {
 
 int device_ex_tuned(const void *d_points, int32_t dtype, int64_t n, int32_t d, double eps, int32_t min_pts,
                     int32_t *d_labels, uint8_t *d_core, void *stream, hca_stats *stats, int32_t flags,
-                    const hca_tuning &tune) {
+                    const hca_tuning &tune, double *ext_out) {
     int rc = check_common(d_points, dtype, n, d, eps, min_pts, d_labels);
     if (rc) return rc;
     if (stats) {
@@ -124,6 +127,7 @@ int device_ex_tuned(const void *d_points, int32_t dtype, int64_t n, int32_t d, d
     a.stats = stats;
     a.flags = flags;
     a.tune = tune;
+    a.ext_out = ext_out;
     return dispatch(a, dtype);
 }
 
@@ -165,6 +169,41 @@ int batched_tuned(const void *d_points, int32_t dtype, int32_t n_sets, const int
     return dispatch(a, dtype);
 }
 
+namespace {
+
+// The graph a host thread keeps for repeated identical calls of hca_dbscan_device_ex: the key
+// of its last call and, once that call repeated, a plan captured with the extents it measured.
+struct CallKey {
+    int dev = -1;
+    unsigned long long ctx = 0;
+    const void *pts = nullptr;
+    int32_t *lab = nullptr;
+    uint8_t *core = nullptr;
+    int64_t n = 0;
+    int32_t d = 0, dtype = 0, min_pts = 0, flags = 0;
+    double eps = 0.0;
+    hca_tuning tune = kDefaultTuning;
+    bool operator==(const CallKey &o) const {
+        return dev == o.dev && ctx == o.ctx && pts == o.pts && lab == o.lab && core == o.core && n == o.n &&
+               d == o.d && dtype == o.dtype && min_pts == o.min_pts && flags == o.flags && eps == o.eps &&
+               memcmp(&tune, &o.tune, sizeof(tune)) == 0;
+    }
+};
+
+struct RepeatCache {
+    bool have = false;  // key holds the thread's last call
+    CallKey key;
+    hca_plan *plan = nullptr;
+    void drop() {
+        if (plan) hca_plan_destroy(plan);
+        plan = nullptr;
+    }
+};
+
+thread_local RepeatCache t_repeat;
+
+}  // namespace
+
 }  // namespace hca
 
 using namespace hca;
@@ -172,8 +211,55 @@ using namespace hca;
 extern "C" int hca_dbscan_device_ex(const void *d_points, int32_t dtype, int64_t n, int32_t d,
                                     double eps, int32_t min_pts, int32_t *d_labels, uint8_t *d_core,
                                     void *stream, hca_stats *stats, int32_t flags) {
-    return device_ex_tuned(d_points, dtype, n, d, eps, min_pts, d_labels, d_core, stream, stats, flags,
-                           tuning_for(d));
+    const hca_tuning tune = tuning_for(d);
+    if ((flags & (HCA_FLAG_TIMING | HCA_FLAG_NO_GRAPH_CACHE)) || n <= 0 ||
+        check_common(d_points, dtype, n, d, eps, min_pts, d_labels) != HCA_OK)
+        return device_ex_tuned(d_points, dtype, n, d, eps, min_pts, d_labels, d_core, stream, stats, flags, tune);
+    CallKey k;
+    if (cudaGetDevice(&k.dev) != cudaSuccess) return HCA_ECUDA;
+    k.ctx = current_context_id();
+    k.pts = d_points;
+    k.lab = d_labels;
+    k.core = d_core;
+    k.n = n;
+    k.d = d;
+    k.dtype = dtype;
+    k.min_pts = min_pts;
+    k.flags = flags;
+    k.eps = eps;
+    k.tune = tune;
+    RepeatCache &c = t_repeat;
+    const bool same = c.have && k.ctx != 0 && c.key == k;
+    if (same && c.plan) {
+        int rc = hca_plan_launch(c.plan, stream);
+        if (rc == HCA_OK) rc = hca_plan_wait(c.plan, stream, stats);
+        if (rc != HCA_ERANGE) return rc;
+        c.drop();  // points outside the captured extents: run the call afresh
+    }
+    std::vector<double> ext((size_t)2 * d, 0.0);
+    const int rc = device_ex_tuned(d_points, dtype, n, d, eps, min_pts, d_labels, d_core, stream, stats, flags,
+                                   tune, ext.data());
+    if (rc != HCA_OK) return rc;
+    if (same && !c.plan) {
+        // the call repeated: capture it with the extents it measured (a failure, e.g. no memory
+        // for a second workspace, only leaves the calls uncached)
+        hca_plan *p = nullptr;
+        if (plan_create_single(&p, d_points, dtype, n, d, eps, min_pts, ext.data(), ext.data() + d, d_labels,
+                               d_core, flags) == HCA_OK)
+            c.plan = p;
+        cudaGetLastError();
+    } else if (!same) {
+        c.drop();
+        c.key = k;
+        c.have = true;
+    }
+    return HCA_OK;
+}
+
+extern "C" int hca_graph_cache_release(void) {
+    t_repeat.drop();
+    t_repeat.have = false;
+    return HCA_OK;
 }
 
 extern "C" int hca_dbscan_batched(const void *d_points, int32_t dtype, int32_t n_sets, const int64_t *offsets,

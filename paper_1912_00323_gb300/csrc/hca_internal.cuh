@@ -190,10 +190,24 @@ struct RunArgs {
     DevCounters *h_ext = nullptr;        // pinned host copy of the counters (nullptr: the thread's)
     void *h_stage = nullptr;             // pinned staging of the batched tables (deferred calls)
     bool deferred = false;               // no host synchronisation: the caller checks the status
+    // optional outputs: the measured extents of a single-set call without declared extents
+    // (host, 2 d values: d minima then d maxima), and the launch count and key bits of the call
+    double *ext_out = nullptr;
+    int *launches_out = nullptr;
+    int *key_bits_out = nullptr;
 };
 
 // The tuning in effect for dimension d (tune.cu).
 hca_tuning tuning_for(int d);
+
+// The unique id of the calling thread's current CUDA context, 0 when there is none or the
+// driver cannot say (sort_static.cu).
+unsigned long long current_context_id();
+
+// A plan of one set with the given flags (plan.cu; hca_plan_create is this with flags 0).
+int plan_create_single(hca_plan **out, const void *d_points, int32_t dtype, int64_t n, int32_t d, double eps,
+                       int32_t min_pts, const double *box_min, const double *box_max, int32_t *d_labels,
+                       uint8_t *d_core, int32_t flags);
 
 // api.cu: argument checks, dispatch to the pipelines, and the clustering calls with an
 // explicit tuning.
@@ -202,7 +216,7 @@ int check_common(const void *pts, int32_t dtype, int64_t n, int32_t d, double ep
                  const void *labels);
 int device_ex_tuned(const void *d_points, int32_t dtype, int64_t n, int32_t d, double eps, int32_t min_pts,
                     int32_t *d_labels, uint8_t *d_core, void *stream, hca_stats *stats, int32_t flags,
-                    const hca_tuning &tune);
+                    const hca_tuning &tune, double *ext_out = nullptr);
 int batched_tuned(const void *d_points, int32_t dtype, int32_t n_sets, const int64_t *offsets, int32_t d,
                   const double *eps, const int32_t *min_pts, int32_t *d_labels, uint8_t *d_core, void *stream,
                   hca_stats *stats, int32_t flags, const hca_tuning &tune);

@@ -428,6 +428,11 @@ int run_hd(const RunArgs &a) {
         if (cudaMemcpyAsync(h, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) { rc = HCA_ECUDA; goto out; }
         if (h->nan_seen) { rc = HCA_EINVAL; goto out; }
+        if (a.ext_out && !batched)
+            for (int i = 0; i < d; ++i) {
+                a.ext_out[i] = dec_double(hmm[i]);
+                a.ext_out[d + i] = dec_double(hmm[64 + i]);
+            }
         if (batched)
             rc = build_grids([&](int set, int i) { return dec_double(smm[(size_t)set * 64 + i]); },
                              [&](int set, int i) { return dec_double(smm[((size_t)nsets + set) * 64 + i]); });
@@ -578,6 +583,8 @@ int run_hd(const RunArgs &a) {
         rc = HCA_ECUDA;
         goto out;
     }
+    if (a.launches_out) *a.launches_out = launches;
+    if (a.key_bits_out) *a.key_bits_out = sort_bits;
     if (a.deferred) goto out;  // the caller synchronises and reads the status from h
     if (cudaStreamSynchronize(s) != cudaSuccess) { rc = HCA_ECUDA; goto out; }
     if (boxed && h->nan_seen) { rc = HCA_EINVAL; goto out; }

@@ -467,6 +467,11 @@ int run_lowd(const RunArgs &a) {
         if (cudaMemcpyAsync(h, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) { rc = HCA_ECUDA; goto out; }
         if (h->nan_seen) { rc = HCA_EINVAL; goto out; }
+        if (a.ext_out && !batched)
+            for (int i = 0; i < D; ++i) {
+                a.ext_out[i] = dec_double(h->minmax_enc[i]);
+                a.ext_out[D + i] = dec_double(h->minmax_enc[kMaxD + i]);
+            }
         if (batched)
             rc = build_grids([&](int set, int i) { return dec_double(hmm[(size_t)set * kMaxD + i]); },
                              [&](int set, int i) { return dec_double(hmm[(size_t)kMaxD * nsets + (size_t)set * kMaxD + i]); });
@@ -605,6 +610,8 @@ int run_lowd(const RunArgs &a) {
         rc = HCA_ECUDA;
         goto out;
     }
+    if (a.launches_out) *a.launches_out = launches;
+    if (a.key_bits_out) *a.key_bits_out = sort_bits;
     if (a.deferred) goto out;  // the caller synchronises and reads the status from h
     if (cudaStreamSynchronize(s) != cudaSuccess) { rc = HCA_ECUDA; goto out; }
     if (boxed && h->nan_seen) { rc = HCA_EINVAL; goto out; }

@@ -26,6 +26,9 @@ struct PlanPart {
     hca::GroupBuffers gb = {};
     hca::DevCounters *h = nullptr;   // pinned: the counters of the last launch
     void *stage = nullptr;           // pinned: per-set tables the graph copies to the device
+    int32_t flags = 0;               // HCA_FLAG_* of the captured call (no timing)
+    int launches = 0;                // kernels the captured call launches
+    int key_bits = 0;                // bits of its cell keys
 };
 
 }  // namespace
@@ -60,7 +63,7 @@ void release(hca_plan *p) {
 
 hca::RunArgs part_args(const PlanPart &pt, const void *pts, int32_t *lab, uint8_t *core) {
     hca::RunArgs a;
-    a.flags = 0;  // plans run the default path (FP32 filter, tensor-core tiles where they apply)
+    a.flags = pt.flags;  // hca_plan_create: 0, the default path (FP32 filter, tensor-core tiles)
     a.d_points = pts;
     a.n = pt.g.n;
     a.d = pt.g.d;
@@ -97,7 +100,7 @@ void part_buffers(const PlanPart &pt, const void *d_points, int32_t dtype, int32
 }
 
 int create(hca_plan **out, const void *d_points, int32_t dtype, bool batched, std::vector<hca::SetGroup> &groups,
-           int32_t *d_labels, uint8_t *d_core) {
+           int32_t *d_labels, uint8_t *d_core, int32_t flags) {
     using namespace hca;
     hca_plan *p = new hca_plan();
     int rc = HCA_OK;
@@ -112,6 +115,7 @@ int create(hca_plan **out, const void *d_points, int32_t dtype, bool batched, st
         PlanPart &pt = p->parts.back();
         pt.g = g;
         pt.batched = batched;
+        pt.flags = flags & ~HCA_FLAG_TIMING;
     }
     if (p->parts.empty()) {
         release(p);
@@ -183,6 +187,8 @@ int create(hca_plan **out, const void *d_points, int32_t dtype, bool batched, st
         a.h_stage = pt.stage;
         a.deferred = true;
         a.stream = s;
+        a.launches_out = &pt.launches;
+        a.key_bits_out = &pt.key_bits;
         rc = dispatch(a, dtype);
         if (rc == HCA_OK && pt.g.gather) group_scatter(pt.g, pt.gb, d_labels, d_core, s);
         cudaGraph_t g = nullptr;
@@ -213,10 +219,11 @@ bool valid_box(const double *mn, const double *mx, size_t count) {
 
 }  // namespace
 
-extern "C" int hca_plan_create(hca_plan **out, const void *d_points, int32_t dtype, int64_t n, int32_t d,
-                               double eps, int32_t min_pts, const double *box_min, const double *box_max,
-                               int32_t *d_labels, uint8_t *d_core) {
-    using namespace hca;
+namespace hca {
+
+int plan_create_single(hca_plan **out, const void *d_points, int32_t dtype, int64_t n, int32_t d, double eps,
+                       int32_t min_pts, const double *box_min, const double *box_max, int32_t *d_labels,
+                       uint8_t *d_core, int32_t flags) {
     if (!out) return HCA_EINVAL;
     *out = nullptr;
     if (!box_min || !box_max) return HCA_EINVAL;
@@ -237,7 +244,15 @@ extern "C" int hca_plan_create(hca_plan **out, const void *d_points, int32_t dty
     g.far_pts = {0};
     g.far_lab = {0};
     g.n = n;
-    return create(out, d_points, dtype, false, groups, d_labels, d_core);
+    return create(out, d_points, dtype, false, groups, d_labels, d_core, flags);
+}
+
+}  // namespace hca
+
+extern "C" int hca_plan_create(hca_plan **out, const void *d_points, int32_t dtype, int64_t n, int32_t d,
+                               double eps, int32_t min_pts, const double *box_min, const double *box_max,
+                               int32_t *d_labels, uint8_t *d_core) {
+    return hca::plan_create_single(out, d_points, dtype, n, d, eps, min_pts, box_min, box_max, d_labels, d_core, 0);
 }
 
 extern "C" int hca_plan_create_batched(hca_plan **out, const void *d_points, int32_t dtype, int32_t n_sets,
@@ -259,7 +274,7 @@ extern "C" int hca_plan_create_batched(hca_plan **out, const void *d_points, int
     if (n == 0 || !d_points || !d_labels) return HCA_EINVAL;
     const size_t esz = dtype == HCA_F32 ? 4 : 8;
     if (((uintptr_t)d_points) % esz || ((uintptr_t)d_labels) % 4) return HCA_EINVAL;
-    return create(out, d_points, dtype, true, groups, d_labels, d_core);
+    return create(out, d_points, dtype, true, groups, d_labels, d_core, 0);
 }
 
 extern "C" int hca_plan_launch(hca_plan *plan, void *stream) {
@@ -278,6 +293,7 @@ extern "C" int hca_plan_wait(hca_plan *plan, void *stream, hca_stats *stats) {
     for (const PlanPart &pt : plan->parts) {
         const hca::DevCounters *h = pt.h;
         if (stats) {
+            stats->n_points += pt.g.n;
             stats->n_cells += h->n_cells;
             stats->n_pencils += h->n_pencils;
             stats->n_dense_cells += h->n_dense;
@@ -285,6 +301,21 @@ extern "C" int hca_plan_wait(hca_plan *plan, void *stream, hca_stats *stats) {
             stats->n_core_points += h->n_core;
             stats->n_clusters += h->n_clusters;
             stats->n_noise += h->n_noise;
+            if (pt.key_bits > stats->key_bits) {
+                stats->key_bits = pt.key_bits;
+                stats->sort_passes = (pt.key_bits + 7) / 8;
+            }
+            stats->kernel_launches += pt.launches;
+            stats->n_count_chunks += (int64_t)h->work[0];
+            stats->n_rep_tests += (int64_t)h->work[1];
+            stats->n_rep_hits += (int64_t)h->work[2];
+            stats->n_exhaustive_pairs += (int64_t)h->work[3];
+            stats->n_exhaustive_chunks += (int64_t)h->work[4];
+            stats->n_border_chunks += (int64_t)h->work[5];
+            stats->n_tc_tiles += (int64_t)h->work[6];
+            stats->n_tc_rechecks += (int64_t)h->work[7];
+            stats->n_tc_pairs += (int64_t)h->tc_pairs;
+            stats->workspace_bytes += (int64_t)pt.ws_bytes;
         }
         int r = HCA_OK;
         if (h->nan_seen) r = HCA_EINVAL;

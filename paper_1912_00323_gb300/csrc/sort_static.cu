@@ -19,16 +19,6 @@
 #include "hca_internal.cuh"
 
 namespace hca {
-namespace {
-
-constexpr int64_t kMaxPairs = HCA_SORT_NOALLOC_MAX_PAIRS;
-constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-constexpr size_t kHistElems = sort_hist_elems(kMaxPairs);
-constexpr size_t kOffVals = align256(sizeof(uint64_t) * kMaxPairs);
-constexpr size_t kOffHist = kOffVals + align256(sizeof(uint32_t) * kMaxPairs);
-constexpr size_t kScratchBytes = kOffHist + align256(sizeof(uint32_t) * kHistElems);
-
-__device__ __align__(256) unsigned char g_sort_scratch[kScratchBytes];
 
 // The unique id of the calling thread's current CUDA context (0 when none is current or the
 // driver does not provide the query).  Driver entry points are found through the runtime, so
@@ -57,6 +47,17 @@ unsigned long long current_context_id() {
     if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
     return id;
 }
+
+namespace {
+
+constexpr int64_t kMaxPairs = HCA_SORT_NOALLOC_MAX_PAIRS;
+constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t kHistElems = sort_hist_elems(kMaxPairs);
+constexpr size_t kOffVals = align256(sizeof(uint64_t) * kMaxPairs);
+constexpr size_t kOffHist = kOffVals + align256(sizeof(uint32_t) * kMaxPairs);
+constexpr size_t kScratchBytes = kOffHist + align256(sizeof(uint32_t) * kHistElems);
+
+__device__ __align__(256) unsigned char g_sort_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;

@@ -147,3 +147,9 @@ def test_workspace_bound_on_the_host(pkg):
     assert lib.hca_workspace_bytes(10, 3, 9, 0, ctypes.byref(out)) == pkg.HCA_EINVAL
     assert lib.hca_workspace_bytes(-1, 3, 0, 0, ctypes.byref(out)) == pkg.HCA_EINVAL
     assert lib.hca_workspace_bytes(10, 3, 0, 0, None) == pkg.HCA_EINVAL
+
+
+def test_graph_cache_release_without_a_graph(pkg):
+    """A thread that holds no graph of repeated calls releases nothing (no device needed)."""
+    assert pkg.load().hca_graph_cache_release() == pkg.HCA_OK
+    pkg.hca_graph_cache_release()
