@@ -463,6 +463,57 @@ def config_c3(pkg, torch, stream, flush, steps, warmup, bf16_burst, peak_kind):
     return r
 
 
+def literal_divergence(db, core, lit):
+    """Where the printed algorithm's labels (lit) depart from DBSCAN's (db, with core flags):
+    noise_clustered = DBSCAN noise points the printed algorithm puts in a cluster; split =
+    DBSCAN clusters whose core points fall into several printed clusters; merged = printed
+    clusters holding core points of several DBSCAN clusters; points_moved = clustered points
+    whose printed cluster is not the one holding most of their DBSCAN cluster's core points."""
+    core = core.astype(bool)
+    split, merged, majority = 0, 0, {}
+    for cid in np.unique(db[core]):
+        vals, cnt = np.unique(lit[core & (db == cid)], return_counts=True)
+        split += int(len(vals) > 1)
+        majority[int(cid)] = int(vals[np.argmax(cnt)])
+    for lid in np.unique(lit[core]):
+        merged += int(len(np.unique(db[core & (lit == lid)])) > 1)
+    clustered = db >= 0
+    maj = np.array([majority[int(c)] for c in db[clustered]], dtype=np.int64)
+    return {"n": int(len(db)), "dbscan_clusters": len(majority), "printed_clusters": int(len(np.unique(lit))),
+            "dbscan_noise": int((~clustered).sum()), "noise_clustered": int(((~clustered) & (lit >= 0)).sum()),
+            "split": split, "merged": merged, "points_moved": int((lit[clustered] != maj).sum())}
+
+
+def config_literal(pkg, torch, stream):
+    """The paper's Algorithms 2-4 as printed (hca_dbscan_literal_device: representatives only,
+    strict "<", no MINPTS) beside DBSCAN (hca_dbscan_device) on blobs2d, mixed3d and six small
+    batched sets: how far the printed algorithm departs, and its time on mixed3d."""
+    from paper_1912_00323_gb300 import workloads
+    out = {}
+    cases = [("blobs2d",) + workloads.blobs2d(), ("mixed3d",) + workloads.mixed3d()]
+    for k, (X, e, m) in enumerate(workloads.batched_sets(n_sets=6, n_min=1_000, n_max=20_000, dims=(2, 3))):
+        cases.append((f"batched set {k}", X, e, m))
+    for name, X, e, m in cases:
+        pts = torch.from_numpy(X).cuda()
+        core = torch.empty(len(X), dtype=torch.uint8, device="cuda")
+        db = pkg.hca_dbscan_device(pts, e, m, core=core, graph_cache=False).cpu().numpy()
+        lit = pkg.hca_dbscan_literal_device(pts, e).cpu().numpy()
+        row = literal_divergence(db, core.cpu().numpy(), lit)
+        if name == "mixed3d":
+            ms = []
+            for _ in range(5):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pkg.hca_dbscan_literal_device(pts, e, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            row["ms_per_call"] = statistics.median(ms)
+        out[name] = row
+    return out
+
+
 def config_batched(pkg, torch, stream, flush, steps, warmup, n_sets, plain_sample=16):
     """4096 sets (n log-uniform [1e3, 2e5], d in {2, 3, 8}, own eps and MINPTS) in their
     generated order: one hca_dbscan_batched call per step, each d autotuned first; the same
@@ -896,6 +947,7 @@ def run_ours(args):
             "batched": config_batched(pkg, torch, stream, flush, max(2, min(args.steps, 4)), 1, args.sets),
             "serving": config_serving(pkg, torch, 10.0, 2.0, args.rate, args.workers, 64, plain_jobs=150,
                                       plain_seconds=15.0, burst_jobs=64),
+            "literal_ablation": config_literal(pkg, torch, stream),
         }
 
     if rank != 0:

@@ -321,6 +321,24 @@ HCA_API int hca_plan_launch(hca_plan *plan, void *stream);
 HCA_API int hca_plan_wait(hca_plan *plan, void *stream, hca_stats *stats);
 HCA_API int hca_plan_destroy(hca_plan *plan);
 
+/*
+ * hca_dbscan_literal_device -- the paper's Algorithms 2-4 as printed (an ablation, not DBSCAN),
+ * for 1 <= d <= 4.  Hypercubes of side exactly eps / sqrt(d) from the per-dimension minimum
+ * (Algorithm 1); per cube and each of the 3^d - 1 directions the representative point closest
+ * to the cube's face, edge or corner in that direction, the smallest input index among equally
+ * close points (Algorithm 2); neighbouring cubes are the offsets in [-R, R]^d, R =
+ * ceil(sqrt(d)), without the cube itself and the corner cubes (Sec. 2, "Depth First Search");
+ * two neighbouring cubes join when their representatives of complementary directions are
+ * strictly closer than eps in double precision (Algorithm 3); every non-empty cube is in a
+ * cluster (no MINPTS, no noise; Algorithm 4).  Labels: the smallest input index of the cluster.
+ *   d_points, d_labels, stream  as hca_dbscan_device.
+ * HCA_EINVAL for d > 4 or a NaN; HCA_ERANGE when the band indices need more than 64 key bits.
+ * Synchronous.  Compare with hca_dbscan_device to see where the printed algorithm departs
+ * from DBSCAN.
+ */
+HCA_API int hca_dbscan_literal_device(const void *d_points, int32_t dtype, int64_t n, int32_t d, double eps,
+                                      int32_t *d_labels, void *stream);
+
 /* Free the calling thread's graph of repeated calls and its workspace (hca_dbscan_device), if
  * it holds one; the thread's next calls start over.  HCA_OK.  The paper has no counterpart. */
 HCA_API int hca_graph_cache_release(void);

@@ -32,6 +32,7 @@ ABI_FUNCTIONS = ("hca_dbscan", "hca_dbscan_device", "hca_dbscan_device_ex", "hca
                  "hca_radix_sort_pairs", "hca_tuning_get", "hca_tuning_set", "hca_autotune",
                  "hca_autotune_batched", "hca_plan_create", "hca_plan_create_batched", "hca_plan_launch",
                  "hca_plan_wait", "hca_plan_destroy", "hca_workspace_bytes", "hca_graph_cache_release",
+                 "hca_dbscan_literal_device",
                  "hca_strerror", "hca_version")
 
 
@@ -126,6 +127,8 @@ def load():
         getattr(lib, f).restype = ctypes.c_int
     lib.hca_workspace_bytes.argtypes = [i64, i32, i32, i32, ctypes.POINTER(i64)]
     lib.hca_graph_cache_release.argtypes = []
+    lib.hca_dbscan_literal_device.argtypes = [vp, i32, i64, i32, dbl, vp, vp]
+    lib.hca_dbscan_literal_device.restype = ctypes.c_int
     lib.hca_graph_cache_release.restype = ctypes.c_int
     lib.hca_workspace_bytes.restype = ctypes.c_int
     lib.hca_strerror.argtypes = [ctypes.c_int]
@@ -288,6 +291,26 @@ def hca_dbscan_batched(points, offsets, eps, min_pts, dims=None, labels=None, co
         raise HcaError(rc, "hca_dbscan_batched")
     if stats or timing:
         return labels, st.as_dict()
+    return labels
+
+
+def hca_dbscan_literal_device(points, eps: float, labels=None, stream=None):
+    """The paper's Algorithms 2-4 as printed (representative points only, strict "<", no
+    MINPTS; an ablation, not DBSCAN) on a CUDA tensor of shape (n, d), d <= 4.  Returns the
+    int32 labels (every point in a cluster)."""
+    import torch
+    lib = load()
+    if not points.is_cuda:
+        raise ValueError("hca_dbscan_literal_device takes a CUDA tensor")
+    pts = points.contiguous()
+    n = pts.shape[0]
+    d = pts.shape[1] if pts.dim() == 2 else 1
+    if labels is None:
+        labels = torch.empty(n, dtype=torch.int32, device=pts.device)
+    rc = lib.hca_dbscan_literal_device(pts.data_ptr(), _dtype_code(pts.dtype), n, d, float(eps),
+                                       labels.data_ptr(), _stream_ptr(stream))
+    if rc != HCA_OK:
+        raise HcaError(rc, "hca_dbscan_literal_device")
     return labels
 
 

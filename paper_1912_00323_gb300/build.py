@@ -18,7 +18,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhca_dbscan.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "scan.cu", "sort.cu", "sort_static.cu", "lowd_f32.cu", "lowd_f64.cu",
-           "hd_f32.cu", "hd_f64.cu", "server.cu", "tune.cu", "plan.cu", "multi.cu"]
+           "hd_f32.cu", "hd_f64.cu", "server.cu", "tune.cu", "plan.cu", "multi.cu",
+           "literal.cu"]
 
 
 def _nvcc():

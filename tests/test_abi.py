@@ -153,3 +153,10 @@ def test_graph_cache_release_without_a_graph(pkg):
     """A thread that holds no graph of repeated calls releases nothing (no device needed)."""
     assert pkg.load().hca_graph_cache_release() == pkg.HCA_OK
     pkg.hca_graph_cache_release()
+
+
+def test_literal_entry_point_rejects_high_d_on_the_host(pkg):
+    """The printed algorithm's neighbour block is enumerated for d <= 4 only."""
+    lib = pkg.load()
+    assert lib.hca_dbscan_literal_device(None, pkg.HCA_F32, 0, 5, 1.0, None, None) == pkg.HCA_EINVAL
+    assert lib.hca_dbscan_literal_device(None, pkg.HCA_F32, 0, 2, 1.0, None, None) == pkg.HCA_OK
