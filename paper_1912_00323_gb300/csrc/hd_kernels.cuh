@@ -172,23 +172,63 @@ static __global__ void __launch_bounds__(256) k_box_check_hd(const double *__res
 template <typename T>
 __global__ void __launch_bounds__(256) k_minmax_rt(const T *__restrict__ in, int64_t n, int d, DevCounters *ctr,
                                                   unsigned long long *mm /* [2 * 64] */) {
+    // each thread walks one dimension (a stride that is a multiple of d), four independent
+    // loads in flight; the block folds its threads per dimension in shared memory, then one
+    // global atomic per block and dimension
+    __shared__ unsigned long long smn[64], smx[64];
+    __shared__ int snan;
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+        smn[i] = ~0ull;
+        smx[i] = 0ull;
+    }
+    if (threadIdx.x == 0) snan = 0;
+    __syncthreads();
     const int64_t total = n * d;
     const int64_t threads = (int64_t)gridDim.x * blockDim.x;
     const int64_t stride = (threads / d) * d;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (tid >= stride) return;
-    T mn = sizeof(T) == 4 ? (T)FLT_MAX : (T)DBL_MAX, mx = -mn;
-    bool nan = false;
-    for (int64_t e = tid; e < total; e += stride) {
-        const T x = in[e];
-        nan |= (x != x);
-        mn = x < mn ? x : mn;
-        mx = x > mx ? x : mx;
+    if (tid < stride) {
+        T mn[4], mx[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            mn[u] = sizeof(T) == 4 ? (T)FLT_MAX : (T)DBL_MAX;
+            mx[u] = -mn[u];
+        }
+        bool nan = false;
+        int64_t e = tid;
+        for (; e + 3 * stride < total; e += 4 * stride) {
+            T x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = __ldg(in + e + u * stride);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                nan |= (x[u] != x[u]);
+                mn[u] = x[u] < mn[u] ? x[u] : mn[u];
+                mx[u] = x[u] > mx[u] ? x[u] : mx[u];
+            }
+        }
+        for (; e < total; e += stride) {
+            const T x = __ldg(in + e);
+            nan |= (x != x);
+            mn[0] = x < mn[0] ? x : mn[0];
+            mx[0] = x > mx[0] ? x : mx[0];
+        }
+#pragma unroll
+        for (int u = 1; u < 4; ++u) {
+            mn[0] = mn[u] < mn[0] ? mn[u] : mn[0];
+            mx[0] = mx[u] > mx[0] ? mx[u] : mx[0];
+        }
+        const int dim = (int)(tid % d);
+        atomicMin(&smn[dim], (unsigned long long)enc_double((double)mn[0]));
+        atomicMax(&smx[dim], (unsigned long long)enc_double((double)mx[0]));
+        if (nan) snan = 1;
     }
-    const int dim = (int)(tid % d);
-    atomicMin(&mm[dim], (unsigned long long)enc_double((double)mn));
-    atomicMax(&mm[64 + dim], (unsigned long long)enc_double((double)mx));
-    if (nan) atomicOr(&ctr->nan_seen, 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+        if (smn[i] != ~0ull) atomicMin(&mm[i], smn[i]);
+        if (smx[i] != 0ull) atomicMax(&mm[64 + i], smx[i]);
+    }
+    if (threadIdx.x == 0 && snan) atomicOr(&ctr->nan_seen, 1u);
 }
 
 // Coarse cell keys from the three projected dimensions (Algorithm 1 on a grid of side >= eps).

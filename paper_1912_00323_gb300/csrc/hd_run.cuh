@@ -177,14 +177,16 @@ void run_tc_phases(HdView<float, DP> &hv, cudaStream_t s, char *b, int64_t n, in
     k_uf_init_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
     k_hook_hd<float, DP><<<gcell, hd_block, smem, s>>>(hv);
     for (int r = 0; r < 6; ++r) k_jump_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
-    // (nch is free once the chunk tables are scanned)
-    tc::k_tc_cell_root<DP><<<gpts, 256, 0, s>>>(hv, nch);
+    // (nch and nch2 are free once the chunk tables are scanned)
+    tc::k_tc_cell_root_clear<<<gpts, 256, 0, s>>>(ctr, nch, nch2);
+    tc::k_tc_cell_root<DP><<<gpts, 256, 0, s>>>(hv, nch, nch2);
+    tc::k_tc_cell_root_final<<<gpts, 256, 0, s>>>(ctr, nch, nch2);
     tmark(2);
     tc::k_tc_hd<DP, tc::kMerge><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch1, cx, clist, nclist, clab, nch});
     tmark(3);
     k_merge_hd<float, DP><<<gcell, hd_block, smem, s>>>(hv);
     k_compress_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
-    launches += 12;
+    launches += 14;
     mark(8);
     // ---- Algorithm 4: canonical ids, core labels, border and noise points ----
     k_comp_min_hd<float, DP><<<gpts, 256, 0, s>>>(hv);

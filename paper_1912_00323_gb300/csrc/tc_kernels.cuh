@@ -670,25 +670,47 @@ __device__ __forceinline__ uint32_t tc_chunks(uint32_t rows, uint32_t min_rows) 
     return rows >= min_rows ? (rows + (uint32_t)kTile - 1u) / (uint32_t)kTile : 0u;
 }
 
-// The one root of every coarse cell's core points (~0 when they differ or there are none), one
-// warp per cell, with read-only finds (nothing hooks meanwhile).
+// The one root of every coarse cell's core points (~0 when they differ or there are none),
+// with read-only finds (nothing hooks meanwhile), in three launches so that a cell of
+// thousands of points is spread over many warps: clear, one warp per 32-point chunk folding
+// its core points' roots into the cell's smallest (lo) and largest (hi) root, then per cell
+// lo if lo == hi.
+static __global__ void __launch_bounds__(256) k_tc_cell_root_clear(const DevCounters *ctr, uint32_t *__restrict__ lo,
+                                                                  uint32_t *__restrict__ hi) {
+    const uint32_t C = ctr->n_cells;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+        lo[c] = 0xffffffffu;
+        hi[c] = 0u;
+    }
+}
+
 template <int DP>
-__global__ void __launch_bounds__(256) k_tc_cell_root(HdView<float, DP> v, uint32_t *__restrict__ cell_root) {
+__global__ void __launch_bounds__(256) k_tc_cell_root(HdView<float, DP> v, uint32_t *__restrict__ lo,
+                                                     uint32_t *__restrict__ hi) {
     const int lane = threadIdx.x & 31;
-    const uint32_t C = v.ctr->n_cells;
+    const uint32_t C = v.ctr->n_cells, NC = v.ctr->n_chunks;
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < C; c += warps) {
+    for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < NC; t += warps) {
+        const uint32_t A = chunk_cell(v.chunk_off, C, t);
+        const uint32_t e = v.cell_start[A + 1], p = v.cell_start[A] + 32u * (t - v.chunk_off[A]) + lane;
         uint32_t mn = 0xffffffffu, mx = 0u;
-        for (uint32_t j = v.cell_start[c] + lane; j < v.cell_start[c + 1]; j += 32) {
-            if (!v.core[j]) continue;
-            const uint32_t r = uf_root_readonly(v.parent, j, v.ctr);
-            mn = min(mn, r);
-            mx = max(mx, r);
+        if (p < e && v.core[p]) {
+            mn = mx = uf_root_readonly(v.parent, p, v.ctr);
         }
         mn = __reduce_min_sync(0xffffffffu, mn);
         mx = __reduce_max_sync(0xffffffffu, mx);
-        if (lane == 0) cell_root[c] = (mn != 0xffffffffu && mn == mx) ? mn : 0xffffffffu;
+        if (lane == 0 && mn != 0xffffffffu) {
+            atomicMin(lo + A, mn);
+            atomicMax(hi + A, mx);
+        }
     }
+}
+
+static __global__ void __launch_bounds__(256) k_tc_cell_root_final(const DevCounters *ctr, uint32_t *__restrict__ lo,
+                                                                  const uint32_t *__restrict__ hi) {
+    const uint32_t C = ctr->n_cells;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x)
+        if (lo[c] != hi[c]) lo[c] = 0xffffffffu;
 }
 
 // 128-row chunks of the counts for every coarse cell with at least min_rows points.
