@@ -3,8 +3,9 @@
 // A first kernel counts the digits of every pass over all keys (the counts do not depend on
 // the order, so one read of the keys serves all passes); a caller that produced the keys may
 // pass these counts in instead.  Each pass kernel then takes a tile of 13,312 keys (1024
-// threads x 13), ranks every key stably among the keys of its tile with the same digit (warp
-// match + per-warp digit counters + an exclusive scan across warps), publishes the tile's digit
+// threads x 13), ranks every key stably among the keys of its tile with the same digit (the
+// lanes of a warp with one digit found by a match instruction or by shared-memory OR masks,
+// per-warp digit counters, an exclusive scan across warps), publishes the tile's digit
 // counts, scatters the tile through shared memory in digit order, learns how many keys of each
 // digit the earlier tiles hold by decoupled look-back, and writes the digit runs out with
 // coalesced stores.
@@ -90,9 +91,13 @@ struct PassSmem {
     uint32_t lb_kind[kQuarters][kRadix];  // 0 window read through, 1 met a PREFIX, 2 met an unpublished word
     int32_t lb_next[kRadix];              // nearest predecessor not yet added, per digit (-1: done)
     uint32_t tile_id, pad[3];
-    K keys[kSortTile];
+    union {
+        uint32_t wmask[kSortWarps][kRadix];  // ranking: per-warp lane masks of each digit
+        K keys[kSortTile];                   // then: the tile in digit order
+    };
     uint32_t vals[kSortTile];
 };
+static_assert(sizeof(uint32_t) * kSortWarps * kRadix <= sizeof(uint32_t) * kSortTile, "masks fit the key array");
 
 // One pass: rank within the tile, publish the tile's digit counts, scatter the tile into
 // shared memory in digit order, look back for the counts of the earlier tiles, write out.
@@ -107,7 +112,10 @@ __global__ void __launch_bounds__(kSortThreads, 1) k_os_pass(
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int dg = threadIdx.x & (kRadix - 1), q = threadIdx.x / kRadix;
     const uint32_t mask = (1u << mask_bits) - 1u;
-    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&S.whist[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) {
+        (&S.whist[0][0])[i] = 0;
+        (&S.wmask[0][0])[i] = 0;
+    }
     if (threadIdx.x == 0) S.tile_id = atomicAdd(ticket, 1u);
     __syncthreads();
     const uint32_t tile = S.tile_id;
@@ -130,10 +138,25 @@ __global__ void __launch_bounds__(kSortThreads, 1) k_os_pass(
         const bool valid = i < n;
         v[r] = valid ? vals_in[i] : 0u;
         const uint32_t d = valid ? ((uint32_t)(k[r] >> shift) & mask) : (uint32_t)kRadix;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        // the lanes holding the same digit: a match instruction when lane 0's digit recurs
+        // often (few distinct digits), else one shared-memory OR per lane into the warp's
+        // digit masks (many distinct digits, where the match instruction is slow)
+        const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+        const bool use_match = __popc(__ballot_sync(0xffffffffu, d == d0)) >= 4;
+        unsigned peers = 0u;
+        if (use_match) {
+            peers = __match_any_sync(0xffffffffu, d);
+        } else {
+            if (valid) atomicOr(&S.wmask[warp][d], 1u << lane);
+            __syncwarp();
+            if (valid) peers = S.wmask[warp][d];
+        }
         const uint32_t before = valid ? S.whist[warp][d] : 0u;
         __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) S.whist[warp][d] = before + __popc(peers);
+        if (valid && lane == __ffs(peers) - 1) {
+            S.whist[warp][d] = before + __popc(peers);
+            if (!use_match) S.wmask[warp][d] = 0u;  // clean for the next key
+        }
         __syncwarp();
         const uint32_t rk = before + __popc(peers & ((1u << lane) - 1u));
         if (r & 1) rank2[r >> 1] |= rk << 16;
