@@ -17,6 +17,10 @@
 // two million keys needs three round trips instead of the dozens that a 4096-key tile with a
 // few words per trip needed.
 //
+// Up to kFullSumTiles tiles (about 3.4 million keys) a tile instead sums the published counts
+// of all earlier tiles (eight loads in flight per thread, no prefix published): with every
+// tile running at once no prefix would be there to shorten the look-back anyway.
+//
 // Look-back: a tile publishes, per digit, first its own count (state AGG) and then the count of
 // all tiles up to and including itself (state PREFIX).  A tile reads its predecessors'
 // words from the nearest one backwards, adding AGG values until it meets a PREFIX.  Tiles take
@@ -46,6 +50,10 @@ constexpr int kHistThreads = 256;
 static_assert(kSortTile == kSortTileKeys, "tile size shared with the scratch sizing");
 static_assert(kQuarters * kRadix == kSortThreads, "whole quarters of digits");
 constexpr uint32_t kSpinLimit = 1u << 24;
+// Up to this many tiles a tile sums the counts of all earlier tiles instead of the decoupled
+// look-back (at two million keys all ~150 tiles run at once, so the look-back finds no
+// published prefix and reads the same words over three round trips)
+constexpr int kFullSumTiles = 256;
 constexpr uint64_t kStateAgg = 1, kStatePrefix = 2;
 
 __device__ __forceinline__ uint64_t os_pack(uint32_t epoch, uint64_t state, uint32_t value) {
@@ -106,7 +114,7 @@ __global__ void __launch_bounds__(kSortThreads, 1) k_os_pass(
     const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, K *__restrict__ keys_out,
     uint32_t *__restrict__ vals_out, int64_t n, int shift, int mask_bits,
     const uint32_t *__restrict__ ghist_pass, unsigned long long *status, uint32_t *ticket, uint32_t epoch,
-    uint32_t *err) {
+    uint32_t *err, bool full_sum) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     PassSmem<K> &S = *reinterpret_cast<PassSmem<K> *>(sm_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -217,7 +225,39 @@ __global__ void __launch_bounds__(kSortThreads, 1) k_os_pass(
     // (excluded); the quarter-0 thread then joins the quarters in order.  Bounded wait.
     uint32_t excl = 0, spins = 0;
     int32_t next = (int32_t)tile - 1;  // quarter 0: nearest predecessor not yet added (-1: done)
-    for (;;) {
+    if (full_sum) {
+        // few tiles: sum every earlier tile's own count (quarter q takes the tiles q, q + 4, ...,
+        // eight loads in flight); no inclusive prefix is published or read.  Bounded waits.
+        uint32_t sum = 0;
+        for (int32_t i0 = q; i0 < (int32_t)tile; i0 += kQuarters * 8) {
+            unsigned long long w[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int32_t i = i0 + kQuarters * u;
+                w[u] = i < (int32_t)tile ? st[(uint64_t)i * kRadix + dg] : os_pack(epoch, kStateAgg, 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int32_t i = i0 + kQuarters * u;
+                uint32_t tries = 0;
+                while (((uint32_t)(w[u] >> 34)) != epoch || ((uint32_t)(w[u] >> 32) & 3u) == 0u) {
+                    if (++tries > kSpinLimit) {
+                        atomicOr(err, 2u);
+                        break;
+                    }
+                    w[u] = st[(uint64_t)i * kRadix + dg];
+                }
+                sum += (uint32_t)w[u];
+            }
+        }
+        S.lb_sum[q][dg] = sum;
+        __syncthreads();
+        if (q == 0)
+#pragma unroll
+            for (int qq = 0; qq < kQuarters; ++qq) excl += S.lb_sum[qq][dg];
+        next = -1;
+    }
+    while (!full_sum) {
         const int32_t j = S.lb_next[dg];
         if (j >= 0) {
             const int32_t hi = j - kLbWords * q;
@@ -266,7 +306,7 @@ __global__ void __launch_bounds__(kSortThreads, 1) k_os_pass(
         if (__syncthreads_and(q != 0 || next < 0)) break;
     }
     if (q == 0) {
-        if (tile > 0) st[(uint64_t)tile * kRadix + dg] = os_pack(epoch, kStatePrefix, excl + count);
+        if (tile > 0 && !full_sum) st[(uint64_t)tile * kRadix + dg] = os_pack(epoch, kStatePrefix, excl + count);
         S.goff[dg] = gdig + excl;
     }
     __syncthreads();
@@ -316,7 +356,8 @@ bool radix_sort_pairs(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt, 
         const int shift = begin_bit + 8 * p;
         const int bits = (end_bit - shift) < 8 ? (end_bit - shift) : 8;
         k_os_pass<K><<<nb, kSortThreads, smem, s>>>(kin, vin, kout, vout, n, shift, bits, ghist + p * kRadix,
-                                                    status, tickets + p, (uint32_t)(p + 1), err);
+                                                    status, tickets + p, (uint32_t)(p + 1), err,
+                                                    nb <= kFullSumTiles);
         K *tk = kin; kin = kout; kout = tk;
         uint32_t *tv = vin; vin = vout; vout = tv;
         flipped = !flipped;

@@ -219,7 +219,7 @@ def test_error_codes(env):
     assert e.value.code == pkg.HCA_ERANGE
 
 
-@pytest.mark.parametrize("n", [2, 100, 4096, 4097, 13312, 13313, 1_000_003, 4_000_037])
+@pytest.mark.parametrize("n", [2, 100, 4096, 4097, 13312, 13313, 1_000_003, 3_407_872, 3_407_873, 4_000_037])
 @pytest.mark.parametrize("kbytes,bits", [(4, (0, 32)), (4, (0, 13)), (8, (0, 64)), (8, (5, 41))])
 def test_radix_sort_matches_stable_argsort(env, n, kbytes, bits):
     torch, pkg, _ = env
