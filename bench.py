@@ -50,7 +50,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one radix sort pass
 # (k_os_pass) on the mixed3d workload at n = 2,000,000, from an ncu capture of that kernel;
 # None until a capture of the current kernel exists
-SORT_PASS_TRAFFIC_MIXED3D_2M = None
+SORT_PASS_TRAFFIC_MIXED3D_2M = 16_050_000  # dram read + write per k_os_pass launch (ncu, mean of 4)
 
 # Nominal dense tensor-core rates of a GB300 (TFLOP/s): the TF32 peak of the tile kernel is the
 # measured bf16 GEMM rate scaled by their ratio
