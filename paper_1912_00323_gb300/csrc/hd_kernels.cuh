@@ -799,40 +799,12 @@ __global__ void __launch_bounds__(32 * kHdMaxWarps) k_labels_hd(HdView<T, DP> v)
 
 
 // Batched calls: per-set min / max of every dimension (mm[set * 64 + i] min encodings,
-// mm[(nsets + set) * 64 + i] max encodings); a warp whose points share one set reduces first.
+// mm[(nsets + set) * 64 + i] max encodings), by seg_minmax.
 template <typename T>
 __global__ void __launch_bounds__(256) k_minmax_rt_seg(const T *__restrict__ in, int64_t n, int d,
                                                       const int64_t *set_off, int nsets,
                                                       unsigned long long *mm, DevCounters *ctr) {
-    const int lane = lane_id();
-    bool nan = false;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
-         base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = base + lane;
-        const bool valid = j < n;
-        const uint32_t set = valid ? set_of_point(set_off, nsets, j) : 0xffffffffu;
-        const uint32_t s0 = __shfl_sync(0xffffffffu, set, 0);
-        const bool uniform = __all_sync(0xffffffffu, !valid || set == s0);
-        for (int i = 0; i < d; ++i) {
-            const double x = valid ? (double)in[j * d + i] : 0.0;
-            nan |= valid && (x != x);
-            if (uniform) {
-                double a = valid ? x : DBL_MAX, b = valid ? x : -DBL_MAX;
-                for (int o = 16; o; o >>= 1) {
-                    a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
-                    b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
-                }
-                if (lane == 0) {
-                    atomicMin(&mm[(uint64_t)s0 * 64 + i], (unsigned long long)enc_double(a));
-                    atomicMax(&mm[((uint64_t)nsets + s0) * 64 + i], (unsigned long long)enc_double(b));
-                }
-            } else if (valid) {
-                atomicMin(&mm[(uint64_t)set * 64 + i], (unsigned long long)enc_double(x));
-                atomicMax(&mm[((uint64_t)nsets + set) * 64 + i], (unsigned long long)enc_double(x));
-            }
-        }
-    }
-    if (__any_sync(0xffffffffu, nan) && lane == 0) atomicOr(&ctr->nan_seen, 1u);
+    seg_minmax<T>(in, n, d, set_off, nsets, mm, 64, ctr);
 }
 
 // Batched calls: coarse cell keys with the set id above them; each set projects on its own

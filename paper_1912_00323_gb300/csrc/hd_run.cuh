@@ -407,7 +407,7 @@ int run_hd(const RunArgs &a) {
         cudaMemsetAsync(d_smm, 0xff, sizeof(unsigned long long) * 64 * nsets, s);
         cudaMemsetAsync(d_smm + (size_t)64 * nsets, 0, sizeof(unsigned long long) * 64 * nsets, s);
         upload(d_setoff, a.h_off, sizeof(int64_t) * (nsets + 1), stage_setoff);
-        k_minmax_rt_seg<T><<<grid_for(n, 256, sms, 4), 256, 0, s>>>((const T *)a.d_points, n, d, d_setoff, nsets,
+        k_minmax_rt_seg<T><<<grid_for(n, 256, sms, 8), 256, 0, s>>>((const T *)a.d_points, n, d, d_setoff, nsets,
                                                                    d_smm, ctr);
         if (!boxed) {
             smm.resize((size_t)2 * 64 * nsets);

@@ -91,8 +91,9 @@ __device__ __forceinline__ uint32_t next_chunk(uint32_t *counter) {
     return __shfl_sync(0xffffffffu, t, 0);
 }
 
-// Items [0, N) to warps in batches of kItemBatch taken from counter ctr->lowd_next[slot].
-constexpr uint32_t kItemBatch = 4;
+// Items [0, N) to warps in batches of kItemBatch taken from counter ctr->lowd_next[slot] (one
+// item at a time: the label list is short, so batches left most warps idle).
+constexpr uint32_t kItemBatch = 1;
 #define LOWD_FOR_EACH(v, X, N, slot)                                                                  \
     for (uint32_t b_ = next_chunk(&(v).ctr->lowd_next[slot]) * kItemBatch; b_ < (N);                \
          b_ = next_chunk(&(v).ctr->lowd_next[slot]) * kItemBatch)                                   \
@@ -1481,41 +1482,130 @@ __global__ void __launch_bounds__(256) k_box_check(BoxArgs single, const double 
     }
 }
 
-// Per-set min / max (origin shift, Sec. 2) and NaN check; mm[set * kMaxD + i] = min encoding,
-// mm[(nsets + set) * kMaxD + i] = max encoding.  A warp whose points share one set reduces first.
+// Per-set min / max of every dimension for a batched call (set s = points [set_off[s],
+// set_off[s + 1]), d values each; mm[s * stride + i] and mm[(nsets + s) * stride + i] receive
+// the order-preserving codes of the minimum and maximum of dimension i).  Each warp takes a
+// contiguous run of points, so it crosses few set boundaries: lanes hold running minima and
+// maxima of fixed dimensions (lane % d, for d <= 32 and 32 / d points per step; dimensions
+// lane and lane + 32 for larger d), and the warp folds them into the set's words with one
+// atomic per dimension at each set boundary and at the end of its run.
+template <typename T>
+__device__ __forceinline__ void seg_minmax(const T *__restrict__ in, int64_t n, int d, const int64_t *set_off,
+                                           int nsets, unsigned long long *mm, int stride, DevCounters *ctr) {
+    const int lane = lane_id();
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t per = (n + warps - 1) / warps;
+    const int64_t j0 = gw * per, j1 = min(n, j0 + per);
+    const int g = d <= 32 ? 32 / d : 1;   // points per step
+    const int dim = d <= 32 ? lane % d : lane;
+    const int slot = d <= 32 ? lane / d : 0;
+    const bool lane_on = slot < g;
+    const T big = sizeof(T) == 4 ? (T)FLT_MAX : (T)DBL_MAX;
+    bool nan = false;
+    if (j0 < j1) {
+        uint32_t set = set_of_point(set_off, nsets, j0);
+        int64_t next = __ldg(set_off + set + 1);
+        T mn0 = big, mx0 = -big, mn1 = big, mx1 = -big;
+        bool any = false;
+        auto flush = [&]() {
+            if (!any) return;
+            if (d <= 32) {
+                // fold the point slots of each dimension into lanes 0 .. d - 1
+                for (int k = 1; k < g; ++k) {
+                    const T a = __shfl_sync(0xffffffffu, mn0, min(lane + k * d, 31));
+                    const T b = __shfl_sync(0xffffffffu, mx0, min(lane + k * d, 31));
+                    if (lane < d) {
+                        mn0 = a < mn0 ? a : mn0;
+                        mx0 = b > mx0 ? b : mx0;
+                    }
+                }
+                if (lane < d) {
+                    atomicMin(&mm[(uint64_t)set * stride + lane], (unsigned long long)enc_double((double)mn0));
+                    atomicMax(&mm[((uint64_t)nsets + set) * stride + lane], (unsigned long long)enc_double((double)mx0));
+                }
+            } else {
+                if (lane < d) {
+                    atomicMin(&mm[(uint64_t)set * stride + lane], (unsigned long long)enc_double((double)mn0));
+                    atomicMax(&mm[((uint64_t)nsets + set) * stride + lane], (unsigned long long)enc_double((double)mx0));
+                }
+                if (lane + 32 < d) {
+                    atomicMin(&mm[(uint64_t)set * stride + lane + 32], (unsigned long long)enc_double((double)mn1));
+                    atomicMax(&mm[((uint64_t)nsets + set) * stride + lane + 32],
+                              (unsigned long long)enc_double((double)mx1));
+                }
+            }
+            mn0 = big; mx0 = -big; mn1 = big; mx1 = -big;
+            any = false;
+        };
+        for (int64_t j = j0; j < j1;) {
+            while (j >= next) {  // warp-uniform: the run enters the next non-empty set
+                flush();
+                ++set;
+                next = __ldg(set_off + set + 1);
+            }
+            const int64_t stop = min(j1, next);
+            if (stop - j >= 4 * g) {
+                // four full steps, their loads in flight together
+                T x0[4], x1[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t p = j + u * g + slot;
+                    x0[u] = lane_on && (d <= 32 || lane < d) ? __ldg(in + p * d + dim) : (T)0;
+                    x1[u] = d > 32 && lane + 32 < d ? __ldg(in + p * d + lane + 32) : (T)0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (lane_on && (d <= 32 || lane < d)) {
+                        nan |= (x0[u] != x0[u]);
+                        mn0 = x0[u] < mn0 ? x0[u] : mn0;
+                        mx0 = x0[u] > mx0 ? x0[u] : mx0;
+                    }
+                    if (d > 32 && lane + 32 < d) {
+                        nan |= (x1[u] != x1[u]);
+                        mn1 = x1[u] < mn1 ? x1[u] : mn1;
+                        mx1 = x1[u] > mx1 ? x1[u] : mx1;
+                    }
+                }
+                any = true;
+                j += 4 * g;
+                continue;
+            }
+            const int take = (int)min((int64_t)g, stop - j);
+            const int64_t p = j + slot;
+            if (lane_on && slot < take) {
+                if (d <= 32) {
+                    const T x = __ldg(in + p * d + dim);
+                    nan |= (x != x);
+                    mn0 = x < mn0 ? x : mn0;
+                    mx0 = x > mx0 ? x : mx0;
+                } else {
+                    if (lane < d) {
+                        const T x = __ldg(in + p * d + lane);
+                        nan |= (x != x);
+                        mn0 = x < mn0 ? x : mn0;
+                        mx0 = x > mx0 ? x : mx0;
+                    }
+                    if (lane + 32 < d) {
+                        const T x = __ldg(in + p * d + lane + 32);
+                        nan |= (x != x);
+                        mn1 = x < mn1 ? x : mn1;
+                        mx1 = x > mx1 ? x : mx1;
+                    }
+                }
+            }
+            any = true;
+            j += take;
+        }
+        flush();
+    }
+    if (__any_sync(0xffffffffu, nan) && lane == 0) atomicOr(&ctr->nan_seen, 1u);
+}
+
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_minmax_seg(const T *__restrict__ in, int64_t n, const int64_t *set_off,
                                                    int nsets, unsigned long long *mm, DevCounters *ctr) {
-    const int lane = lane_id();
-    bool nan = false;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
-         base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = base + lane;
-        const bool valid = j < n;
-        const uint32_t set = valid ? set_of_point(set_off, nsets, j) : 0xffffffffu;
-        const uint32_t s0 = __shfl_sync(0xffffffffu, set, 0);
-        const bool uniform = __all_sync(0xffffffffu, !valid || set == s0);
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            const double x = valid ? (double)in[j * D + i] : 0.0;
-            nan |= valid && (x != x);
-            if (uniform) {
-                double a = valid ? x : DBL_MAX, b = valid ? x : -DBL_MAX;
-                for (int o = 16; o; o >>= 1) {
-                    a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
-                    b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
-                }
-                if (lane == 0) {
-                    atomicMin(&mm[(uint64_t)s0 * kMaxD + i], (unsigned long long)enc_double(a));
-                    atomicMax(&mm[((uint64_t)nsets + s0) * kMaxD + i], (unsigned long long)enc_double(b));
-                }
-            } else if (valid) {
-                atomicMin(&mm[(uint64_t)set * kMaxD + i], (unsigned long long)enc_double(x));
-                atomicMax(&mm[((uint64_t)nsets + set) * kMaxD + i], (unsigned long long)enc_double(x));
-            }
-        }
-    }
-    if (__any_sync(0xffffffffu, nan) && lane == 0) atomicOr(&ctr->nan_seen, 1u);
+    seg_minmax<T>(in, n, D, set_off, nsets, mm, kMaxD, ctr);
 }
 
 // Algorithm 1 per set, with the set id above the cell key bits.

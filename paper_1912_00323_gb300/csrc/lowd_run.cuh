@@ -434,7 +434,7 @@ int run_lowd(const RunArgs &a) {
         cudaMemsetAsync(d_mm, 0xff, sizeof(uint64_t) * kMaxD * nsets, s);
         cudaMemsetAsync(d_mm + (size_t)kMaxD * nsets, 0, sizeof(uint64_t) * kMaxD * nsets, s);
         upload(d_setoff, a.h_off, sizeof(int64_t) * (nsets + 1), stage_setoff);
-        k_minmax_seg<T, D><<<grid_for(n, 256, sms, 4), 256, 0, s>>>((const T *)a.d_points, n, d_setoff, nsets,
+        k_minmax_seg<T, D><<<grid_for(n, 256, sms, 8), 256, 0, s>>>((const T *)a.d_points, n, d_setoff, nsets,
                                                                   (unsigned long long *)d_mm, ctr);
         if (!boxed) {
             hmm.resize((size_t)2 * kMaxD * nsets);
