@@ -184,17 +184,33 @@ void run_tc_phases(HdView<float, DP> &hv, cudaStream_t s, char *b, int64_t n, in
     tmark(2);
     tc::k_tc_hd<DP, tc::kMerge><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch1, cx, clist, nclist, clab, nch});
     tmark(3);
-    k_merge_hd<float, DP><<<gcell, hd_block, smem, s>>>(hv);
+    // the CUDA-core unions take the cells below the threshold; from one core row on every cell
+    // with a core point is on the tensor cores and nothing is left for them
+    if (tune.min[1] > 1) {
+        k_merge_hd<float, DP><<<gcell, hd_block, smem, s>>>(hv);
+        ++launches;
+    }
     k_compress_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
-    launches += 14;
+    launches += 13;
     mark(8);
     // ---- Algorithm 4: canonical ids, core labels, border and noise points ----
     k_comp_min_hd<float, DP><<<gpts, 256, 0, s>>>(hv);
+    // the cells below the labels threshold on a second stream beside the tensor-core labels:
+    // the two write the labels of disjoint cells
+    const detail::SideStream ss = detail::side_stream();
+    const bool fork = ss.ok && cudaEventRecord(ss.fork, s) == cudaSuccess &&
+                      cudaStreamWaitEvent(ss.s, ss.fork, 0) == cudaSuccess;
+    if (fork) k_labels_hd<float, DP><<<gcell, hd_block, smem, ss.s>>>(hv);
     tc::k_tc_core_labels<DP><<<gpts, 256, 0, s>>>(hv, tc::Tables{ch2, cx, clist, nclist, clab, nullptr}, nsets, clab);
     tmark(4);
     tc::k_tc_hd<DP, tc::kLabels><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch2, cx, clist, nclist, clab, nullptr});
     tmark(5);
-    k_labels_hd<float, DP><<<gcell, hd_block, smem, s>>>(hv);
+    if (fork) {
+        cudaEventRecord(ss.join, ss.s);
+        cudaStreamWaitEvent(s, ss.join, 0);
+    } else {
+        k_labels_hd<float, DP><<<gcell, hd_block, smem, s>>>(hv);
+    }
     launches += 4;
     mark(9);
 }

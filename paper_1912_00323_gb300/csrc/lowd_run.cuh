@@ -243,6 +243,33 @@ inline DevCounters *host_counters() {
     return hc.p;
 }
 
+// A second stream of the calling thread on the current device, with the events that fork work
+// onto it from a call's stream and join it back (kept for the thread's lifetime); ok is false
+// when they could not be created, and the caller then stays on its own stream.
+struct SideStream {
+    bool ok = false;
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+inline SideStream side_stream() {
+    struct Slots {
+        SideStream v[64];
+        bool tried[64] = {};
+    };
+    thread_local Slots slots;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SideStream();
+    SideStream &ss = slots.v[dev];
+    if (!slots.tried[dev]) {
+        slots.tried[dev] = true;
+        ss.ok = cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking) == cudaSuccess &&
+                cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming) == cudaSuccess &&
+                cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming) == cudaSuccess;
+    }
+    return ss;
+}
+
 inline int grid_for(int64_t work, int per_block, int sms, int max_per_sm) {
     int64_t b = (work + per_block - 1) / per_block;
     const int64_t cap = (int64_t)sms * max_per_sm;
@@ -601,8 +628,20 @@ int run_lowd(const RunArgs &a) {
     mark(8);
     // ---- Algorithm 4: cluster ids, border and noise ----
     k_comp_min<T, D><<<gpts, 256, 0, s>>>(v);
-    k_label_core<T, D><<<gpts, 256, 0, s>>>(v);
-    k_labels<T, D><<<gwarp, 256, 0, s>>>(v, st.n_all);
+    {
+        // the core points' labels (point-parallel, bandwidth) on a second stream beside the
+        // border search (latency-bound, few cells): they write disjoint points
+        const SideStream ss = side_stream();
+        if (ss.ok && cudaEventRecord(ss.fork, s) == cudaSuccess && cudaStreamWaitEvent(ss.s, ss.fork, 0) == cudaSuccess) {
+            k_label_core<T, D><<<gpts, 256, 0, ss.s>>>(v);
+            k_labels<T, D><<<gwarp, 256, 0, s>>>(v, st.n_all);
+            cudaEventRecord(ss.join, ss.s);
+            cudaStreamWaitEvent(s, ss.join, 0);
+        } else {
+            k_label_core<T, D><<<gpts, 256, 0, s>>>(v);
+            k_labels<T, D><<<gwarp, 256, 0, s>>>(v, st.n_all);
+        }
+    }
     launches += 3;
     mark(9);
     if (cudaGetLastError() != cudaSuccess) { rc = HCA_ECUDA; goto out; }
