@@ -549,6 +549,15 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
                     uint32_t dv[32];
                     tmem_ld32(t_lane + c0, dv);
                     if (!need) continue;
+                    if (MODE != kMerge) {
+                        // 32 candidates all proved outside (the common case for the rows that
+                        // scan their whole neighbourhood: noise and border points) cost one
+                        // maximum each instead of the classification
+                        float mx = __uint_as_float(dv[0]);
+#pragma unroll
+                        for (int j = 1; j < 32; ++j) mx = fmaxf(mx, __uint_as_float(dv[j]));
+                        if (mx < thr_near) continue;
+                    }
                     if (MODE == kCount) {
                         // cnt: pairs surely within eps (D > rowA); cnt_hi: pairs not proved
                         // outside (D >= thr_near)
