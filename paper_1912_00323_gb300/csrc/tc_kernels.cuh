@@ -549,7 +549,7 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
                     uint32_t dv[32];
                     tmem_ld32(t_lane + c0, dv);
                     if (!need) continue;
-                    if (MODE != kMerge) {
+                    {
                         // 32 candidates all proved outside (the common case for the rows that
                         // scan their whole neighbourhood: noise and border points) cost one
                         // maximum each instead of the classification
