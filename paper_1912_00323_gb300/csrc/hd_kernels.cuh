@@ -69,6 +69,10 @@ __device__ __forceinline__ bool hd_within(const float *a, const float (&q)[DP], 
     float s = 0.f;
 #pragma unroll
     for (int i = 0; i < DP; i += 4) {
+        // the sum of squares only grows (fma of a square into a non-negative sum rounds to at
+        // least the sum), so a partial sum above hi32 already decides the pair: when every
+        // lane of the warp is there, the rest of the dimensions are skipped
+        if (i == DP / 2 && s > g.hi32) return false;
         const float4 av = *reinterpret_cast<const float4 *>(a + i);
         float t = __fsub_rn(av.x, q[i]);     s = __fmaf_rn(t, t, s);
         t = __fsub_rn(av.y, q[i + 1]);       s = __fmaf_rn(t, t, s);
