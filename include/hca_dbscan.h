@@ -361,7 +361,7 @@ HCA_API int hca_graph_cache_release(void);
  *   cta_warps      coarse grid: warps per CTA of the CUDA-core chunk kernels (counts, first
  *                  links, unions, labels; one 32-point chunk per warp, its rows staged in the
  *                  CTA's shared memory): 2, 4 or 8.
- * Defaults: path 0, tc_handoff 8, first_links 1, cta_warps 4; thresholds 16 / 16 / 4 for
+ * Defaults: path 0, tc_handoff 8, first_links 1, cta_warps 4; thresholds 16 / 1 / 4 for
  * d <= 8 and 8 / 1 / 1 for d > 8.
  */
 typedef struct hca_tuning {

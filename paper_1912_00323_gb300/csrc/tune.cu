@@ -20,15 +20,16 @@ bool g_tune_init = false;
 
 // Defaults per d: the coarse-grid split measured fastest across the workloads, with first
 // links in every cell (leaving them out of tensor-core cells wins a few percent on many small
-// sets but loses up to 8x on a set of a million points) — d <= 8: thresholds 16 / 16 / 4;
-// d > 8 (the 16-D anisotropic clusters): 8 / 1 / 1 (the unions of every cell with a core
-// point on the tensor cores: a cell of one to three core points next to a cluster streams
-// the cluster's core points, 128 per tile there against 32 per warp step on the CUDA cores).
+// sets but loses up to 8x on a set of a million points) — d <= 8: thresholds 16 / 1 / 4;
+// d > 8 (the 16-D anisotropic clusters): 8 / 1 / 1.  From one core row on the unions of every
+// cell with a core point run on the tensor cores: a cell of one to three core points next to
+// a cluster streams the cluster's core points, 128 per tile there against 32 per warp step on
+// the CUDA cores.
 hca_tuning default_tuning(int d) {
     hca_tuning t = kDefaultTuning;
     if (d <= 8) {
         t.tc_min_count = 16;
-        t.tc_min_merge = 16;
+        t.tc_min_merge = 1;
         t.tc_min_labels = 4;
         t.first_links = 1;
     } else {
