@@ -120,8 +120,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
     return done != 0;
 }
 
-// 32 consecutive accumulator columns of this warp's 32 lanes (lane i of warp w = row 32 w + i).
-__device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&v)[32]) {
+// 32 consecutive accumulator columns of this warp's 32 lanes (lane i of warp w = row 32 w + i),
+// issued without waiting: the registers hold the values after tmem_ld_wait.
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t addr, uint32_t (&v)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -130,7 +131,48 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&v)[32]) {
           "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
           "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
         : "r"(addr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Wait for this thread's outstanding tensor-memory loads.  The registers of v pass through the
+// wait, so that no use of them is scheduled before it; reg_tie does the same for a second set.
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&v)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                   "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]),
+                   "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]),
+                   "+r"(v[24]), "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
+                 :
+                 : "memory");
+}
+
+__device__ __forceinline__ void reg_tie(uint32_t (&v)[32]) {
+    asm volatile(""
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                   "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]),
+                   "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]),
+                   "+r"(v[24]), "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
+                 :
+                 : "memory");
+}
+
+// Three-input maximum (PTX max.f32 with three sources).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// Largest of 32 FP32 values, as a tree of three-input maxima (17 instructions, four dependent
+// steps, instead of a chain of 31).
+__device__ __forceinline__ float max32(const uint32_t (&v)[32]) {
+    float a[11];
+#pragma unroll
+    for (int j = 0; j < 10; ++j)
+        a[j] = fmax3(__uint_as_float(v[3 * j]), __uint_as_float(v[3 * j + 1]), __uint_as_float(v[3 * j + 2]));
+    a[10] = fmaxf(__uint_as_float(v[30]), __uint_as_float(v[31]));
+    const float b0 = fmax3(a[0], a[1], a[2]), b1 = fmax3(a[3], a[4], a[5]), b2 = fmax3(a[6], a[7], a[8]);
+    const float b3 = fmaxf(a[9], a[10]);
+    return fmaxf(fmax3(b0, b1, b2), b3);
 }
 
 template <int DP>
@@ -342,7 +384,7 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
         {
             const float4 *src = reinterpret_cast<const float4 *>(v.pts + (uint64_t)p * DP);
 #pragma unroll
-            for (int k = 0; k < DP / 4; ++k) q[k] = have ? src[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int k = 0; k < DP / 4; ++k) q[k] = src[k];  // point 0 past the rows; zeroed when staged
             if (tid == 0) {
 #pragma unroll
                 for (int k = 0; k < DP / 4; ++k) *reinterpret_cast<float4 *>(S.cen + 4 * k) = q[k];
@@ -469,12 +511,14 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
             const uint32_t u = ub + (uint32_t)tid;
             pre_in = u < L;
             pre_k = pre_in ? stream_index(S.rpre, S.rq0, nspan, u) : 0u;
-            const uint32_t qp = pre_in ? (MODE == kCount ? pre_k : __ldg(tt.core_list + pre_k)) : 0u;
+            // past the stream: list index 0 (a valid point), zeroed when staged; the loads are
+            // not waited for here (no select on their values) but at the staging of the block
+            const uint32_t qp = MODE == kCount ? pre_k : __ldg(tt.core_list + pre_k);
             const float4 *src = reinterpret_cast<const float4 *>(v.pts + (uint64_t)qp * DP);
 #pragma unroll
-            for (int k = 0; k < DP / 4; ++k) q[k] = pre_in ? src[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (MODE == kMerge) pre_pay = pre_in ? __ldcg(v.parent + qp) : 0xffffffffu;  // an ancestor of qp
-            if (MODE == kLabels) pre_pay = pre_in ? __ldg(tt.core_lab + pre_k) : kNoLabel;
+            for (int k = 0; k < DP / 4; ++k) q[k] = src[k];
+            if (MODE == kMerge) pre_pay = __ldcg(v.parent + qp);  // an ancestor of qp
+            if (MODE == kLabels) pre_pay = __ldg(tt.core_lab + pre_k);
         };
         if (L > 0) prefetch(0);
         for (uint32_t ub = 0; ub < L; ub += kTile) {
@@ -509,8 +553,9 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
                 S.cidx[tid] = pre_k;
             }
             if (MODE == kLabels) {
-                S.cpay[tid] = pre_pay;
-                uint32_t gm = pre_pay;
+                const uint32_t lq = pre_in ? pre_pay : kNoLabel;
+                S.cpay[tid] = lq;
+                uint32_t gm = lq;
                 gm = __reduce_min_sync(0xffffffffu, gm);
                 if ((tid & 31) == 0) S.gsum[warp] = gm;
             }
@@ -545,71 +590,87 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
             if (tid == 0) n_pairs += (unsigned long long)min((uint32_t)kTile, rend - k0) * nq;
             bool need = have && (MODE != kCount || !done);
             if (__any_sync(0xffffffffu, need)) {
-                for (uint32_t c0 = 0; c0 < nq; c0 += 32) {
-                    uint32_t dv[32];
-                    tmem_ld32(t_lane + c0, dv);
-                    if (!need) continue;
-                    {
+                // counts and labels: 64 columns per wait, the second 32 read even past nq
+                // (allocated columns; their values are not used); unions: 32 (the registers
+                // of a second set slowed the union-find loop)
+                constexpr int NH = MODE == kMerge ? 1 : 2;
+                for (uint32_t c0 = 0; c0 < nq; c0 += 32u * NH) {
+                    uint32_t dv[NH][32];
+                    tmem_ld32_issue(t_lane + c0, dv[0]);
+                    if (NH == 2) tmem_ld32_issue(t_lane + c0 + 32, dv[NH - 1]);
+                    tmem_ld_wait(dv[0]);
+                    if (NH == 2) reg_tie(dv[NH - 1]);
+#pragma unroll
+                    for (int h = 0; h < NH; ++h) {
+                        const uint32_t cg = c0 + 32u * (uint32_t)h;
+                        if (cg >= nq || !need) continue;
                         // 32 candidates all proved outside (the common case for the rows that
                         // scan their whole neighbourhood: noise and border points) cost one
                         // maximum each instead of the classification
-                        float mx = __uint_as_float(dv[0]);
+                        if (MODE == kMerge) {  // the tree's registers push the union loop into spills
+                            float mx = __uint_as_float(dv[h][0]);
 #pragma unroll
-                        for (int j = 1; j < 32; ++j) mx = fmaxf(mx, __uint_as_float(dv[j]));
-                        if (mx < thr_near) continue;
-                    }
-                    if (MODE == kCount) {
-                        // cnt: pairs surely within eps (D > rowA); cnt_hi: pairs not proved
-                        // outside (D >= thr_near)
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const float dd = __uint_as_float(dv[j]);
-                            cnt += dd > rowA ? 1u : 0u;
-                            cnt_hi += dd < thr_near ? 0u : 1u;
+                            for (int j = 1; j < 32; ++j) mx = fmaxf(mx, __uint_as_float(dv[h][j]));
+                            if (mx < thr_near) continue;
+                        } else if (max32(dv[h]) < thr_near) {
+                            continue;
                         }
-                        if (cnt >= G.min_pts) need = false;
-                    } else {
-                        uint32_t in_m = 0, near_m = 0;
+                        if (MODE == kCount) {
+                            // cnt: pairs surely within eps (D > rowA); cnt_hi: pairs not proved
+                            // outside (D >= thr_near); four partial tallies each
+                            uint32_t ci[4] = {0u, 0u, 0u, 0u}, ch[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const float dd = __uint_as_float(dv[j]);
-                            const bool in = dd > rowA;
-                            in_m |= (uint32_t)in << j;
-                            near_m |= (uint32_t)(!in && !(dd < thr_near)) << j;
-                        }
-                        uint32_t m = in_m | near_m;  // near: decided by the exact predicate
-                        // candidates sharing the row's tree node need no test; nor do ids that
-                        // cannot lower the row's label
-                        if (MODE == kMerge && rp == ref) m &= S.gsum[c0 >> 5];
-                        if (MODE == kLabels && S.gsum[c0 >> 5] >= best) m = 0;
-                        while (m) {
-                            const int j = __ffs(m) - 1;
-                            m &= m - 1;
-                            const uint32_t col = c0 + (uint32_t)j;
-                            const bool inside = (in_m >> j) & 1u;
-                            const uint32_t ck2 = S.cidx[col];
-                            if (MODE == kMerge) {
-                                if (ck2 <= rk || S.cpay[col] == rp) continue;
-                                const uint32_t qp = __ldg(tt.core_list + ck2);
-                                bool hit = inside;
-                                if (!hit) {
-                                    ++n_re;
-                                    hit = within_pts<DP>(v.pts, p, qp, G);
+                            for (int j = 0; j < 32; ++j) {
+                                const float dd = __uint_as_float(dv[h][j]);
+                                ci[j & 3] += dd > rowA ? 1u : 0u;
+                                ch[j & 3] += dd < thr_near ? 0u : 1u;
+                            }
+                            cnt += (ci[0] + ci[1]) + (ci[2] + ci[3]);
+                            cnt_hi += (ch[0] + ch[1]) + (ch[2] + ch[3]);
+                            if (cnt >= G.min_pts) need = false;
+                        } else {
+                            uint32_t in_m = 0, near_m = 0;
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                const float dd = __uint_as_float(dv[h][j]);
+                                const bool in = dd > rowA;
+                                in_m |= (uint32_t)in << j;
+                                near_m |= (uint32_t)(!in && !(dd < thr_near)) << j;
+                            }
+                            uint32_t m = in_m | near_m;  // near: decided by the exact predicate
+                            // candidates sharing the row's tree node need no test; nor do ids
+                            // that cannot lower the row's label
+                            if (MODE == kMerge && rp == ref) m &= S.gsum[cg >> 5];
+                            if (MODE == kLabels && S.gsum[cg >> 5] >= best) m = 0;
+                            while (m) {
+                                const int j = __ffs(m) - 1;
+                                m &= m - 1;
+                                const uint32_t col = cg + (uint32_t)j;
+                                const bool inside = (in_m >> j) & 1u;
+                                const uint32_t ck2 = S.cidx[col];
+                                if (MODE == kMerge) {
+                                    if (ck2 <= rk || S.cpay[col] == rp) continue;
+                                    const uint32_t qp = __ldg(tt.core_list + ck2);
+                                    bool hit = inside;
+                                    if (!hit) {
+                                        ++n_re;
+                                        hit = within_pts<DP>(v.pts, p, qp, G);
+                                    }
+                                    if (hit) {
+                                        uf_union(v.parent, p, qp, v.ctr);
+                                        rp = uf_find(v.parent, p, v.ctr);
+                                        S.cpay[col] = rp;  // now an ancestor of qp too: later rows skip it
+                                    }
+                                } else {
+                                    const uint32_t lq = S.cpay[col];
+                                    if (lq >= best) continue;
+                                    bool hit = inside;
+                                    if (!hit) {
+                                        ++n_re;
+                                        hit = within_pts<DP>(v.pts, p, __ldg(tt.core_list + ck2), G);
+                                    }
+                                    if (hit) best = lq;
                                 }
-                                if (hit) {
-                                    uf_union(v.parent, p, qp, v.ctr);
-                                    rp = uf_find(v.parent, p, v.ctr);
-                                    S.cpay[col] = rp;  // now an ancestor of qp too: later rows skip it
-                                }
-                            } else {
-                                const uint32_t lq = S.cpay[col];
-                                if (lq >= best) continue;
-                                bool hit = inside;
-                                if (!hit) {
-                                    ++n_re;
-                                    hit = within_pts<DP>(v.pts, p, __ldg(tt.core_list + ck2), G);
-                                }
-                                if (hit) best = lq;
                             }
                         }
                     }
