@@ -179,9 +179,9 @@ template <int DP>
 struct Smem {
     static constexpr int KP = DP + 8;  // K of the MMA: coordinates and the threshold columns
     float a_hi[kTile * KP];    // rows: centred coordinates (TF32 hi part), (1, 1, 0, ...)
-    float a_lo[kTile * KP];    // rows: the lo parts, zeros
+    float a_lo[kTile * KP];    // rows: the lo parts (threshold columns unused)
     float b_hi[kTile * KP];    // candidates: centred coordinates (hi), (-colA_hi, -colA_lo, 0, ...)
-    float b_lo[kTile * KP];    // candidates: the lo parts, zeros
+    float b_lo[kTile * KP];    // candidates: the lo parts (threshold columns unused)
     float cen[DP];             // the centre c (row 0 of the chunk, original coordinates)
     uint32_t cpay[kTile];      // per candidate: tree node (unions) or cluster id (labels)
     uint32_t cidx[kTile];      // per candidate: list index
@@ -234,15 +234,22 @@ __device__ __forceinline__ float stage_split(float *hi_op, float *lo_op, int row
     return nrm;
 }
 
-// Columns [DP, DP + 8) of an operand row pair: w0 in the hi part, zeros elsewhere.
+// Columns [DP, DP + 8) of the hi operand, set once per CTA: the rows' (1, 1, 0, ...) and the
+// candidates' trailing zeros (columns DP + 4 .. DP + 7).  The lo operands' threshold columns
+// are never read (the threshold K step multiplies the hi parts only).
 template <int DP, int KP>
-__device__ __forceinline__ void stage_extra(float *hi_op, float *lo_op, int row, float4 w0) {
+__device__ __forceinline__ void stage_extra_const(float *a_hi, float *b_hi, int row) {
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     const uint32_t o0 = op_offset<KP>(row, DP), o1 = op_offset<KP>(row, DP + 4);
-    *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(hi_op) + o0) = w0;
-    *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(hi_op) + o1) = z;
-    *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(lo_op) + o0) = z;
-    *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(lo_op) + o1) = z;
+    *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(a_hi) + o0) = make_float4(1.f, 1.f, 0.f, 0.f);
+    *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(a_hi) + o1) = z;
+    *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(b_hi) + o1) = z;
+}
+
+// The candidate's threshold columns: (-colA_hi, -colA_lo, 0, 0) at columns DP .. DP + 3.
+template <int DP, int KP>
+__device__ __forceinline__ void stage_threshold(float *b_hi, int row, float4 w0) {
+    *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(b_hi) + op_offset<KP>(row, DP)) = w0;
 }
 
 // box_far for a row held in registers (four coordinates per float4).
@@ -342,6 +349,7 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
                      "r"(kTile));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    stage_extra_const<DP, KP>(S.a_hi, S.b_hi, tid);  // made visible to the MMA by each block's proxy fence
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
@@ -495,7 +503,6 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
         __syncthreads();
         const uint32_t L = S.rpre[kMaxRng];
         const float na = stage_split<DP, KP>(S.a_hi, S.a_lo, tid, q, S.cen, have);
-        stage_extra<DP, KP>(S.a_hi, S.a_lo, tid, make_float4(1.f, 1.f, 0.f, 0.f));
         const float lo = (float)(G.eps2 * (1.0 - 0x1p-20));
         const float hi = (float)(G.eps2 * (1.0 + 0x1p-20));
         const float rowA = 0.5f * __fsub_rn(__fmul_rn(na, 1.000244140625f), lo);  // (1 + 2^-12) |x|^2
@@ -549,7 +556,7 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
                 const float nb = stage_split<DP, KP>(S.b_hi, S.b_lo, tid, q, S.cen, pre_in);
                 const float colA = pre_in ? 0.5f * __fmul_rn(nb, 1.000244140625f) : 0x1p110f;
                 const float chi = tf32_trunc(colA);
-                stage_extra<DP, KP>(S.b_hi, S.b_lo, tid, make_float4(-chi, -__fsub_rn(colA, chi), 0.f, 0.f));
+                stage_threshold<DP, KP>(S.b_hi, tid, make_float4(-chi, -__fsub_rn(colA, chi), 0.f, 0.f));
                 S.cidx[tid] = pre_k;
             }
             if (MODE == kLabels) {
