@@ -43,8 +43,9 @@ struct DevCounters {
     uint64_t minmax_enc[2 * kMaxD];  // order-preserving encodings of min (first kMaxD) / max per dim
     uint32_t nan_seen;
     uint32_t n_chunks;     // 32-point chunks of the coarse cells (high-dimensional path)
-    uint32_t n_tc_chunks[3];  // 128-row chunks of the tensor-core phases: counts, unions, labels
-    uint32_t tc_next[3];      // next unclaimed chunk of each tensor-core phase
+    uint32_t n_tc_chunks[4];  // work items of the tensor-core phases: counts, unions (the first window of
+                              // every 128-row chunk), labels; [3]: the unions' other windows
+    uint32_t tc_next[3];      // next unclaimed item of each tensor-core phase
     uint32_t hd_next[4];      // next unclaimed 32-point chunk: counts, first links, unions, labels
     uint32_t lowd_next[5];    // next unclaimed batch (labels: [4])
     unsigned long long work[8];  // work counters (see hca_stats)

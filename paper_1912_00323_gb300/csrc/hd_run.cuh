@@ -168,9 +168,13 @@ void run_tc_phases(HdView<float, DP> &hv, cudaStream_t s, char *b, int64_t n, in
     tc::k_tc_core_flags<<<gpts, 256, 0, s>>>(hv.core, n, flags);
     exclusive_scan_u32(flags, cx, n, nullptr, cx + n, part, s, &launches);
     tc::k_tc_partition<<<gpts, 256, 0, s>>>(hv.core, cx, n, clist, nclist);
-    tc::k_tc_chunks_split<<<gpts, 256, 0, s>>>(hv.cell_start, cx, ctr, tune.min[1], tune.min[2], nch, nch2);
+    // (flags and ch0 are free once cx is scanned and the counts are done: the unions' later
+    // windows take them)
+    tc::k_tc_chunks_split<<<gpts, 256, 0, s>>>(hv.cell_start, cx, ctr, hv.ranges, hv.n_half, hv.n_all, tune.min[1],
+                                               tune.min[2], nch, flags, nch2);
     exclusive_scan_u32(nch, ch1, n, &ctr->n_cells, &ctr->n_tc_chunks[tc::kMerge], part, s, &launches);
     exclusive_scan_u32(nch2, ch2, n, &ctr->n_cells, &ctr->n_tc_chunks[tc::kLabels], part, s, &launches);
+    exclusive_scan_u32(flags, ch0, n, &ctr->n_cells, &ctr->n_tc_chunks[3], part, s, &launches);
     launches += 3;
     mark(7);
     // ---- Definitions 3-5: first links, pointer jumping, then the remaining unions ----
@@ -182,7 +186,8 @@ void run_tc_phases(HdView<float, DP> &hv, cudaStream_t s, char *b, int64_t n, in
     tc::k_tc_cell_root<DP><<<gpts, 256, 0, s>>>(hv, nch, nch2);
     tc::k_tc_cell_root_final<<<gpts, 256, 0, s>>>(ctr, nch, nch2);
     tmark(2);
-    tc::k_tc_hd<DP, tc::kMerge><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch1, cx, clist, nclist, clab, nch});
+    // window-major items: the first window of every chunk, then the other windows
+    tc::k_tc_hd<DP, tc::kMerge><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch1, cx, clist, nclist, clab, nch, ch0});
     tmark(3);
     // the CUDA-core unions take the cells below the threshold; from one core row on every cell
     // with a core point is on the tensor cores and nothing is left for them

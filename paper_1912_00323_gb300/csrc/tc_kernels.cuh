@@ -54,7 +54,44 @@ constexpr uint32_t kLBO = 128;             // bytes between core matrices along 
 constexpr uint32_t kWaitLimit = 1u << 22;  // mbarrier polls before a wait gives up
 constexpr size_t kMinSmem = 48 * 1024;     // per CTA: at most 4 CTAs (4 x 128 TMEM columns) per SM
 constexpr int kMaxRng = 32;                // neighbour ranges per cell (the coarse grid has 9)
+constexpr uint32_t kSegCand = 16 * kTile;  // unions: candidates per work item (a window of the stream)
+constexpr uint32_t kSplitBelow = 32;       // unions: windows only with fewer chunks per CTA than this
 enum { kCount = 0, kMerge = 1, kLabels = 2 };
+
+// Unions: core points of neighbour range k of cell A before any pruning (range 0, the cell's
+// own pencil, from A on).  The unpruned stream of A is ranges 0 .. n_half - 1 end to end.
+__device__ __forceinline__ uint32_t merge_range_len(const uint2 *ranges, int n_all, const uint32_t *cell_start,
+                                                    const uint32_t *cx, uint32_t A, int k) {
+    uint2 rg = ranges[(uint64_t)A * n_all + k];
+    if (k == 0) rg.x = A;
+    return rg.x < rg.y ? cx[cell_start[rg.y]] - cx[cell_start[rg.x]] : 0u;
+}
+
+// Windows of a 128-row chunk of the unions: one per kSegCand candidates of the unpruned
+// stream (an upper bound of the pruned one); window w is the blocks of the pruned stream from
+// w * kSegCand on (none when the pruning left fewer).  The items are handed out window-major:
+// the first windows of all chunks, then the others, so that no item of a cell with a long
+// neighbourhood runs far longer than the rest, and the later windows mostly find the trees that
+// the first ones joined (their blocks of one tree are skipped).  With kSplitBelow or more
+// chunks per CTA the chunks spread evenly as they are, and each runs whole.
+__device__ __forceinline__ uint32_t merge_windows(uint32_t len) {
+    return len > kSegCand ? (len + kSegCand - 1u) / kSegCand : 1u;
+}
+
+// Cell of work item t: the last c with off[c] <= t, by a 32-way search (one round of loads per
+// level instead of one per halving).  A full warp calls it; every lane returns the result.
+__device__ __forceinline__ uint32_t chunk_cell_warp(const uint32_t *off, uint32_t C, uint32_t t) {
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t lo = 0, hi = C;  // off[lo] <= t, and off[hi] > t unless hi == C
+    while (hi - lo > 1u) {
+        const uint32_t step = (hi - lo + 31u) >> 5;
+        const uint32_t piv = lo + lane * step;
+        const unsigned ok = __ballot_sync(0xffffffffu, piv < hi && __ldg(off + piv) <= t);
+        lo += (uint32_t)(31 - __clz(ok)) * step;  // the ok lanes are a prefix (off is nondecreasing)
+        hi = min(hi, lo + step);
+    }
+    return lo;
+}
 
 // Row and candidate lists of the three phases.
 struct Tables {
@@ -65,6 +102,8 @@ struct Tables {
     const uint32_t *core_lab;   // cluster id of every core point, by core-list index (labels phase)
     const uint32_t *cell_root;  // unions: the one root of a cell's core points (~0 if they differ or
                                 // there are none), taken before the phase; nullptr: unused
+    const uint32_t *choff_later;  // unions: first item of every coarse cell among the windows after
+                                  // the first of its chunks (chunks x (windows - 1) per cell)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -192,6 +231,7 @@ struct Smem {
     uint32_t bcell[kMaxRng];   // unions, labels: the neighbour cells, range by range
     uint32_t bnear[kMaxRng];   // 1: some row lies within eps of the cell's box
     uint32_t nbc, bover;       // number of those cells; 1 if they did not fit (no pruning)
+    uint32_t cell, nwin;       // the item's coarse cell; unions: windows per chunk of it
     uint64_t mbar;
     uint32_t taddr, ref, next, pad;
 };
@@ -252,15 +292,15 @@ __device__ __forceinline__ void stage_threshold(float *b_hi, int row, float4 w0)
     *reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(b_hi) + op_offset<KP>(row, DP)) = w0;
 }
 
-// box_far for a row held in registers (four coordinates per float4).
+// box_far for a row held in registers (four coordinates per float4), the box in shared memory.
 template <int DP>
-__device__ __forceinline__ bool box_far_reg(const float4 (&a)[DP / 4], const float *lo, const float *hi,
-                                            const GridParams &g) {
+__device__ __forceinline__ bool box_far_sh(const float4 (&a)[DP / 4], const float *lo, const float *hi,
+                                           const GridParams &g) {
     float s = 0.f;
 #pragma unroll
     for (int k = 0; k < DP / 4; ++k) {
-        const float4 l = __ldg(reinterpret_cast<const float4 *>(lo) + k);
-        const float4 h = __ldg(reinterpret_cast<const float4 *>(hi) + k);
+        const float4 l = reinterpret_cast<const float4 *>(lo)[k];
+        const float4 h = reinterpret_cast<const float4 *>(hi)[k];
         float t = fmaxf(fmaxf(__fsub_rn(l.x, a[k].x), __fsub_rn(a[k].x, h.x)), 0.f); s = __fmaf_rn(t, t, s);
         t = fmaxf(fmaxf(__fsub_rn(l.y, a[k].y), __fsub_rn(a[k].y, h.y)), 0.f);       s = __fmaf_rn(t, t, s);
         t = fmaxf(fmaxf(__fsub_rn(l.z, a[k].z), __fsub_rn(a[k].z, h.z)), 0.f);       s = __fmaf_rn(t, t, s);
@@ -356,7 +396,9 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
     const uint32_t taddr = S.taddr;
     const uint32_t t_lane = taddr + ((uint32_t)(warp * 32) << 16);
     const uint32_t idesc = idesc_tf32();
-    const uint32_t C = v.ctr->n_cells, NC = v.ctr->n_tc_chunks[MODE];
+    const uint32_t C = v.ctr->n_cells, N0 = v.ctr->n_tc_chunks[MODE];
+    const bool split = MODE == kMerge && N0 < kSplitBelow * gridDim.x;
+    const uint32_t NC = split ? N0 + v.ctr->n_tc_chunks[3] : N0;  // unions: first windows, then the rest
     const int n_rng = MODE == kMerge ? v.n_half : v.n_all;
     uint32_t phase = 0;
     bool failed = false;  // CTA-uniform
@@ -365,11 +407,29 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
 
     for (;;) {
         __syncthreads();  // every thread is done with the shared memory of the previous chunk
-        if (tid == 0) S.next = failed ? NC : atomicAdd(&v.ctr->tc_next[MODE], 1u);
+        if (warp == 0) {  // the next item and its cell (and the unions' windows per chunk)
+            uint32_t t = 0;
+            if (tid == 0) t = failed ? NC : atomicAdd(&v.ctr->tc_next[MODE], 1u);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            uint32_t A = 0, nwin = 1;
+            if (t < NC) {
+                const bool later = MODE == kMerge && t >= N0;
+                A = later ? chunk_cell_warp(tt.choff_later, C, t - N0) : chunk_cell_warp(tt.choff, C, t);
+                if (later) {
+                    uint32_t len = tid < n_rng ? merge_range_len(v.ranges, v.n_all, v.cell_start, tt.cx, A, tid) : 0u;
+                    nwin = merge_windows(__reduce_add_sync(0xffffffffu, len));
+                }
+            }
+            if (tid == 0) {
+                S.next = t;
+                S.cell = A;
+                S.nwin = nwin;
+            }
+        }
         __syncthreads();
         const uint32_t t = S.next;
         if (t >= NC) break;
-        const uint32_t A = chunk_cell(tt.choff, C, t);
+        const uint32_t A = S.cell;
         const uint32_t aset = set_of_key(v, v.cell_key[A]);
         const GridParams &G = params_of(v, aset);
         const uint32_t cs0 = v.cell_start[A], cs1 = v.cell_start[A + 1];
@@ -384,7 +444,13 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
             rbeg = cs0 - tt.cx[cs0];
             rend = cs1 - tt.cx[cs1];
         }
-        const uint32_t k0 = rbeg + (uint32_t)kTile * (t - tt.choff[A]);  // list index of row 0
+        // unions: t < N0: item t - choff[A] = chunk, window 0; then item t - N0 - choff_later[A]
+        // = chunk * (nwin - 1) + window - 1
+        const bool later = MODE == kMerge && t >= N0;
+        const uint32_t item = later ? t - N0 - tt.choff_later[A] : t - tt.choff[A];
+        const uint32_t nw = later ? S.nwin - 1u : 1u;
+        const uint32_t win = later ? 1u + item % nw : 0u;
+        const uint32_t k0 = rbeg + (uint32_t)kTile * (item / nw);  // list index of row 0
         const uint32_t rk = k0 + (uint32_t)tid;
         const bool have = rk < rend;
         const uint32_t p = have ? row_point<MODE>(tt, rk) : 0u;
@@ -434,11 +500,19 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
             by_cell = S.bover == 0u;
             if (by_cell) {
                 const uint32_t nbc = S.nbc;
+                // the boxes of the listed cells, loaded by all threads at once into b_lo (free
+                // until the first block is staged): cell i's lo at 2 DP i, its hi DP further
+                float *bx = S.b_lo;
+                for (uint32_t f = tid; f < nbc * (DP / 2); f += kTile) {
+                    const uint32_t i = f / (DP / 2), r = f % (DP / 2);
+                    const uint64_t c = S.bcell[i];
+                    const float *src = r < DP / 4 ? v.box_lo + c * DP + 4 * r : v.box_hi + c * DP + 4 * (r - DP / 4);
+                    *reinterpret_cast<float4 *>(bx + (size_t)i * 2 * DP + 4 * r) = __ldg(reinterpret_cast<const float4 *>(src));
+                }
+                __syncthreads();
                 if (have)
-                    for (uint32_t i = 0; i < nbc; ++i) {
-                        const uint64_t c = S.bcell[i];
-                        if (!box_far_reg<DP>(q, v.box_lo + c * DP, v.box_hi + c * DP, G)) S.bnear[i] = 1u;
-                    }
+                    for (uint32_t i = 0; i < nbc; ++i)
+                        if (!box_far_sh<DP>(q, bx + (size_t)i * 2 * DP, bx + (size_t)i * 2 * DP + DP, G)) S.bnear[i] = 1u;
                 __syncthreads();
                 if (warp == 0) {
                     uint32_t q0 = 0, len = 0;
@@ -501,7 +575,11 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
             if (tid == 31) S.rpre[kMaxRng] = incl;  // stream length
         }
         __syncthreads();
-        const uint32_t L = S.rpre[kMaxRng];
+        // the item's part of the stream: all of it, or for the unions window win of kSegCand
+        const uint32_t L_all = S.rpre[kMaxRng];
+        const uint32_t u0 = MODE == kMerge ? min(L_all, win * kSegCand) : 0u;
+        const uint32_t L = split ? min(L_all, u0 + kSegCand) : L_all;
+        if (MODE == kMerge && u0 >= L && win > 0u) continue;  // the pruning left nothing in this window
         const float na = stage_split<DP, KP>(S.a_hi, S.a_lo, tid, q, S.cen, have);
         const float lo = (float)(G.eps2 * (1.0 - 0x1p-20));
         const float hi = (float)(G.eps2 * (1.0 + 0x1p-20));
@@ -527,8 +605,8 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
             if (MODE == kMerge) pre_pay = __ldcg(v.parent + qp);  // an ancestor of qp
             if (MODE == kLabels) pre_pay = __ldg(tt.core_lab + pre_k);
         };
-        if (L > 0) prefetch(0);
-        for (uint32_t ub = 0; ub < L; ub += kTile) {
+        if (u0 < L) prefetch(u0);
+        for (uint32_t ub = u0; ub < L; ub += kTile) {
             const bool cin = pre_in;
             const uint32_t nq = min((uint32_t)kTile, L - ub);
             uint32_t rq = 0xffffffffu, ref = 0xffffffffu;
@@ -818,17 +896,29 @@ static __global__ void __launch_bounds__(256) k_tc_partition(const uint8_t *__re
     }
 }
 
-// 128-row chunks of every coarse cell for the unions (core rows) and the labels (non-core rows).
+// Work items of every coarse cell: for the unions, 128-row chunks of core rows (first launch)
+// and those chunks times the windows after the first (second launch); for the labels, 128-row
+// chunks of non-core rows.
 static __global__ void __launch_bounds__(256) k_tc_chunks_split(const uint32_t *__restrict__ cell_start,
                                                                const uint32_t *__restrict__ cx, const DevCounters *ctr,
+                                                               const uint2 *__restrict__ ranges, int n_half, int n_all,
                                                                uint32_t min_core, uint32_t min_nc,
                                                                uint32_t *__restrict__ nch_core,
+                                                               uint32_t *__restrict__ nch_later,
                                                                uint32_t *__restrict__ nch_nc) {
     const uint32_t C = ctr->n_cells;
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
         const uint32_t s = cell_start[c], e = cell_start[c + 1];
         const uint32_t nc = cx[e] - cx[s];
-        nch_core[c] = tc_chunks(nc, min_core);
+        const uint32_t chunks = tc_chunks(nc, min_core);
+        uint32_t later = 0;
+        if (chunks) {
+            uint32_t len = 0;
+            for (int k = 0; k < n_half; ++k) len += merge_range_len(ranges, n_all, cell_start, cx, c, k);
+            later = chunks * (merge_windows(len) - 1u);
+        }
+        nch_core[c] = chunks;
+        nch_later[c] = later;
         nch_nc[c] = tc_chunks(e - s - nc, min_nc);
     }
 }

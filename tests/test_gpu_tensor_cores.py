@@ -141,6 +141,41 @@ def test_aniso16d_reduced_on_tensor_cores(env, n, clusters):
     check(got, want)
 
 
+@pytest.mark.parametrize("n,clusters", [(20000, 1), (40000, 2)])
+def test_dense_clusters_split_union_streams(env, n, clusters):
+    """One or two clusters of 18,000 points: the unions' candidate streams hold more core
+    points than one window (2,048), so every 128-row chunk runs as several work items; the
+    labels and core flags equal the oracle's."""
+    _, _, oracle = env
+    X, eps, mp = workloads.aniso16d(n=n, n_clusters=clusters)
+    want = oracle.grid(X.astype(np.float64), eps, mp)
+    got = run(env, X, eps, mp)
+    assert got[2]["n_tc_tiles"] > 0
+    check(got, want)
+
+
+def test_batched_many_chunks_whole_union_streams(env):
+    """About eight million d = 8 points in 140 sets: more than 32 core-row chunks per resident
+    CTA, so every unions chunk runs whole (no windows); tensor-core labels equal the CUDA-core
+    labels of the same call and, on the two smallest sets, the oracle's."""
+    torch, pkg, oracle = env
+    sets = workloads.batched_sets(n_sets=140, n_min=30000, n_max=100000, dims=(8,), seed=81)
+    X = np.concatenate([s[0] for s in sets], axis=0)
+    off = np.zeros(len(sets) + 1, np.int64)
+    off[1:] = np.cumsum([len(s[0]) for s in sets])
+    t = torch.from_numpy(X).cuda()
+    eps = [s[1] for s in sets]
+    mp = [s[2] for s in sets]
+    lab, st = pkg.hca_dbscan_batched(t, off, eps, mp, stats=True)
+    assert st["n_tc_tiles"] > 0 and st["n_core_points"] > 32 * 128 * 4 * 152
+    ref = pkg.hca_dbscan_batched(t, off, eps, mp, tensor_cores=False).cpu().numpy()
+    lab = lab.cpu().numpy()
+    np.testing.assert_array_equal(lab, ref)
+    for s in np.argsort([len(x[0]) for x in sets])[:2]:
+        want = oracle.grid(sets[s][0].astype(np.float64), eps[s], mp[s])
+        np.testing.assert_array_equal(lab[off[s]:off[s + 1]], want[0], err_msg=f"set {s}")
+
+
 def test_batched_sets_on_tensor_cores(env):
     """The batched recipe at d = 8 (per-set eps and MINPTS): tensor-core labels equal the
     CUDA-core labels of the same call and, on every tenth set, the oracle's."""
