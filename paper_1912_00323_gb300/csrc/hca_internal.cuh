@@ -46,6 +46,8 @@ struct DevCounters {
     uint32_t n_tc_chunks[4];  // work items of the tensor-core phases: counts, unions (the first window of
                               // every 128-row chunk), labels; [3]: the unions' other windows
     uint32_t tc_next[3];      // next unclaimed item of each tensor-core phase
+    uint32_t n_tc_recount;    // chunks of the tensor-core recount of handed-over rows
+    uint32_t tc_next_recount;
     uint32_t hd_next[4];      // next unclaimed 32-point chunk: counts, first links, unions, labels
     uint32_t lowd_next[5];    // next unclaimed batch (labels: [4])
     unsigned long long work[8];  // work counters (see hca_stats)

@@ -156,13 +156,29 @@ void run_tc_phases(HdView<float, DP> &hv, cudaStream_t s, char *b, int64_t n, in
     hv.tc_pos = flags;  // free until the core numbering
     // ---- Definition 2: exact counts over the neighbouring coarse cells ----
     cudaMemsetAsync(hv.cell_core, 0, (size_t)n, s);
+    cudaMemsetAsync(hv.core, 0, (size_t)n, s);  // the recount below lists the rows with core = 2
     tc::k_tc_chunks_count<<<gpts, 256, 0, s>>>(hv.cell_start, ctr, tune.min[0], nch);
     exclusive_scan_u32(nch, ch0, n, &ctr->n_cells, &ctr->n_tc_chunks[tc::kCount], part, s, &launches);
     tmark(0);
     tc::k_tc_hd<DP, tc::kCount><<<grid_tc, tc::kTile, tc_smem, s>>>(hv, tc::Tables{ch0, cx, clist, nclist, clab, nullptr});
+    // the rows those chunks handed over, in cells with at least kRecountMin of them, counted again
+    // from the start, 128 per chunk (cx, clist, nclist, nch2 and ch1 are free until the core
+    // numbering); the rest, and what the recount hands over, go to the CUDA-core count
+    tc::k_tc_handed_flags<<<gpts, 256, 0, s>>>(hv.core, n, nclist);
+    exclusive_scan_u32(nclist, cx, n, nullptr, cx + n, part, s, &launches);
+    tc::k_tc_handed_list<<<gpts, 256, 0, s>>>(hv.core, cx, n, clist);
+    tc::k_tc_chunks_recount<<<gpts, 256, 0, s>>>(hv.cell_start, cx, ctr, hv.ranges, hv.n_all, tc::kRecountMin, nch2);
+    exclusive_scan_u32(nch2, ch1, n, &ctr->n_cells, &ctr->n_tc_recount, part, s, &launches);
+    // per listed row: the tallies summed over its windows and the windows done (nch, ch0 and
+    // nclist are free once scanned / once the first count is done)
+    cudaMemsetAsync(nch, 0, 4 * (size_t)n, s);
+    cudaMemsetAsync(ch0, 0, 4 * (size_t)n, s);
+    cudaMemsetAsync(nclist, 0, 4 * (size_t)n, s);
+    tc::k_tc_hd<DP, tc::kCount><<<grid_tc, tc::kTile, tc_smem, s>>>(
+        hv, tc::Tables{ch1, cx, nullptr, nullptr, nullptr, nullptr, nullptr, clist, nch, ch0, nclist});
     tmark(1);
     k_count_hd<float, DP><<<gcell, hd_block, smem, s>>>(hv);
-    launches += 3;
+    launches += 7;
     mark(6);
     // core numbering, core and non-core lists, chunk tables of the unions and the labels
     tc::k_tc_core_flags<<<gpts, 256, 0, s>>>(hv.core, n, flags);

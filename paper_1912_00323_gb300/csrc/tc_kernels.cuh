@@ -104,7 +104,25 @@ struct Tables {
                                 // there are none), taken before the phase; nullptr: unused
     const uint32_t *choff_later;  // unions: first item of every coarse cell among the windows after
                                   // the first of its chunks (chunks x (windows - 1) per cell)
+    const uint32_t *row_list;     // counts: nullptr = every point of the cell; else the recount of the
+                                  // rows the first count handed over (ascending; cx = its scan)
+    uint32_t *rc_in, *rc_hi, *rc_done;  // recount, per row of the list: the two tallies summed
+                                        // over the windows, and the windows done (zeroed)
 };
+
+// A coarse cell whose first tensor-core count handed over at least this many rows counts them
+// again on the tensor cores (128 per chunk) instead of leaving them to the CUDA-core count.
+// The recount's rows scan their whole neighbourhood (few reach MINPTS early), so each chunk
+// runs as windows of kSegCand candidates, one work item each; a row's tallies are summed over
+// its windows, and the last window to finish decides the row.
+constexpr uint32_t kRecountMin = 32;
+
+// Counts: points of neighbour range k of cell A (the stream is ranges 0 .. n_all - 1 end to end).
+__device__ __forceinline__ uint32_t count_range_len(const uint2 *ranges, int n_all, const uint32_t *cell_start,
+                                                    uint32_t A, int k) {
+    const uint2 rg = ranges[(uint64_t)A * n_all + k];
+    return rg.x < rg.y ? cell_start[rg.y] - cell_start[rg.x] : 0u;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -341,7 +359,8 @@ __device__ __forceinline__ bool within_pts(const float *pts, uint32_t i, uint32_
 
 template <int MODE>
 __device__ __forceinline__ uint32_t row_point(const Tables &tt, uint32_t k) {
-    return MODE == kCount ? k : MODE == kMerge ? __ldg(tt.core_list + k) : __ldg(tt.nc_list + k);
+    if (MODE == kCount) return tt.row_list ? __ldg(tt.row_list + k) : k;
+    return MODE == kMerge ? __ldg(tt.core_list + k) : __ldg(tt.nc_list + k);
 }
 
 // Candidate u of the chunk's stream: the neighbour ranges laid end to end (list indices
@@ -396,7 +415,9 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
     const uint32_t taddr = S.taddr;
     const uint32_t t_lane = taddr + ((uint32_t)(warp * 32) << 16);
     const uint32_t idesc = idesc_tf32();
-    const uint32_t C = v.ctr->n_cells, N0 = v.ctr->n_tc_chunks[MODE];
+    const bool recount = MODE == kCount && tt.row_list != nullptr;
+    const uint32_t C = v.ctr->n_cells, N0 = recount ? v.ctr->n_tc_recount : v.ctr->n_tc_chunks[MODE];
+    uint32_t *const next = recount ? &v.ctr->tc_next_recount : &v.ctr->tc_next[MODE];
     const bool split = MODE == kMerge && N0 < kSplitBelow * gridDim.x;
     const uint32_t NC = split ? N0 + v.ctr->n_tc_chunks[3] : N0;  // unions: first windows, then the rest
     const int n_rng = MODE == kMerge ? v.n_half : v.n_all;
@@ -409,7 +430,7 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
         __syncthreads();  // every thread is done with the shared memory of the previous chunk
         if (warp == 0) {  // the next item and its cell (and the unions' windows per chunk)
             uint32_t t = 0;
-            if (tid == 0) t = failed ? NC : atomicAdd(&v.ctr->tc_next[MODE], 1u);
+            if (tid == 0) t = failed ? NC : atomicAdd(next, 1u);
             t = __shfl_sync(0xffffffffu, t, 0);
             uint32_t A = 0, nwin = 1;
             if (t < NC) {
@@ -417,6 +438,10 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
                 A = later ? chunk_cell_warp(tt.choff_later, C, t - N0) : chunk_cell_warp(tt.choff, C, t);
                 if (later) {
                     uint32_t len = tid < n_rng ? merge_range_len(v.ranges, v.n_all, v.cell_start, tt.cx, A, tid) : 0u;
+                    nwin = merge_windows(__reduce_add_sync(0xffffffffu, len));
+                }
+                if (recount) {
+                    uint32_t len = tid < n_rng ? count_range_len(v.ranges, v.n_all, v.cell_start, A, tid) : 0u;
                     nwin = merge_windows(__reduce_add_sync(0xffffffffu, len));
                 }
             }
@@ -435,8 +460,8 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
         const uint32_t cs0 = v.cell_start[A], cs1 = v.cell_start[A + 1];
         uint32_t rbeg, rend;
         if (MODE == kCount) {
-            rbeg = cs0;
-            rend = cs1;
+            rbeg = tt.row_list ? tt.cx[cs0] : cs0;
+            rend = tt.row_list ? tt.cx[cs1] : cs1;
         } else if (MODE == kMerge) {
             rbeg = tt.cx[cs0];
             rend = tt.cx[cs1];
@@ -448,8 +473,8 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
         // = chunk * (nwin - 1) + window - 1
         const bool later = MODE == kMerge && t >= N0;
         const uint32_t item = later ? t - N0 - tt.choff_later[A] : t - tt.choff[A];
-        const uint32_t nw = later ? S.nwin - 1u : 1u;
-        const uint32_t win = later ? 1u + item % nw : 0u;
+        const uint32_t nw = later ? S.nwin - 1u : recount ? S.nwin : 1u;
+        const uint32_t win = later ? 1u + item % nw : recount ? item % nw : 0u;
         const uint32_t k0 = rbeg + (uint32_t)kTile * (item / nw);  // list index of row 0
         const uint32_t rk = k0 + (uint32_t)tid;
         const bool have = rk < rend;
@@ -577,8 +602,8 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
         __syncthreads();
         // the item's part of the stream: all of it, or for the unions window win of kSegCand
         const uint32_t L_all = S.rpre[kMaxRng];
-        const uint32_t u0 = MODE == kMerge ? min(L_all, win * kSegCand) : 0u;
-        const uint32_t L = split ? min(L_all, u0 + kSegCand) : L_all;
+        const uint32_t u0 = MODE == kMerge || recount ? min(L_all, win * kSegCand) : 0u;
+        const uint32_t L = split || recount ? min(L_all, u0 + kSegCand) : L_all;
         if (MODE == kMerge && u0 >= L && win > 0u) continue;  // the pruning left nothing in this window
         const float na = stage_split<DP, KP>(S.a_hi, S.a_lo, tid, q, S.cen, have);
         const float lo = (float)(G.eps2 * (1.0 - 0x1p-20));
@@ -766,9 +791,9 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
             if (MODE == kCount) {
                 const int open = __syncthreads_count(!done);
                 if (open == 0) break;
-                if (open <= (int)v.tc_handoff && ub + 2 * kTile < L) {
-                    // few rows left and more than one block to go: the CUDA-core count continues
-                    // them from the next candidate on
+                if (!recount && open <= (int)v.tc_handoff && ub + 2 * kTile < L) {
+                    // few rows left and more than one block to go: the recount or the CUDA-core
+                    // count continues them
                     // the rows resume from the next block if none saw an undecided pair, else
                     // all start over (one start position per chunk)
                     handed = !done;
@@ -784,7 +809,27 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
             }
         }
         if (failed) continue;  // the loop head ends this CTA
-        if (MODE == kCount) {
+        if (recount) {
+            // this window's tallies (a row that reached MINPTS here stopped early: it is core);
+            // the last of the row's windows decides it, as below
+            if (have) {
+                atomicAdd(tt.rc_in + rk, cnt);
+                atomicAdd(tt.rc_hi + rk, cnt_hi);
+                __threadfence();
+                if (atomicAdd(tt.rc_done + rk, 1u) == nw - 1u) {
+                    __threadfence();
+                    const uint32_t in = atomicAdd(tt.rc_in + rk, 0u), up = atomicAdd(tt.rc_hi + rk, 0u);
+                    const bool is_core = in >= G.min_pts;
+                    const bool undecided = !is_core && up >= G.min_pts;
+                    if (undecided) {  // counted exactly by the CUDA-core count, from the start
+                        v.tc_cnt[p] = 0u;
+                        v.tc_pos[p] = 0u;
+                    }
+                    v.core[p] = undecided ? 2 : (is_core ? 1 : 0);
+                    if (is_core) v.cell_core[A] = 1;
+                }
+            }
+        } else if (MODE == kCount) {
             // every candidate seen: a row with cnt < MINPTS <= cnt_hi is counted exactly there
             if (have && !handed && cnt < G.min_pts && cnt_hi >= G.min_pts) {
                 handed = true;
@@ -875,6 +920,39 @@ static __global__ void __launch_bounds__(256) k_tc_chunks_count(const uint32_t *
     const uint32_t C = ctr->n_cells;
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x)
         nch[c] = tc_chunks(cell_start[c + 1] - cell_start[c], min_rows);
+}
+
+// The recount of handed-over rows: their flags (core = 2, set only by the tensor-core count; the
+// other cells' flags are still 0), their list (ascending) from the scan hx of the flags, and the
+// 128-row chunks of every cell with at least min_rows of them.
+static __global__ void __launch_bounds__(256) k_tc_handed_flags(const uint8_t *__restrict__ core, int64_t n,
+                                                               uint32_t *__restrict__ f) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        f[j] = core[j] == 2 ? 1u : 0u;
+}
+
+static __global__ void __launch_bounds__(256) k_tc_handed_list(const uint8_t *__restrict__ core,
+                                                              const uint32_t *__restrict__ hx, int64_t n,
+                                                              uint32_t *__restrict__ list) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        if (core[j] == 2) list[hx[j]] = (uint32_t)j;
+}
+
+static __global__ void __launch_bounds__(256) k_tc_chunks_recount(const uint32_t *__restrict__ cell_start,
+                                                                 const uint32_t *__restrict__ hx,
+                                                                 const DevCounters *ctr,
+                                                                 const uint2 *__restrict__ ranges, int n_all,
+                                                                 uint32_t min_rows, uint32_t *__restrict__ nch) {
+    const uint32_t C = ctr->n_cells;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+        uint32_t items = tc_chunks(hx[cell_start[c + 1]] - hx[cell_start[c]], min_rows);
+        if (items) {
+            uint32_t len = 0;
+            for (int k = 0; k < n_all; ++k) len += count_range_len(ranges, n_all, cell_start, c, k);
+            items *= merge_windows(len);
+        }
+        nch[c] = items;
+    }
 }
 
 // Core flags as uint32 for the scan that numbers the core points.
