@@ -361,8 +361,8 @@ HCA_API int hca_graph_cache_release(void);
  *   cta_warps      coarse grid: warps per CTA of the CUDA-core chunk kernels (counts, first
  *                  links, unions, labels; one 32-point chunk per warp, its rows staged in the
  *                  CTA's shared memory): 2, 4 or 8.
- * Defaults: path 0, first_links 1, cta_warps 4; thresholds 16 / 1 / 4 and tc_handoff 4 for
- * d <= 8, 8 / 1 / 1 and tc_handoff 8 for d > 8.
+ * Defaults: path 0, tc_handoff 32, first_links 1, cta_warps 4; thresholds 16 / 1 / 4 for
+ * d <= 8 and 8 / 1 / 1 for d > 8.
  */
 typedef struct hca_tuning {
     int32_t path;
@@ -387,7 +387,7 @@ HCA_API int hca_tuning_set(int32_t d, const hca_tuning *t);
  * events on `stream`, keeping its minimum.  Candidates: both neighbour searches for d = 3, 4;
  * for the coarse grid with float input, first links on / off and several row thresholds; then,
  * on the coarse grid, 2 and 8 warps per CTA (cta_warps) with the rest of the fastest of those,
- * and with float input the tensor-core handoff at 2, 4, 8 and 16 open rows (tc_handoff).
+ * and with float input the tensor-core handoff at 8, 16, 32 and 64 open rows (tc_handoff).
  *   out       host, nullable: the tuning kept.   best_ms  host, nullable: its time.
  * Synchronous.  Returns HCA_OK, or the first error of a candidate run (nothing is changed).
  */

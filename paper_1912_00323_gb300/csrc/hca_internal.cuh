@@ -26,7 +26,7 @@ constexpr uint32_t kErrBox = 8u;   // a point lies outside the extents a plan de
 // Base tuning (include/hca_dbscan.h): dimension-chosen neighbour search; tensor-core tiles
 // from 8 rows (counts, unions) and 2 non-core rows (labels); hand-off at 8 open count rows;
 // first links everywhere.  The defaults per d (tune.cu) adjust the split from it.
-constexpr hca_tuning kDefaultTuning = {0, 8, 8, 2, 8, 1, 4};
+constexpr hca_tuning kDefaultTuning = {0, 8, 8, 2, 32, 1, 4};
 
 // Device counters and status, one struct per call in the workspace.
 struct DevCounters {

@@ -20,9 +20,11 @@ bool g_tune_init = false;
 
 // Defaults per d: the coarse-grid split measured fastest across the workloads, with first
 // links in every cell (leaving them out of tensor-core cells wins a few percent on many small
-// sets but loses up to 8x on a set of a million points) — d <= 8: thresholds 16 / 1 / 4 and
-// handoff at 4 open rows (3% faster than 8 on the d = 8 sets of the batched workload);
-// d > 8 (the 16-D anisotropic clusters): 8 / 1 / 1, handoff at 8.  From one core row on the unions of every
+// sets but loses up to 8x on a set of a million points) — d <= 8: thresholds 16 / 1 / 4;
+// d > 8 (the 16-D anisotropic clusters): 8 / 1 / 1.  Tensor-core count chunks hand over at 32
+// open rows (the tensor-core recount takes them, in windows: against 8, 5% faster on the d = 8
+// sets of the batched workload, 7-14% on the largest d = 9 and 16 serving jobs, equal on the
+// 16-D workload).  From one core row on the unions of every
 // cell with a core point run on the tensor cores: a cell of one to three core points next to
 // a cluster streams the cluster's core points, 128 per tile there against 32 per warp step on
 // the CUDA cores.
@@ -32,7 +34,6 @@ hca_tuning default_tuning(int d) {
         t.tc_min_count = 16;
         t.tc_min_merge = 1;
         t.tc_min_labels = 4;
-        t.tc_handoff = 4;
         t.first_links = 1;
     } else {
         t.tc_min_count = 8;
@@ -91,7 +92,7 @@ std::vector<hca_tuning> candidates(int d, int32_t dtype) {
 // Time `run` (one clustering on `s`) under every candidate: one untimed run, then `repeats`
 // timed runs, minimum kept.  Then, on the coarse grid, the CTA size of the CUDA-core chunk
 // kernels (2 and 8 warps besides the default 4) with the rest of the fastest candidate, and
-// with float input the open rows at which a tensor-core count chunk hands over (2, 4, 8, 16).
+// with float input the open rows at which a tensor-core count chunk hands over (8, 16, 32, 64).
 // Stores the fastest for d.
 template <typename Run>
 int tune_with(int d, int32_t dtype, cudaStream_t s, int repeats, Run run, hca_tuning *out, double *best_ms) {
@@ -139,7 +140,7 @@ int tune_with(int d, int32_t dtype, cudaStream_t s, int repeats, Run run, hca_tu
     }
     if (rc == HCA_OK && pick.path == 2 && dtype == HCA_F32) {
         const hca_tuning base = pick;
-        for (int h : {2, 4, 8, 16}) {
+        for (int h : {8, 16, 32, 64}) {
             if (h == base.tc_handoff) continue;
             hca_tuning t = base;
             t.tc_handoff = h;

@@ -107,7 +107,7 @@ def test_autotune_keeps_labels(env):
     t = torch.from_numpy(X).cuda()
     tune, ms = pkg.hca_autotune(t, eps, mp, repeats=1)
     assert ms > 0 and tune["path"] == 2
-    assert tune["cta_warps"] in (2, 4, 8) and tune["tc_handoff"] in (2, 4, 8, 16)
+    assert tune["cta_warps"] in (2, 4, 8) and tune["tc_handoff"] in (8, 16, 32, 64)
     assert pkg.hca_tuning_get(16) == tune
     check(run(env, X, eps, mp), want)
 

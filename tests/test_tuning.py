@@ -17,9 +17,9 @@ def pkg():
         pkg.hca_tuning_set(d, None)
 
 
-LOW_D = {"path": 0, "tc_min_count": 16, "tc_min_merge": 1, "tc_min_labels": 4, "tc_handoff": 4,
+LOW_D = {"path": 0, "tc_min_count": 16, "tc_min_merge": 1, "tc_min_labels": 4, "tc_handoff": 32,
          "first_links": 1, "cta_warps": 4}
-HIGH_D = {"path": 0, "tc_min_count": 8, "tc_min_merge": 1, "tc_min_labels": 1, "tc_handoff": 8,
+HIGH_D = {"path": 0, "tc_min_count": 8, "tc_min_merge": 1, "tc_min_labels": 1, "tc_handoff": 32,
           "first_links": 1, "cta_warps": 4}
 
 
