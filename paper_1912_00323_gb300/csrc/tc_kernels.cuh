@@ -250,6 +250,7 @@ struct Smem {
     uint32_t bnear[kMaxRng];   // 1: some row lies within eps of the cell's box
     uint32_t nbc, bover;       // number of those cells; 1 if they did not fit (no pruning)
     uint32_t cell, nwin;       // the item's coarse cell; unions: windows per chunk of it
+    uint32_t la[3], pad3;      // unions: blocks of a look-ahead round not skippable (rotating)
     uint64_t mbar;
     uint32_t taddr, ref, next, pad;
 };
@@ -516,6 +517,7 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
                 for (uint32_t j = 0; j < cnt; ++j)
                     if (incl - cnt + j < (uint32_t)kMaxRng) S.bcell[incl - cnt + j] = lo + j;
                 S.bnear[tid] = 0u;
+                if (tid < 3) S.la[tid] = 0u;
                 if (tid == 0) {
                     S.nbc = total < (uint32_t)kMaxRng ? total : (uint32_t)kMaxRng;
                     S.bover = total > (uint32_t)kMaxRng ? 1u : 0u;
@@ -631,6 +633,7 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
             if (MODE == kLabels) pre_pay = __ldg(tt.core_lab + pre_k);
         };
         if (u0 < L) prefetch(u0);
+        uint32_t la_r = 0;  // unions: look-ahead rounds of this item
         for (uint32_t ub = u0; ub < L; ub += kTile) {
             const bool cin = pre_in;
             const uint32_t nq = min((uint32_t)kTile, L - ub);
@@ -647,7 +650,37 @@ __global__ void __launch_bounds__(kTile) k_tc_hd(HdView<float, DP> v, Tables tt)
                 ref = S.ref;
                 if (__syncthreads_and((!have || rp == ref) && (!cin || rq == ref))) {
                     ++n_skip;
-                    if (ub + kTile < L) prefetch(ub + kTile);
+                    // look ahead: the tree nodes of the next four blocks' candidates at once
+                    // (independent load chains), skipping every block whose candidates all
+                    // share the rows' node; the first one that does not is prefetched
+                    uint32_t nb = ub + kTile;
+                    while (nb < L) {
+                        unsigned bad = 0;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const uint32_t u = nb + (uint32_t)j * kTile + (uint32_t)tid;
+                            if (u < L) {
+                                const uint32_t k2 = stream_index(S.rpre, S.rq0, nspan, u);
+                                const uint32_t x = __ldcg(v.parent + __ldcg(v.parent + __ldg(tt.core_list + k2)));
+                                if (x != ref) bad |= 1u << j;
+                            }
+                        }
+                        bad = __reduce_or_sync(0xffffffffu, bad);
+                        // slot la_r % 3 was cleared in the previous round (or at the chunk
+                        // start); nobody reads slot (la_r + 1) % 3 in this round
+                        if ((tid & 31) == 0 && bad) atomicOr(&S.la[la_r % 3u], bad);
+                        if (tid == 0) S.la[(la_r + 1u) % 3u] = 0u;
+                        __syncthreads();
+                        const uint32_t nblk = min(4u, (L - nb + (uint32_t)kTile - 1u) / (uint32_t)kTile);
+                        const unsigned stop = S.la[la_r % 3u] | (0xfu << nblk);
+                        ++la_r;
+                        const uint32_t js = (uint32_t)__ffs(stop) - 1u;  // blocks skipped in this round
+                        n_skip += js;
+                        nb += js * (uint32_t)kTile;
+                        if (js < 4u) break;
+                    }
+                    if (nb < L) prefetch(nb);
+                    ub = nb - (uint32_t)kTile;
                     continue;
                 }
                 S.cpay[tid] = rq;
