@@ -377,20 +377,27 @@ __device__ __forceinline__ uint32_t stream_index(const uint32_t *rpre, const uin
 
 // One phase over tensor-core tiles (MODE = kCount, kMerge or kLabels) for the coarse cells
 // with at least tc_min[MODE] rows of that phase (the other cells are left to the CUDA-core
-// kernels); persistent CTAs take 128-row chunks from a counter.  The candidates of a chunk
-// (its neighbour ranges laid end to end) stream through in blocks of 128; the next block's
-// rows are loaded into registers while the current block is multiplied and classified.
+// kernels); persistent CTAs take work items from a counter, warp 0 finding the item's cell.
+// An item is a 128-row chunk of one cell; for the unions of a call with few chunks, a window
+// of kSegCand candidates of a chunk's stream (first windows of all chunks, then the rest).  The
+// candidates of an item (its neighbour ranges laid end to end, for the unions and labels only
+// the cells whose box some row reaches) stream through in blocks of 128; the next block's rows
+// are loaded into registers while the current block is multiplied and classified.
 //   kCount:  rows = every point of the cell, candidates = every point of the 27 neighbouring
 //            cells; core[p] = (|N_eps(p)| >= MINPTS).  Two tallies per row: pairs surely within
 //            eps and pairs not proved outside; a row stops once the first reaches MINPTS.  Once
 //            at most tc_handoff rows of a chunk are open the chunk stops, and those rows get
 //            core[p] = 2 with their count and the next stream position (or zero and zero for
-//            all of them if one saw an undecided pair); a row that ends with MINPTS between the tallies gets core[p] =
-//            2, zero and zero.  The CUDA-core count continues them exactly.
+//            all of them if one saw an undecided pair); a row that ends with MINPTS between
+//            the tallies gets core[p] = 2, zero and zero.  The CUDA-core count continues them
+//            exactly.  With tt.row_list (the recount): rows = the handed-over rows of the cell,
+//            one item per window of kSegCand candidates; the tallies are summed over the
+//            windows and the last window of a row decides it the same way.
 //   kMerge:  rows = core points, candidates = core points of the upper half of the
 //            neighbourhood after the row (each unordered pair once); a pair within eps whose
 //            trees differ is joined.  A block whose rows and candidates all share one tree
-//            node is skipped before the MMA.
+//            node is skipped before the MMA, and after a skip the next four blocks are tested
+//            at once.
 //   kLabels: rows = non-core points, candidates = core points of the 27 cells; the row takes
 //            the smallest cluster id among the candidates within eps, else -1.
 template <int DP, int MODE>
