@@ -95,7 +95,7 @@ __device__ __forceinline__ uint32_t chunk_cell_warp(const uint32_t *off, uint32_
 
 // Row and candidate lists of the three phases.
 struct Tables {
-    const uint32_t *choff;      // first 128-row chunk of every coarse cell (this phase)
+    const uint32_t *choff;      // first work item of every coarse cell (this launch)
     const uint32_t *cx;         // exclusive scan of the core flags over sorted points (n + 1)
     const uint32_t *core_list;  // core points, ascending
     const uint32_t *nc_list;    // non-core points, ascending
