@@ -409,9 +409,10 @@ def pair_rates(stats, stage, d):
 
 
 def tensor_roofline(stats, tc_ms, d, bf16_burst, peak_kind):
-    """The tensor-core tile kernel (k_tc_hd, one launch per phase): algorithmic flops =
-    candidate pairs x 2 d; duration = the CUDA-event time of its three launches; peak = the
-    measured bf16 GEMM rate x (nominal TF32 / nominal bf16)."""
+    """The tensor-core tile kernel (k_tc_hd): algorithmic flops = candidate pairs x 2 d;
+    duration = the CUDA-event time of its four launches (counts, the recount of the rows the
+    counts hand over with the few kernels that list them, unions, labels); peak = the measured
+    bf16 GEMM rate x (nominal TF32 / nominal bf16)."""
     t = sum(tc_ms.values())
     pairs = stats["n_tc_pairs"]
     if t <= 0 or pairs <= 0:
@@ -423,7 +424,7 @@ def tensor_roofline(stats, tc_ms, d, bf16_burst, peak_kind):
     kp = dp + 8
     mmas = kp // 8 + 2 * (dp // 8)   # hi.hi per K step, hi.lo and lo.hi on the coordinate steps
     issued = stats["n_tc_tiles"] * mmas * 2.0 * 128 * 128 * 8
-    return {"bound": "tensor", "kernel": "k_tc_hd (counts, unions, labels: three launches)",
+    return {"bound": "tensor", "kernel": "k_tc_hd (counts + recount, unions, labels: four launches)",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
             "algorithmic_flops": flops, "candidate_pairs": int(pairs), "launch_ms": tc_ms,
             "issued_mma_flops": issued, "issued_tflops": issued / (t / 1e3) / 1e12,
