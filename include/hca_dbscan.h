@@ -274,7 +274,7 @@ HCA_API int hca_radix_sort_pairs(void *d_keys, uint32_t *d_vals, int64_t n, int3
  * alternate keys and values of 2^18 pairs plus the sort's look-back words), held on every GPU
  * that loads the library until the process exits.  The first call in a CUDA context of a
  * device looks up that array's device address (cudaGetSymbolAddress) and caches it for that
- * context; make that first call before any stream capture.  A cudaDeviceReset ends the
+ * context.  A cudaDeviceReset ends the
  * context, and the next call looks the address up again.  Calls no cudaMalloc, cudaFree or
  * other allocating routine.  Synchronous: the call reads the sort's status word back and
  * returns after the sort is complete on `stream`.
