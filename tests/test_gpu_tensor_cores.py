@@ -154,6 +154,23 @@ def test_dense_clusters_split_union_streams(env, n, clusters):
     check(got, want)
 
 
+def test_recount_windows_from_early_handoff(env):
+    """Two dense clusters with the handoff at 127 open rows: nearly every row leaves its first
+    tensor-core count after one block and is counted again in windows of 2,048 candidates, the
+    tallies summed over the windows; labels and core flags equal the oracle's."""
+    _, pkg, oracle = env
+    X, eps, mp = workloads.aniso16d(n=40000, n_clusters=2)
+    want = oracle.grid(X.astype(np.float64), eps, mp)
+    base = pkg.hca_tuning_get(16)
+    try:
+        pkg.hca_tuning_set(16, dict(base, tc_handoff=127))
+        got = run(env, X, eps, mp)
+    finally:
+        pkg.hca_tuning_set(16, None)
+    assert got[2]["n_tc_tiles"] > 0
+    check(got, want)
+
+
 def test_batched_many_chunks_whole_union_streams(env):
     """About eight million d = 8 points in 140 sets: more than 32 core-row chunks per resident
     CTA, so every unions chunk runs whole (no windows); tensor-core labels equal the CUDA-core
